@@ -1,0 +1,465 @@
+"""FP64 CPU oracle of the field-window estimator -- TEST INFRASTRUCTURE ONLY.
+
+This module is the parity reference for the CUDA path.  Only the test suite,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it; the product path never calls it.  It shares no code with the CUDA library:
+its inputs come from ``synthetic/`` and everything else is computed here, in
+float64, by the plainest route that follows the paper:
+
+  step                          paper passage
+  ----------------------------  ---------------------------------------------------
+  node / fraction rule          Eq. (phi_projection) with a centred order-p B-spline
+  B-spline scatter  eps_l       Eq. (phi_projection): eps_l = sum_i w_i phi_l(x_i)
+  density contrast  delta       delta = n / nbar - 1 (Sec. 2, notation)
+  forward FFT                   non-unitary convention f^(k) = int f e^{-ik.x} (Sec. 2)
+  basis autocorrelation  Phi^   Sec. 3.5 window construction, K_W = W^ Phi^
+  shell window (l = 0)          Eq. (Wshell_k) difference of two top-hats
+  multipole shell  (xi_l)       Sec. 3.4.3: (2l+1) i^l j_l(kr) L_l(mu_k); finite bin
+                                = radial average of j_l
+  harmonic shell   (zeta_l)     Eq. (multipole-window): 4 pi i^l j_l(kr) Y_lm(k^)
+  xi via Parseval               Eq. (pair-counting-kspace)
+  xi via cell contraction       Eq. (pair-counting), Eq. (2rdEs)
+  Landy-Szalay with uniform R   Eq. (xi-deltaDD-over-RR)
+  zeta_l                        Eq. (2-fold-translation), Eq. (particle_nfold)
+
+Readings of silent or ambiguous points (all restated in the design notes):
+  * basis: centred cardinal B-spline M_p on unit cell spacing, partition of unity;
+  * node rule: u = fl32(x * fl32(N/L)); for odd p, v = fl32(u + 0.5) else v = u;
+    i = floor(v); t = v - i; first node i - (p/2 - 1) (even p) or i - (p-1)/2 (odd p);
+  * Phi^(n) = prod_d sinc^{2p}(pi n_d / N), unaliased; K = 0 on every Nyquist plane;
+  * delta^(0) := 0;
+  * finite-bin j_l = r^2-weighted (volume) average over [r_lo, r_hi);
+  * the exact self-pair term SN is subtracted from xi and xi_l;
+  * zeta_l are Legendre coefficients, computed with conj(a) on the first field,
+    returned raw (self terms included), normalised by 1/(4 pi N^3).
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against facts the
+paper or mathematics fixes (closed forms, identities, brute force).  No function
+is "parity unpinned".
+"""
+from __future__ import annotations
+
+from math import comb, factorial
+
+import numpy as np
+import scipy.special as sps
+
+__all__ = [
+    "scale_f32", "node_rule", "bspline", "node_weights", "assign", "delta_from_eps",
+    "signed_freqs", "phi_hat_1d", "shell_avg_jl", "shell_window_l0", "window_xi",
+    "window_zeta", "xi_parseval", "xi_cell_contraction", "self_pair_table",
+    "kappa_from_K", "shot_noise", "xi_multipoles", "zeta_multipoles", "lm_modes",
+    "keff_pair_direct", "xi_brute_force", "direct_convolution",
+]
+
+
+# --------------------------------------------------------------------------
+# (a1) index bookkeeping
+# --------------------------------------------------------------------------
+def scale_f32(N: int, L: float) -> np.float32:
+    """Grid units per length unit, N/L computed in float64 and rounded to float32."""
+    return np.float32(float(N) / float(L))
+
+
+def node_rule(pos: np.ndarray, N: int, L: float, p: int):
+    """Return (first_node[n,3] int64 in [0,N), dist[n,3,p] float64).
+
+    dist[i, d, o] = u_{i,d} - (first + o) is the signed offset of point i from
+    its o-th supporting node along axis d, in grid units.  The rule follows the
+    compact support of phi_{jl} in Eq. (phi_projection): exactly the p nodes
+    with |u - l| < p/2 carry weight.
+    """
+    s = scale_f32(N, L)
+    u = np.asarray(pos, dtype=np.float32) * s            # IEEE float32 multiply
+    if p % 2 == 1:
+        v = u + np.float32(0.5)                          # float32 add
+    else:
+        v = u
+    fl = np.floor(v)
+    i0 = fl.astype(np.int64)
+    t = (v - fl).astype(np.float64)                      # exact in float32
+    if p % 2 == 0:
+        first = i0 - (p // 2 - 1)
+        base = t + (p // 2 - 1)
+    else:
+        first = i0 - (p - 1) // 2
+        base = t - 0.5 + (p - 1) // 2
+    o = np.arange(p, dtype=np.float64)
+    dist = base[..., None] - o                           # [n,3,p]
+    return np.mod(first, N), dist
+
+
+def bspline(p: int, x: np.ndarray) -> np.ndarray:
+    """Centred cardinal B-spline M_p(x) of order p (degree p-1), float64.
+
+    Written as the truncated-power sum
+        M_p(x) = 1/(p-1)! * sum_{k=0}^{p} (-1)^k C(p,k) (x + p/2 - k)_+^{p-1},
+    the textbook closed form of p-fold convolution of the unit box, evaluated
+    at -|x| (M_p is even).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    if p == 1:
+        return np.where((x >= -0.5) & (x < 0.5), 1.0, 0.0)
+    # M_p is even; evaluating at -|x| makes only the k = 0 term survive near the
+    # support edge, which avoids cancellation between large terms there
+    xa = -np.abs(x)
+    acc = np.zeros_like(x)
+    for k in range(p + 1):
+        y = xa + p / 2.0 - k
+        acc += (-1) ** k * comb(p, k) * np.where(y > 0, y, 0.0) ** (p - 1)
+    out = acc / factorial(p - 1)
+    # outside the support the sum cancels to rounding noise; make it exact
+    return np.where(np.abs(x) < p / 2.0, out, 0.0)
+
+
+def node_weights(pos, N, L, p):
+    """(first_node[n,3], m[n,3,p]) with m = M_p(dist): phi_{jl}(x_i) per axis."""
+    first, dist = node_rule(pos, N, L, p)
+    return first, bspline(p, dist)
+
+
+# --------------------------------------------------------------------------
+# (a2) scatter, Eq. (phi_projection)
+# --------------------------------------------------------------------------
+def assign(pos, w, N: int, L: float, p: int, chunk: int = 400_000):
+    """eps_l = sum_i w_i prod_d M_p(u_{i,d} - l_d) on the periodic N^3 grid.
+
+    Returns (eps[N,N,N] float64, sum_w, sum_w2).  w=None means unit weights.
+    """
+    pos = np.asarray(pos)
+    n = pos.shape[0]
+    w = np.ones(n, dtype=np.float64) if w is None else np.asarray(w, dtype=np.float64)
+    eps = np.zeros(N ** 3, dtype=np.float64)
+    for s0 in range(0, n, chunk):
+        first, m = node_weights(pos[s0:s0 + chunk], N, L, p)
+        ww = w[s0:s0 + chunk]
+        o = np.arange(p)
+        ix = (first[:, 0, None] + o) % N                 # [c,p]
+        iy = (first[:, 1, None] + o) % N
+        iz = (first[:, 2, None] + o) % N
+        flat = (ix[:, :, None, None] * N + iy[:, None, :, None]) * N + iz[:, None, None, :]
+        val = (ww[:, None, None, None] * m[:, 0, :, None, None]
+               * m[:, 1, None, :, None] * m[:, 2, None, None, :])
+        eps += np.bincount(flat.ravel(), weights=val.ravel(), minlength=N ** 3)
+    return eps.reshape(N, N, N), float(w.sum()), float((w * w).sum())
+
+
+def delta_from_eps(eps, sum_w):
+    """delta = eps / eps_bar - 1 with eps_bar = sum_w / N^3 (uniform random field)."""
+    N3 = eps.size
+    return eps / (sum_w / N3) - 1.0
+
+
+# --------------------------------------------------------------------------
+# Fourier-space windows
+# --------------------------------------------------------------------------
+def signed_freqs(N: int) -> np.ndarray:
+    """Integer frequencies n in FFT order: 0, 1, ..., N/2-1, -N/2, ..., -1."""
+    return np.rint(np.fft.fftfreq(N, d=1.0 / N)).astype(np.int64)
+
+
+def phi_hat_1d(N: int, p: int) -> np.ndarray:
+    """sinc^{2p}(pi n / N) in FFT order: FT of the autocorrelation M_p * M_p = M_2p."""
+    n = signed_freqs(N).astype(np.float64)
+    x = np.pi * n / N
+    s = np.ones_like(x)
+    nz = x != 0
+    s[nz] = np.sin(x[nz]) / x[nz]
+    return s ** (2 * p)
+
+
+def _gl_nodes(m):
+    x, wt = np.polynomial.legendre.leggauss(m)
+    return x, wt
+
+
+def shell_avg_jl(ell: int, k: np.ndarray, r_lo: float, r_hi: float, panels: int | None = None):
+    """r^2-weighted average of j_l(k r) over r in [r_lo, r_hi] (float64).
+
+    Composite 16-point Gauss-Legendre in r; the number of panels keeps the
+    phase advance k*dr per panel below ~1.5 rad so the rule is exact to
+    float64 rounding.  j_l from scipy (library routine).
+    """
+    k = np.asarray(k, dtype=np.float64)
+    if panels is None:
+        kmax = float(np.max(k)) if k.size else 0.0
+        panels = max(1, int(np.ceil(kmax * (r_hi - r_lo) / 1.5)))
+    x, wt = _gl_nodes(16)
+    edges = np.linspace(r_lo, r_hi, panels + 1)
+    num = np.zeros_like(k)
+    for a, b in zip(edges[:-1], edges[1:]):
+        r = 0.5 * (b - a) * x + 0.5 * (a + b)
+        rw = 0.5 * (b - a) * wt * r * r
+        num += (sps.spherical_jn(ell, k[..., None] * r) * rw).sum(axis=-1)
+    den = (r_hi ** 3 - r_lo ** 3) / 3.0
+    return num / den
+
+
+def _sphere_hat(x):
+    """3 (sin x - x cos x) / x^3 (Table A1 row b), with its Taylor series at small x."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    sm = np.abs(x) < 1e-2
+    xs = x[sm]
+    out[sm] = 1.0 - xs ** 2 / 10.0 + xs ** 4 / 280.0 - xs ** 6 / 15120.0
+    xl = x[~sm]
+    out[~sm] = 3.0 * (np.sin(xl) - xl * np.cos(xl)) / xl ** 3
+    return out
+
+
+def shell_window_l0(k, r_lo, r_hi):
+    """Eq. (Wshell_k): volume-normalised difference of two spherical top-hats."""
+    vp, vm = r_hi ** 3, r_lo ** 3
+    return (vp * _sphere_hat(k * r_hi) - vm * _sphere_hat(k * r_lo)) / (vp - vm)
+
+
+def _mode_grid(N, L, half=False):
+    """Signed integer modes (n_x, n_y, n_z), |n|^2, |k| and the Nyquist mask.
+
+    half=True keeps n_z in [0, N/2] only (the layout of a real-to-complex FFT).
+    """
+    n = signed_freqs(N)
+    nzs = np.arange(N // 2 + 1, dtype=np.int64) if half else n
+    nx, ny, nz = np.meshgrid(n, n, nzs, indexing="ij")
+    nyq = (np.abs(nx) == N // 2) | (np.abs(ny) == N // 2) | (np.abs(nz) == N // 2)
+    q = nx * nx + ny * ny + nz * nz
+    k = (2.0 * np.pi / L) * np.sqrt(q.astype(np.float64))
+    return nx, ny, nz, q, k, nyq
+
+
+def _radial_table(ell, q, L, r_lo, r_hi):
+    """<j_l>_bin(k) evaluated once per distinct |n|^2 (k = 2 pi |n| / L), scattered back."""
+    uq, inv = np.unique(q.ravel(), return_inverse=True)
+    ku = (2.0 * np.pi / L) * np.sqrt(uq.astype(np.float64))
+    if ell == 0:
+        vals = shell_window_l0(ku, r_lo, r_hi)
+    else:
+        vals = shell_avg_jl(ell, ku, r_lo, r_hi)
+    return vals[inv].reshape(q.shape)
+
+
+def window_xi(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int,
+              half: bool = False) -> np.ndarray:
+    """K_{b,l}(n) = (2l+1) i^l <j_l>_b(k) L_l(k_z/k) Phi^(n) for even l (real), Nyquist = 0.
+
+    l = 0 is the finite shell of Eq. (Wshell_k); the line of sight is the z axis.
+    half=True returns only n_z in [0, N/2] (rfft layout).
+    """
+    if ell % 2:
+        raise ValueError("odd l gives an identically zero auto-multipole")
+    nx, ny, nz, q, k, nyq = _mode_grid(N, L, half)
+    rad = _radial_table(ell, q, L, r_lo, r_hi)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = np.where(q > 0, nz / np.sqrt(q.astype(np.float64)), 0.0)
+    leg = sps.eval_legendre(ell, mu)
+    ph = phi_hat_1d(N, p)
+    phz = ph[: N // 2 + 1] if half else ph
+    phz = phz.copy()
+    if half:
+        phz[N // 2] = ph[N // 2]                       # n_z = +N/2 equals -N/2 in magnitude
+    phi3 = ph[:, None, None] * ph[None, :, None] * phz[None, None, :]
+    K = (2 * ell + 1) * np.real(1j ** ell) * rad * leg * phi3
+    K[nyq] = 0.0
+    return K
+
+
+def window_zeta(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int, m: int) -> np.ndarray:
+    """K_{b,lm}(n) = 4 pi i^l <j_l>_b(k) Y_lm(k^) Phi^(n), Eq. (multipole-window); complex.
+
+    Y_lm orthonormal with the Condon-Shortley phase (scipy.special.sph_harm_y);
+    Nyquist planes are zero.  At n = 0 the direction is taken as +z (the
+    value multiplies delta^(0) = 0 and never matters).
+    """
+    nx, ny, nz, q, k, nyq = _mode_grid(N, L)
+    rad = _radial_table(ell, q, L, r_lo, r_hi)
+    r = np.sqrt(q.astype(np.float64))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ct = np.where(q > 0, nz / r, 1.0)
+    theta = np.arccos(np.clip(ct, -1.0, 1.0))
+    phi = np.mod(np.arctan2(ny.astype(np.float64), nx.astype(np.float64)), 2 * np.pi)
+    Y = sps.sph_harm_y(ell, m, theta, phi)
+    ph = phi_hat_1d(N, p)
+    phi3 = ph[:, None, None] * ph[None, :, None] * ph[None, None, :]
+    K = 4.0 * np.pi * (1j ** ell) * rad * Y * phi3
+    K[nyq] = 0.0
+    return K
+
+
+# --------------------------------------------------------------------------
+# contractions
+# --------------------------------------------------------------------------
+def forward(delta):
+    """delta^ = sum_l delta_l e^{-2 pi i n.l/N} (numpy FFT), with delta^(0) := 0."""
+    dh = np.fft.fftn(delta)
+    dh[0, 0, 0] = 0.0
+    return dh
+
+
+def xi_parseval(delta_hat, K):
+    """Eq. (pair-counting-kspace): (1/N^3) sum_l delta delta~ = (1/N^6) sum_n |delta^_n|^2 K(n)."""
+    N3 = delta_hat.size
+    return float(np.sum(np.abs(delta_hat) ** 2 * K).real) / (N3 * N3)
+
+
+def xi_parseval_half(delta_hat_half, K_half, N):
+    """Eq. (pair-counting-kspace) on the rfft half spectrum (n_z in [0, N/2]).
+
+    The full sum counts each n_z in (0, N/2) twice (its mirror -n is the
+    complex conjugate with the same |.|^2 and K), and n_z = 0, N/2 once.
+    """
+    wz = np.full(N // 2 + 1, 2.0)
+    wz[0] = 1.0
+    wz[N // 2] = 1.0
+    s = np.sum(np.abs(delta_hat_half) ** 2 * K_half * wz[None, None, :])
+    return float(s) / float(N) ** 6
+
+
+def xi_cell_contraction(delta, delta_hat, K):
+    """Eq. (pair-counting)/(2rdEs): (1/N^3) sum_l delta_l delta~_l with delta~ = iFFT(delta^ K)."""
+    filt = np.fft.ifftn(delta_hat * K)
+    return float(np.sum(delta * filt.real)) / delta.size
+
+
+def self_pair_table(pos, w, N, L, p):
+    """S[a,b,c] = sum_i w_i^2 prod_d s(a_d; x_i), s(d; x) = sum_l phi_l(x) phi_{l+d}(x), 0 <= a_d < p."""
+    pos = np.asarray(pos)
+    n = pos.shape[0]
+    w = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    _, m = node_weights(pos, N, L, p)                   # [n,3,p]
+    s = np.zeros((n, 3, p))
+    for d in range(p):
+        s[:, :, d] = np.sum(m[:, :, : p - d] * m[:, :, d:], axis=-1)
+    S = np.einsum("i,ia,ib,ic->abc", w * w, s[:, 0, :], s[:, 1, :], s[:, 2, :])
+    return S
+
+
+def kappa_from_K(K):
+    """kappa(d) = (1/N^3) sum_n K(n) e^{+2 pi i n.d/N}: the window on the lattice of lags."""
+    return np.fft.ifftn(K)
+
+
+def shot_noise(S, K, N, sum_w):
+    """SN = (1/(N^3 eps_bar^2)) sum_i w_i^2 K_eff(x_i, x_i), K_eff(x,x) = sum_d kappa(d) s(d).
+
+    The lag sum runs over d in [-(p-1), p-1]^3 using the even table S(|d|).
+    """
+    p = S.shape[0]
+    kap = kappa_from_K(K).real
+    tot = 0.0
+    for dx in range(-(p - 1), p):
+        for dy in range(-(p - 1), p):
+            for dz in range(-(p - 1), p):
+                tot += S[abs(dx), abs(dy), abs(dz)] * kap[dx % N, dy % N, dz % N]
+    eps_bar = sum_w / N ** 3
+    return tot / (N ** 3 * eps_bar * eps_bar)
+
+
+def xi_multipoles(pos, w, N, L, p, r_edges, ells=(0,), route="parseval"):
+    """xi_l(r_b) for every bin b and even l: Landy-Szalay Delta DD / RR with uniform R.
+
+    Returns dict(xi=[n_ell, n_bins], sn=[n_ell, n_bins], raw=[n_ell, n_bins]).
+    raw is (1/N^3) sum delta delta~ before the self-pair subtraction.
+    """
+    eps, sw, _ = assign(pos, w, N, L, p)
+    delta = delta_from_eps(eps, sw)
+    dh = forward(delta)
+    S = self_pair_table(pos, w, N, L, p)
+    nb = len(r_edges) - 1
+    raw = np.zeros((len(ells), nb))
+    sn = np.zeros((len(ells), nb))
+    for a, ell in enumerate(ells):
+        for b in range(nb):
+            K = window_xi(N, L, p, r_edges[b], r_edges[b + 1], ell)
+            if route == "parseval":
+                raw[a, b] = xi_parseval(dh, K)
+            else:
+                raw[a, b] = xi_cell_contraction(delta, dh, K)
+            sn[a, b] = shot_noise(S, K, N, sw)
+    return dict(xi=raw - sn, sn=sn, raw=raw, delta=delta, delta_hat=dh)
+
+
+def lm_modes(l_max: int):
+    """(l, m) with m >= 0 in l-major order; count (l_max+1)(l_max+2)/2 (Sec. 4.5)."""
+    return [(l, m) for l in range(l_max + 1) for m in range(l + 1)]
+
+
+def zeta_multipoles(delta, N, L, p, r_edges, l_max):
+    """zeta_l(b1, b2) = 1/(4 pi N^3) sum_x delta(x) sum_{m=-l}^{l} conj(a_{b1 lm}(x)) a_{b2 lm}(x).
+
+    a_{b lm} = iFFT[delta^ K_{b lm}] (Eq. iFFT-multipoleSFC) is built for every
+    m in [-l, l] -- no conjugation shortcut.  Returns [l_max+1, nb, nb] float64
+    and the largest |imaginary part| seen (should be rounding noise).
+    """
+    dh = forward(delta)
+    nb = len(r_edges) - 1
+    out = np.zeros((l_max + 1, nb, nb))
+    imag_max = 0.0
+    for ell in range(l_max + 1):
+        acc = np.zeros((nb, nb), dtype=np.complex128)
+        for m in range(-ell, ell + 1):
+            fields = []
+            for b in range(nb):
+                K = window_zeta(N, L, p, r_edges[b], r_edges[b + 1], ell, m)
+                fields.append(np.fft.ifftn(dh * K))
+            for b1 in range(nb):
+                c1 = np.conj(fields[b1]) * delta
+                for b2 in range(nb):
+                    acc[b1, b2] += np.sum(c1 * fields[b2])
+        acc /= 4.0 * np.pi * N ** 3
+        out[ell] = acc.real
+        imag_max = max(imag_max, float(np.max(np.abs(acc.imag))))
+    return out, imag_max
+
+
+# --------------------------------------------------------------------------
+# brute-force cross-checks of the oracle itself (tiny inputs only)
+# --------------------------------------------------------------------------
+def keff_pair_direct(kap_real, first_i, m_i, first_j, m_j, N):
+    """K_eff(x_i, x_j) = sum_{l in supp i} sum_{m in supp j} phi_l(x_i) phi_m(x_j) kappa(l - m).
+
+    All p^3 x p^3 node pairs are summed one by one.
+    """
+    p = m_i.shape[-1]
+    tot = 0.0
+    for a in range(p):
+        for b in range(p):
+            for c in range(p):
+                wi = m_i[0, a] * m_i[1, b] * m_i[2, c]
+                li = ((first_i[0] + a) % N, (first_i[1] + b) % N, (first_i[2] + c) % N)
+                for a2 in range(p):
+                    for b2 in range(p):
+                        for c2 in range(p):
+                            wj = m_j[0, a2] * m_j[1, b2] * m_j[2, c2]
+                            d = ((li[0] - first_j[0] - a2) % N, (li[1] - first_j[1] - b2) % N,
+                                 (li[2] - first_j[2] - c2) % N)
+                            tot += wi * wj * kap_real[d]
+    return tot
+
+
+def xi_brute_force(pos, w, N, L, p, K):
+    """xi = (1/(N^3 eps_bar^2)) sum_{i != j} w_i w_j K_eff(x_i, x_j) - K(0): pairs one by one."""
+    pos = np.asarray(pos)
+    n = pos.shape[0]
+    w = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    first, m = node_weights(pos, N, L, p)
+    kap = kappa_from_K(K).real
+    tot = 0.0
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                tot += w[i] * w[j] * keff_pair_direct(kap, first[i], m[i], first[j], m[j], N)
+    eps_bar = w.sum() / N ** 3
+    return tot / (N ** 3 * eps_bar ** 2) - float(K[0, 0, 0].real)
+
+
+def direct_convolution(field, kap):
+    """eps~_l = sum_m kappa(l - m) field_m over all N^3 lags (O(N^6); tiny grids only)."""
+    N = field.shape[0]
+    out = np.zeros(field.shape, dtype=np.result_type(field, kap))
+    for dx in range(N):
+        for dy in range(N):
+            for dz in range(N):
+                c = kap[dx, dy, dz]
+                if c != 0:
+                    out += c * np.roll(field, shift=(dx, dy, dz), axis=(0, 1, 2))
+    return out
