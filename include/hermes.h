@@ -1,0 +1,187 @@
+/*
+ * hermes.h -- C ABI of the B300 field-window estimator (libhermes.so).
+ *
+ * The library computes the paper's in-situ clustering statistics on one GPU:
+ *   (a) a weighted catalogue is projected onto an N^3 periodic grid of order-p
+ *       B-spline scaling functions (Eq. phi_projection, Sec. 3.1);
+ *   (b) the density contrast is Fourier transformed (Sec. 2 convention);
+ *   (c) the spectrum is multiplied by shell windows K = W^ Phi^ (Sec. 3.5, the
+ *       K_W equation) -- plain shells (Eq. Wshell_k), Legendre-weighted shells
+ *       (Sec. 3.4.3) and Y_lm-weighted shells (Eq. multipole-window) -- and
+ *       inverse transformed;
+ *   (d) the filtered fields are contracted cell by cell into xi(r), xi_l(s) and
+ *       zeta_l(r1, r2) (Eq. pair-counting, Eq. 2rdEs, Eq. 2-fold-translation),
+ *       normalised as Delta DD / RR with analytic uniform randoms
+ *       (Eq. xi-deltaDD-over-RR).
+ *
+ * Conventions common to every entry point:
+ *   - Every function returns a status: HERMES_OK (0) or a negative HERMES_ERR_*.
+ *     Nothing aborts and no C++ exception crosses the ABI.  After an error,
+ *     hermes_last_error() describes it.
+ *   - Output arrays are host float64 arrays owned and sized by the caller.
+ *   - Input pointers are only read during the call; the caller keeps ownership.
+ *   - A context owns all device memory it uses, lives on the CUDA device that
+ *     was current when it was created, and restores the caller's current device
+ *     before returning.  A context must not be used by two host threads at once;
+ *     distinct contexts are independent.
+ *   - Calls are synchronous with respect to their results: when a function that
+ *     writes a host output returns HERMES_OK, the output is complete.
+ */
+#ifndef HERMES_H
+#define HERMES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HERMES_OK 0
+#define HERMES_ERR_ARG (-1)     /* invalid argument (null, size, value)            */
+#define HERMES_ERR_RANGE (-2)   /* data outside the accepted range (positions, r)  */
+#define HERMES_ERR_NOMEM (-3)   /* device or host allocation failed                */
+#define HERMES_ERR_CUDA (-4)    /* a CUDA runtime call failed                      */
+#define HERMES_ERR_TIMEOUT (-5) /* a bounded device wait gave up                   */
+#define HERMES_ERR_STATE (-6)   /* call out of order (e.g. xi before assign)       */
+
+/* flags of hermes_assign */
+#define HERMES_DEVICE_PTR 1u /* pos / w are device pointers on the context's GPU   */
+#define HERMES_WRAP 2u       /* wrap coordinates periodically instead of rejecting */
+
+typedef struct hermes_ctx hermes_ctx;
+
+/*
+ * Create a context for a periodic box of side L, N = 2^j cells per axis and an
+ * order-p centred B-spline basis (p = 4 is cubic).  N = 2^J follows the MRA
+ * resolution level of Sec. 4.1 (task.J, "L = 2**J grid cells per axis").
+ *   L > 0; 4 <= j <= 10 and N == 1 << j; 1 <= p <= 8 and 2p - 1 <= N.
+ * Allocates the resident field (N^3 float32) and its half spectrum.
+ * Errors: HERMES_ERR_ARG on a bad value, HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ * *out is set to NULL on error.
+ */
+int hermes_create(double L, int N, int p, int j, hermes_ctx **out);
+
+/* Free every resource of the context.  NULL is accepted (no-op). */
+int hermes_destroy(hermes_ctx *ctx);
+
+/*
+ * Run all later work of the context on `cuda_stream` (a cudaStream_t of the
+ * context's device), or on the context's own stream when NULL.
+ */
+int hermes_set_stream(hermes_ctx *ctx, void *cuda_stream);
+
+/*
+ * Project a weighted catalogue onto the grid, Eq. (phi_projection):
+ *   eps_l = sum_i w_i prod_d M_p(u_{i,d} - l_d),
+ * then form delta = eps / eps_bar - 1 with eps_bar = sum w / N^3 and transform
+ * it (delta^(0) := 0).  The result replaces the resident field; it is reused by
+ * every later statistic until the next hermes_assign.
+ *   pos : n x 3 float32, row-major (x, y, z), in [0, L).  Index rule: u =
+ *         fl32(x * fl32(N/L)); a coordinate is accepted when 0 <= u <= N, or,
+ *         with HERMES_WRAP, when |u| < 2^22 (cells are then taken modulo N).
+ *   w   : n float32 weights (marks, masses, ...), or NULL for unit weights.
+ *   n   : number of points, n >= 1.
+ *   flags: HERMES_DEVICE_PTR when pos / w are device memory of the context's
+ *         device (e.g. torch tensor data pointers), HERMES_WRAP as above.
+ * Errors: HERMES_ERR_ARG (null pointer, n < 1, a device flag on a non-device
+ * pointer), HERMES_ERR_RANGE (a rejected coordinate, a non-finite weight, or
+ * sum w <= 0; the resident field is then invalid), HERMES_ERR_NOMEM,
+ * HERMES_ERR_CUDA.
+ */
+int hermes_assign(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
+
+/*
+ * Define the radial bins [r_edges[b], r_edges[b+1]) of every later statistic
+ * and tabulate, in float64 on the host, the r^2-weighted bin average of the
+ * spherical Bessel functions <j_l>_b(k) for 0 <= l <= l_max at every discrete
+ * |k| of the grid (Eq. Wshell_k for l = 0; Sec. 3.4.3, "its average over the
+ * corresponding radial window", for l > 0).  Tables are stored as float32.
+ *   r_edges: strictly increasing, r_edges[0] >= 0, r_edges[n_edges-1] <= L/2.
+ *   n_edges: 2 .. 4097.   l_max: 0 .. 12.
+ * Errors: HERMES_ERR_ARG, HERMES_ERR_RANGE (edges out of range), HERMES_ERR_NOMEM.
+ */
+int hermes_window_shells(hermes_ctx *ctx, const double *r_edges, int n_edges, int l_max);
+
+/*
+ * Isotropic 2PCF xi(r_b) of the resident field for every bin (Landy-Szalay
+ * Delta DD / RR with uniform randoms, Eq. xi-deltaDD-over-RR):
+ *   xi_b = (1/N^3) sum_x delta(x) delta~_b(x) - SN_b,
+ * delta~_b = iFFT[delta^ W^_b Phi^], W^_b the volume-normalised finite shell
+ * (Eq. Wshell_k), Phi^(n) = prod_d sinc^{2p}(pi n_d / N); SN_b is the exact
+ * self-pair term sum_i w_i^2 K_eff,b(x_i, x_i) / (N^3 eps_bar^2).
+ *   out: n_bins float64.
+ * Errors: HERMES_ERR_STATE (no field or no bins), HERMES_ERR_ARG, HERMES_ERR_CUDA.
+ */
+int hermes_xi(hermes_ctx *ctx, double *out);
+
+/*
+ * Legendre multipoles xi_l(s_b) with the line of sight along +z, kernel
+ * (2l+1) i^l <j_l>_b(k) L_l(k_z/k) Phi^ (Sec. 3.4.3), normalised like xi
+ * (RR_0 = 1 in delta units), self-pair term subtracted.
+ *   ells: n_ells even orders, each 0 <= l <= l_max of the current bins
+ *         (odd orders vanish identically for an auto-correlation).
+ *   out : [n_ells][n_bins] float64.  ells[i] == 0 reproduces hermes_xi.
+ * Errors: HERMES_ERR_STATE, HERMES_ERR_ARG, HERMES_ERR_CUDA.
+ */
+int hermes_xi_multipoles(hermes_ctx *ctx, const int *ells, int n_ells, double *out);
+
+/*
+ * 3PCF Legendre multipoles zeta_l(r_b1, r_b2), 0 <= l <= l_max, from the
+ * harmonic shell fields a_{b,lm} = iFFT[delta^ 4 pi i^l <j_l>_b Y_lm Phi^]
+ * (Eq. multipole-window, Eq. iFFT-multipoleSFC):
+ *   zeta_l(b1,b2) = 1/(4 pi N^3) sum_x delta(x) sum_{m=-l}^{l} conj(a_{b1,lm}) a_{b2,lm},
+ * so that zeta(r1, r2, theta) = sum_l zeta_l L_l(cos theta)
+ * (Eq. 2-fold-translation).  Only m >= 0 fields are built; m < 0 follows by
+ * conjugation.  Returned raw: the diagonal b1 == b2 includes self triplets.
+ *   out: [l_max+1][n_bins][n_bins] float64 (symmetric in b1, b2).
+ *   Requires n_bins <= 16.
+ * Errors: HERMES_ERR_STATE, HERMES_ERR_ARG (too many bins), HERMES_ERR_NOMEM,
+ * HERMES_ERR_CUDA.
+ */
+int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
+
+/* Text of the last error of this context (never NULL; empty after success). */
+const char *hermes_last_error(const hermes_ctx *ctx);
+
+/* ---- inspection hooks (tests and tools; not needed for measurements) ---- */
+
+/* Copy the resident real field delta (N^3 float32, z fastest) to the host. */
+int hermes_debug_get_delta(hermes_ctx *ctx, float *host_out);
+
+/* Copy the resident half spectrum delta^ (N x N x N/2 complex64, k_z in [0, N/2)). */
+int hermes_debug_get_spectrum(hermes_ctx *ctx, float *host_out);
+
+/*
+ * Replace the resident field by a given real delta (N^3 float32 host array),
+ * transform it, and set eps_bar = 1 with an empty self-pair table (planted-field
+ * tests: xi then equals the plain contraction (1/N^3) sum delta delta~).
+ */
+int hermes_debug_set_delta(hermes_ctx *ctx, const float *host_delta);
+
+/*
+ * The device node rule for n points (host arrays): first[i*3+d] = index of the
+ * first supporting node along axis d (mod N; -1 for a rejected coordinate) and
+ * wts[(i*3+d)*p + o] = M_p(u - node_o), o = 0..p-1.  Allocates temporary device
+ * memory.  HERMES_WRAP in flags as for hermes_assign.
+ */
+int hermes_debug_nodes(hermes_ctx *ctx, const float *pos, int64_t n, unsigned flags, int *first, float *wts);
+
+/* sums[0] = sum w, sums[1] = sum w^2, and the p^3 self-pair table (float64). */
+int hermes_debug_get_sums(hermes_ctx *ctx, double *sums2, double *selfpair_p3);
+
+/*
+ * Host-only (no GPU needed): the float64 bin-averaged Bessel table the context
+ * would upload, out[((b*(l_max+1)) + l)*Q + q] for q = |n|^2 in [0, Q),
+ * Q = 3 (N/2 - 1)^2 + 1, k_q = 2 pi sqrt(q) / L.
+ */
+int hermes_shell_table_host(double L, int N, const double *r_edges, int n_edges, int l_max, double *out);
+
+/* Number of table entries Q for a grid of N cells per axis. */
+int64_t hermes_shell_table_len(int N);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HERMES_H */

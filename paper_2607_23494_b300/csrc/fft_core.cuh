@@ -1,0 +1,169 @@
+// Shared-memory Stockham FFT on one line of length M held by M/8 threads.
+//
+// Every thread owns 8 complex values.  Before and after the transform thread t
+// holds elements t + i*T (i = 0..7, T = M/8) of its line, so the first stage
+// can be fed straight from coalesced global loads and the last stage can be
+// stored (or contracted) straight from registers.  Intermediate stages
+// exchange data through shared memory; the layout of a line in shared memory
+// is a policy class (strided tiles vs. contiguous padded lines).
+//
+// Stage plan: radix-8 throughout, with one leading radix-2 or radix-4 stage
+// when log2(M) is not a multiple of 3.  Twiddles come from a table of
+// e^{-2 pi i j / TW} built on the host in float64; the inverse uses conjugates.
+#pragma once
+#include "common.cuh"
+
+namespace hermes {
+
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {  // forward: -i a ; inverse: +i a
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* a) {
+    float2 t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    float2 t = mul_mi<INV>(d13);
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, t);
+    a3 = csub(d02, t);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* a) { dft4<INV>(a[0], a[1], a[2], a[3]); }
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* a) {
+    const float r = 0.70710678118654752440f;
+    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    // o_k *= w8^k, w8 = e^{-+ 2 pi i / 8}
+    float2 w1, w2, w3;
+    if (!INV) {
+        w1 = make_float2((o1.x + o1.y) * r, (o1.y - o1.x) * r);
+        w3 = make_float2((o3.y - o3.x) * r, -(o3.x + o3.y) * r);
+    } else {
+        w1 = make_float2((o1.x - o1.y) * r, (o1.x + o1.y) * r);
+        w3 = make_float2(-(o3.x + o3.y) * r, (o3.x - o3.y) * r);
+    }
+    w2 = mul_mi<INV>(o2);
+    a[0] = cadd(e0, o0);
+    a[4] = csub(e0, o0);
+    a[1] = cadd(e1, w1);
+    a[5] = csub(e1, w1);
+    a[2] = cadd(e2, w2);
+    a[6] = csub(e2, w2);
+    a[3] = cadd(e3, w3);
+    a[7] = csub(e3, w3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(float2* a) {
+    if constexpr (R == 2) dft2<INV>(a);
+    else if constexpr (R == 4) dft4<INV>(a);
+    else dft8<INV>(a);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int j) {
+    float2 w = __ldg(tw + j);
+    return INV ? make_float2(w.x, -w.y) : w;
+}
+
+// Shared-memory line layouts -------------------------------------------------
+// Strided tile: W lines stored position-major, element (pos, col) at pos*W+col.
+template <int W>
+struct SmemStrided {
+    float2* p;
+    int col;
+    __device__ __forceinline__ float2 ld(int pos) const { return p[pos * W + col]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[pos * W + col] = v; }
+};
+// Contiguous line with one padding slot every 8 elements (bank-conflict skew).
+struct SmemLine {
+    float2* p;
+    __device__ __forceinline__ float2 ld(int pos) const { return p[pos + (pos >> 3)]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[pos + (pos >> 3)] = v; }
+};
+template <int M>
+struct LinePad {
+    static constexpr int value = M + M / 8;
+};
+
+constexpr int ilog2c(int m) { return m <= 1 ? 0 : 1 + ilog2c(m >> 1); }
+template <int M>
+struct FirstRadix {
+    static constexpr int lg = ilog2c(M);
+    static constexpr int value = (lg % 3 == 0) ? 8 : (lg % 3 == 1 ? 2 : 4);
+};
+
+// One Stockham stage.  v[u + r*U] is input r of butterfly b = t + u*T.
+template <int M, int R, int NS, bool INV, class S>
+__device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
+    constexpr int T = M / 8;
+    constexpr int U = 8 / R;
+    constexpr bool LAST = (NS * R == M);
+    float2 out[8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int b = t + u * T;
+        const int k = b & (NS - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<INV>(tw, k * r * (TW / (NS * R))));
+        }
+        dftR<R, INV>(x);
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[u + r * U] = x[r];
+    }
+    if constexpr (LAST) {
+        // position b + r*NS = t + (u + r*U)*T: already in the canonical order
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = out[i];
+    } else {
+        __syncthreads();  // everyone finished reading the previous contents
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = t + u * T;
+            const int base = (b / NS) * NS * R + (b & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm.st(base + r * NS, out[u + r * U]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = sm.ld(t + i * T);
+    }
+}
+
+template <int M, int NS, bool INV, class S>
+__device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
+    constexpr int R = (NS == 1) ? FirstRadix<M>::value : 8;
+    fft_stage<M, R, NS, INV, S>(v, t, tw, sm);
+    if constexpr (NS * R < M) fft_stages<M, NS * R, INV, S>(v, t, tw, sm);
+}
+
+// In-register/shared FFT of length M (8 <= M <= TW).  Precondition: v[i] =
+// x[t + i*M/8].  Postcondition: v[i] = X[t + i*M/8], X_k = sum_n x_n
+// e^{-+2 pi i k n / M} (unnormalised).  All threads of the block must call it
+// the same number of times (it contains __syncthreads when M > 8).
+template <int M, bool INV, class S>
+__device__ __forceinline__ void fft_line(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
+    static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
+    fft_stages<M, 1, INV, S>(v, t, tw, sm);
+}
+
+}  // namespace hermes

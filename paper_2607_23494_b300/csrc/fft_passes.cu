@@ -1,0 +1,370 @@
+// 3-D FFT passes of the xi / xi_l path.
+//
+// Layouts (z fastest everywhere):
+//   grid / delta : float  [N][N][N]        real field
+//   spec         : float2 [N][N][N/2]      half spectrum, k_z in [0, N/2); the
+//                                          Nyquist plane k_z = N/2 is not stored
+//                                          because every window is zero there
+//   work         : float2 [S][N][N][N/2]   filtered spectra of one window batch
+//
+// Forward (Sec. 2 convention, e^{-ik.x}): F1 real-to-complex along z fused with
+// delta = eps / eps_bar - 1 (delta is written back in place for the final
+// contraction), F2 along y, F3 along x with delta^(0) := 0.
+//
+// Inverse per batch of S windows (Sec. 3.5, eps_W = iFT[FT(eps) K_W]):
+//   I1 along x: read delta^ once, multiply by K_s = W^_s Phi^ for every window
+//      s of the batch, accumulate the self-pair term sum_n K_s(n) S^(n), inverse
+//      FFT, store;
+//   I2 along y;
+//   I3 complex-to-real along z fused with the cell contraction
+//      sum_x delta(x) delta~_s(x) (Eq. pair-counting / Eq. 2rdEs): the filtered
+//      fields never return to HBM.
+#include "kernels.h"
+#include "fft_core.cuh"
+
+namespace hermes {
+
+template <int N>
+struct Cfg {
+    static constexpr int H = N / 2;
+    static constexpr int W = (N >= 512) ? 8 : (N / 2 < 16 ? N / 2 : 16);  // columns per strided tile
+    static constexpr int TS = (N / 8) * W;                                  // threads per strided tile
+    static constexpr int MZ = N / 2;                                        // half-length z transform
+    static constexpr int TZ = MZ / 8;
+    static constexpr int LZ = (256 / TZ) > 0 ? (256 / TZ) : 1;              // z lines per block
+    static constexpr int ZTHREADS = TZ * LZ;
+    static constexpr size_t SMEM_STRIDED = (size_t)N * W * sizeof(float2);
+    static constexpr size_t SMEM_Z = (size_t)LZ * LinePad<MZ>::value * sizeof(float2);
+};
+
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// F1: real-to-complex along z.  A real line x_0..x_{N-1} is packed as
+// z_j = x_{2j} + i x_{2j+1}, transformed with an N/2-point FFT, and split:
+// X_k = E_k + e^{-2 pi i k/N} O_k, E_k = (Z_k + conj Z_{M-k})/2,
+// O_k = (Z_k - conj Z_{M-k})/(2i), k = 0..N/2-1.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restrict__ grid, float2* __restrict__ spec,
+                                                                 const double* __restrict__ scal, int convert,
+                                                                 const float2* __restrict__ tw) {
+    using C = Cfg<N>;
+    constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value;
+    extern __shared__ float2 smem[];
+    const int t = threadIdx.x % T, li = threadIdx.x / T;
+    const size_t line = (size_t)blockIdx.x * C::LZ + li;
+    const SmemLine sm{smem + li * LP};
+    float2* g = reinterpret_cast<float2*>(grid + line * N);
+    const float inv_mean = convert ? (float)scal[2] : 1.0f;
+    float2 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float2 e = g[t + i * T];
+        if (convert) {
+            e.x = fmaf(e.x, inv_mean, -1.0f);
+            e.y = fmaf(e.y, inv_mean, -1.0f);
+            g[t + i * T] = e;
+        }
+        v[i] = e;
+    }
+    fft_line<M, false>(v, t, tw, sm);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
+    __syncthreads();
+    float2* out = spec + line * (N / 2);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = t + i * T;
+        const float2 zk = v[i];
+        const float2 zm = cconj(sm.ld((M - k) & (M - 1)));
+        const float2 e = cscale(cadd(zk, zm), 0.5f);
+        const float2 d = csub(zk, zm);
+        const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);  // (zk - conj zm) / (2i)
+        const float2 w = __ldg(tw + k * (TW / N));                // e^{-2 pi i k / N}
+        out[k] = cadd(e, cmul(w, o));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Strided complex FFT of length N along one axis, W adjacent columns per block.
+// Element (pos, col) of block (bx, by, bz) is
+//   data[bz*zstride + by*ystride + bx*W + col + pos*pos_stride].
+template <int N, bool INV>
+__global__ void __launch_bounds__(Cfg<N>::TS) k_strided(float2* __restrict__ data, long long pos_stride,
+                                                         long long ystride, long long zstride, int zero_dc,
+                                                         const float2* __restrict__ tw) {
+    using C = Cfg<N>;
+    constexpr int W = C::W, T = N / 8;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    float2* base = data + (size_t)blockIdx.z * zstride + (size_t)blockIdx.y * ystride + (size_t)blockIdx.x * W + col;
+    float2 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = base[(size_t)(t + i * T) * pos_stride];
+    fft_line<N, INV>(v, t, tw, SmemStrided<W>{smem, col});
+    if (zero_dc && blockIdx.x == 0 && blockIdx.y == 0 && col == 0 && t == 0) v[0] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) base[(size_t)(t + i * T) * pos_stride] = v[i];
+}
+
+// Legendre polynomial L_l(mu) by the three-term recurrence.
+__device__ __forceinline__ float legendre(int ell, float mu) {
+    if (ell == 0) return 1.0f;
+    float p0 = 1.0f, p1 = mu;
+    for (int n = 1; n < ell; ++n) {
+        const float p2 = ((float)(2 * n + 1) * mu * p1 - (float)n * p0) / (float)(n + 1);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// cos(2 pi j / N) from the twiddle table.
+template <int N>
+__device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
+    return __ldg(tw + (j & (N - 1)) * (TW / N)).x;
+}
+
+// ---------------------------------------------------------------------------
+// I1: first inverse pass (along x) with the window multiply of a batch of S
+// windows fused in.  Also accumulates sum_n K_s(n) S^(n) over the full
+// spectrum (the half-spectrum sum doubles k_z > 0), where
+// S^(n) = sum_{a,b,c} S(a,b,c) C(n_x,a) C(n_y,b) C(n_z,c), C(n,0) = 1,
+// C(n,a>0) = 2 cos(2 pi n a / N), is the Fourier transform of the even
+// self-pair overlap table.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::TS) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
+                                                              const WinBatch wb, const Tables tb, int P,
+                                                              double* __restrict__ sn_part) {
+    using C = Cfg<N>;
+    constexpr int W = C::W, T = N / 8, H = N / 2;
+    extern __shared__ float2 smem[];
+    __shared__ double red[32];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    const int ky = blockIdx.y, kz = blockIdx.x * W + col;
+    const size_t nblk = (size_t)gridDim.x * gridDim.y;
+    const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t xstride = (size_t)N * H;
+    const float2* src = spec + (size_t)ky * H + kz;
+    float2 v0[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v0[i] = src[(size_t)(t + i * T) * xstride];
+
+    const int ny = signed_freq(ky, N), nz = kz;
+    const bool nyq_y = (ky == H);
+    const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
+    // self-pair transform: U[a] = sum_{b,c} S(a,b,c) C(ky,b) C(kz,c)
+    float cy[8], cz[8], U[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        cy[a] = (a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, ky * a);
+        cz[a] = (a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, kz * a);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        float u = 0.0f;
+        if (a < P) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (b < P) {
+                    float ub = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < P) ub = fmaf(__ldg(tb.stab + (a * P + b) * P + c), cz[c], ub);
+                    u = fmaf(ub, cy[b], u);
+                }
+            }
+        }
+        U[a] = u;
+    }
+    float shat[8], phk[8], mu[8];
+    int q[8];
+    bool nyq[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int kx = t + i * T;
+        const int nx = signed_freq(kx, N);
+        nyq[i] = nyq_y || (kx == H);
+        q[i] = nyq[i] ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
+        phk[i] = __ldg(tb.phi + kx) * phyz;
+        mu[i] = q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f;
+        float sh = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            if (a < P) sh = fmaf((a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, kx * a), U[a], sh);
+        shat[i] = sh;
+    }
+    const float wz = (kz == 0) ? 1.0f : 2.0f;
+
+    for (int s = 0; s < wb.S; ++s) {
+        const float* tab = wb.tab[s];
+        const float sc = wb.scale[s];
+        const int ell = wb.ell[s];
+        float sn = 0.0f;
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float K = 0.0f;
+            if (!nyq[i]) K = sc * __ldg(tab + q[i]) * phk[i] * legendre(ell, mu[i]);
+            sn = fmaf(K, shat[i], sn);
+            v[i] = cscale(v0[i], K);
+        }
+        fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
+        float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
+        const double tot = block_sum_double((double)(sn * wz), red);
+        if (threadIdx.x == 0) sn_part[(size_t)s * nblk + blk] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// I3: complex-to-real along z fused with the cell contraction.
+// Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), X_M = 0;
+// z = IFFT_M(Z') gives x_{2j} = Re z_j, x_{2j+1} = Im z_j (unnormalised).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_contract(const float2* __restrict__ work, int S,
+                                                                          const float* __restrict__ delta,
+                                                                          const float2* __restrict__ tw,
+                                                                          double* __restrict__ dd_part) {
+    using C = Cfg<N>;
+    constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value, H = N / 2;
+    extern __shared__ float2 smem[];
+    __shared__ double red[32];
+    const int t = threadIdx.x % T, li = threadIdx.x / T;
+    const size_t line = (size_t)blockIdx.x * C::LZ + li;
+    const SmemLine sm{smem + li * LP};
+    const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
+    float2 d2[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d2[i] = dl[t + i * T];
+    for (int s = 0; s < S; ++s) {
+        const float2* X = work + (size_t)s * N * N * H + line * H;
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = X[t + i * T];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = t + i * T;
+            const float2 xk = v[i];
+            const float2 xm = (k == 0) ? make_float2(0.f, 0.f) : cconj(sm.ld(M - k));
+            const float2 a = cadd(xk, xm);
+            const float2 w = cconj(__ldg(tw + k * (TW / N)));  // e^{+2 pi i k / N}
+            const float2 c = cmul(w, csub(xk, xm));
+            v[i] = make_float2(a.x - c.y, a.y + c.x);
+        }
+        fft_line<M, true>(v, t, tw, sm);
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc = fmaf(d2[i].x, v[i].x, fmaf(d2[i].y, v[i].y, acc));
+        const double tot = block_sum_double((double)acc, red);
+        if (threadIdx.x == 0) dd_part[(size_t)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+
+template <int N>
+static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, int convert, const Tables& tb,
+                                cudaStream_t st) {
+    using C = Cfg<N>;
+    cudaError_t e;
+    if ((e = allow_smem(k_fwd_z_r2c<N>, C::SMEM_Z)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_strided<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    k_fwd_z_r2c<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(grid, spec, scal, convert, tb.tw);
+    const long long H = N / 2;
+    dim3 g(H / C::W, N, 1);
+    // along y: pos stride H, blockIdx.y = x
+    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, H, (long long)N * H, 0, 0, tb.tw);
+    // along x: pos stride N*H, blockIdx.y = y, delta^(0) := 0
+    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, 0, 1, tb.tw);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
+                                const Tables& tb, int P, double* sn_part, double* dd_part, cudaStream_t st) {
+    using C = Cfg<N>;
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_x_window<N>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z)) != cudaSuccess) return e;
+    const long long H = N / 2;
+    dim3 g1(H / C::W, N, 1);
+    k_inv_x_window<N><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb, P, sn_part);
+    dim3 g2(H / C::W, N, wb.S);
+    k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
+    k_inv_z_c2r_contract<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(work, wb.S, delta, tb.tw, dd_part);
+    return cudaGetLastError();
+}
+
+#define HERMES_DISPATCH_N(N, CALL)        \
+    switch (N) {                          \
+        case 16: return CALL(16);         \
+        case 32: return CALL(32);         \
+        case 64: return CALL(64);         \
+        case 128: return CALL(128);       \
+        case 256: return CALL(256);       \
+        case 512: return CALL(512);       \
+        case 1024: return CALL(1024);     \
+        default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb, cudaStream_t st) {
+#define F(n) forward_impl<n>(grid, spec, scal, 1, tb, st)
+    HERMES_DISPATCH_N(N, F)
+#undef F
+}
+
+cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
+                                 cudaStream_t st) {
+#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st)
+    HERMES_DISPATCH_N(N, F)
+#undef F
+}
+
+cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
+                              const Tables& tb, double* sn_part, double* dd_part, cudaStream_t st) {
+#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, st)
+    HERMES_DISPATCH_N(N, F)
+#undef F
+}
+
+static int x_blocks_of(int N) {
+    switch (N) {
+        case 16: return (8 / Cfg<16>::W) * 16;
+        case 32: return (16 / Cfg<32>::W) * 32;
+        case 64: return (32 / Cfg<64>::W) * 64;
+        case 128: return (64 / Cfg<128>::W) * 128;
+        case 256: return (128 / Cfg<256>::W) * 256;
+        case 512: return (256 / Cfg<512>::W) * 512;
+        case 1024: return (512 / Cfg<1024>::W) * 1024;
+    }
+    return 0;
+}
+static int z_blocks_of(int N) {
+    switch (N) {
+        case 16: return 256 / Cfg<16>::LZ;
+        case 32: return 1024 / Cfg<32>::LZ;
+        case 64: return 4096 / Cfg<64>::LZ;
+        case 128: return 16384 / Cfg<128>::LZ;
+        case 256: return 65536 / Cfg<256>::LZ;
+        case 512: return 262144 / Cfg<512>::LZ;
+        case 1024: return 1048576 / Cfg<1024>::LZ;
+    }
+    return 0;
+}
+int inv_x_blocks(int N) { return x_blocks_of(N); }
+int inv_z_blocks(int N) { return z_blocks_of(N); }
+
+}  // namespace hermes

@@ -1,0 +1,706 @@
+// C ABI of the field-window estimator: context, input validation, float64
+// window tables and orchestration of the kernels.  See include/hermes.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hermes.h"
+#include "kernels.h"
+#include "common.cuh"
+
+using namespace hermes;
+
+struct hermes_ctx {
+    double L = 0;
+    int N = 0, p = 0, j = 0, H = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    // device buffers
+    float* grid = nullptr;       // N^3: eps, then delta
+    float2* spec = nullptr;      // N*N*H half spectrum
+    float2* work = nullptr;      // batch of filtered spectra
+    size_t work_bytes = 0;
+    float2* zfields = nullptr;   // harmonic fields (full complex)
+    size_t zfields_bytes = 0;
+    double* part = nullptr;      // block partial sums
+    size_t part_cap = 0;         // doubles
+    double* red = nullptr;       // reduced results
+    size_t red_cap = 0;          // doubles
+    double* scal = nullptr;      // [0] sum w [1] sum w^2 [2] N^3/sum w [3..] reduced sums
+    double* stab_d = nullptr;    // p^3
+    float* stab_f = nullptr;     // p^3
+    unsigned* err = nullptr;
+    float2* tw = nullptr;
+    float* phi = nullptr;
+    float* stage_pos = nullptr;
+    float* stage_w = nullptr;
+    size_t stage_cap = 0;        // points
+    double* host_buf = nullptr;  // pinned readback
+    size_t host_cap = 0;
+    // bins
+    int n_bins = 0, l_max = -1;
+    int64_t Q = 0;
+    std::vector<double> edges;
+    float* rad = nullptr;        // [(b*(l_max+1)+l)*Q + q]
+    // state
+    bool have_field = false;
+    double sum_w = 0, sum_w2 = 0;
+    std::string msg;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(hermes_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->msg = buf;
+    }
+    return code;
+}
+
+int cuda_fail(hermes_ctx* c, cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear sticky non-fatal errors
+    if (e == cudaErrorMemoryAllocation) return fail(c, HERMES_ERR_NOMEM, "%s: out of device memory", what);
+    return fail(c, HERMES_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, what);   \
+    } while (0)
+
+template <class T>
+cudaError_t grow(T*& ptr, size_t& cap_bytes, size_t need_bytes) {
+    if (need_bytes <= cap_bytes && ptr) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap_bytes = 0;
+    cudaError_t e = cudaMalloc((void**)&ptr, need_bytes);
+    if (e == cudaSuccess) cap_bytes = need_bytes;
+    return e;
+}
+
+cudaError_t grow_doubles(double*& ptr, size_t& cap, size_t need) {
+    size_t bytes = cap * sizeof(double);
+    cudaError_t e = grow(ptr, bytes, need * sizeof(double));
+    cap = bytes / sizeof(double);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// float64 window mathematics (host)
+//
+// I_l(x) = int_0^x t^2 j_l(t) dt gives the r^2-weighted bin average
+//   <j_l>_b(k) = 3 [I_l(k r_hi) - I_l(k r_lo)] / (k^3 (r_hi^3 - r_lo^3)).
+// Small x: the power series of j_l integrated term by term.  Larger x: the
+// closed forms built from the sine integral with the recurrences
+//   H_0 = Si, H_1 = 1 - j_0, (m+1) H_{m+1} = m H_{m-1} - (2m+1) j_m       (H_m = int j_m)
+//   J_0 = 1 - cos, J_1 = Si - sin, J_m = (2m-1) H_{m-1} - J_{m-2}        (J_m = int t j_m)
+//   I_0 = sin - x cos, I_1 = 2 - 2 cos - x sin, I_l = (2l-1) J_{l-1} - I_{l-2}
+// which follow from j_l = (2l-1)/t j_{l-1} - j_{l-2} and
+// (2m+1) j_m' = m j_{m-1} - (m+1) j_{m+1}.
+
+// Sine integral Si(x), x >= 0: power series for x <= 2, otherwise
+// Si = pi/2 + Im E1(ix) with E1 evaluated by its continued fraction
+// E1(z) = e^{-z} / (z + 1 - 1^2/(z + 3 - 2^2/(z + 5 - ...))) (modified Lentz).
+double sine_integral(double x) {
+    if (x <= 2.0) {
+        double sum = 0.0, term = x;  // term = (-1)^k x^{2k+1} / (2k+1)!
+        for (int k = 0; k < 40; ++k) {
+            const double add = term / (2.0 * k + 1.0);
+            sum += add;
+            if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+            term *= -x * x / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+        }
+        return sum;
+    }
+    typedef std::complex<double> cd;
+    const double tiny = 1e-300;
+    cd b(1.0, x);
+    cd cc = 1.0 / tiny;
+    cd d = 1.0 / b;
+    cd h = d;
+    for (int i = 1; i < 100000; ++i) {
+        const double a = -(double)i * (double)i;
+        b += 2.0;
+        d = 1.0 / (a * d + b);
+        cc = b + a / cc;
+        const cd del = cc * d;
+        h *= del;
+        if (std::fabs(del.real() - 1.0) + std::fabs(del.imag()) < 1e-16) break;
+    }
+    h *= cd(std::cos(x), -std::sin(x));
+    return 1.5707963267948966192 + h.imag();
+}
+
+double dfact2(int n) {  // n!! for odd n >= -1
+    double r = 1.0;
+    for (int k = n; k > 1; k -= 2) r *= k;
+    return r;
+}
+
+// I_l(x) for l = 0..lmax into out[l].
+void bessel_moment_all(double x, int lmax, double* out) {
+    if (x == 0.0) {
+        for (int l = 0; l <= lmax; ++l) out[l] = 0.0;
+        return;
+    }
+    const double xs = x * x;
+    // series where it is accurate: x < l + 4
+    int first_rec = lmax + 1;
+    for (int l = 0; l <= lmax; ++l) {
+        if (x < l + 4.0) {
+            double s = 1.0, sum = 1.0 / (l + 3.0);
+            for (int k = 1; k < 200; ++k) {
+                s *= -0.5 * xs / ((double)k * (2.0 * l + 2.0 * k + 1.0));
+                const double add = s / (2.0 * k + l + 3.0);
+                sum += add;
+                if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+            }
+            out[l] = sum * std::pow(x, l + 3) / dfact2(2 * l + 1);
+        } else if (first_rec > lmax) {
+            first_rec = l;
+        }
+    }
+    if (first_rec > lmax) return;
+    // closed forms for l >= first_rec (all with x >= l + 4)
+    const double sn = std::sin(x), cs = std::cos(x), si = sine_integral(x);
+    const int M = lmax + 1;
+    std::vector<double> jl(M + 1), Hm(M + 1), Jm(M + 1), Il(M + 1);
+    jl[0] = sn / x;
+    if (M >= 1) jl[1] = sn / xs - cs / x;
+    for (int m = 1; m < M; ++m) jl[m + 1] = (2.0 * m + 1.0) / x * jl[m] - jl[m - 1];
+    Hm[0] = si;
+    Hm[1] = 1.0 - jl[0];
+    for (int m = 1; m + 1 <= M; ++m) Hm[m + 1] = (m * Hm[m - 1] - (2.0 * m + 1.0) * jl[m]) / (m + 1.0);
+    Jm[0] = 1.0 - cs;
+    Jm[1] = si - sn;
+    for (int m = 2; m <= M; ++m) Jm[m] = (2.0 * m - 1.0) * Hm[m - 1] - Jm[m - 2];
+    Il[0] = sn - x * cs;
+    Il[1] = 2.0 - 2.0 * cs - x * sn;
+    for (int l = 2; l <= lmax; ++l) Il[l] = (2.0 * l - 1.0) * Jm[l - 1] - Il[l - 2];
+    for (int l = first_rec; l <= lmax; ++l) out[l] = Il[l];
+}
+
+// out[((b*(lmax+1)) + l)*Q + q] = <j_l>_b(k_q), k_q = 2 pi sqrt(q) / L.
+void build_shell_tables(double L, int64_t Q, const double* edges, int n_edges, int lmax, double* out) {
+    const int nb = n_edges - 1;
+    const int LM = lmax + 1;
+    unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+        std::vector<double> Ie((size_t)n_edges * LM);
+        const int64_t chunk = 256;
+        for (;;) {
+            const int64_t q0 = next.fetch_add(chunk);
+            if (q0 >= Q) break;
+            const int64_t q1 = std::min(Q, q0 + chunk);
+            for (int64_t q = q0; q < q1; ++q) {
+                if (q == 0) {
+                    for (int b = 0; b < nb; ++b)
+                        for (int l = 0; l < LM; ++l) out[((size_t)b * LM + l) * Q] = (l == 0) ? 1.0 : 0.0;
+                    continue;
+                }
+                const double k = 2.0 * M_PI * std::sqrt((double)q) / L;
+                for (int e = 0; e < n_edges; ++e) bessel_moment_all(k * edges[e], lmax, &Ie[(size_t)e * LM]);
+                const double k3 = k * k * k;
+                for (int b = 0; b < nb; ++b) {
+                    const double lo = edges[b], hi = edges[b + 1];
+                    const double den = k3 * (hi * hi * hi - lo * lo * lo) / 3.0;
+                    for (int l = 0; l < LM; ++l)
+                        out[((size_t)b * LM + l) * Q + q] =
+                            (Ie[(size_t)(b + 1) * LM + l] - Ie[(size_t)b * LM + l]) / den;
+                }
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (unsigned i = 1; i < nth; ++i) th.emplace_back(worker);
+    worker();
+    for (auto& t : th) t.join();
+}
+
+int64_t table_len(int N) {
+    const int64_t h = N / 2 - 1;
+    return 3 * h * h + 1;
+}
+
+bool valid_N(int N) { return N >= 16 && N <= 1024 && (N & (N - 1)) == 0; }
+
+Tables tables_of(const hermes_ctx* c) {
+    Tables t;
+    t.tw = c->tw;
+    t.phi = c->phi;
+    t.stab = c->stab_f;
+    return t;
+}
+
+int ensure_host(hermes_ctx* c, size_t n) {
+    if (n <= c->host_cap) return HERMES_OK;
+    if (c->host_buf) cudaFreeHost(c->host_buf);
+    c->host_buf = nullptr;
+    c->host_cap = 0;
+    if (cudaMallocHost((void**)&c->host_buf, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HERMES_ERR_NOMEM, "pinned host buffer of %zu doubles", n);
+    }
+    c->host_cap = n;
+    return HERMES_OK;
+}
+
+int check_ctx(hermes_ctx* c) {
+    if (!c) return HERMES_ERR_ARG;
+    c->msg.clear();
+    return HERMES_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
+    if (!out) return HERMES_ERR_ARG;
+    *out = nullptr;
+    if (!(L > 0.0) || !std::isfinite(L)) return HERMES_ERR_ARG;
+    if (j < 4 || j > 10 || N != (1 << j) || !valid_N(N)) return HERMES_ERR_ARG;
+    if (p < 1 || p > 8 || 2 * p - 1 > N) return HERMES_ERR_ARG;
+    hermes_ctx* c = new (std::nothrow) hermes_ctx;
+    if (!c) return HERMES_ERR_NOMEM;
+    c->L = L;
+    c->N = N;
+    c->p = p;
+    c->j = j;
+    c->H = N / 2;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HERMES_ERR_CUDA;
+    }
+    DeviceGuard g(c->device);
+    auto bail = [&](int code) {
+        hermes_destroy(c);
+        return code;
+    };
+    const size_t n3 = (size_t)N * N * N;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(HERMES_ERR_CUDA);
+    c->stream = c->own_stream;
+    if (cudaMalloc((void**)&c->grid, n3 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->spec, (size_t)N * N * c->H * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->scal, 8 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->stab_d, 512 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->stab_f, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->err, sizeof(unsigned)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->tw, TW * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->phi, N * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    // twiddles e^{-2 pi i j / TW} and Phi^(n) = sinc^{2p}(pi n / N) in float64, stored as float32
+    std::vector<float2> tw(TW);
+    for (int i = 0; i < TW; ++i) {
+        const double a = -2.0 * M_PI * (double)i / (double)TW;
+        tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    std::vector<float> ph(N);
+    for (int k = 0; k < N; ++k) {
+        const int n = k < N / 2 ? k : k - N;
+        const double x = M_PI * (double)n / (double)N;
+        const double s = (n == 0) ? 1.0 : std::sin(x) / x;
+        ph[k] = (float)std::pow(s, 2 * p);
+    }
+    if (cudaMemcpy(c->tw, tw.data(), TW * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) return bail(HERMES_ERR_CUDA);
+    if (cudaMemcpy(c->phi, ph.data(), N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return bail(HERMES_ERR_CUDA);
+    if (cudaMemset(c->stab_f, 0, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_CUDA);
+    if (ensure_host(c, 1024) != HERMES_OK) return bail(HERMES_ERR_NOMEM);
+    *out = c;
+    return HERMES_OK;
+}
+
+int hermes_destroy(hermes_ctx* c) {
+    if (!c) return HERMES_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->grid);
+    cudaFree(c->spec);
+    cudaFree(c->work);
+    cudaFree(c->zfields);
+    cudaFree(c->part);
+    cudaFree(c->red);
+    cudaFree(c->scal);
+    cudaFree(c->stab_d);
+    cudaFree(c->stab_f);
+    cudaFree(c->err);
+    cudaFree(c->tw);
+    cudaFree(c->phi);
+    cudaFree(c->stage_pos);
+    cudaFree(c->stage_w);
+    cudaFree(c->rad);
+    if (c->host_buf) cudaFreeHost(c->host_buf);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    cudaGetLastError();
+    delete c;
+    return HERMES_OK;
+}
+
+int hermes_set_stream(hermes_ctx* c, void* s) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    c->stream = s ? (cudaStream_t)s : c->own_stream;
+    return HERMES_OK;
+}
+
+const char* hermes_last_error(const hermes_ctx* c) {
+    if (!c) return "null context";
+    return c->msg.c_str();
+}
+
+static int check_device_ptr(hermes_ctx* c, const void* p, const char* name) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HERMES_ERR_ARG, "%s is not a valid pointer", name);
+    }
+    if (!(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) || a.device != c->device)
+        return fail(c, HERMES_ERR_ARG, "%s is not device memory of device %d", name, c->device);
+    return HERMES_OK;
+}
+
+int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, unsigned flags) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!pos) return fail(c, HERMES_ERR_ARG, "pos is NULL");
+    if (n < 1) return fail(c, HERMES_ERR_ARG, "empty catalogue (n = %lld): the density contrast is undefined",
+                           (long long)n);
+    if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    DeviceGuard g(c->device);
+    c->have_field = false;
+    cudaStream_t st = c->stream;
+    const int N = c->N, p = c->p;
+    const float* dpos = pos;
+    const float* dw = w;
+    if (flags & HERMES_DEVICE_PTR) {
+        int r = check_device_ptr(c, pos, "pos");
+        if (r) return r;
+        if (w && (r = check_device_ptr(c, w, "w"))) return r;
+    } else {
+        if ((size_t)n > c->stage_cap) {
+            cudaFree(c->stage_pos);
+            cudaFree(c->stage_w);
+            c->stage_pos = nullptr;
+            c->stage_w = nullptr;
+            c->stage_cap = 0;
+            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
+            c->stage_cap = (size_t)n;
+        }
+        CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
+        if (w) CK(cudaMemcpyAsync(c->stage_w, w, (size_t)n * sizeof(float), cudaMemcpyDefault, st), "copy weights");
+        dpos = c->stage_pos;
+        dw = w ? c->stage_w : nullptr;
+    }
+    const size_t n3 = (size_t)N * N * N;
+    const int p3 = p * p * p;
+    const int nblk = 592;
+    CK(grow_doubles(c->part, c->part_cap, (size_t)std::max(2, p3) * nblk), "partials");
+    CK(grow_doubles(c->red, c->red_cap, 1024), "reduction buffer");
+    CK(cudaMemsetAsync(c->grid, 0, n3 * sizeof(float), st), "clear grid");
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    const float s = (float)((double)N / c->L);
+    CK(launch_scatter(N, p, dpos, dw, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st), "scatter");
+    CK(launch_weight_sums(dw, n, c->part, nblk, st), "weight sums");
+    CK(launch_reduce_rows(c->part, 2, nblk, c->red, st), "reduce sums");
+    CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st), "self-pair table");
+    CK(launch_reduce_rows(c->part, p3, nblk, c->stab_d, st), "reduce self-pair");
+    CK(launch_finish_field(c->red, c->stab_d, p3, c->stab_f, N, c->scal, st), "field scalars");
+    CK(cudaMemcpyAsync(c->host_buf, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read sums");
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "assign");
+    if (herr) return fail(c, HERMES_ERR_RANGE, "a coordinate is outside [0, L] (u = x*N/L outside [0, N]) "
+                                               "or a weight is not finite; use HERMES_WRAP to wrap");
+    c->sum_w = c->host_buf[0];
+    c->sum_w2 = c->host_buf[1];
+    if (!(c->sum_w > 0.0) || !std::isfinite(c->sum_w))
+        return fail(c, HERMES_ERR_RANGE, "sum of weights is %g; it must be positive", c->sum_w);
+    CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st), "forward FFT");
+    CK(cudaStreamSynchronize(st), "forward FFT");
+    c->have_field = true;
+    return HERMES_OK;
+}
+
+int64_t hermes_shell_table_len(int N) {
+    if (!valid_N(N)) return -1;
+    return table_len(N);
+}
+
+int hermes_shell_table_host(double L, int N, const double* r_edges, int n_edges, int l_max, double* out) {
+    if (!valid_N(N) || !(L > 0) || !r_edges || !out || n_edges < 2 || l_max < 0 || l_max > 12) return HERMES_ERR_ARG;
+    for (int e = 0; e < n_edges; ++e)
+        if (!std::isfinite(r_edges[e]) || (e > 0 && !(r_edges[e] > r_edges[e - 1])) || r_edges[e] < 0)
+            return HERMES_ERR_RANGE;
+    build_shell_tables(L, table_len(N), r_edges, n_edges, l_max, out);
+    return HERMES_OK;
+}
+
+int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int l_max) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!r_edges) return fail(c, HERMES_ERR_ARG, "r_edges is NULL");
+    if (n_edges < 2 || n_edges > 4097) return fail(c, HERMES_ERR_ARG, "n_edges = %d (need 2..4097)", n_edges);
+    if (l_max < 0 || l_max > 12) return fail(c, HERMES_ERR_ARG, "l_max = %d (need 0..12)", l_max);
+    for (int e = 0; e < n_edges; ++e) {
+        if (!std::isfinite(r_edges[e]) || r_edges[e] < 0.0)
+            return fail(c, HERMES_ERR_RANGE, "r_edges[%d] = %g is negative or not finite", e, r_edges[e]);
+        if (e > 0 && !(r_edges[e] > r_edges[e - 1]))
+            return fail(c, HERMES_ERR_RANGE, "r_edges must increase strictly (index %d)", e);
+    }
+    if (r_edges[n_edges - 1] > 0.5 * c->L)
+        return fail(c, HERMES_ERR_RANGE, "largest edge %g exceeds L/2 = %g", r_edges[n_edges - 1], 0.5 * c->L);
+    DeviceGuard g(c->device);
+    const int64_t Q = table_len(c->N);
+    const int nb = n_edges - 1;
+    const size_t count = (size_t)nb * (l_max + 1) * Q;
+    std::vector<double> host;
+    std::vector<float> host32;
+    try {
+        host.resize(count);
+        host32.resize(count);
+    } catch (...) {
+        return fail(c, HERMES_ERR_NOMEM, "host table of %zu entries", count);
+    }
+    build_shell_tables(c->L, Q, r_edges, n_edges, l_max, host.data());
+    for (size_t i = 0; i < count; ++i) host32[i] = (float)host[i];
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->rad);
+    c->rad = nullptr;
+    c->n_bins = 0;
+    CK(cudaMalloc((void**)&c->rad, count * sizeof(float)), "window tables");
+    CK(cudaMemcpy(c->rad, host32.data(), count * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
+    c->edges.assign(r_edges, r_edges + n_edges);
+    c->n_bins = nb;
+    c->l_max = l_max;
+    c->Q = Q;
+    return HERMES_OK;
+}
+
+int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!ells || !out || n_ells < 1) return fail(c, HERMES_ERR_ARG, "ells/out NULL or n_ells < 1");
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
+    for (int a = 0; a < n_ells; ++a) {
+        if (ells[a] < 0 || ells[a] > c->l_max)
+            return fail(c, HERMES_ERR_ARG, "l = %d outside 0..l_max = %d", ells[a], c->l_max);
+        if (ells[a] & 1) return fail(c, HERMES_ERR_ARG, "odd l = %d vanishes for an auto-correlation", ells[a]);
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, H = c->H, nb = c->n_bins, LM = c->l_max + 1;
+    const int nwin = n_ells * nb;
+    const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
+    int S = (int)std::min<size_t>(16, std::max<size_t>(1, ((size_t)8 << 30) / win_bytes));
+    S = std::min(S, nwin);
+    S = std::min(S, MAX_BATCH);
+    CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
+    const int xb = inv_x_blocks(N), zb = inv_z_blocks(N);
+    CK(grow_doubles(c->part, c->part_cap, (size_t)S * (xb + zb)), "partials");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
+    const Tables tb = tables_of(c);
+    for (int w0 = 0; w0 < nwin; w0 += S) {
+        WinBatch wb;
+        wb.S = std::min(S, nwin - w0);
+        for (int s = 0; s < wb.S; ++s) {
+            const int widx = w0 + s;
+            const int a = widx / nb, b = widx % nb;
+            const int ell = ells[a];
+            wb.tab[s] = c->rad + ((size_t)b * LM + ell) * c->Q;
+            // (2l+1) i^l for even l
+            wb.scale[s] = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));
+            wb.ell[s] = ell;
+        }
+        double* sn_part = c->part;
+        double* dd_part = c->part + (size_t)wb.S * xb;
+        CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st), "inverse passes");
+        CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st), "reduce self-pair sums");
+        CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st), "reduce contractions");
+    }
+    CK(ensure_host(c, (size_t)2 * nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    CK(cudaStreamSynchronize(st), "xi");
+    const double n3 = (double)N * N * N;
+    const double n6 = n3 * n3;
+    const double eps_bar = c->sum_w / n3;
+    for (int widx = 0; widx < nwin; ++widx) {
+        const double dd = c->host_buf[widx] / n6;
+        const double sn = c->host_buf[nwin + widx] / (n6 * eps_bar * eps_bar);
+        out[widx] = dd - sn;
+    }
+    return HERMES_OK;
+}
+
+int hermes_xi(hermes_ctx* c, double* out) {
+    const int zero = 0;
+    return hermes_xi_multipoles(c, &zero, 1, out);
+}
+
+int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
+    if (c->n_bins > 16) return fail(c, HERMES_ERR_ARG, "zeta_l supports at most 16 bins (have %d)", c->n_bins);
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, nb = c->n_bins, LM = c->l_max + 1;
+    const size_t n3 = (size_t)N * N * N;
+    CK(grow(c->zfields, c->zfields_bytes, (size_t)nb * n3 * sizeof(float2)), "harmonic fields");
+    const int zb = zeta_z_blocks(N);
+    CK(grow_doubles(c->part, c->part_cap, (size_t)256 * zb), "partials");
+    const int nlm = LM * (LM + 1) / 2;
+    CK(grow_doubles(c->red, c->red_cap, (size_t)256 * nlm), "reduction buffer");
+    const Tables tb = tables_of(c);
+    int lm = 0;
+    for (int ell = 0; ell < LM; ++ell) {
+        for (int m = 0; m <= ell; ++m, ++lm) {
+            HarmBatch hb;
+            hb.S = nb;
+            hb.ell = ell;
+            hb.m = m;
+            double norm = std::sqrt((2.0 * ell + 1.0) / (4.0 * M_PI) * std::tgamma(ell - m + 1.0) /
+                                    std::tgamma(ell + m + 1.0));
+            norm *= ((m & 1) ? -1.0 : 1.0) * dfact2(2 * m - 1);
+            hb.ylm_norm = (float)(4.0 * M_PI * norm);
+            for (int b = 0; b < nb; ++b) hb.tab[b] = c->rad + ((size_t)b * LM + ell) * c->Q;
+            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, st), "harmonic fields");
+            CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st), "reduce Gram");
+        }
+    }
+    CK(ensure_host(c, (size_t)256 * nlm) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)256 * nlm * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read Gram");
+    CK(cudaStreamSynchronize(st), "zeta");
+    const double nn = (double)N;
+    const double scale = 1.0 / (4.0 * M_PI * std::pow(nn, 9));
+    lm = 0;
+    for (int ell = 0; ell < LM; ++ell) {
+        double* o = out + (size_t)ell * nb * nb;
+        for (int i = 0; i < nb * nb; ++i) o[i] = 0.0;
+        for (int m = 0; m <= ell; ++m, ++lm) {
+            const double* G = c->host_buf + (size_t)256 * lm;
+            const double wm = (m == 0) ? 1.0 : 2.0;
+            for (int b1 = 0; b1 < nb; ++b1)
+                for (int b2 = 0; b2 < nb; ++b2) {
+                    const double gv = (b1 <= b2) ? G[b1 * 16 + b2] : G[b2 * 16 + b1];  // exact symmetry
+                    o[b1 * nb + b2] += wm * gv * scale;
+                }
+        }
+    }
+    return HERMES_OK;
+}
+
+int hermes_debug_get_delta(hermes_ctx* c, float* host_out) {
+    if (check_ctx(c) || !host_out) return HERMES_ERR_ARG;
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
+    DeviceGuard g(c->device);
+    const size_t n3 = (size_t)c->N * c->N * c->N;
+    CK(cudaMemcpyAsync(host_out, c->grid, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "read delta");
+    CK(cudaStreamSynchronize(c->stream), "read delta");
+    return HERMES_OK;
+}
+
+int hermes_debug_get_spectrum(hermes_ctx* c, float* host_out) {
+    if (check_ctx(c) || !host_out) return HERMES_ERR_ARG;
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
+    DeviceGuard g(c->device);
+    const size_t cnt = (size_t)c->N * c->N * c->H;
+    CK(cudaMemcpyAsync(host_out, c->spec, cnt * sizeof(float2), cudaMemcpyDeviceToHost, c->stream), "read spectrum");
+    CK(cudaStreamSynchronize(c->stream), "read spectrum");
+    return HERMES_OK;
+}
+
+int hermes_debug_set_delta(hermes_ctx* c, const float* host_delta) {
+    if (check_ctx(c) || !host_delta) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    const size_t n3 = (size_t)c->N * c->N * c->N;
+    c->have_field = false;
+    CK(cudaMemcpyAsync(c->grid, host_delta, n3 * sizeof(float), cudaMemcpyDefault, c->stream), "write delta");
+    CK(cudaMemsetAsync(c->stab_f, 0, 512 * sizeof(float), c->stream), "clear self-pair");
+    CK(cudaMemsetAsync(c->stab_d, 0, 512 * sizeof(double), c->stream), "clear self-pair");
+    CK(launch_delta_to_spec(c->N, c->grid, c->spec, c->scal, tables_of(c), c->stream), "forward FFT");
+    CK(cudaStreamSynchronize(c->stream), "set delta");
+    c->sum_w = (double)n3;  // eps_bar = 1
+    c->sum_w2 = 0.0;
+    c->have_field = true;
+    return HERMES_OK;
+}
+
+int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned flags, int* host_first,
+                       float* host_wts) {
+    if (check_ctx(c) || !host_pos || !host_first || !host_wts || n < 1) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int p = c->p;
+    float* dpos = nullptr;
+    int* dfirst = nullptr;
+    float* dw = nullptr;
+    int rc = HERMES_OK;
+    unsigned herr = 0;
+    cudaError_t e = cudaMalloc((void**)&dpos, (size_t)n * 3 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dfirst, (size_t)n * 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dw, (size_t)n * 3 * p * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, host_pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = launch_nodes(c->N, p, dpos, n, (float)((double)c->N / c->L), (flags & HERMES_WRAP) ? 1 : 0, dfirst, dw,
+                         c->err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_first, dfirst, (size_t)n * 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_wts, dw, (size_t)n * 3 * p * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "node rule");
+    else if (herr) rc = fail(c, HERMES_ERR_RANGE, "a coordinate is outside the accepted range");
+    cudaFree(dpos);
+    cudaFree(dfirst);
+    cudaFree(dw);
+    return rc;
+}
+
+int hermes_debug_get_sums(hermes_ctx* c, double* sums2, double* selfpair) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
+    DeviceGuard g(c->device);
+    if (sums2) {
+        sums2[0] = c->sum_w;
+        sums2[1] = c->sum_w2;
+    }
+    if (selfpair) {
+        const int p3 = c->p * c->p * c->p;
+        CK(cudaMemcpyAsync(selfpair, c->stab_d, p3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read table");
+        CK(cudaStreamSynchronize(c->stream), "read table");
+    }
+    return HERMES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal launcher declarations shared by the C ABI implementation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hermes {
+
+constexpr int MAX_BATCH = 32;  // windows evaluated per launch of the first inverse pass
+
+// One batch of real (xi / xi_l) windows: radial table per window and the
+// Legendre order of its angular factor.  scale multiplies the table value.
+struct WinBatch {
+    const float* tab[MAX_BATCH];
+    float scale[MAX_BATCH];
+    int ell[MAX_BATCH];
+    int S;
+};
+
+// One batch of complex harmonic windows for a fixed (l, m): one radial table per bin.
+struct HarmBatch {
+    const float* tab[MAX_BATCH];
+    int S;      // number of bins in this batch
+    int ell, m;
+    float ylm_norm;  // N_lm (-1)^m (2m-1)!!  times 4 pi
+};
+
+struct Tables {
+    const float2* tw;     // [TW] e^{-2 pi i j / TW}
+    const float* phi;     // [N]  sinc^{2p}(pi n / N), FFT order
+    const float* stab;    // [p^3] self-pair table (float)
+};
+
+// scatter.cu
+cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
+                           int wrap, unsigned* err, cudaStream_t st);
+cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
+                         unsigned* err, cudaStream_t st);
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
+                            int nblk, cudaStream_t st);
+cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st);
+cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3, float* stab_f, int N,
+                                double* scal, cudaStream_t st);
+
+// fft_passes.cu
+cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
+                           cudaStream_t st);
+int inv_x_blocks(int N);
+int inv_z_blocks(int N);
+cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta,
+                              const WinBatch& wb, const Tables& tb, double* sn_part, double* dd_part,
+                              cudaStream_t st);
+cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
+                                 cudaStream_t st);
+
+// zeta.cu
+int zeta_z_blocks(int N);
+cudaError_t launch_zeta_lm(int N, const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
+                           const Tables& tb, double* gram_part, cudaStream_t st);
+
+}  // namespace hermes

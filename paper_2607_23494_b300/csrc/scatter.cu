@@ -1,0 +1,281 @@
+// B-spline scatter of a weighted point catalogue onto the periodic N^3 grid,
+// Eq. (phi_projection): eps_l = sum_i w_i prod_d M_p(u_{i,d} - l_d), plus the
+// float64 cell-sum reductions (sum w, sum w^2) and the self-pair overlap table
+// S(a,b,c) = sum_i w_i^2 prod_d s(a_d; x_i) with s(d; x) = sum_l phi_l(x) phi_{l+d}(x).
+//
+// Node rule (bit-exact with the oracle): u = fl32(x * s), s = fl32(N/L);
+// v = u (+0.5 in float32 for odd p); i = floor(v); t = v - i; the p supporting
+// nodes are i - (p/2 - 1) + o (even p) or i - (p-1)/2 + o (odd p), o = 0..p-1,
+// all taken modulo N; node o carries the uniform B-spline basis value b_o(t).
+#include "kernels.h"
+#include "common.cuh"
+
+namespace hermes {
+
+// Uniform B-spline basis values b_0..b_{P-1} at local parameter t in [0,1):
+// b_o = M_P(distance from node o), via the Cox-de Boor recursion on integer knots.
+template <int P>
+__device__ __forceinline__ void bspline_basis(float t, float (&b)[P]) {
+    b[0] = 1.0f;
+#pragma unroll
+    for (int d = 1; d < P; ++d) {
+        const float inv_d = 1.0f / (float)d;
+        b[d] = 0.0f;
+#pragma unroll
+        for (int j = d; j >= 0; --j) {
+            float left = (j > 0) ? (t + (float)(d - j)) * b[j - 1] : 0.0f;
+            float right = (j < d) ? ((float)(j + 1) - t) * b[j] : 0.0f;
+            b[j] = (left + right) * inv_d;
+        }
+    }
+}
+
+// Returns false if the coordinate is outside the accepted range.
+template <int P>
+__device__ __forceinline__ bool node_rule(float x, float s, int N, int wrap, int& first, float (&b)[P]) {
+    const float u = __fmul_rn(x, s);
+    const bool ok = wrap ? (fabsf(u) < 4194304.0f) : (u >= 0.0f && u <= (float)N);
+    if (!ok) return false;
+    const float v = (P & 1) ? __fadd_rn(u, 0.5f) : u;
+    const float fl = floorf(v);
+    const float t = __fsub_rn(v, fl);
+    const int i0 = (int)fl;
+    first = (P & 1) ? i0 - (P - 1) / 2 : i0 - (P / 2 - 1);
+    bspline_basis<P>(t, b);
+    return true;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, const float* __restrict__ w,
+                                                 int64_t n, float* __restrict__ grid, float s, int N, int wrap,
+                                                 unsigned* __restrict__ err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int msk = N - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float x = __ldg(pos + 3 * i), y = __ldg(pos + 3 * i + 1), z = __ldg(pos + 3 * i + 2);
+        const float wi = w ? __ldg(w + i) : 1.0f;
+        float bx[P], by[P], bz[P];
+        int fx, fy, fz;
+        bool ok = node_rule<P>(x, s, N, wrap, fx, bx) & node_rule<P>(y, s, N, wrap, fy, by) &
+                  node_rule<P>(z, s, N, wrap, fz, bz);
+        if (!ok || !isfinite(wi)) {
+            atomicOr(err, 1u);
+            continue;
+        }
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const int ix = (fx + a) & msk;
+            const float wa = wi * bx[a];
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const int iy = (fy + b) & msk;
+                const float wab = wa * by[b];
+                float* row = grid + ((size_t)ix * N + iy) * N;
+#pragma unroll
+                for (int c = 0; c < P; ++c) atomicAdd(row + ((fz + c) & msk), wab * bz[c]);
+            }
+        }
+    }
+}
+
+// Node rule of every point, for inspection: first node (mod N) and the p basis
+// values per axis; err bit 1 marks a rejected coordinate.
+template <int P>
+__global__ void __launch_bounds__(256) k_nodes(const float* __restrict__ pos, int64_t n, float s, int N, int wrap,
+                                               int* __restrict__ first, float* __restrict__ wts,
+                                               unsigned* __restrict__ err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float b[P];
+        int f = 0;
+        const bool ok = node_rule<P>(pos[3 * i + d], s, N, wrap, f, b);
+        if (!ok) atomicOr(err, 1u);
+        first[3 * i + d] = ok ? (f & (N - 1)) : -1;
+#pragma unroll
+        for (int o = 0; o < P; ++o) wts[(3 * i + d) * P + o] = ok ? b[o] : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_weight_sums(const float* __restrict__ w, int64_t n,
+                                                     double* __restrict__ part) {
+    __shared__ double red[8];
+    double s1 = 0.0, s2 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v = w ? (double)__ldg(w + i) : 1.0;
+        s1 += v;
+        s2 += v * v;
+    }
+    double t1 = block_sum_double(s1, red);
+    double t2 = block_sum_double(s2, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t1;
+        part[gridDim.x + blockIdx.x] = t2;
+    }
+}
+
+// Self-pair overlap table.  Each warp stages 32 points' per-axis overlaps in
+// shared memory; every lane owns table entries e = lane + 32k and accumulates
+// them over the staged points (float32), then the block sums in float64.
+template <int P>
+__global__ void __launch_bounds__(256) k_selfpair(const float* __restrict__ pos, const float* __restrict__ w,
+                                                  int64_t n, float s, int N, double* __restrict__ part) {
+    constexpr int P3 = P * P * P;
+    constexpr int E = (P3 + 31) / 32;
+    constexpr int STRIDE = 3 * P + 1;
+    __shared__ float stage[8][32][STRIDE];
+    __shared__ double tot[P3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float acc[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) acc[k] = 0.0f;
+    const int64_t nwarps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    for (int64_t base = gw * 32; base < n; base += nwarps_total * 32) {
+        const int64_t i = base + lane;
+        float* my = stage[wid][lane];
+        if (i < n) {
+            float b[3][P];
+            int f;
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ok &= node_rule<P>(__ldg(pos + 3 * i + d), s, N, 1, f, b[d]);
+            const float wi = w ? __ldg(w + i) : 1.0f;
+            my[0] = ok ? wi * wi : 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    float sacc = 0.0f;
+#pragma unroll
+                    for (int o = 0; o + a < P; ++o) sacc = fmaf(b[d][o], b[d][o + a], sacc);
+                    my[1 + d * P + a] = sacc;
+                }
+            }
+        } else {
+            my[0] = 0.0f;
+#pragma unroll
+            for (int q = 1; q < STRIDE; ++q) my[q] = 0.0f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int e = lane + 32 * k;
+            if (e < P3) {
+                const int a = e / (P * P), bb = (e / P) % P, c = e % P;
+                float sacc = 0.0f;
+                for (int j = 0; j < 32; ++j) {
+                    const float* q = stage[wid][j];
+                    sacc = fmaf(q[0] * q[1 + a], q[1 + P + bb] * q[1 + 2 * P + c], sacc);
+                }
+                acc[k] += sacc;
+            }
+        }
+        __syncwarp();
+    }
+    for (int e = threadIdx.x; e < P3; e += blockDim.x) tot[e] = 0.0;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nw; ++q) {  // warps add in turn: fixed order, no atomics
+        if (wid == q) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int e = lane + 32 * k;
+                if (e < P3) tot[e] += (double)acc[k];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < P3; e += blockDim.x) part[(size_t)e * gridDim.x + blockIdx.x] = tot[e];
+}
+
+// out[r] = sum_c part[r*cols + c], one block per row (deterministic order).
+__global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ part, int cols,
+                                                     double* __restrict__ out) {
+    __shared__ double red[8];
+    const double* row = part + (size_t)blockIdx.x * cols;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += row[c];
+    s = block_sum_double(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// scal[0] = sum w, scal[1] = sum w^2, scal[2] = N^3 / sum w (the inverse mean);
+// float copy of the self-pair table for the window kernels.
+__global__ void k_finish_field(const double* __restrict__ sums, const double* __restrict__ stab_d, int p3,
+                               float* __restrict__ stab_f, int N, double* __restrict__ scal) {
+    if (threadIdx.x == 0) {
+        scal[0] = sums[0];
+        scal[1] = sums[1];
+        scal[2] = (double)N * (double)N * (double)N / sums[0];
+    }
+    for (int e = threadIdx.x; e < p3; e += blockDim.x) stab_f[e] = (float)stab_d[e];
+}
+
+static int nblocks_for(int64_t n, int per_block, int cap) {
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
+                           int wrap, unsigned* err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int nb = nblocks_for(n, 256, 148 * 32);
+    switch (p) {
+#define HERMES_SC(P) \
+    case P: k_scatter<P><<<nb, 256, 0, st>>>(pos, w, n, grid, s, N, wrap, err); break;
+        HERMES_SC(1) HERMES_SC(2) HERMES_SC(3) HERMES_SC(4) HERMES_SC(5) HERMES_SC(6) HERMES_SC(7) HERMES_SC(8)
+#undef HERMES_SC
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
+                         unsigned* err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int nb = (int)((n + 255) / 256);
+    switch (p) {
+#define HERMES_ND(P) \
+    case P: k_nodes<P><<<nb, 256, 0, st>>>(pos, n, s, N, wrap, first, wts, err); break;
+        HERMES_ND(1) HERMES_ND(2) HERMES_ND(3) HERMES_ND(4) HERMES_ND(5) HERMES_ND(6) HERMES_ND(7) HERMES_ND(8)
+#undef HERMES_ND
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st) {
+    k_weight_sums<<<nblk, 256, 0, st>>>(w, n, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
+                            int nblk, cudaStream_t st) {
+    switch (p) {
+#define HERMES_SP(P) \
+    case P: k_selfpair<P><<<nblk, 256, 0, st>>>(pos, w, n, s, N, part); break;
+        HERMES_SP(1) HERMES_SP(2) HERMES_SP(3) HERMES_SP(4) HERMES_SP(5) HERMES_SP(6) HERMES_SP(7) HERMES_SP(8)
+#undef HERMES_SP
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    k_reduce_rows<<<rows, 256, 0, st>>>(part, cols, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3, float* stab_f, int N,
+                                double* scal, cudaStream_t st) {
+    k_finish_field<<<1, 256, 0, st>>>(sums, stab_d, p3, stab_f, N, scal);
+    return cudaGetLastError();
+}
+
+}  // namespace hermes

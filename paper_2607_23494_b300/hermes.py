@@ -1,0 +1,216 @@
+"""Python binding of libhermes.so (ctypes; argument marshalling only).
+
+Every step of the estimator runs in the CUDA library; this module converts
+numpy arrays / torch tensors to pointers and status codes to exceptions.  If the
+shared library is missing the import fails loudly -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhermes.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_RANGE = -2
+ERR_NOMEM = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_STATE = -6
+DEVICE_PTR = 1
+WRAP = 2
+
+_NAMES = {ERR_ARG: "HERMES_ERR_ARG", ERR_RANGE: "HERMES_ERR_RANGE", ERR_NOMEM: "HERMES_ERR_NOMEM",
+          ERR_CUDA: "HERMES_ERR_CUDA", ERR_TIMEOUT: "HERMES_ERR_TIMEOUT", ERR_STATE: "HERMES_ERR_STATE"}
+
+
+class HermesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhermes.so not built at {LIB_PATH}; run `python paper_2607_23494_b300/build.py`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp, fp, u32 = C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_double), C.c_void_p, C.c_uint
+    sig = {
+        "hermes_create": (i32, [C.c_double, i32, i32, i32, C.POINTER(vp)]),
+        "hermes_destroy": (i32, [vp]),
+        "hermes_set_stream": (i32, [vp, vp]),
+        "hermes_assign": (i32, [vp, fp, fp, i64, u32]),
+        "hermes_window_shells": (i32, [vp, dp, i32, i32]),
+        "hermes_xi": (i32, [vp, dp]),
+        "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
+        "hermes_zeta_multipoles": (i32, [vp, dp]),
+        "hermes_last_error": (C.c_char_p, [vp]),
+        "hermes_debug_get_delta": (i32, [vp, fp]),
+        "hermes_debug_get_spectrum": (i32, [vp, fp]),
+        "hermes_debug_set_delta": (i32, [vp, fp]),
+        "hermes_debug_get_sums": (i32, [vp, dp, dp]),
+        "hermes_debug_nodes": (i32, [vp, fp, i64, u32, fp, fp]),
+        "hermes_shell_table_host": (i32, [C.c_double, i32, dp, i32, i32, dp]),
+        "hermes_shell_table_len": (i64, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def shell_table_host(L: float, N: int, r_edges: Sequence[float], l_max: int) -> np.ndarray:
+    """Host-built float64 table <j_l>_b(k_q), shape [n_bins, l_max+1, Q]."""
+    e = np.ascontiguousarray(r_edges, dtype=np.float64)
+    Q = int(_lib.hermes_shell_table_len(N))
+    if Q < 0:
+        raise HermesError(ERR_ARG, f"bad N={N}")
+    out = np.empty((len(e) - 1, l_max + 1, Q), dtype=np.float64)
+    rc = _lib.hermes_shell_table_host(float(L), int(N), _dptr(e), len(e), int(l_max), _dptr(out))
+    if rc != OK:
+        raise HermesError(rc, "hermes_shell_table_host")
+    return out
+
+
+class Context:
+    """One resident field on one GPU: hermes_create ... hermes_destroy."""
+
+    def __init__(self, L: float, N: int, p: int = 4):
+        j = int(N).bit_length() - 1
+        h = C.c_void_p()
+        rc = _lib.hermes_create(float(L), int(N), int(p), j, C.byref(h))
+        if rc != OK:
+            raise HermesError(rc, f"hermes_create(L={L}, N={N}, p={p})")
+        self._h = h
+        self.L, self.N, self.p = float(L), int(N), int(p)
+        self.n_bins = 0
+        self.l_max = -1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hermes_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            msg = _lib.hermes_last_error(self._h)
+            raise HermesError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_stream(self, stream) -> None:
+        """stream: a torch.cuda.Stream, an integer handle, or None for the context's own stream."""
+        handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._check(_lib.hermes_set_stream(self._h, handle), "hermes_set_stream")
+
+    def assign(self, pos, w=None, wrap: bool = False) -> None:
+        """pos: (n,3) float32 numpy array or CUDA tensor; w: (n,) float32 or None."""
+        flags = WRAP if wrap else 0
+        if hasattr(pos, "data_ptr"):  # torch tensor
+            import torch
+            assert pos.dtype == torch.float32 and pos.is_contiguous() and pos.dim() == 2 and pos.shape[1] == 3
+            n = pos.shape[0]
+            wp = None
+            if w is not None:
+                assert w.dtype == torch.float32 and w.is_contiguous() and w.shape[0] == n
+                wp = w.data_ptr() if w.is_cuda else w.data_ptr()
+            if pos.is_cuda:
+                flags |= DEVICE_PTR
+                if w is not None and not w.is_cuda:
+                    raise ValueError("pos and w must live on the same kind of memory")
+            rc = _lib.hermes_assign(self._h, pos.data_ptr(), wp, n, flags)
+        else:
+            pos = np.ascontiguousarray(pos, dtype=np.float32)
+            if pos.ndim != 2 or pos.shape[1] != 3:
+                raise ValueError("pos must have shape (n, 3)")
+            n = pos.shape[0]
+            wp = None
+            if w is not None:
+                w = np.ascontiguousarray(w, dtype=np.float32)
+                if w.shape != (n,):
+                    raise ValueError("w must have shape (n,)")
+                wp = w.ctypes.data
+            rc = _lib.hermes_assign(self._h, pos.ctypes.data if n else None, wp, n, flags)
+        self._check(rc, "hermes_assign")
+
+    def window_shells(self, r_edges: Sequence[float], l_max: int = 0) -> None:
+        e = np.ascontiguousarray(r_edges, dtype=np.float64)
+        self._check(_lib.hermes_window_shells(self._h, _dptr(e), len(e), int(l_max)), "hermes_window_shells")
+        self.n_bins = len(e) - 1
+        self.l_max = int(l_max)
+
+    def xi(self) -> np.ndarray:
+        out = np.empty(self.n_bins, dtype=np.float64)
+        self._check(_lib.hermes_xi(self._h, _dptr(out)), "hermes_xi")
+        return out
+
+    def xi_multipoles(self, ells: Sequence[int]) -> np.ndarray:
+        ea = np.ascontiguousarray(ells, dtype=np.int32)
+        out = np.empty((len(ea), self.n_bins), dtype=np.float64)
+        self._check(_lib.hermes_xi_multipoles(self._h, ea.ctypes.data_as(C.POINTER(C.c_int)), len(ea), _dptr(out)),
+                    "hermes_xi_multipoles")
+        return out
+
+    def zeta_multipoles(self) -> np.ndarray:
+        out = np.empty((self.l_max + 1, self.n_bins, self.n_bins), dtype=np.float64)
+        self._check(_lib.hermes_zeta_multipoles(self._h, _dptr(out)), "hermes_zeta_multipoles")
+        return out
+
+    # inspection hooks
+    def get_delta(self) -> np.ndarray:
+        out = np.empty((self.N,) * 3, dtype=np.float32)
+        self._check(_lib.hermes_debug_get_delta(self._h, out.ctypes.data), "hermes_debug_get_delta")
+        return out
+
+    def get_spectrum(self) -> np.ndarray:
+        out = np.empty((self.N, self.N, self.N // 2), dtype=np.complex64)
+        self._check(_lib.hermes_debug_get_spectrum(self._h, out.ctypes.data), "hermes_debug_get_spectrum")
+        return out
+
+    def set_delta(self, delta: np.ndarray) -> None:
+        d = np.ascontiguousarray(delta, dtype=np.float32)
+        assert d.shape == (self.N,) * 3
+        self._check(_lib.hermes_debug_set_delta(self._h, d.ctypes.data), "hermes_debug_set_delta")
+
+    def nodes(self, pos, wrap: bool = False):
+        """Device node rule: (first[n,3] int32, weights[n,3,p] float32)."""
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+        n = pos.shape[0]
+        first = np.empty((n, 3), dtype=np.int32)
+        wts = np.empty((n, 3, self.p), dtype=np.float32)
+        self._check(_lib.hermes_debug_nodes(self._h, pos.ctypes.data, n, WRAP if wrap else 0,
+                                            first.ctypes.data, wts.ctypes.data), "hermes_debug_nodes")
+        return first, wts
+
+    def get_sums(self):
+        s = np.empty(2, dtype=np.float64)
+        t = np.empty(self.p ** 3, dtype=np.float64)
+        self._check(_lib.hermes_debug_get_sums(self._h, _dptr(s), _dptr(t)), "hermes_debug_get_sums")
+        return s, t.reshape(self.p, self.p, self.p)

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (the estimator's stated bar): indices and bin bookkeeping exact;
+xi, xi_l and zeta_l within 1e-4 relative or 1e-6 absolute of the oracle.
+Intermediate fields (delta, delta^) are compared at the float32 level.
+"""
+import numpy as np
+import pytest
+
+from oracle import hermes_oracle as O
+from synthetic import catalogues as S
+
+pytestmark = pytest.mark.gpu
+
+REL, ABS = 1e-4, 1e-6
+
+
+def _hermes():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_23494_b300 import hermes as H
+    return H
+
+
+def _close(got, ref, rel=REL, ab=ABS):
+    got, ref = np.asarray(got), np.asarray(ref)
+    err = np.abs(got - ref)
+    bad = err > np.maximum(rel * np.abs(ref), ab)
+    assert not bad.any(), (f"{bad.sum()} of {bad.size} outside tolerance; worst abs err {err.max():.3e}; "
+                           f"got {got[bad][:5]} ref {ref[bad][:5]}")
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 8])
+def test_scatter_and_delta_match_oracle(p):
+    H = _hermes()
+    N, L = 32, 100.0
+    pos = S.mixed_poisson_sp(5000, L, seed=30 + p)
+    w = S.lognormal_masses(5000, seed=3)
+    with H.Context(L, N, p) as ctx:
+        ctx.assign(pos, w)
+        d = ctx.get_delta().astype(np.float64)
+        sums, tab = ctx.get_sums()
+    eps, sw, sw2 = O.assign(pos, w, N, L, p)
+    dref = O.delta_from_eps(eps, sw)
+    assert np.max(np.abs(d - dref) / (1.0 + np.abs(dref))) < 2e-5
+    assert sums[0] == pytest.approx(sw, rel=1e-12)
+    assert sums[1] == pytest.approx(sw2, rel=1e-12)
+    np.testing.assert_allclose(tab, O.self_pair_table(pos, w, N, L, p), rtol=2e-5)
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_node_bookkeeping_is_bit_exact(p):
+    # first supporting node of every point and axis: identical integers on both sides,
+    # including coordinates on knots, at 0, at the largest float32 below L and u = N
+    H = _hermes()
+    N, L = 64, 1000.0
+    rng = np.random.default_rng(40 + p)
+    pos = rng.uniform(0, L, size=(20000, 3)).astype(np.float32)
+    edge = np.array([0.0, np.nextafter(np.float32(L), np.float32(0)), L / N * 7, L / N * 7.5,
+                     np.float32(L / 2)], dtype=np.float32)
+    pos[:5] = edge[:, None]
+    with H.Context(L, N, p) as ctx:
+        first, wts = ctx.nodes(pos)
+        wfirst, _ = ctx.nodes((pos + np.float32(3 * L)).astype(np.float32), wrap=True)
+    ref_first, ref_w = O.node_weights(pos, N, L, p)
+    np.testing.assert_array_equal(first, ref_first)
+    np.testing.assert_allclose(wts, ref_w, atol=2e-7)
+    assert np.all(wfirst >= 0)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128])
+def test_forward_spectrum_matches_oracle(N):
+    H = _hermes()
+    L = 200.0
+    pos = S.mixed_poisson_sp(8000, L, seed=N)
+    with H.Context(L, N, 4) as ctx:
+        ctx.assign(pos)
+        spec = ctx.get_spectrum().astype(np.complex128)
+        d = ctx.get_delta().astype(np.float64)
+    ref = np.fft.rfftn(d)[:, :, : N // 2]
+    ref[0, 0, 0] = 0
+    rel = np.linalg.norm(spec - ref) / np.linalg.norm(ref)
+    assert rel < 2e-6, rel
+    assert np.max(np.abs(spec - ref)) < 1e-5 * np.max(np.abs(ref))
+
+
+def test_planted_single_mode_exact_closed_form():
+    # delta = cos(2 pi n0.l/N) gives xi_b = K_b(n0)/2 and xi_l the same with K_{b,l}
+    H = _hermes()
+    N, L, p = 32, 160.0, 4
+    n0 = (3, -2, 5)
+    l = np.arange(N)
+    d = np.cos(2 * np.pi * (n0[0] * l[:, None, None] + n0[1] * l[None, :, None] + n0[2] * l[None, None, :]) / N)
+    edges = [8.0, 14.0, 20.0, 30.0]
+    with H.Context(L, N, p) as ctx:
+        ctx.set_delta(d)
+        ctx.window_shells(edges, l_max=4)
+        got = ctx.xi_multipoles([0, 2, 4])
+    for a, ell in enumerate((0, 2, 4)):
+        for b in range(3):
+            K = O.window_xi(N, L, p, edges[b], edges[b + 1], ell)
+            ref = 0.5 * K[n0[0] % N, n0[1] % N, n0[2] % N]
+            assert abs(got[a, b] - ref) <= max(2e-5 * abs(ref), 1e-7), (ell, b, got[a, b], ref)
+
+
+def test_xi_config_two_point_plain():
+    # 20,000 points: half uniform Poisson, half Soneira-Peebles; L = 250, 64^3, p = 4,
+    # 20 linear shells in [5, 105); unit weights
+    H = _hermes()
+    L, N, p = 250.0, 64, 4
+    pos = S.mixed_poisson_sp(20000, L, seed=2024)
+    edges = np.linspace(5.0, 105.0, 21)
+    with H.Context(L, N, p) as ctx:
+        ctx.assign(pos)
+        ctx.window_shells(edges, l_max=0)
+        got = ctx.xi()
+    ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0,))["xi"][0]
+    _close(got, ref)
+
+
+def test_xi_multipoles_and_marked_ragged_batches():
+    # 3 multipoles x 13 bins = 39 windows: batches of 16 leave a ragged tail of 7
+    H = _hermes()
+    L, N, p = 300.0, 64, 4
+    pos = S.lognormal_catalogue(30000, L, seed=77, n_grid=64)
+    mass = S.lognormal_masses(pos.shape[0], seed=78)
+    edges = np.linspace(4.0, 82.0, 14)
+    ells = (0, 2, 4)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=4)
+        ctx.assign(pos)
+        got = ctx.xi_multipoles(ells)
+        ctx.assign(pos, mass)
+        got_m = ctx.xi_multipoles(ells)
+    ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=ells)["xi"]
+    ref_m = O.xi_multipoles(pos, mass, N, L, p, edges, ells=ells)["xi"]
+    _close(got, ref)
+    _close(got_m, ref_m)
+
+
+def test_xi_other_orders_and_sizes():
+    H = _hermes()
+    for (N, p, L) in [(16, 2, 50.0), (32, 3, 120.0), (128, 6, 400.0)]:
+        pos = S.mixed_poisson_sp(6000, L, seed=N + p)
+        edges = np.linspace(L / 40, L / 4, 6)
+        with H.Context(L, N, p) as ctx:
+            ctx.assign(pos)
+            ctx.window_shells(edges, l_max=2)
+            got = ctx.xi_multipoles([0, 2])
+        ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2))["xi"]
+        _close(got, ref)
+
+
+def test_single_point_and_wrap_and_device_pointers():
+    import torch
+    H = _hermes()
+    L, N, p = 100.0, 32, 4
+    edges = [2.0, 6.0, 12.0]
+    one = np.array([[10.0, 20.0, 30.0]], dtype=np.float32)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=0)
+        ctx.assign(one)
+        g1 = ctx.xi()
+        r = O.xi_multipoles(one, None, N, L, p, edges)
+        # one point: xi = -1 exactly, computed as raw - SN with SN ~ N^3 kappa ~ 600; the
+        # float32 fields leave an absolute error ~2e-7 SN (the error model of sparse catalogues)
+        assert np.all(np.abs(g1 - r["xi"][0]) <= np.maximum(1e-6, 4e-7 * r["sn"][0]))
+        # wrapped coordinates give the same field as the wrapped catalogue
+        pos = S.poisson_uniform(3000, L, seed=9)
+        shifted = (pos + np.float32(L)).astype(np.float32)
+        with pytest.raises(H.HermesError) as ei:
+            ctx.assign(shifted)
+        assert ei.value.code == H.ERR_RANGE
+        with pytest.raises(H.HermesError) as ei:
+            ctx.xi()
+        assert ei.value.code == H.ERR_STATE
+        ctx.assign(pos)
+        base = ctx.xi()
+        ctx.assign(shifted, wrap=True)
+        wrapped = ctx.xi()
+        ref = O.xi_multipoles(shifted, None, N, L, p, edges)["xi"][0]
+        _close(wrapped, ref)
+        _close(base, O.xi_multipoles(pos, None, N, L, p, edges)["xi"][0])
+        # torch device tensors through HERMES_DEVICE_PTR, on a torch stream
+        tpos = torch.from_numpy(pos).cuda()
+        tw = torch.ones(pos.shape[0], dtype=torch.float32, device="cuda")
+        s = torch.cuda.Stream()
+        ctx.set_stream(s)
+        ctx.assign(tpos, tw)
+        dev = ctx.xi()
+        ctx.set_stream(None)
+        np.testing.assert_allclose(dev, base, rtol=1e-6, atol=1e-9)
+
+
+def test_argument_errors():
+    H = _hermes()
+    with H.Context(100.0, 32, 4) as ctx:
+        with pytest.raises(H.HermesError) as ei:
+            ctx.xi()
+        assert ei.value.code == H.ERR_STATE
+        with pytest.raises(H.HermesError) as ei:
+            ctx.window_shells([1.0, 60.0], 0)          # beyond L/2
+        assert ei.value.code == H.ERR_RANGE
+        with pytest.raises(H.HermesError) as ei:
+            ctx.assign(np.zeros((0, 3), np.float32))   # empty catalogue
+        assert ei.value.code == H.ERR_ARG
+        ctx.window_shells(np.linspace(1, 40, 18), 2)
+        ctx.assign(S.poisson_uniform(100, 100.0, 1))
+        with pytest.raises(H.HermesError) as ei:
+            ctx.xi_multipoles([1])
+        assert ei.value.code == H.ERR_ARG
+        with pytest.raises(H.HermesError) as ei:
+            ctx.zeta_multipoles()                      # 17 bins > 16
+        assert ei.value.code == H.ERR_ARG
+        bad = S.poisson_uniform(10, 100.0, 2)
+        bad[3, 1] = np.nan
+        with pytest.raises(H.HermesError) as ei:
+            ctx.assign(bad)
+        assert ei.value.code == H.ERR_RANGE
+
+
+@pytest.mark.parametrize("N,nb,l_max", [(16, 3, 3), (32, 4, 4), (32, 16, 2)])
+def test_zeta_multipoles_match_oracle(N, nb, l_max):
+    H = _hermes()
+    L, p = 4.0 * N, 4
+    pos = S.mixed_poisson_sp(3000, L, seed=N + nb)
+    edges = np.linspace(L / 32, L / 3, nb + 1)
+    with H.Context(L, N, p) as ctx:
+        ctx.assign(pos)
+        ctx.window_shells(edges, l_max=l_max)
+        got = ctx.zeta_multipoles()
+        d = ctx.get_delta().astype(np.float64)
+    eps, sw, _ = O.assign(pos, None, N, L, p)
+    ref, imag = O.zeta_multipoles(O.delta_from_eps(eps, sw), N, L, p, edges, l_max)
+    _close(got, ref)
+    for ell in range(l_max + 1):
+        np.testing.assert_array_equal(got[ell], got[ell].T)

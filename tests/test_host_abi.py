@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry point,
+validates arguments before touching a GPU, and its float64 host window tables
+agree with the oracle's independent quadrature."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import hermes_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hermes.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hermes_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2607_23494_b300 import hermes as H
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(H.lib(), n), n
+
+
+def test_create_rejects_bad_arguments_without_a_gpu():
+    from paper_2607_23494_b300 import hermes as H
+    lib = H.lib()
+    h = ctypes.c_void_p()
+    assert lib.hermes_create(100.0, 48, 4, 5, ctypes.byref(h)) == H.ERR_ARG   # not a power of two
+    assert lib.hermes_create(100.0, 64, 4, 5, ctypes.byref(h)) == H.ERR_ARG   # N != 2^j
+    assert lib.hermes_create(-1.0, 64, 4, 6, ctypes.byref(h)) == H.ERR_ARG
+    assert lib.hermes_create(100.0, 64, 9, 6, ctypes.byref(h)) == H.ERR_ARG   # p > 8
+    assert lib.hermes_create(100.0, 16, 9, 4, ctypes.byref(h)) == H.ERR_ARG
+    assert lib.hermes_create(100.0, 64, 4, 6, None) == H.ERR_ARG
+    assert lib.hermes_destroy(None) == H.OK
+    assert lib.hermes_shell_table_len(48) == -1
+
+
+def test_no_gpu_means_an_error_status_not_a_crash():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2607_23494_b300 import hermes as H
+    h = ctypes.c_void_p()
+    assert H.lib().hermes_create(100.0, 64, 4, 6, ctypes.byref(h)) == H.ERR_CUDA
+    assert not h.value
+
+
+@pytest.mark.parametrize("N,L", [(64, 250.0), (32, 1000.0)])
+def test_host_shell_tables_match_oracle_quadrature(N, L):
+    from paper_2607_23494_b300 import shell_table_host
+    edges = [0.0, 2.0, 5.0, 7.5, 30.0, 100.0, L / 2]
+    l_max = 6
+    tab = shell_table_host(L, N, edges, l_max)
+    Q = tab.shape[-1]
+    assert Q == 3 * (N // 2 - 1) ** 2 + 1
+    q = np.arange(Q)
+    k = 2 * np.pi * np.sqrt(q) / L
+    for b in range(len(edges) - 1):
+        lo, hi = edges[b], edges[b + 1]
+        ref0 = O.shell_window_l0(k, lo, hi)
+        np.testing.assert_allclose(tab[b, 0], ref0, rtol=1e-10, atol=1e-13)
+        for ell in range(1, l_max + 1):
+            ref = O.shell_avg_jl(ell, k, lo, hi)
+            np.testing.assert_allclose(tab[b, ell], ref, rtol=1e-8, atol=1e-11,
+                                       err_msg=f"bin {b} l {ell}")
+
+
+def test_host_tables_reject_bad_edges():
+    from paper_2607_23494_b300 import hermes as H
+    with pytest.raises(H.HermesError):
+        H.shell_table_host(100.0, 32, [5.0, 5.0, 10.0], 0)
+    with pytest.raises(H.HermesError):
+        H.shell_table_host(100.0, 32, [-1.0, 5.0], 0)
