@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the field-window estimator on B300.
+
+One step = one full 2PCF measurement of a 512^3 field through the C ABI:
+  1e7 points Poisson-sampled from a lognormal field (P(k) ~ k^-1.5 exp(-(k/0.5)^2),
+  sigma_ln = 1) in a periodic box L = 1000 Mpc/h, cubic B-spline (p = 4);
+  40 linear shells in [2, 202) Mpc/h; multipoles l = 0, 2, 4 along z;
+  done once with unit weights and once with log-normal masses (marked field):
+  2 scatters + 2 forward 3-D FFTs + 240 windows (window multiply, inverse 3-D FFT,
+  cell contraction, self-pair subtraction).
+metric = grid cells x windows per second = 512^3 * 240 / step time.
+
+Also reported: the 3PCF multipoles zeta_l (2e6 points, L = 500, 512^3, 16 shells in
+[10, 170), l_max = 6) as an extra measurement, the dominant kernel's achieved HBM
+bandwidth from live CUDA events, clocks sampled during the timed region, an
+end-to-end number through host buffers, and the FP64 oracle timed on the host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hermes|reference] [--no-zeta]
+Under torchrun every rank runs its own replica (independent catalogue); the
+value is the aggregate over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-cell x window evals/s at 512^3"
+UNIT = "cell-window/s"
+
+# workload (the isotropic + anisotropic 2PCF configuration, with its marked variant)
+L2, N2, P2, NPTS2 = 1000.0, 512, 4, 10_000_000
+EDGES2 = np.linspace(2.0, 202.0, 41)
+ELLS2 = (0, 2, 4)
+# 3PCF multipoles configuration
+L3, N3, NPTS3 = 500.0, 512, 2_000_000
+EDGES3 = np.linspace(10.0, 170.0, 17)
+LMAX3 = 6
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gen_catalogue(seed: int):
+    from synthetic import catalogues as S
+    pos = S.lognormal_catalogue(NPTS2, L2, seed=seed, n_grid=512)
+    mass = S.lognormal_masses(pos.shape[0], seed=seed + 1)
+    return pos, mass
+
+
+def gen_catalogue3(seed: int):
+    from synthetic import catalogues as S
+    return S.lognormal_catalogue(NPTS3, L3, seed=seed, n_grid=512)
+
+
+def alg_bytes(name: str, launches: int, n_windows: int, n_batches: int, n_pts_bytes: float) -> float | None:
+    """Algorithmic HBM bytes of one kernel class over the timed region (N = 512)."""
+    n3 = float(N2) ** 3
+    if name == "inv_y":
+        return 8.0 * n3 * n_windows
+    if name == "inv_x_window":
+        return 4.0 * n3 * (n_windows + n_batches)
+    if name == "inv_z_c2r_contract":
+        return 4.0 * n3 * (n_windows + n_batches)
+    if name == "fwd_z_r2c":
+        return 12.0 * n3 * launches
+    if name in ("fwd_y", "fwd_x"):
+        return 8.0 * n3 * launches
+    if name == "scatter":
+        return n_pts_bytes + 4.0 * n3 * launches
+    return None
+
+
+def run_hermes(args, rank, world, local_rank):
+    import torch
+    from paper_2607_23494_b300 import Context
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    pos, mass = gen_catalogue(1234 + 17 * rank)
+    n = pos.shape[0]
+    pos_d = torch.from_numpy(pos).to(dev)
+    mass_d = torch.from_numpy(mass).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(L2, N2, P2)
+    ctx.set_stream(stream)
+    ctx.window_shells(EDGES2, l_max=4)
+    nb = len(EDGES2) - 1
+    windows_per_step = 2 * len(ELLS2) * nb
+    batches_per_step = 2 * -(-(len(ELLS2) * nb) // 16)
+
+    def step(p_, m_):
+        ctx.assign(p_)
+        a = ctx.xi_multipoles(ELLS2)
+        ctx.assign(p_, m_)
+        b = ctx.xi_multipoles(ELLS2)
+        return a, b
+
+    for _ in range(args.warmup):
+        step(pos_d, mass_d)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    ctx.trace(True)
+    launches0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res = step(pos_d, mass_d)
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    dev_ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    trace = ctx.trace_read()
+    ctx.trace(False)
+    clk = clocks.stop()
+    ms_t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_per_step = ms_max / args.steps
+    cells = float(N2) ** 3
+    value = world * cells * windows_per_step * args.steps / (ms_max / 1e3)
+
+    # end to end through host buffers (pinned), host->device copies inside the timed region
+    pos_h = torch.from_numpy(pos).pin_memory().numpy()
+    mass_h = torch.from_numpy(mass).pin_memory().numpy()
+    step(pos_h, mass_h)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pos_h, mass_h)
+    e1.record(stream)
+    stream.synchronize()
+    barrier()
+    e2e_t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+    e2e_value = world * cells * windows_per_step * args.steps / (e2e_ms / 1e3)
+    h2d = 12 * n + (12 * n + 4 * n)
+    d2h = 2 * 20 + 2 * 16 * (len(ELLS2) * nb)
+
+    # roofline of the dominant kernel (live events on the launching stream)
+    pk, pk_src = peaks()
+    total_k_ms = sum(v[0] for v in trace.values()) or 1.0
+    kern = {}
+    for name, (kms, cnt) in sorted(trace.items(), key=lambda kv: -kv[1][0]):
+        b = alg_bytes(name, cnt, windows_per_step * args.steps, batches_per_step * args.steps,
+                      (12 * n + 16 * n) * args.steps)
+        kern[name] = {"ms": round(kms, 3), "launches": cnt, "share": round(kms / total_k_ms, 4),
+                      "alg_GBps": round(b / (kms / 1e3) / 1e9, 1) if b else None}
+    dom = max(trace.items(), key=lambda kv: kv[1][0])[0]
+    dom_b = alg_bytes(dom, trace[dom][1], windows_per_step * args.steps, batches_per_step * args.steps,
+                      (12 * n + 16 * n) * args.steps)
+    achieved = dom_b / (trace[dom][0] / 1e3) / 1e9 if dom_b else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
+            "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
+            "traffic": None, "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured"
+            else "fallback 6.4 TB/s"}
+
+    zeta = None
+    if not args.no_zeta:
+        zeta = run_zeta(args, dev, stream, rank)
+
+    ctx.close()
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2PCF xi + xi_l (l=0,2,4) of a 1e7-point lognormal catalogue, unit weights and "
+                                   "log-normal mass marks, 512^3 grid, L=1000 Mpc/h, p=4, 40 shells [2,202)",
+                       "grid": N2, "L": L2, "p": P2, "n_points": n, "n_bins": nb, "ells": list(ELLS2),
+                       "windows_per_step": windows_per_step, "parallelism": f"replicas x{world}",
+                       "l2": "no flush needed: every pass streams >=512 MB (grid 512 MB, spectra 8 GB) > 126 MB L2"},
+            "clocks": clk,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "ms_per_step": round(e2e_ms / args.steps, 3),
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernels": kern,
+            "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
+        }
+        if zeta:
+            out["zeta"] = zeta
+    return out, pos
+
+
+def run_zeta(args, dev, stream, rank):
+    import torch
+    from paper_2607_23494_b300 import Context
+    pos = gen_catalogue3(4321 + 17 * rank)
+    pos_d = torch.from_numpy(pos).to(dev)
+    ctx = Context(L3, N3, 4)
+    ctx.set_stream(stream)
+    ctx.window_shells(EDGES3, l_max=LMAX3)
+
+    def step():
+        ctx.assign(pos_d)
+        return ctx.zeta_multipoles()
+
+    step()
+    torch.cuda.synchronize()
+    ctx.trace(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    zsteps = max(1, min(2, args.steps))
+    e0.record(stream)
+    for _ in range(zsteps):
+        z = step()
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / zsteps
+    tr = ctx.trace_read()
+    ctx.close()
+    nb = len(EDGES3) - 1
+    nfields = nb * (LMAX3 + 1) * (LMAX3 + 2) // 2
+    n3 = float(N3) ** 3
+    tot = sum(v[0] for v in tr.values()) or 1.0
+    kern = {k: {"ms": round(v[0] / zsteps, 3), "launches": v[1] // zsteps, "share": round(v[0] / tot, 4)}
+            for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0])}
+    # algorithmic bytes of the y pass: read + write of every complex field (16 B / cell)
+    y_ms = tr.get("zeta_y", (0.0, 0))[0] / zsteps
+    return {"workload": "zeta_l, 2e6-point lognormal catalogue, L=500, 512^3, 16 shells [10,170), l_max=6",
+            "ms_per_step": round(ms, 2), "complex_fields": nfields,
+            "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
+            "zeta_y_GBps": round(16.0 * n3 * nfields / (y_ms / 1e3) / 1e9, 1) if y_ms else None,
+            "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])]}
+
+
+def oracle_sample(pos):
+    """FP64 oracle on a bounded sample: 512^3 grid, 500k points, one l=0 window (half-spectrum route)."""
+    from oracle import hermes_oracle as O
+    sub = pos[:500_000]
+    t = time.perf_counter()
+    O.xi_multipoles(sub, None, N2, L2, P2, [2.0, 7.0], ells=(0,), route="half")
+    dt = time.perf_counter() - t
+    return float(N2) ** 3 / dt, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, one window per step on a resident field."""
+    from oracle import hermes_oracle as O
+    pos, _ = gen_catalogue(1234)
+    sub = pos[:1_000_000]
+    t0 = time.perf_counter()
+    eps, sw, _ = O.assign(sub, None, N2, L2, P2)
+    delta = O.delta_from_eps(eps, sw)
+    del eps
+    dh = O.forward_half(delta)
+    S = O.self_pair_table(sub, None, N2, L2, P2)
+    setup = time.perf_counter() - t0
+
+    def one(b):
+        K = O.window_xi(N2, L2, P2, EDGES2[b], EDGES2[b + 1], 0, half=True)
+        return O.xi_parseval_half(dh, K, N2) - O.shot_noise_half(S, K, N2, sw)
+
+    for i in range(args.warmup):
+        one(i % 40)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        one(i % 40)
+    dt = (time.perf_counter() - t) / args.steps
+    value = float(N2) ** 3 / dt
+    sample = (f"one l=0 shell window per step (window kernel, Parseval sum, self-pair term) on a resident "
+              f"512^3 field of the first 1e6 of the 1e7 points; field setup {setup:.1f} s outside the steps; "
+              f"numpy single thread")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "2PCF xi + xi_l (l=0,2,4) of a 1e7-point lognormal catalogue, unit weights and "
+                                   "log-normal mass marks, 512^3 grid, L=1000 Mpc/h, p=4, 40 shells [2,202)",
+                       "grid": N2, "L": L2, "p": P2},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hermes", choices=["hermes", "reference"])
+    ap.add_argument("--no-zeta", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)))
+        return 0
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out, pos = run_hermes(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            v, dt = oracle_sample(pos)
+            out["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"512^3 grid, first 500k of the 1e7 points, one l=0 shell window "
+                                             f"(scatter, FFT, window, Parseval sum, self-pair term): {dt:.1f} s, "
+                                             f"numpy single thread; per-catalogue work not amortised"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

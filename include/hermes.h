@@ -144,6 +144,29 @@ int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
 /* Text of the last error of this context (never NULL; empty after success). */
 const char *hermes_last_error(const hermes_ctx *ctx);
 
+/* ---- tracing (per-kernel device time; not in the paper, which reports stage times only) ---- */
+
+/*
+ * Enable (on != 0) or disable per-launch timing.  While enabled, every kernel
+ * launch of the context is bracketed by CUDA events recorded on the launching
+ * stream.  Enabling or disabling clears the accumulated totals.
+ */
+int hermes_trace_enable(hermes_ctx *ctx, int on);
+
+/*
+ * Per kernel class k (0 <= k < n, see hermes_kernel_name): accumulated device
+ * milliseconds and launch counts since the last enable/read; then clears them.
+ * Synchronises the context's stream.  Returns the number of kernel classes (>= 0)
+ * or an error status.  ms / launches may be NULL.
+ */
+int hermes_trace_read(hermes_ctx *ctx, double *ms, int64_t *launches, int n);
+
+/* Name of kernel class k ("" when out of range). */
+const char *hermes_kernel_name(int k);
+
+/* Total kernels this context has launched since it was created (-1 for NULL). */
+int64_t hermes_launch_count(const hermes_ctx *ctx);
+
 /* ---- inspection hooks (tests and tools; not needed for measurements) ---- */
 
 /* Copy the resident real field delta (N^3 float32, z fastest) to the host. */

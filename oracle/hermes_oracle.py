@@ -228,13 +228,16 @@ def _mode_grid(N, L, half=False):
 
 
 def _radial_table(ell, q, L, r_lo, r_hi):
-    """<j_l>_bin(k) evaluated once per distinct |n|^2 (k = 2 pi |n| / L), scattered back."""
+    """<j_l>_bin(k) at every mode, k = 2 pi |n| / L.
+
+    l = 0 uses the closed form of Eq. (Wshell_k) mode by mode; l > 0 evaluates
+    the quadrature once per distinct |n|^2 and scatters it back.
+    """
+    if ell == 0:
+        return shell_window_l0((2.0 * np.pi / L) * np.sqrt(q.astype(np.float64)), r_lo, r_hi)
     uq, inv = np.unique(q.ravel(), return_inverse=True)
     ku = (2.0 * np.pi / L) * np.sqrt(uq.astype(np.float64))
-    if ell == 0:
-        vals = shell_window_l0(ku, r_lo, r_hi)
-    else:
-        vals = shell_avg_jl(ell, ku, r_lo, r_hi)
+    vals = shell_avg_jl(ell, ku, r_lo, r_hi)
     return vals[inv].reshape(q.shape)
 
 
@@ -291,6 +294,13 @@ def window_zeta(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int, m:
 def forward(delta):
     """delta^ = sum_l delta_l e^{-2 pi i n.l/N} (numpy FFT), with delta^(0) := 0."""
     dh = np.fft.fftn(delta)
+    dh[0, 0, 0] = 0.0
+    return dh
+
+
+def forward_half(delta):
+    """delta^ on the rfft half spectrum (n_z in [0, N/2]), with delta^(0) := 0."""
+    dh = np.fft.rfftn(delta)
     dh[0, 0, 0] = 0.0
     return dh
 
@@ -354,21 +364,43 @@ def shot_noise(S, K, N, sum_w):
     return tot / (N ** 3 * eps_bar * eps_bar)
 
 
+def shot_noise_half(S, K_half, N, sum_w):
+    """shot_noise() with kappa from the half spectrum of the real, even kernel (irfftn)."""
+    p = S.shape[0]
+    kap = np.fft.irfftn(K_half, s=(N, N, N), axes=(0, 1, 2))
+    tot = 0.0
+    for dx in range(-(p - 1), p):
+        for dy in range(-(p - 1), p):
+            for dz in range(-(p - 1), p):
+                tot += S[abs(dx), abs(dy), abs(dz)] * kap[dx % N, dy % N, dz % N]
+    eps_bar = sum_w / N ** 3
+    return tot / (N ** 3 * eps_bar * eps_bar)
+
+
 def xi_multipoles(pos, w, N, L, p, r_edges, ells=(0,), route="parseval"):
     """xi_l(r_b) for every bin b and even l: Landy-Szalay Delta DD / RR with uniform R.
+
+    route: "parseval" (full spectrum), "half" (rfft half spectrum, same sums),
+    or "cell" (inverse transform and cell-by-cell contraction).
 
     Returns dict(xi=[n_ell, n_bins], sn=[n_ell, n_bins], raw=[n_ell, n_bins]).
     raw is (1/N^3) sum delta delta~ before the self-pair subtraction.
     """
     eps, sw, _ = assign(pos, w, N, L, p)
     delta = delta_from_eps(eps, sw)
-    dh = forward(delta)
+    del eps
+    dh = forward_half(delta) if route == "half" else forward(delta)
     S = self_pair_table(pos, w, N, L, p)
     nb = len(r_edges) - 1
     raw = np.zeros((len(ells), nb))
     sn = np.zeros((len(ells), nb))
     for a, ell in enumerate(ells):
         for b in range(nb):
+            if route == "half":
+                K = window_xi(N, L, p, r_edges[b], r_edges[b + 1], ell, half=True)
+                raw[a, b] = xi_parseval_half(dh, K, N)
+                sn[a, b] = shot_noise_half(S, K, N, sw)
+                continue
             K = window_xi(N, L, p, r_edges[b], r_edges[b + 1], ell)
             if route == "parseval":
                 raw[a, b] = xi_parseval(dh, K)

@@ -276,24 +276,31 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_contract(const f
 
 template <int N>
 static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, int convert, const Tables& tb,
-                                cudaStream_t st) {
+                                cudaStream_t st, const Tracer& tr) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_fwd_z_r2c<N>, C::SMEM_Z)) != cudaSuccess) return e;
     if ((e = allow_smem(k_strided<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    tr(K_FWD_Z_R2C, 0, st);
     k_fwd_z_r2c<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(grid, spec, scal, convert, tb.tw);
+    tr(K_FWD_Z_R2C, 1, st);
     const long long H = N / 2;
     dim3 g(H / C::W, N, 1);
     // along y: pos stride H, blockIdx.y = x
+    tr(K_FWD_Y, 0, st);
     k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, H, (long long)N * H, 0, 0, tb.tw);
+    tr(K_FWD_Y, 1, st);
     // along x: pos stride N*H, blockIdx.y = y, delta^(0) := 0
+    tr(K_FWD_X, 0, st);
     k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, 0, 1, tb.tw);
+    tr(K_FWD_X, 1, st);
     return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                                const Tables& tb, int P, double* sn_part, double* dd_part, cudaStream_t st) {
+                                const Tables& tb, int P, double* sn_part, double* dd_part, cudaStream_t st,
+                                const Tracer& tr) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_inv_x_window<N>, C::SMEM_STRIDED)) != cudaSuccess) return e;
@@ -301,10 +308,16 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z)) != cudaSuccess) return e;
     const long long H = N / 2;
     dim3 g1(H / C::W, N, 1);
+    tr(K_INV_X_WINDOW, 0, st);
     k_inv_x_window<N><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb, P, sn_part);
+    tr(K_INV_X_WINDOW, 1, st);
     dim3 g2(H / C::W, N, wb.S);
+    tr(K_INV_Y, 0, st);
     k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
+    tr(K_INV_Y, 1, st);
+    tr(K_INV_Z_C2R_CONTRACT, 0, st);
     k_inv_z_c2r_contract<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(work, wb.S, delta, tb.tw, dd_part);
+    tr(K_INV_Z_C2R_CONTRACT, 1, st);
     return cudaGetLastError();
 }
 
@@ -320,22 +333,23 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
         default: return cudaErrorInvalidValue; \
     }
 
-cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb, cudaStream_t st) {
-#define F(n) forward_impl<n>(grid, spec, scal, 1, tb, st)
+cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb, cudaStream_t st,
+                           const Tracer& tr) {
+#define F(n) forward_impl<n>(grid, spec, scal, 1, tb, st, tr)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }
 
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
-                                 cudaStream_t st) {
-#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st)
+                                 cudaStream_t st, const Tracer& tr) {
+#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st, tr)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }
 
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                              const Tables& tb, double* sn_part, double* dd_part, cudaStream_t st) {
-#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, st)
+                              const Tables& tb, double* sn_part, double* dd_part, cudaStream_t st, const Tracer& tr) {
+#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, st, tr)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }

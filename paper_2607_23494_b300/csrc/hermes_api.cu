@@ -56,6 +56,19 @@ struct hermes_ctx {
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
     std::string msg;
+    // tracing: launch counter always on; event pairs per launch when enabled
+    int64_t launches = 0;
+    bool trace_on = false;
+    struct Pending {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open_ev = nullptr;
+    double trace_ms[K_COUNT] = {0};
+    int64_t trace_n[K_COUNT] = {0};
+    Tracer tracer{nullptr, nullptr};
 };
 
 namespace {
@@ -262,6 +275,56 @@ Tables tables_of(const hermes_ctx* c) {
     return t;
 }
 
+cudaEvent_t pool_event(hermes_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void trace_mark(void* vc, int id, int phase, cudaStream_t st) {
+    hermes_ctx* c = (hermes_ctx*)vc;
+    if (phase == 0) ++c->launches;
+    if (!c->trace_on) return;
+    if (phase == 0) {
+        c->open_ev = pool_event(c);
+        if (c->open_ev) cudaEventRecord(c->open_ev, st);
+    } else if (c->open_ev) {
+        cudaEvent_t b = pool_event(c);
+        if (b) {
+            cudaEventRecord(b, st);
+            c->pending.push_back({id, c->open_ev, b});
+        } else {
+            c->pool.push_back(c->open_ev);
+        }
+        c->open_ev = nullptr;
+    }
+}
+
+// Fold finished event pairs into the per-kernel totals (synchronises the stream).
+void trace_collect(hermes_ctx* c) {
+    if (c->pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            c->trace_ms[p.id] += ms;
+            c->trace_n[p.id] += 1;
+        }
+        c->pool.push_back(p.a);
+        c->pool.push_back(p.b);
+    }
+    cudaGetLastError();
+    c->pending.clear();
+}
+
 int ensure_host(hermes_ctx* c, size_t n) {
     if (n <= c->host_cap) return HERMES_OK;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -299,6 +362,8 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
     c->p = p;
     c->j = j;
     c->H = N / 2;
+    c->tracer.ctx = c;
+    c->tracer.mark = trace_mark;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -361,6 +426,11 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->stage_w);
     cudaFree(c->rad);
     if (c->host_buf) cudaFreeHost(c->host_buf);
+    for (auto& p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     cudaGetLastError();
     delete c;
@@ -429,12 +499,12 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
     CK(cudaMemsetAsync(c->grid, 0, n3 * sizeof(float), st), "clear grid");
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     const float s = (float)((double)N / c->L);
-    CK(launch_scatter(N, p, dpos, dw, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st), "scatter");
-    CK(launch_weight_sums(dw, n, c->part, nblk, st), "weight sums");
-    CK(launch_reduce_rows(c->part, 2, nblk, c->red, st), "reduce sums");
-    CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st), "self-pair table");
-    CK(launch_reduce_rows(c->part, p3, nblk, c->stab_d, st), "reduce self-pair");
-    CK(launch_finish_field(c->red, c->stab_d, p3, c->stab_f, N, c->scal, st), "field scalars");
+    CK(launch_scatter(N, p, dpos, dw, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st, c->tracer), "scatter");
+    CK(launch_weight_sums(dw, n, c->part, nblk, st, c->tracer), "weight sums");
+    CK(launch_reduce_rows(c->part, 2, nblk, c->red, st, c->tracer), "reduce sums");
+    CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st, c->tracer), "self-pair table");
+    CK(launch_reduce_rows(c->part, p3, nblk, c->stab_d, st, c->tracer), "reduce self-pair");
+    CK(launch_finish_field(c->red, c->stab_d, p3, c->stab_f, N, c->scal, st, c->tracer), "field scalars");
     CK(cudaMemcpyAsync(c->host_buf, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read sums");
     unsigned herr = 0;
     CK(cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
@@ -445,7 +515,7 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
     c->sum_w2 = c->host_buf[1];
     if (!(c->sum_w > 0.0) || !std::isfinite(c->sum_w))
         return fail(c, HERMES_ERR_RANGE, "sum of weights is %g; it must be positive", c->sum_w);
-    CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st), "forward FFT");
+    CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st, c->tracer), "forward FFT");
     CK(cudaStreamSynchronize(st), "forward FFT");
     c->have_field = true;
     return HERMES_OK;
@@ -542,9 +612,9 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
         }
         double* sn_part = c->part;
         double* dd_part = c->part + (size_t)wb.S * xb;
-        CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st), "inverse passes");
-        CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st), "reduce self-pair sums");
-        CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st), "reduce contractions");
+        CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st, c->tracer), "inverse passes");
+        CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st, c->tracer), "reduce self-pair sums");
+        CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
     }
     CK(ensure_host(c, (size_t)2 * nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
     CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
@@ -593,8 +663,8 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
             norm *= ((m & 1) ? -1.0 : 1.0) * dfact2(2 * m - 1);
             hb.ylm_norm = (float)(4.0 * M_PI * norm);
             for (int b = 0; b < nb; ++b) hb.tab[b] = c->rad + ((size_t)b * LM + ell) * c->Q;
-            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, st), "harmonic fields");
-            CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st), "reduce Gram");
+            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, st, c->tracer), "harmonic fields");
+            CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st, c->tracer), "reduce Gram");
         }
     }
     CK(ensure_host(c, (size_t)256 * nlm) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
@@ -648,7 +718,7 @@ int hermes_debug_set_delta(hermes_ctx* c, const float* host_delta) {
     CK(cudaMemcpyAsync(c->grid, host_delta, n3 * sizeof(float), cudaMemcpyDefault, c->stream), "write delta");
     CK(cudaMemsetAsync(c->stab_f, 0, 512 * sizeof(float), c->stream), "clear self-pair");
     CK(cudaMemsetAsync(c->stab_d, 0, 512 * sizeof(double), c->stream), "clear self-pair");
-    CK(launch_delta_to_spec(c->N, c->grid, c->spec, c->scal, tables_of(c), c->stream), "forward FFT");
+    CK(launch_delta_to_spec(c->N, c->grid, c->spec, c->scal, tables_of(c), c->stream, c->tracer), "forward FFT");
     CK(cudaStreamSynchronize(c->stream), "set delta");
     c->sum_w = (double)n3;  // eps_bar = 1
     c->sum_w2 = 0.0;
@@ -674,7 +744,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = launch_nodes(c->N, p, dpos, n, (float)((double)c->N / c->L), (flags & HERMES_WRAP) ? 1 : 0, dfirst, dw,
-                         c->err, st);
+                         c->err, st, c->tracer);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_first, dfirst, (size_t)n * 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_wts, dw, (size_t)n * 3 * p * sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -686,6 +756,44 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
     cudaFree(dw);
     return rc;
 }
+
+static const char* const kKernelNames[K_COUNT] = {
+    "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
+    "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes"};
+
+int hermes_trace_enable(hermes_ctx* c, int on) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    trace_collect(c);
+    for (int i = 0; i < K_COUNT; ++i) {
+        c->trace_ms[i] = 0.0;
+        c->trace_n[i] = 0;
+    }
+    c->trace_on = on != 0;
+    return HERMES_OK;
+}
+
+int hermes_trace_read(hermes_ctx* c, double* ms, int64_t* launches, int n) {
+    if (check_ctx(c) || n < 0) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    trace_collect(c);
+    for (int i = 0; i < n && i < K_COUNT; ++i) {
+        if (ms) ms[i] = c->trace_ms[i];
+        if (launches) launches[i] = c->trace_n[i];
+    }
+    for (int i = 0; i < K_COUNT; ++i) {
+        c->trace_ms[i] = 0.0;
+        c->trace_n[i] = 0;
+    }
+    return K_COUNT;
+}
+
+const char* hermes_kernel_name(int id) {
+    if (id < 0 || id >= K_COUNT) return "";
+    return kKernelNames[id];
+}
+
+int64_t hermes_launch_count(const hermes_ctx* c) { return c ? c->launches : -1; }
 
 int hermes_debug_get_sums(hermes_ctx* c, double* sums2, double* selfpair) {
     if (check_ctx(c)) return HERMES_ERR_ARG;

@@ -5,7 +5,22 @@
 
 namespace hermes {
 
-constexpr int MAX_BATCH = 32;  // windows evaluated per launch of the first inverse pass
+constexpr int MAX_BATCH = 32;
+
+// Kernel classes reported by the tracer.
+enum KernelId {
+    K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_COUNT
+};
+
+// Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
+struct Tracer {
+    void* ctx;
+    void (*mark)(void* ctx, int kernel_id, int phase, cudaStream_t st);
+    void operator()(int id, int phase, cudaStream_t st) const {
+        if (mark) mark(ctx, id, phase, st);
+    }
+};  // windows evaluated per launch of the first inverse pass
 
 // One batch of real (xi / xi_l) windows: radial table per window and the
 // Legendre order of its angular factor.  scale multiplies the table value.
@@ -32,30 +47,30 @@ struct Tables {
 
 // scatter.cu
 cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
-                           int wrap, unsigned* err, cudaStream_t st);
+                           int wrap, unsigned* err, cudaStream_t st, const Tracer& tr);
 cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
-                         unsigned* err, cudaStream_t st);
-cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st);
+                         unsigned* err, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr);
 cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
-                            int nblk, cudaStream_t st);
-cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st);
+                            int nblk, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st, const Tracer& tr);
 cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3, float* stab_f, int N,
-                                double* scal, cudaStream_t st);
+                                double* scal, cudaStream_t st, const Tracer& tr);
 
 // fft_passes.cu
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
-                           cudaStream_t st);
+                           cudaStream_t st, const Tracer& tr);
 int inv_x_blocks(int N);
 int inv_z_blocks(int N);
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta,
                               const WinBatch& wb, const Tables& tb, double* sn_part, double* dd_part,
-                              cudaStream_t st);
+                              cudaStream_t st, const Tracer& tr);
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const Tracer& tr);
 
 // zeta.cu
 int zeta_z_blocks(int N);
 cudaError_t launch_zeta_lm(int N, const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                           const Tables& tb, double* gram_part, cudaStream_t st);
+                           const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr);
 
 }  // namespace hermes

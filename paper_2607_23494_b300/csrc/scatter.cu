@@ -222,9 +222,10 @@ static int nblocks_for(int64_t n, int per_block, int cap) {
 }
 
 cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
-                           int wrap, unsigned* err, cudaStream_t st) {
+                           int wrap, unsigned* err, cudaStream_t st, const Tracer& tr) {
     if (n == 0) return cudaSuccess;
     const int nb = nblocks_for(n, 256, 148 * 32);
+    tr(K_SCATTER, 0, st);
     switch (p) {
 #define HERMES_SC(P) \
     case P: k_scatter<P><<<nb, 256, 0, st>>>(pos, w, n, grid, s, N, wrap, err); break;
@@ -232,13 +233,15 @@ cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64
 #undef HERMES_SC
         default: return cudaErrorInvalidValue;
     }
+    tr(K_SCATTER, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
-                         unsigned* err, cudaStream_t st) {
+                         unsigned* err, cudaStream_t st, const Tracer& tr) {
     if (n == 0) return cudaSuccess;
     const int nb = (int)((n + 255) / 256);
+    tr(K_NODES, 0, st);
     switch (p) {
 #define HERMES_ND(P) \
     case P: k_nodes<P><<<nb, 256, 0, st>>>(pos, n, s, N, wrap, first, wts, err); break;
@@ -246,16 +249,20 @@ cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int
 #undef HERMES_ND
         default: return cudaErrorInvalidValue;
     }
+    tr(K_NODES, 1, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st) {
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr) {
+    tr(K_WEIGHT_SUMS, 0, st);
     k_weight_sums<<<nblk, 256, 0, st>>>(w, n, part);
+    tr(K_WEIGHT_SUMS, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
-                            int nblk, cudaStream_t st) {
+                            int nblk, cudaStream_t st, const Tracer& tr) {
+    tr(K_SELFPAIR, 0, st);
     switch (p) {
 #define HERMES_SP(P) \
     case P: k_selfpair<P><<<nblk, 256, 0, st>>>(pos, w, n, s, N, part); break;
@@ -263,18 +270,24 @@ cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int6
 #undef HERMES_SP
         default: return cudaErrorInvalidValue;
     }
+    tr(K_SELFPAIR, 1, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st) {
+cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st,
+                               const Tracer& tr) {
     if (rows <= 0) return cudaSuccess;
+    tr(K_REDUCE, 0, st);
     k_reduce_rows<<<rows, 256, 0, st>>>(part, cols, out);
+    tr(K_REDUCE, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3, float* stab_f, int N,
-                                double* scal, cudaStream_t st) {
+                                double* scal, cudaStream_t st, const Tracer& tr) {
+    tr(K_FINISH, 0, st);
     k_finish_field<<<1, 256, 0, st>>>(sums, stab_d, p3, stab_f, N, scal);
+    tr(K_FINISH, 1, st);
     return cudaGetLastError();
 }
 

@@ -265,31 +265,37 @@ int zeta_z_blocks(int N) {
 
 template <int N>
 static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                             const Tables& tb, double* gram_part, cudaStream_t st) {
+                             const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr) {
     using C = ZCfg<N>;
     cudaError_t e;
     if ((e = allow_smem_z(k_zeta_x<N>, C::SMEM_X)) != cudaSuccess) return e;
     if ((e = allow_smem_z(k_zeta_y<N>, C::SMEM_X)) != cudaSuccess) return e;
     if ((e = allow_smem_z(k_zeta_z_gram<N>, C::SMEM_Z)) != cudaSuccess) return e;
     dim3 g1(N / C::W, N, 1);
+    tr(K_ZETA_X, 0, st);
     k_zeta_x<N><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hb, tb);
+    tr(K_ZETA_X, 1, st);
     dim3 g2(N / C::W, N, hb.S);
+    tr(K_ZETA_Y, 0, st);
     k_zeta_y<N><<<g2, C::TS, C::SMEM_X, st>>>(fields, tb.tw);
+    tr(K_ZETA_Y, 1, st);
+    tr(K_ZETA_Z_GRAM, 0, st);
     k_zeta_z_gram<N><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw, gram_part);
+    tr(K_ZETA_Z_GRAM, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zeta_lm(int N, const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                           const Tables& tb, double* gram_part, cudaStream_t st) {
+                           const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr) {
     if (hb.S < 1 || hb.S > 16) return cudaErrorInvalidValue;
     switch (N) {
-        case 16: return zeta_impl<16>(spec, fields, delta, hb, tb, gram_part, st);
-        case 32: return zeta_impl<32>(spec, fields, delta, hb, tb, gram_part, st);
-        case 64: return zeta_impl<64>(spec, fields, delta, hb, tb, gram_part, st);
-        case 128: return zeta_impl<128>(spec, fields, delta, hb, tb, gram_part, st);
-        case 256: return zeta_impl<256>(spec, fields, delta, hb, tb, gram_part, st);
-        case 512: return zeta_impl<512>(spec, fields, delta, hb, tb, gram_part, st);
-        case 1024: return zeta_impl<1024>(spec, fields, delta, hb, tb, gram_part, st);
+        case 16: return zeta_impl<16>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 32: return zeta_impl<32>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 64: return zeta_impl<64>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 128: return zeta_impl<128>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 256: return zeta_impl<256>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 512: return zeta_impl<512>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 1024: return zeta_impl<1024>(spec, fields, delta, hb, tb, gram_part, st, tr);
     }
     return cudaErrorInvalidValue;
 }

@@ -57,6 +57,10 @@ def _load() -> C.CDLL:
         "hermes_debug_nodes": (i32, [vp, fp, i64, u32, fp, fp]),
         "hermes_shell_table_host": (i32, [C.c_double, i32, dp, i32, i32, dp]),
         "hermes_shell_table_len": (i64, [i32]),
+        "hermes_trace_enable": (i32, [vp, i32]),
+        "hermes_trace_read": (i32, [vp, dp, C.POINTER(i64), i32]),
+        "hermes_kernel_name": (C.c_char_p, [i32]),
+        "hermes_launch_count": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +186,22 @@ class Context:
         out = np.empty((self.l_max + 1, self.n_bins, self.n_bins), dtype=np.float64)
         self._check(_lib.hermes_zeta_multipoles(self._h, _dptr(out)), "hermes_zeta_multipoles")
         return out
+
+    # tracing
+    def trace(self, on: bool = True) -> None:
+        self._check(_lib.hermes_trace_enable(self._h, 1 if on else 0), "hermes_trace_enable")
+
+    def trace_read(self) -> dict:
+        """{kernel name: (device ms, launches)} since the last enable/read."""
+        ms = np.zeros(32, dtype=np.float64)
+        cnt = np.zeros(32, dtype=np.int64)
+        k = _lib.hermes_trace_read(self._h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)), 32)
+        if k < 0:
+            self._check(k, "hermes_trace_read")
+        return {_lib.hermes_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k) if cnt[i] > 0}
+
+    def launch_count(self) -> int:
+        return int(_lib.hermes_launch_count(self._h))
 
     # inspection hooks
     def get_delta(self) -> np.ndarray:

@@ -81,7 +81,10 @@ def test_cell_route_equals_parseval_route():
     edges = [5.0, 15.0, 25.0, 35.0]
     a = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2), route="parseval")
     b = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2), route="cell")
+    c = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2), route="half")
     np.testing.assert_allclose(a["xi"], b["xi"], rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(a["xi"], c["xi"], rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(a["sn"], c["sn"], rtol=1e-10, atol=1e-13)
 
 
 def test_poisson_catalogue_is_uncorrelated():
