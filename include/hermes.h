@@ -92,6 +92,31 @@ int hermes_set_stream(hermes_ctx *ctx, void *cuda_stream);
 int hermes_assign(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
 
 /*
+ * hermes_assign for callers that cannot allocate GPU memory at call time:
+ * code running while a CUDA stream is being captured into a graph, serving
+ * loops that must not stall on the allocator, or hosts whose device memory is
+ * owned by another allocator (a framework's caching pool).  It does what
+ * hermes_assign does, with the same arguments and errors, but calls no
+ * cudaMalloc, cudaFree or other allocating routine.  (The paper has no
+ * counterpart; this is an interface of this library only.)
+ *   - pos / w must already be device memory of the context's device (no host
+ *     staging copy); HERMES_DEVICE_PTR is implied, HERMES_WRAP is honoured.
+ *   - The block partial sums of the weight and self-pair reductions use one
+ *     fixed 256 KiB array in device memory (32768 float64), which every GPU
+ *     that loads the library keeps until the process exits.  The context order p
+ *     must satisfy 2 + max(2, p^3) * 148 <= 32768, i.e. p <= 6; a larger p is
+ *     rejected with HERMES_ERR_ARG and a message naming the limit.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress), which may load the library's device code; make
+ *     that first call before any stream capture begins.
+ *   - Every call on a device shares the array: calls whose work overlaps on the
+ *     GPU (other contexts on other streams included) race on it; serialise them.
+ *     Each call overwrites every entry it reads, so no state carries over.
+ * The context must have been created (hermes_create allocates the field).
+ */
+int hermes_assign_noalloc(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
+
+/*
  * Define the radial bins [r_edges[b], r_edges[b+1]) of every later statistic
  * and tabulate, in float64 on the host, the r^2-weighted bin average of the
  * spherical Bessel functions <j_l>_b(k) for 0 <= l <= l_max at every discrete

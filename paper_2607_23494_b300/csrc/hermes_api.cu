@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -812,3 +813,88 @@ int hermes_debug_get_sums(hermes_ctx* c, double* sums2, double* selfpair) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// hermes_assign_noalloc: hermes_assign for callers that must not allocate.
+//
+// The per-block partial sums of the weight and self-pair reductions live in
+// this file-scope device array instead of context buffers that grow on demand.
+// In host code the name g_assign_scratch is only a host-side stand-in: its
+// device address is looked up once per device with cudaGetSymbolAddress and
+// passed to the kernels.  Every context and every call on a device shares the
+// array, so calls whose work overlaps on the GPU race on it.
+namespace {
+constexpr int kNoallocBlocks = 148;
+constexpr size_t kNoallocDoubles = 32768;  // 256 KiB
+static __device__ __align__(256) double g_assign_scratch[kNoallocDoubles];
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+int noalloc_scratch(hermes_ctx* c, double** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (c->device < 0 || c->device >= 256) return fail(c, HERMES_ERR_ARG, "device ordinal %d out of range", c->device);
+    if (!g_noalloc_ptr[c->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_assign_scratch);  // the calling device is current
+        if (e != cudaSuccess) return cuda_fail(c, e, "address of the static scratch array");
+        g_noalloc_ptr[c->device] = (double*)p;
+    }
+    *out = g_noalloc_ptr[c->device];
+    return HERMES_OK;
+}
+
+void count_only_mark(void* vc, int, int phase, cudaStream_t) {
+    if (phase == 0) ++((hermes_ctx*)vc)->launches;
+}
+}  // namespace
+
+extern "C" int hermes_assign_noalloc(hermes_ctx* c, const float* pos, const float* w, int64_t n, unsigned flags) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!pos) return fail(c, HERMES_ERR_ARG, "pos is NULL");
+    if (n < 1) return fail(c, HERMES_ERR_ARG, "empty catalogue (n = %lld): the density contrast is undefined",
+                           (long long)n);
+    if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    const int N = c->N, p = c->p;
+    const int p3 = p * p * p;
+    const size_t need = 2 + (size_t)std::max(2, p3) * kNoallocBlocks;
+    if (need > kNoallocDoubles)
+        return fail(c, HERMES_ERR_ARG,
+                    "hermes_assign_noalloc: its fixed scratch holds %zu doubles, order p = %d needs %zu "
+                    "(p <= 6 fits); use hermes_assign", kNoallocDoubles, p, need);
+    DeviceGuard g(c->device);
+    int r = check_device_ptr(c, pos, "pos");
+    if (r) return r;
+    if (w && (r = check_device_ptr(c, w, "w"))) return r;
+    double* scratch = nullptr;
+    if ((r = noalloc_scratch(c, &scratch))) return r;
+    double* sums = scratch;      // [2] reduced sum w, sum w^2
+    double* part = scratch + 2;  // [max(2,p^3)][kNoallocBlocks] partials, fully overwritten
+    c->have_field = false;
+    cudaStream_t st = c->stream;
+    const Tracer tr{c, count_only_mark};
+    const size_t n3 = (size_t)N * N * N;
+    CK(cudaMemsetAsync(c->grid, 0, n3 * sizeof(float), st), "clear grid");
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    const float s = (float)((double)N / c->L);
+    CK(launch_scatter(N, p, pos, w, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st, tr), "scatter");
+    CK(launch_weight_sums(w, n, part, kNoallocBlocks, st, tr), "weight sums");
+    CK(launch_reduce_rows(part, 2, kNoallocBlocks, sums, st, tr), "reduce sums");
+    CK(launch_selfpair(N, p, pos, w, n, s, part, kNoallocBlocks, st, tr), "self-pair table");
+    CK(launch_reduce_rows(part, p3, kNoallocBlocks, c->stab_d, st, tr), "reduce self-pair");
+    CK(launch_finish_field(sums, c->stab_d, p3, c->stab_f, N, c->scal, st, tr), "field scalars");
+    // both read-backs land in the pinned buffer allocated when the context was created
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + 2);
+    CK(cudaMemcpyAsync(c->host_buf, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read sums");
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "assign");
+    if (*hflag) return fail(c, HERMES_ERR_RANGE, "a coordinate is outside [0, L] (u = x*N/L outside [0, N]) "
+                                               "or a weight is not finite; use HERMES_WRAP to wrap");
+    c->sum_w = c->host_buf[0];
+    c->sum_w2 = c->host_buf[1];
+    if (!(c->sum_w > 0.0) || !std::isfinite(c->sum_w))
+        return fail(c, HERMES_ERR_RANGE, "sum of weights is %g; it must be positive", c->sum_w);
+    CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st, tr), "forward FFT");
+    CK(cudaStreamSynchronize(st), "forward FFT");
+    c->have_field = true;
+    return HERMES_OK;
+}

@@ -45,6 +45,7 @@ def _load() -> C.CDLL:
         "hermes_destroy": (i32, [vp]),
         "hermes_set_stream": (i32, [vp, vp]),
         "hermes_assign": (i32, [vp, fp, fp, i64, u32]),
+        "hermes_assign_noalloc": (i32, [vp, fp, fp, i64, u32]),
         "hermes_window_shells": (i32, [vp, dp, i32, i32]),
         "hermes_xi": (i32, [vp, dp]),
         "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
@@ -163,6 +164,13 @@ class Context:
                 wp = w.ctypes.data
             rc = _lib.hermes_assign(self._h, pos.ctypes.data if n else None, wp, n, flags)
         self._check(rc, "hermes_assign")
+
+    def assign_noalloc(self, pos, w=None, wrap: bool = False) -> None:
+        """hermes_assign_noalloc: pos / w are CUDA tensors; no device memory is allocated."""
+        n = pos.shape[0]
+        rc = _lib.hermes_assign_noalloc(self._h, pos.data_ptr(), None if w is None else w.data_ptr(), n,
+                                        WRAP if wrap else 0)
+        self._check(rc, "hermes_assign_noalloc")
 
     def window_shells(self, r_edges: Sequence[float], l_max: int = 0) -> None:
         e = np.ascontiguousarray(r_edges, dtype=np.float64)
