@@ -358,6 +358,22 @@ def run_reference(args):
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile_case():
+    """Small case for ncu captures: 512^3 field of 300k Poisson points, 5 l=0 windows (one batch)."""
+    import torch
+    from paper_2607_23494_b300 import Context
+    from synthetic import catalogues as S
+    pos = torch.from_numpy(S.poisson_uniform(300_000, L2, seed=7)).cuda()
+    ctx = Context(L2, N2, P2)
+    ctx.window_shells(np.linspace(2.0, 52.0, 6), l_max=0)
+    ctx.assign(pos)
+    for _ in range(2):
+        x = ctx.xi()
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_case": "xi 512^3, 5 windows", "xi": [float(v) for v in x]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,7 +382,11 @@ def main():
     ap.add_argument("--impl", default="hermes", choices=["hermes", "reference"])
     ap.add_argument("--no-zeta", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case()
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

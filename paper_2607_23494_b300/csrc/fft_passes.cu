@@ -138,13 +138,12 @@ __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
 // C(n,a>0) = 2 cos(2 pi n a / N), is the Fourier transform of the even
 // self-pair overlap table.
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::TS) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
+__global__ void __launch_bounds__(Cfg<N>::TS, (Cfg<N>::TS > 512 ? 1 : 2)) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
                                                               const WinBatch wb, const Tables tb, int P,
                                                               double* __restrict__ sn_part) {
     using C = Cfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
     extern __shared__ float2 smem[];
-    __shared__ double red[32];
     const int col = threadIdx.x % W, t = threadIdx.x / W;
     const int ky = blockIdx.y, kz = blockIdx.x * W + col;
     const size_t nblk = (size_t)gridDim.x * gridDim.y;
@@ -182,35 +181,47 @@ __global__ void __launch_bounds__(Cfg<N>::TS) k_inv_x_window(const float2* __res
         }
         U[a] = u;
     }
-    float shat[8], phk[8], mu[8];
+    // Phi^ and the Nyquist mask are folded into the spectrum and the self-pair
+    // transform once, so per window K' = scale * table[q] * L_l(mu) only:
+    //   v = (delta^ Phi^) K',  sn += K' (S^ Phi^)
+    float shat[8];
     int q[8];
-    bool nyq[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int kx = t + i * T;
         const int nx = signed_freq(kx, N);
-        nyq[i] = nyq_y || (kx == H);
-        q[i] = nyq[i] ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
-        phk[i] = __ldg(tb.phi + kx) * phyz;
-        mu[i] = q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f;
+        const bool nyq = nyq_y || (kx == H);
+        q[i] = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
+        const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
+        v0[i] = cscale(v0[i], ph);
         float sh = 0.0f;
 #pragma unroll
         for (int a = 0; a < 8; ++a)
             if (a < P) sh = fmaf((a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, kx * a), U[a], sh);
-        shat[i] = sh;
+        shat[i] = sh * ph;
     }
     const float wz = (kz == 0) ? 1.0f : 2.0f;
-
+    // per-warp partial self-pair sums; one float64 reduction per window at the end
+    constexpr int NW = (C::TS + 31) / 32;
+    constexpr unsigned MASK = C::TS >= 32 ? 0xffffffffu : ((1u << C::TS) - 1u);
+    __shared__ float wsn[NW][MAX_BATCH];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float leg[8];
+    int leg_ell = -1;
     for (int s = 0; s < wb.S; ++s) {
         const float* tab = wb.tab[s];
         const float sc = wb.scale[s];
         const int ell = wb.ell[s];
+        if (ell != leg_ell) {  // windows come l-major, so this runs once per l in a batch
+#pragma unroll
+            for (int i = 0; i < 8; ++i) leg[i] = legendre(ell, q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f);
+            leg_ell = ell;
+        }
         float sn = 0.0f;
         float2 v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            float K = 0.0f;
-            if (!nyq[i]) K = sc * __ldg(tab + q[i]) * phk[i] * legendre(ell, mu[i]);
+            const float K = sc * __ldg(tab + q[i]) * leg[i];
             sn = fmaf(K, shat[i], sn);
             v[i] = cscale(v0[i], K);
         }
@@ -218,8 +229,16 @@ __global__ void __launch_bounds__(Cfg<N>::TS) k_inv_x_window(const float2* __res
         float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
 #pragma unroll
         for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
-        const double tot = block_sum_double((double)(sn * wz), red);
-        if (threadIdx.x == 0) sn_part[(size_t)s * nblk + blk] = tot;
+        sn *= wz;
+#pragma unroll
+        for (int o = (C::TS >= 32 ? 16 : C::TS / 2); o > 0; o >>= 1) sn += __shfl_xor_sync(MASK, sn, o);
+        if (lane == 0) wsn[wid][s] = sn;
+    }
+    __syncthreads();
+    if (threadIdx.x < wb.S) {
+        double tot = 0.0;
+        for (int w = 0; w < NW; ++w) tot += (double)wsn[w][threadIdx.x];
+        sn_part[(size_t)threadIdx.x * nblk + blk] = tot;
     }
 }
 
@@ -228,15 +247,17 @@ __global__ void __launch_bounds__(Cfg<N>::TS) k_inv_x_window(const float2* __res
 // Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), X_M = 0;
 // z = IFFT_M(Z') gives x_{2j} = Re z_j, x_{2j+1} = Im z_j (unnormalised).
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_contract(const float2* __restrict__ work, int S,
-                                                                          const float* __restrict__ delta,
-                                                                          const float2* __restrict__ tw,
-                                                                          double* __restrict__ dd_part) {
+__global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(const float2* __restrict__ work, int S,
+                                                                             const float* __restrict__ delta,
+                                                                             const float2* __restrict__ tw,
+                                                                             double* __restrict__ dd_part) {
     using C = Cfg<N>;
     constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value, H = N / 2;
+    constexpr int NW = C::ZTHREADS / 32;
     extern __shared__ float2 smem[];
-    __shared__ double red[32];
+    __shared__ float wdd[NW][MAX_BATCH];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
     const SmemLine sm{smem + li * LP};
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
@@ -245,29 +266,54 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_contract(const f
     for (int i = 0; i < 8; ++i) d2[i] = dl[t + i * T];
     for (int s = 0; s < S; ++s) {
         const float2* X = work + (size_t)s * N * N * H + line * H;
-        float2 v[8];
+        float2 v[8], xm[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = X[t + i * T];
-        __syncthreads();
+        if constexpr (T == 32) {
+            // one line per warp: X_{M-k} of element k = t + iT sits in lane 32-t, slot 7-i
+            // (lane 0 holds its own partners in slot 8-i; X_M = 0)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
-        __syncthreads();
+            for (int i = 0; i < 8; ++i) xm[i] = make_float2(__shfl_sync(0xffffffffu, v[7 - i].x, (32 - t) & 31),
+                                                          __shfl_sync(0xffffffffu, v[7 - i].y, (32 - t) & 31));
+            if (t == 0) {
+                xm[0] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 1; i < 8; ++i) xm[i] = v[8 - i];
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = t + i * T;
+                xm[i] = (k == 0) ? make_float2(0.f, 0.f) : sm.ld(M - k);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = t + i * T;
             const float2 xk = v[i];
-            const float2 xm = (k == 0) ? make_float2(0.f, 0.f) : cconj(sm.ld(M - k));
-            const float2 a = cadd(xk, xm);
+            const float2 xc = cconj(xm[i]);
+            const float2 a = cadd(xk, xc);
             const float2 w = cconj(__ldg(tw + k * (TW / N)));  // e^{+2 pi i k / N}
-            const float2 c = cmul(w, csub(xk, xm));
+            const float2 c = cmul(w, csub(xk, xc));
             v[i] = make_float2(a.x - c.y, a.y + c.x);
         }
         fft_line<M, true>(v, t, tw, sm);
         float acc = 0.0f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc = fmaf(d2[i].x, v[i].x, fmaf(d2[i].y, v[i].y, acc));
-        const double tot = block_sum_double((double)acc, red);
-        if (threadIdx.x == 0) dd_part[(size_t)s * gridDim.x + blockIdx.x] = tot;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) wdd[wid][s] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < S) {
+        double tot = 0.0;
+        for (int w = 0; w < NW; ++w) tot += (double)wdd[w][threadIdx.x];
+        dd_part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = tot;
     }
 }
 
