@@ -8,8 +8,9 @@
 // is a policy class (strided tiles vs. contiguous padded lines).
 //
 // Stage plan: radix-8 throughout, with one leading radix-2 or radix-4 stage
-// when log2(M) is not a multiple of 3.  Twiddles come from a table of
-// e^{-2 pi i j / TW} built on the host in float64; the inverse uses conjugates.
+// when log2(M) is not a multiple of 3.  Twiddles come from tables built on the
+// host in float64 and laid out so each load is coalesced; the inverse uses
+// conjugates.
 #pragma once
 #include "common.cuh"
 
@@ -75,30 +76,51 @@ __device__ __forceinline__ void dftR(float2* a) {
     else dft8<INV>(a);
 }
 
+// Twiddle tables (one buffer, built on the host in float64, stored as float32):
+//   tw[L + j]                       = e^{-2 pi i j / L},  L = 2, 4, ..., TW, 0 <= j < L
+//   tw[STAGE_TW + 7 (NS-1) + (r-1) NS + k] = e^{-2 pi i k r / (8 NS)}, 1 <= r < 8, 0 <= k < NS
+// The second block serves the radix-8 Stockham stages: for a fixed r the
+// twiddles of consecutive butterflies are adjacent, so every load is coalesced
+// and exact to float32 rounding.
+constexpr int STAGE_TW = 2 * TW;
+constexpr int TW_ENTRIES = STAGE_TW + 7 * TW;
 template <bool INV>
-__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int j) {
-    float2 w = __ldg(tw + j);
+__device__ __forceinline__ float2 twiddle_l(const float2* __restrict__ tw, int L, int j) {
+    float2 w = __ldg(tw + L + j);
+    return INV ? make_float2(w.x, -w.y) : w;
+}
+template <bool INV>
+__device__ __forceinline__ float2 twiddle_stage8(const float2* __restrict__ tw, int NS, int r, int k) {
+    float2 w = __ldg(tw + STAGE_TW + 7 * (NS - 1) + (r - 1) * NS + k);
     return INV ? make_float2(w.x, -w.y) : w;
 }
 
 // Shared-memory line layouts -------------------------------------------------
-// Strided tile: W lines stored position-major, element (pos, col) at pos*W+col.
+// Strided tile: W lines stored position-major, element (pos, col) at
+// pos*W + col, plus 4 padding slots after every 8 rows (bank skew for the
+// Stockham write patterns of 512-point tiles).
 template <int W>
 struct SmemStrided {
     float2* p;
     int col;
-    __device__ __forceinline__ float2 ld(int pos) const { return p[pos * W + col]; }
-    __device__ __forceinline__ void st(int pos, float2 v) const { p[pos * W + col] = v; }
+    static constexpr int words(int n) { return n * W + (n / 8) * 4; }
+    __device__ __forceinline__ int at(int pos) const { return pos * W + col + (pos >> 3) * 4; }
+    __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
 };
-// Contiguous line with one padding slot every 8 elements (bank-conflict skew).
+// Contiguous line of length M with one padding slot every 2^SH elements.
+constexpr int line_shift(int m) { return m >= 128 ? 4 : (m == 32 ? 2 : 3); }
+template <int M>
 struct SmemLine {
+    static constexpr int SH = line_shift(M);
     float2* p;
-    __device__ __forceinline__ float2 ld(int pos) const { return p[pos + (pos >> 3)]; }
-    __device__ __forceinline__ void st(int pos, float2 v) const { p[pos + (pos >> 3)] = v; }
+    __device__ __forceinline__ static int at(int pos) { return pos + (pos >> SH); }
+    __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
 };
 template <int M>
 struct LinePad {
-    static constexpr int value = M + M / 8;
+    static constexpr int value = M + (M >> line_shift(M)) + 1;
 };
 
 constexpr int ilog2c(int m) { return m <= 1 ? 0 : 1 + ilog2c(m >> 1); }
@@ -123,8 +145,9 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
         if constexpr (NS > 1) {
+            static_assert(R == 8, "only the leading stage may use radix 2 or 4");
 #pragma unroll
-            for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<INV>(tw, k * r * (TW / (NS * R))));
+            for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], twiddle_stage8<INV>(tw, NS, r, k));
         }
         dftR<R, INV>(x);
 #pragma unroll

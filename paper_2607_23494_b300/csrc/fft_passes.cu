@@ -33,7 +33,7 @@ struct Cfg {
     static constexpr int TZ = MZ / 8;
     static constexpr int LZ = (256 / TZ) > 0 ? (256 / TZ) : 1;              // z lines per block
     static constexpr int ZTHREADS = TZ * LZ;
-    static constexpr size_t SMEM_STRIDED = (size_t)N * W * sizeof(float2);
+    static constexpr size_t SMEM_STRIDED = (size_t)SmemStrided<W>::words(N) * sizeof(float2);
     static constexpr size_t SMEM_Z = (size_t)LZ * LinePad<MZ>::value * sizeof(float2);
 };
 
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
     extern __shared__ float2 smem[];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemLine sm{smem + li * LP};
+    const SmemLine<M> sm{smem + li * LP};
     float2* g = reinterpret_cast<float2*>(grid + line * N);
     const float inv_mean = convert ? (float)scal[2] : 1.0f;
     float2 v[8];
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
         const float2 e = cscale(cadd(zk, zm), 0.5f);
         const float2 d = csub(zk, zm);
         const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);  // (zk - conj zm) / (2i)
-        const float2 w = __ldg(tw + k * (TW / N));                // e^{-2 pi i k / N}
+        const float2 w = __ldg(tw + N + k);                       // e^{-2 pi i k / N}
         out[k] = cadd(e, cmul(w, o));
     }
 }
@@ -127,7 +127,7 @@ __device__ __forceinline__ float legendre(int ell, float mu) {
 // cos(2 pi j / N) from the twiddle table.
 template <int N>
 __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
-    return __ldg(tw + (j & (N - 1)) * (TW / N)).x;
+    return __ldg(tw + N + (j & (N - 1))).x;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemLine sm{smem + li * LP};
+    const SmemLine<M> sm{smem + li * LP};
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
     float2 d2[8];
 #pragma unroll
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
             const float2 xk = v[i];
             const float2 xc = cconj(xm[i]);
             const float2 a = cadd(xk, xc);
-            const float2 w = cconj(__ldg(tw + k * (TW / N)));  // e^{+2 pi i k / N}
+            const float2 w = cconj(__ldg(tw + N + k));  // e^{+2 pi i k / N}
             const float2 c = cmul(w, csub(xk, xc));
             v[i] = make_float2(a.x - c.y, a.y + c.x);
         }

@@ -17,6 +17,7 @@
 #include "../../include/hermes.h"
 #include "kernels.h"
 #include "common.cuh"
+#include "fft_core.cuh"
 
 using namespace hermes;
 
@@ -384,14 +385,23 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
     if (cudaMalloc((void**)&c->stab_d, 512 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (cudaMalloc((void**)&c->stab_f, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (cudaMalloc((void**)&c->err, sizeof(unsigned)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->tw, TW * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (cudaMalloc((void**)&c->tw, TW_ENTRIES * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (cudaMalloc((void**)&c->phi, N * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    // twiddles e^{-2 pi i j / TW} and Phi^(n) = sinc^{2p}(pi n / N) in float64, stored as float32
-    std::vector<float2> tw(TW);
-    for (int i = 0; i < TW; ++i) {
-        const double a = -2.0 * M_PI * (double)i / (double)TW;
-        tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    // multi-level twiddles tw[L + j] = e^{-2 pi i j / L} (L = 2, 4, ..., TW) and
+    // Phi^(n) = sinc^{2p}(pi n / N), in float64, stored as float32
+    std::vector<float2> tw(TW_ENTRIES, make_float2(0.f, 0.f));
+    for (int Lv = 2; Lv <= TW; Lv *= 2)
+        for (int i = 0; i < Lv; ++i) {
+            const double a = -2.0 * M_PI * (double)i / (double)Lv;
+            tw[Lv + i] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    // radix-8 stage twiddles e^{-2 pi i k r / (8 NS)}, [r-1][k] per NS
+    for (int NS = 2; 8 * NS <= TW; NS *= 2)
+        for (int r = 1; r < 8; ++r)
+            for (int k = 0; k < NS; ++k) {
+                const double a = -2.0 * M_PI * (double)k * (double)r / (8.0 * NS);
+                tw[STAGE_TW + 7 * (NS - 1) + (r - 1) * NS + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
     std::vector<float> ph(N);
     for (int k = 0; k < N; ++k) {
         const int n = k < N / 2 ? k : k - N;
@@ -399,7 +409,7 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
         const double s = (n == 0) ? 1.0 : std::sin(x) / x;
         ph[k] = (float)std::pow(s, 2 * p);
     }
-    if (cudaMemcpy(c->tw, tw.data(), TW * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) return bail(HERMES_ERR_CUDA);
+    if (cudaMemcpy(c->tw, tw.data(), TW_ENTRIES * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     if (cudaMemcpy(c->phi, ph.data(), N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     if (cudaMemset(c->stab_f, 0, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     if (ensure_host(c, 1024) != HERMES_OK) return bail(HERMES_ERR_NOMEM);

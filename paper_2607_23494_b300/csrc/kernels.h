@@ -40,7 +40,7 @@ struct HarmBatch {
 };
 
 struct Tables {
-    const float2* tw;     // [TW] e^{-2 pi i j / TW}
+    const float2* tw;     // twiddle tables, layout in fft_core.cuh
     const float* phi;     // [N]  sinc^{2p}(pi n / N), FFT order
     const float* stab;    // [p^3] self-pair table (float)
 };

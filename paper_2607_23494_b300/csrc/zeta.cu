@@ -30,7 +30,7 @@ struct ZCfg {
     static constexpr int NZS = ZT / 16;                   // z slices in the Gram phase
     static constexpr int ZPER = N / NZS;                  // z values per slice
     static constexpr int LPZ = LinePad<N>::value + 4;     // line stride: +8 words skew per line
-    static constexpr size_t SMEM_X = (size_t)N * W * sizeof(float2);
+    static constexpr size_t SMEM_X = (size_t)SmemStrided<W>::words(N) * sizeof(float2);
     static constexpr size_t SMEM_Z = (size_t)16 * LPZ * sizeof(float2) + (size_t)N * sizeof(float);
 };
 static_assert(ZCfg<16>::ZPER >= 1 && ZCfg<1024>::NZS == 32, "z-pass layout");
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
             }
-            const SmemLine sm{smem + b * LPZ};
+            const SmemLine<N> sm{smem + b * LPZ};
             fft_line<N, true>(v, t, tw, sm);
 #pragma unroll
             for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
             const int z0 = zs * ZPER;
             for (int z = z0; z < z0 + ZPER; ++z) {
                 const float d = dsm[z];
-                const int zp = z + (z >> 3);
+                const int zp = SmemLine<N>::at(z);
                 float2 a1[4], a2[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
