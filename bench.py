@@ -158,7 +158,7 @@ def run_hermes(args, rank, world, local_rank):
     ctx.window_shells(EDGES2, l_max=4)
     nb = len(EDGES2) - 1
     windows_per_step = 2 * len(ELLS2) * nb
-    batches_per_step = 2 * -(-(len(ELLS2) * nb) // 16)
+    batches_per_step = 2 * len(ELLS2) * -(-nb // 16)
 
     def step(p_, m_):
         ctx.assign(p_)

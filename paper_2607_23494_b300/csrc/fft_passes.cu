@@ -138,7 +138,7 @@ __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
 // C(n,a>0) = 2 cos(2 pi n a / N), is the Fourier transform of the even
 // self-pair overlap table.
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::TS, (Cfg<N>::TS > 512 ? 1 : 2)) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
+__global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
                                                               const WinBatch wb, const Tables tb, int P,
                                                               double* __restrict__ sn_part) {
     using C = Cfg<N>;
@@ -206,33 +206,40 @@ __global__ void __launch_bounds__(Cfg<N>::TS, (Cfg<N>::TS > 512 ? 1 : 2)) k_inv_
     constexpr unsigned MASK = C::TS >= 32 ? 0xffffffffu : ((1u << C::TS) - 1u);
     __shared__ float wsn[NW][MAX_BATCH];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float leg[8];
-    int leg_ell = -1;
-    for (int s = 0; s < wb.S; ++s) {
-        const float* tab = wb.tab[s];
-        const float sc = wb.scale[s];
-        const int ell = wb.ell[s];
-        if (ell != leg_ell) {  // windows come l-major, so this runs once per l in a batch
+    // the batch shares one order l: fold scale * L_l(k_z/k) into the inputs once
 #pragma unroll
-            for (int i = 0; i < 8; ++i) leg[i] = legendre(ell, q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f);
-            leg_ell = ell;
+    for (int i = 0; i < 8; ++i) {
+        const float a = wb.scale * legendre(wb.ell, q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f);
+        v0[i] = cscale(v0[i], a);
+        shat[i] *= a;
+    }
+    const int nbp = wb.nbp;
+    for (int g = 0; g < wb.S; g += 4) {
+        // radial factors of windows g..g+3 at every element: one 16-byte load each
+        float4 tv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tv[i] = __ldg(reinterpret_cast<const float4*>(wb.tab + (size_t)q[i] * nbp + g));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int s = g + j;
+            if (s >= wb.S) break;  // uniform across the block
+            float sn = 0.0f;
+            float2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float K = j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w));
+                sn = fmaf(K, shat[i], sn);
+                v[i] = cscale(v0[i], K);
+            }
+            fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
+            float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
+            sn *= wz;
+#pragma unroll
+            for (int o = (C::TS >= 32 ? 16 : C::TS / 2); o > 0; o >>= 1) sn += __shfl_xor_sync(MASK, sn, o);
+            if (lane == 0) wsn[wid][s] = sn;
         }
-        float sn = 0.0f;
-        float2 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float K = sc * __ldg(tab + q[i]) * leg[i];
-            sn = fmaf(K, shat[i], sn);
-            v[i] = cscale(v0[i], K);
-        }
-        fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
-        float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
-        sn *= wz;
-#pragma unroll
-        for (int o = (C::TS >= 32 ? 16 : C::TS / 2); o > 0; o >>= 1) sn += __shfl_xor_sync(MASK, sn, o);
-        if (lane == 0) wsn[wid][s] = sn;
     }
     __syncthreads();
     if (threadIdx.x < wb.S) {

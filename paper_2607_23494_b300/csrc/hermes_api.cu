@@ -52,8 +52,9 @@ struct hermes_ctx {
     // bins
     int n_bins = 0, l_max = -1;
     int64_t Q = 0;
+    int nbp = 0;                 // bins padded to a multiple of 4
     std::vector<double> edges;
-    float* rad = nullptr;        // [(b*(l_max+1)+l)*Q + q]
+    float* rad = nullptr;        // [(l*Q + q)*nbp + b]
     // state
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
@@ -562,27 +563,36 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     DeviceGuard g(c->device);
     const int64_t Q = table_len(c->N);
     const int nb = n_edges - 1;
+    const int nbp = (nb + 3) & ~3;
     const size_t count = (size_t)nb * (l_max + 1) * Q;
+    const size_t count_dev = (size_t)nbp * (l_max + 1) * Q;
     std::vector<double> host;
     std::vector<float> host32;
     try {
         host.resize(count);
-        host32.resize(count);
+        host32.assign(count_dev, 0.0f);
     } catch (...) {
         return fail(c, HERMES_ERR_NOMEM, "host table of %zu entries", count);
     }
     build_shell_tables(c->L, Q, r_edges, n_edges, l_max, host.data());
-    for (size_t i = 0; i < count; ++i) host32[i] = (float)host[i];
+    // device layout bin-fastest: [(l*Q + q)*nbp + b]
+    for (int b = 0; b < nb; ++b)
+        for (int l = 0; l <= l_max; ++l) {
+            const double* src = host.data() + ((size_t)b * (l_max + 1) + l) * Q;
+            float* dst = host32.data() + (size_t)l * Q * nbp + b;
+            for (int64_t q = 0; q < Q; ++q) dst[(size_t)q * nbp] = (float)src[q];
+        }
     cudaStreamSynchronize(c->stream);
     cudaFree(c->rad);
     c->rad = nullptr;
     c->n_bins = 0;
-    CK(cudaMalloc((void**)&c->rad, count * sizeof(float)), "window tables");
-    CK(cudaMemcpy(c->rad, host32.data(), count * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
+    CK(cudaMalloc((void**)&c->rad, count_dev * sizeof(float)), "window tables");
+    CK(cudaMemcpy(c->rad, host32.data(), count_dev * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
     c->edges.assign(r_edges, r_edges + n_edges);
     c->n_bins = nb;
     c->l_max = l_max;
     c->Q = Q;
+    c->nbp = nbp;
     return HERMES_OK;
 }
 
@@ -601,31 +611,34 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     const int N = c->N, H = c->H, nb = c->n_bins, LM = c->l_max + 1;
     const int nwin = n_ells * nb;
     const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
-    int S = (int)std::min<size_t>(16, std::max<size_t>(1, ((size_t)8 << 30) / win_bytes));
-    S = std::min(S, nwin);
-    S = std::min(S, MAX_BATCH);
+    // windows per launch: up to 16 within an 8 GiB work buffer, a multiple of 4
+    // (bin offsets b0 = 0, S, 2S, ... must stay 16-byte aligned in the tables), at least 4
+    int S = (int)std::min<size_t>(16, ((size_t)8 << 30) / win_bytes) & ~3;
+    S = std::max(S, 4);
+    S = std::min(S, std::max(nb, 1));  // one batch per order when the bins fit
     CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
     const int xb = inv_x_blocks(N), zb = inv_z_blocks(N);
     CK(grow_doubles(c->part, c->part_cap, (size_t)S * (xb + zb)), "partials");
     CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
     const Tables tb = tables_of(c);
-    for (int w0 = 0; w0 < nwin; w0 += S) {
-        WinBatch wb;
-        wb.S = std::min(S, nwin - w0);
-        for (int s = 0; s < wb.S; ++s) {
-            const int widx = w0 + s;
-            const int a = widx / nb, b = widx % nb;
-            const int ell = ells[a];
-            wb.tab[s] = c->rad + ((size_t)b * LM + ell) * c->Q;
-            // (2l+1) i^l for even l
-            wb.scale[s] = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));
-            wb.ell[s] = ell;
+    // batches never cross an order: bins b0 .. b0+S-1 of one l (b0 a multiple of S)
+    for (int a = 0; a < n_ells; ++a) {
+        const int ell = ells[a];
+        for (int b0 = 0; b0 < nb; b0 += S) {
+            WinBatch wb;
+            wb.S = std::min(S, nb - b0);
+            wb.tab = c->rad + (size_t)ell * c->Q * c->nbp + b0;
+            wb.nbp = c->nbp;
+            wb.ell = ell;
+            wb.scale = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));  // (2l+1) i^l, l even
+            const int w0 = a * nb + b0;
+            double* sn_part = c->part;
+            double* dd_part = c->part + (size_t)wb.S * xb;
+            CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st, c->tracer),
+               "inverse passes");
+            CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st, c->tracer), "reduce self-pair sums");
+            CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
         }
-        double* sn_part = c->part;
-        double* dd_part = c->part + (size_t)wb.S * xb;
-        CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st, c->tracer), "inverse passes");
-        CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st, c->tracer), "reduce self-pair sums");
-        CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
     }
     CK(ensure_host(c, (size_t)2 * nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
     CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
@@ -673,7 +686,8 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
                                     std::tgamma(ell + m + 1.0));
             norm *= ((m & 1) ? -1.0 : 1.0) * dfact2(2 * m - 1);
             hb.ylm_norm = (float)(4.0 * M_PI * norm);
-            for (int b = 0; b < nb; ++b) hb.tab[b] = c->rad + ((size_t)b * LM + ell) * c->Q;
+            hb.tab = c->rad + (size_t)ell * c->Q * c->nbp;
+            hb.nbp = c->nbp;
             CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, st, c->tracer), "harmonic fields");
             CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st, c->tracer), "reduce Gram");
         }

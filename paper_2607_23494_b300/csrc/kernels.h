@@ -22,19 +22,25 @@ struct Tracer {
     }
 };  // windows evaluated per launch of the first inverse pass
 
-// One batch of real (xi / xi_l) windows: radial table per window and the
-// Legendre order of its angular factor.  scale multiplies the table value.
+// Radial tables are stored bin-fastest: rad[(l*Q + q)*nbp + b], nbp a multiple
+// of 4, so one 16-byte load returns the values of 4 consecutive bins at |n|^2 = q.
+
+// One batch of real (xi / xi_l) windows: consecutive bins b0 .. b0+S-1 of one
+// even order l.  tab = rad + l*Q*nbp + b0; window s uses tab[q*nbp + s].
 struct WinBatch {
-    const float* tab[MAX_BATCH];
-    float scale[MAX_BATCH];
-    int ell[MAX_BATCH];
+    const float* tab;
+    int nbp;
     int S;
+    int ell;
+    float scale;  // (2l+1) i^l, real for even l
 };
 
-// One batch of complex harmonic windows for a fixed (l, m): one radial table per bin.
+// One batch of complex harmonic windows: all bins of a fixed (l, m).
+// tab = rad + l*Q*nbp; bin b uses tab[q*nbp + b].
 struct HarmBatch {
-    const float* tab[MAX_BATCH];
-    int S;      // number of bins in this batch
+    const float* tab;
+    int nbp;
+    int S;      // number of bins (<= 16)
     int ell, m;
     float ylm_norm;  // N_lm (-1)^m (2m-1)!!  times 4 pi
 };

@@ -76,7 +76,7 @@ __device__ __forceinline__ float2 ylm_unnorm(int ell, int m, int nx, int ny, int
 
 // Z1 ------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_x(const float2* __restrict__ spec, float2* __restrict__ fields,
+__global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restrict__ spec, float2* __restrict__ fields,
                                                          const HarmBatch hb, const Tables tb) {
     using C = ZCfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_x(const float2* __restrict
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
     float2 v0[8];
     int q[8];
-    bool nyq[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int kx = t + i * T;
@@ -102,22 +101,31 @@ __global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_x(const float2* __restrict
         } else {
             d = make_float2(0.f, 0.f);
         }
-        nyq[i] = (kx == H) || (ky == H) || (kz == H);
+        const bool nyq = (kx == H) || (ky == H) || (kz == H);
         const int qq = nx * nx + ny * ny + nz * nz;
-        q[i] = nyq[i] ? 0 : qq;  // table index stays in range on Nyquist lanes
+        q[i] = nyq ? 0 : qq;  // table index stays in range on Nyquist lanes
         const float2 y = ylm_unnorm(hb.ell, hb.m, nx, ny, nz, qq);
         const float2 ang = mul_ipow(cscale(y, hb.ylm_norm * __ldg(tb.phi + kx) * phyz), hb.ell);
-        v0[i] = cmul(d, ang);
+        v0[i] = nyq ? make_float2(0.f, 0.f) : cmul(d, ang);
     }
-    for (int b = 0; b < hb.S; ++b) {
-        const float* tab = hb.tab[b];
-        float2 v[8];
+    const int nbp = hb.nbp;
+    for (int g = 0; g < hb.S; g += 4) {
+        float4 tv[8];  // radial factors of bins g..g+3: one 16-byte load per element
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = nyq[i] ? make_float2(0.f, 0.f) : cscale(v0[i], __ldg(tab + q[i]));
-        fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
-        float2* dst = fields + (size_t)b * n3 + (size_t)ky * N + kz;
+        for (int i = 0; i < 8; ++i) tv[i] = __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
 #pragma unroll
-        for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N] = v[i];
+        for (int j = 0; j < 4; ++j) {
+            const int b = g + j;
+            if (b >= hb.S) break;  // uniform across the block
+            float2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                v[i] = cscale(v0[i], j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
+            fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
+            float2* dst = fields + (size_t)b * n3 + (size_t)ky * N + kz;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N] = v[i];
+        }
     }
 }
 
