@@ -22,6 +22,9 @@
 #include "kernels.h"
 #include "fft_core.cuh"
 
+#include <cooperative_groups.h>
+#include <cstdlib>
+
 namespace hermes {
 
 template <int N>
@@ -325,6 +328,181 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
 }
 
 // ---------------------------------------------------------------------------
+// Fused I2 + I3 on a thread-block cluster.  The (y, k_z) plane of one x and one
+// window (N x N/2 complex, 1 MiB at N = 512) is split over CL CTAs:
+//   y phase : CTA c holds the k_z slab [c*KZ, (c+1)*KZ) for every y and runs the
+//             inverse y FFTs (strided tile, as I2);
+//   exchange: every element is written into the shared memory of the CTA that
+//             owns its y line (distributed shared memory, one cluster barrier);
+//   z phase : CTA c owns the y lines [c*YP, (c+1)*YP): complex-to-real along z
+//             and the contraction with delta, whose slab stays in shared memory
+//             for every window of the batch.
+// Per window the plane is read from HBM once (4 B per cell) and never written.
+namespace cg = cooperative_groups;
+
+template <int N>
+struct YZCfg {
+    static constexpr int H = N / 2;
+    static constexpr int CL = (N >= 512) ? 16 : (N == 256 ? 4 : 1);
+    static constexpr int KZ = H / CL;                 // k_z columns per CTA (y phase)
+    static constexpr int YP = N / CL;                 // y lines per CTA (z phase)
+    static constexpr int THREADS = KZ * (N / 8);
+    static_assert(THREADS == YP * (H / 8), "both phases use every thread");
+    static constexpr int A_WORDS = SmemStrided<KZ>::words(N);
+    static constexpr int LPB = LinePad<H>::value;
+    static constexpr int B_WORDS = YP * LPB;
+    static constexpr size_t SMEM = (size_t)(A_WORDS + B_WORDS + YP * H) * sizeof(float2);
+};
+
+template <int N>
+__device__ __forceinline__ void yz_cluster_sync() {
+    if constexpr (YZCfg<N>::CL > 1) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(YZCfg<N>::THREADS, 1)
+    k_inv_yz_contract(const float2* __restrict__ work, int S, const float* __restrict__ delta,
+                      const float2* __restrict__ tw, double* __restrict__ dd_part) {
+    using C = YZCfg<N>;
+    constexpr int H = N / 2, CL = C::CL, KZ = C::KZ, YP = C::YP, TY = N / 8, TZ = H / 8, LPB = C::LPB;
+    constexpr int NW = (C::THREADS + 31) / 32;
+    constexpr unsigned MASK = C::THREADS >= 32 ? 0xffffffffu : ((1u << C::THREADS) - 1u);
+    extern __shared__ float4 smem_raw[];
+    float2* bufA = reinterpret_cast<float2*>(smem_raw);
+    float2* bufB = bufA + C::A_WORDS;
+    float2* dsl = bufB + C::B_WORDS;  // delta slab, pairs (2j, 2j+1): [YP][H]
+    __shared__ float wdd[NW][MAX_BATCH];
+    const int x = blockIdx.y;
+    int c = 0;
+    if constexpr (CL > 1) c = (int)cg::this_cluster().block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int col = tid % KZ, ty = tid / KZ;          // y phase
+    const int tz = tid % TZ, yl = tid / TZ;           // z phase
+    const int kz0 = c * KZ;
+    const float2* dsrc = reinterpret_cast<const float2*>(delta + ((size_t)x * N + (size_t)c * YP) * N);
+    for (int e = tid; e < YP * H; e += C::THREADS) dsl[e] = dsrc[e];
+    yz_cluster_sync<N>();  // every CTA of the cluster runs before any remote access
+    for (int s = 0; s < S; ++s) {
+        const float2* src = work + (size_t)s * N * N * H + (size_t)x * N * H + kz0 + col;
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = src[(size_t)(ty + i * TY) * H];
+        fft_line<N, true>(v, ty, tw, SmemStrided<KZ>{bufA, col});
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int y = ty + i * TY;
+            float2* rb = bufB;
+            if constexpr (CL > 1) rb = cg::this_cluster().map_shared_rank(bufB, y / YP);
+            rb[(y % YP) * LPB + SmemLine<H>::at(kz0 + col)] = v[i];
+        }
+        yz_cluster_sync<N>();  // the transposed plane is complete in every CTA
+        const SmemLine<H> sm{bufB + yl * LPB};
+        float2 w[8], xm[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = tz + i * TZ;
+            w[i] = sm.ld(k);
+            xm[i] = (k == 0) ? make_float2(0.f, 0.f) : sm.ld(H - k);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = tz + i * TZ;
+            const float2 xc = cconj(xm[i]);
+            const float2 a = cadd(w[i], xc);
+            const float2 wk = cconj(__ldg(tw + N + k));  // e^{+2 pi i k / N}
+            const float2 cc = cmul(wk, csub(w[i], xc));
+            w[i] = make_float2(a.x - cc.y, a.y + cc.x);
+        }
+        fft_line<H, true>(w, tz, tw, sm);
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float2 d = dsl[yl * H + tz + i * TZ];
+            acc = fmaf(d.x, w[i].x, fmaf(d.y, w[i].y, acc));
+        }
+#pragma unroll
+        for (int o = (C::THREADS >= 32 ? 16 : C::THREADS / 2); o > 0; o >>= 1) acc += __shfl_xor_sync(MASK, acc, o);
+        if (lane == 0) wdd[wid][s] = acc;
+        yz_cluster_sync<N>();  // every CTA finished reading its plane slice before the next scatter
+    }
+    __syncthreads();
+    if (tid < S) {
+        double tot = 0.0;
+        for (int q = 0; q < NW; ++q) tot += (double)wdd[q][tid];
+        const size_t nblk = (size_t)gridDim.y * CL;
+        dd_part[(size_t)tid * nblk + (size_t)x * CL + c] = tot;
+    }
+}
+
+// Whether the fused y-z pass can run: N <= 512, a cluster of CL CTAs with SMEM
+// bytes each fits the device, and HERMES_YZ_FUSED is not "0".
+template <int N>
+static bool yz_fused_ok() {
+    if constexpr (N > 512) {
+        return false;
+    } else {
+        const char* env = getenv("HERMES_YZ_FUSED");
+        if (env && env[0] == '0') return false;
+        static int state = -1;  // per N: -1 unknown, 0 no, 1 yes
+        if (state >= 0) return state == 1;
+        using C = YZCfg<N>;
+        state = 0;
+        if (cudaFuncSetAttribute(k_inv_yz_contract<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (C::CL > 8 &&
+            cudaFuncSetAttribute(k_inv_yz_contract<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (C::CL > 1) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C::CL;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(C::CL, N, 1);
+            cfg.blockDim = dim3(C::THREADS, 1, 1);
+            cfg.dynamicSmemBytes = C::SMEM;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_inv_yz_contract<N>, &cfg) != cudaSuccess ||
+                nclusters < 1) {
+                cudaGetLastError();
+                return false;
+            }
+        }
+        state = 1;
+        return true;
+    }
+}
+
+template <int N>
+static cudaError_t launch_yz(const float2* work, int S, const float* delta, const float2* tw, double* dd_part,
+                             cudaStream_t st) {
+    using C = YZCfg<N>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C::CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C::CL, N, 1);
+    cfg.blockDim = dim3(C::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_inv_yz_contract<N>, work, S, delta, tw, dd_part);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 
 template <int N>
@@ -364,6 +542,14 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     tr(K_INV_X_WINDOW, 0, st);
     k_inv_x_window<N><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb, P, sn_part);
     tr(K_INV_X_WINDOW, 1, st);
+    if constexpr (N <= 512) {
+        if (yz_fused_ok<N>()) {
+            tr(K_INV_YZ_CONTRACT, 0, st);
+            e = launch_yz<N>(work, wb.S, delta, tb.tw, dd_part, st);
+            tr(K_INV_YZ_CONTRACT, 1, st);
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
+    }
     dim3 g2(H / C::W, N, wb.S);
     tr(K_INV_Y, 0, st);
     k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
@@ -432,6 +618,16 @@ static int z_blocks_of(int N) {
     return 0;
 }
 int inv_x_blocks(int N) { return x_blocks_of(N); }
-int inv_z_blocks(int N) { return z_blocks_of(N); }
+int inv_z_blocks(int N) {
+    switch (N) {
+        case 16: return yz_fused_ok<16>() ? 16 * YZCfg<16>::CL : z_blocks_of(N);
+        case 32: return yz_fused_ok<32>() ? 32 * YZCfg<32>::CL : z_blocks_of(N);
+        case 64: return yz_fused_ok<64>() ? 64 * YZCfg<64>::CL : z_blocks_of(N);
+        case 128: return yz_fused_ok<128>() ? 128 * YZCfg<128>::CL : z_blocks_of(N);
+        case 256: return yz_fused_ok<256>() ? 256 * YZCfg<256>::CL : z_blocks_of(N);
+        case 512: return yz_fused_ok<512>() ? 512 * YZCfg<512>::CL : z_blocks_of(N);
+    }
+    return z_blocks_of(N);
+}
 
 }  // namespace hermes

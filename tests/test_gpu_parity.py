@@ -236,3 +236,22 @@ def test_zeta_multipoles_match_oracle(N, nb, l_max):
     _close(got, ref)
     for ell in range(l_max + 1):
         np.testing.assert_array_equal(got[ell], got[ell].T)
+
+
+@pytest.mark.parametrize("N,L,n", [(64, 300.0, 30000), (256, 1000.0, 200000), (512, 1000.0, 300000)])
+def test_fused_yz_pass_matches_three_pass_path(N, L, n, monkeypatch):
+    # the cluster kernel (inverse y + c2r z + contraction in one pass) against the
+    # separate y and z passes, and both against the oracle where it is affordable
+    H = _hermes()
+    pos = S.lognormal_catalogue(n, L, seed=N, n_grid=64)
+    edges = np.linspace(L / 100, L / 10, 6)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HERMES_YZ_FUSED", flag)
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(edges, l_max=2)
+            ctx.assign(pos)
+            res[flag] = ctx.xi_multipoles([0, 2])
+    np.testing.assert_allclose(res["1"], res["0"], rtol=2e-5, atol=1e-7)
+    if N <= 64:
+        _close(res["1"], O.xi_multipoles(pos, None, N, L, 4, edges, ells=(0, 2))["xi"])
