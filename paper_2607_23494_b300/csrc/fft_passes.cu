@@ -435,15 +435,17 @@ __global__ void __launch_bounds__(YZCfg<N>::THREADS, 1)
     }
 }
 
-// Whether the fused y-z pass can run: N <= 512, a cluster of CL CTAs with SMEM
-// bytes each fits the device, and HERMES_YZ_FUSED is not "0".
+// Whether the fused y-z pass runs: only when HERMES_YZ_FUSED=1 (opt-in: with one
+// 1024-thread CTA per SM and two cluster barriers per window it is latency-bound
+// and slower than the separate y and z passes on B300), N <= 512, and a cluster
+// of CL CTAs with SMEM bytes each fits the device.
 template <int N>
 static bool yz_fused_ok() {
     if constexpr (N > 512) {
         return false;
     } else {
         const char* env = getenv("HERMES_YZ_FUSED");
-        if (env && env[0] == '0') return false;
+        if (!env || env[0] != '1') return false;
         static int state = -1;  // per N: -1 unknown, 0 no, 1 yes
         if (state >= 0) return state == 1;
         using C = YZCfg<N>;

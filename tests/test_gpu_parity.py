@@ -246,7 +246,7 @@ def test_fused_yz_pass_matches_three_pass_path(N, L, n, monkeypatch):
     pos = S.lognormal_catalogue(n, L, seed=N, n_grid=64)
     edges = np.linspace(L / 100, L / 10, 6)
     res = {}
-    for flag in ("1", "0"):
+    for flag in ("1", "0"):  # opt-in cluster kernel vs the default three-pass path
         monkeypatch.setenv("HERMES_YZ_FUSED", flag)
         with H.Context(L, N, 4) as ctx:
             ctx.window_shells(edges, l_max=2)
