@@ -374,6 +374,21 @@ def run_profile_case():
     print(json.dumps({"profile_case": "xi 512^3, 5 windows", "xi": [float(v) for v in x]}))
 
 
+def run_profile_zeta():
+    """Small zeta case for ncu captures: 256^3 field, 200k points, 16 shells, l_max = 1."""
+    import torch
+    from paper_2607_23494_b300 import Context
+    from synthetic import catalogues as S
+    pos = torch.from_numpy(S.poisson_uniform(200_000, L3, seed=8)).cuda()
+    ctx = Context(L3, 256, 4)
+    ctx.window_shells(np.linspace(10.0, 170.0, 17), l_max=1)
+    ctx.assign(pos)
+    z = ctx.zeta_multipoles()
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_case": "zeta 256^3, 16 shells, l_max 1", "zeta00": float(z[0, 0, 0])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,9 +398,13 @@ def main():
     ap.add_argument("--no-zeta", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
+    ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case()
+        return 0
+    if args.profile_zeta:
+        run_profile_zeta()
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

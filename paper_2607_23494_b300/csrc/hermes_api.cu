@@ -675,6 +675,7 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
     const int nlm = LM * (LM + 1) / 2;
     CK(grow_doubles(c->red, c->red_cap, (size_t)256 * nlm), "reduction buffer");
     const Tables tb = tables_of(c);
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     int lm = 0;
     for (int ell = 0; ell < LM; ++ell) {
         for (int m = 0; m <= ell; ++m, ++lm) {
@@ -688,14 +689,19 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
             hb.ylm_norm = (float)(4.0 * M_PI * norm);
             hb.tab = c->rad + (size_t)ell * c->Q * c->nbp;
             hb.nbp = c->nbp;
-            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, st, c->tracer), "harmonic fields");
+            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, c->err, st, c->tracer),
+               "harmonic fields");
             CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st, c->tracer), "reduce Gram");
         }
     }
     CK(ensure_host(c, (size_t)256 * nlm) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(ensure_host(c, (size_t)256 * nlm + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
     CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)256 * nlm * sizeof(double), cudaMemcpyDeviceToHost, st),
        "read Gram");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)256 * nlm);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
     CK(cudaStreamSynchronize(st), "zeta");
+    if (*hflag & 2u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on the tensor-core pipeline gave up");
     const double nn = (double)N;
     const double scale = 1.0 / (4.0 * M_PI * std::pow(nn, 9));
     lm = 0;
@@ -785,7 +791,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract"};
+    "inv_yz_contract", "zeta_z_gram_tc"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;

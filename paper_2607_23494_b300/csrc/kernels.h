@@ -10,7 +10,7 @@ constexpr int MAX_BATCH = 32;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -77,6 +77,6 @@ cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double*
 // zeta.cu
 int zeta_z_blocks(int N);
 cudaError_t launch_zeta_lm(int N, const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                           const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr);
+                           const Tables& tb, double* gram_part, unsigned* err, cudaStream_t st, const Tracer& tr);
 
 }  // namespace hermes

@@ -45,6 +45,44 @@ __device__ __forceinline__ bool node_rule(float x, float s, int N, int wrap, int
     return true;
 }
 
+// Adds w*b[c] to row[(z0 + c) mod N], c = 0..P-1, with as few atomic
+// operations as the alignment allows: the run of P contiguous cells is cut at
+// 16- and 8-byte boundaries into float4 / float2 / float atomics (vector
+// atomics: sm_90+, natural alignment; rows start 16-byte aligned as N >= 16).
+// A is (z0 mod 4), known per instantiation, so every index is static.
+template <int P, int A, int C>
+__device__ __forceinline__ void add_aligned(float* p, float w, const float (&b)[P]) {
+    if constexpr (C < P) {
+        constexpr int al = (A + C) & 3;
+        if constexpr (al == 0 && C + 4 <= P) {
+            atomicAdd(reinterpret_cast<float4*>(p + C), make_float4(w * b[C], w * b[C + 1], w * b[C + 2], w * b[C + 3]));
+            add_aligned<P, A, C + 4>(p, w, b);
+        } else if constexpr ((al & 1) == 0 && C + 2 <= P) {
+            atomicAdd(reinterpret_cast<float2*>(p + C), make_float2(w * b[C], w * b[C + 1]));
+            add_aligned<P, A, C + 2>(p, w, b);
+        } else {
+            atomicAdd(p + C, w * b[C]);
+            add_aligned<P, A, C + 1>(p, w, b);
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void add_run(float* row, int z0, int N, float w, const float (&b)[P]) {
+    if (z0 + P > N) {  // the run wraps around the periodic edge: scalar atomics
+#pragma unroll
+        for (int c = 0; c < P; ++c) atomicAdd(row + ((z0 + c) & (N - 1)), w * b[c]);
+        return;
+    }
+    float* p = row + z0;
+    switch (z0 & 3) {
+        case 0: add_aligned<P, 0, 0>(p, w, b); break;
+        case 1: add_aligned<P, 1, 0>(p, w, b); break;
+        case 2: add_aligned<P, 2, 0>(p, w, b); break;
+        default: add_aligned<P, 3, 0>(p, w, b); break;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, const float* __restrict__ w,
                                                  int64_t n, float* __restrict__ grid, float s, int N, int wrap,
@@ -62,6 +100,7 @@ __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, 
             atomicOr(err, 1u);
             continue;
         }
+        const int z0 = fz & msk;
 #pragma unroll
         for (int a = 0; a < P; ++a) {
             const int ix = (fx + a) & msk;
@@ -71,8 +110,7 @@ __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, 
                 const int iy = (fy + b) & msk;
                 const float wab = wa * by[b];
                 float* row = grid + ((size_t)ix * N + iy) * N;
-#pragma unroll
-                for (int c = 0; c < P; ++c) atomicAdd(row + ((fz + c) & msk), wab * bz[c]);
+                add_run<P>(row, z0, N, wab, bz);
             }
         }
     }

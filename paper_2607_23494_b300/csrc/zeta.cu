@@ -17,6 +17,8 @@
 #include "kernels.h"
 #include "fft_core.cuh"
 
+#include <cstdlib>
+
 namespace hermes {
 
 template <int N>
@@ -252,10 +254,253 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     for (int e = tid; e < 256; e += blockDim.x) part[(size_t)e * gridDim.x + blockIdx.x] = tot[e];
 }
 
+// Z3 on the tensor cores ---------------------------------------------------
+// Same line loop and z transforms as k_zeta_z_gram; the Gram runs on tcgen05.
+// With K = (z, Re/Im) the Gram is a plain product G = A B:
+//   A[r][k] = delta(z) * X_b(k),  B[k][c] = X_b'(k),  X_b(2z) = Re a_b(z), X_b(2z+1) = Im a_b(z).
+// Split precision with TF32: x = x_hi + x_lo (x_hi = tf32(x), x_lo = x - x_hi),
+// one MMA computes every needed term: A rows = [Y_hi (16 bins); Y_lo (16 bins);
+// 96 zero rows] (M = 128), B columns = [X_hi | X_lo] (N = 32), so
+//   G = D[0:16, 0:16] + D[0:16, 16:32] + D[16:32, 0:16]   (hi*hi + hi*lo + lo*hi)
+// with D accumulated in float32 in tensor memory over one line and drained to
+// float64 (two accumulators alternate between lines).  Operands are staged in shared memory in the no-swizzle K-major
+// layout (8-row x 16-byte core matrices), K chunks of 64, double-buffered; one
+// thread issues the MMAs and commits them to an mbarrier per buffer.  Every
+// wait is bounded: on expiry the kernel sets err bit 2 and carries on, so the
+// host reports HERMES_ERR_TIMEOUT instead of hanging.
+namespace tc {
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the completion of phase `parity` of barrier b; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    for (int i = 0; i < (1 << 20); ++i)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// shared-memory matrix descriptor: no swizzle, K-major, start / LBO / SBO in bytes
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// kind::tf32, D f32, A and B K-major, M = 128, N = 32
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr int KCH = 64;                 // K elements per staged chunk (32 z values)
+constexpr int CORE_ROW_GROUP = 2048;    // bytes between 8-row groups (16 K core matrices x 128 B)
+constexpr int A_BYTES = 128 * KCH * 4;  // 32 KiB
+constexpr int B_BYTES = 32 * KCH * 4;   // 8 KiB
+__device__ __forceinline__ uint32_t off(int r, int k) {
+    return (uint32_t)((r >> 3) * CORE_ROW_GROUP + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+}  // namespace tc
+
+template <int N>
+struct ZTcCfg {
+    static constexpr int LPZ = ZCfg<N>::LPZ;
+    static constexpr size_t OPS = 2 * (size_t)(tc::A_BYTES + tc::B_BYTES);  // 80 KiB, 1024-aligned start
+    static constexpr size_t SMEM = OPS + (size_t)16 * LPZ * sizeof(float2) + (size_t)N * sizeof(float);
+};
+
+template <int N>
+__global__ void __launch_bounds__(ZCfg<N>::ZT, 1) k_zeta_z_gram_tc(const float2* __restrict__ fields, int S,
+                                                                    const float* __restrict__ delta,
+                                                                    const float2* __restrict__ tw,
+                                                                    double* __restrict__ part,
+                                                                    unsigned* __restrict__ err) {
+    using C = ZCfg<N>;
+    constexpr int T = C::T, GB = C::GB, LPZ = C::LPZ;
+    extern __shared__ __align__(1024) unsigned char zsm[];
+    unsigned char* opA = zsm;                                   // 2 x A chunk
+    unsigned char* opB = zsm + 2 * tc::A_BYTES;                 // 2 x B chunk
+    float2* E = reinterpret_cast<float2*>(zsm + ZTcCfg<N>::OPS);  // 16 transformed bin lines
+    float* dsm = reinterpret_cast<float*>(E + 16 * LPZ);
+    __shared__ __align__(8) uint64_t mbar[2];   // "empty": MMAs reading buffer b finished
+    __shared__ __align__(8) uint64_t fullb[2];  // "full": every warp wrote its part of buffer b
+    __shared__ uint32_t tmem_slot;
+    const size_t n3 = (size_t)N * N * N;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int bb = tid / T, t = tid % T;
+
+    // zero the operand buffers once (rows 32..127 of A stay zero for good)
+    for (int e = tid; e < (int)(ZTcCfg<N>::OPS / 16); e += blockDim.x)
+        reinterpret_cast<float4*>(zsm)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int NWARPS = ZCfg<N>::ZT / 32;
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&fullb[0], NWARPS);
+        tc::mbar_init(&fullb[1], NWARPS);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (wid == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc::su32(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t dtm = tmem_slot;
+
+    double acc64[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc64[c] = 0.0;
+    uint32_t uses[2] = {0, 0}, done[2] = {0, 0};
+    bool timed_out = false;
+    const int rounds = (S + GB - 1) / GB;
+
+    // Line L accumulates into TMEM columns [32 (L & 1), +32).  The accumulator of
+    // line L-1 is drained to float64 while line L is transformed, so each float32
+    // accumulation runs over one line (K = 2N) only.
+    auto wait_all = [&]() {
+#pragma unroll
+        for (int bf = 0; bf < 2; ++bf)
+            if (done[bf] < uses[bf]) {
+                if (!tc::mbar_wait(&mbar[bf], (uses[bf] - 1) & 1)) timed_out = true;
+                done[bf] = uses[bf];
+            }
+    };
+    auto drain = [&](uint32_t col) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (wid == 0) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(dtm + col));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // row = lane: rows 0..15 hold hi*hi (cols 0..15) and hi*lo (16..31); rows 16..31 lo*hi
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                acc64[c] += (double)__uint_as_float(r[c]) + (lane < 16 ? (double)__uint_as_float(r[16 + c]) : 0.0);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+
+    int nlines = 0;
+    for (size_t line = blockIdx.x; line < (size_t)N * N; line += gridDim.x, ++nlines) {
+        for (int r = 0; r < rounds; ++r) {
+            const int b = r * GB + bb;
+            float2 v[8];
+            if (b < S) {
+                const float2* src = fields + (size_t)b * n3 + line * N;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = src[t + i * T];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
+            }
+            const SmemLine<N> sm{E + b * LPZ};
+            fft_line<N, true>(v, t, tw, sm);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
+        }
+        for (int z = tid; z < N; z += blockDim.x) dsm[z] = delta[line * N + z];
+        if (nlines > 0) {  // line L-1 is complete by now in all likelihood: drain its accumulator
+            wait_all();
+            drain(32u * (uint32_t)((nlines - 1) & 1));
+        }
+        __syncthreads();
+        const uint32_t dcol = dtm + 32u * (uint32_t)(nlines & 1);
+        for (int z0 = 0; z0 < N; z0 += tc::KCH / 2) {
+            const int bf = (int)((uses[0] + uses[1]) & 1);
+            if (done[bf] < uses[bf]) {  // the MMAs that last read this buffer must be finished
+                if (!tc::mbar_wait(&mbar[bf], (uses[bf] - 1) & 1)) timed_out = true;
+                done[bf] = uses[bf];
+            }
+            unsigned char* A = opA + bf * tc::A_BYTES;
+            unsigned char* B = opB + bf * tc::B_BYTES;
+            for (int e = tid; e < 16 * (tc::KCH / 2); e += blockDim.x) {
+                const int b = e & 15, zl = e >> 4, z = z0 + zl;
+                const float2 x = E[b * LPZ + SmemLine<N>::at(z)];
+                const float d = dsm[z];
+                const float yr = d * x.x, yi = d * x.y;
+                const uint32_t xrh = tc::to_tf32(x.x), xih = tc::to_tf32(x.y);
+                const uint32_t yrh = tc::to_tf32(yr), yih = tc::to_tf32(yi);
+                const float xrl = x.x - __uint_as_float(xrh), xil = x.y - __uint_as_float(xih);
+                const float yrl = yr - __uint_as_float(yrh), yil = yi - __uint_as_float(yih);
+                const int k = 2 * zl;
+                *reinterpret_cast<float2*>(A + tc::off(b, k)) = make_float2(__uint_as_float(yrh), __uint_as_float(yih));
+                *reinterpret_cast<float2*>(A + tc::off(16 + b, k)) = make_float2(yrl, yil);
+                *reinterpret_cast<float2*>(B + tc::off(b, k)) = make_float2(__uint_as_float(xrh), __uint_as_float(xih));
+                *reinterpret_cast<float2*>(B + tc::off(16 + b, k)) = make_float2(xrl, xil);
+            }
+            // make this thread's operand stores visible to the tensor-core proxy, then
+            // one arrival per warp on the buffer's "full" barrier
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::su32(&fullb[bf])) : "memory");
+            if (tid == 0) {
+                if (!tc::mbar_wait(&fullb[bf], uses[bf] & 1)) timed_out = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = tc::su32(A), b0 = tc::su32(B);
+#pragma unroll
+                for (int kk = 0; kk < tc::KCH / 8; ++kk) {
+                    const uint64_t ad = tc::desc(a0 + kk * 256, 128, tc::CORE_ROW_GROUP);
+                    const uint64_t bd = tc::desc(b0 + kk * 256, 128, tc::CORE_ROW_GROUP);
+                    const uint32_t accum = (z0 == 0 && kk == 0) ? 0u : 1u;  // each line starts afresh
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(tc::IDESC), "r"(accum));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tc::su32(&mbar[bf]))
+                             : "memory");
+            }
+            __syncwarp();
+            ++uses[bf];
+        }
+    }
+    wait_all();
+    if (nlines > 0) drain(32u * (uint32_t)((nlines - 1) & 1));
+    __syncthreads();
+    if (timed_out && lane == 0) atomicOr(err, 2u);
+    // rows 0..15 plus rows 16..31 (lo*hi): G[row][c]
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc64[c] += __shfl_down_sync(0xffffffffu, acc64[c], 16);
+    if (wid == 0 && lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) part[(size_t)(lane * 16 + c) * gridDim.x + blockIdx.x] = acc64[c];
+    }
+    __syncthreads();
+    if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(dtm));
+}
+
+// The tensor-core Gram runs for N >= 32 when HERMES_ZETA_TC=1.  It is correct
+// (split-TF32, parity-tested) but not the default: the pass is bound by loading
+// the bin lines and by the z transforms' block barriers (tensor pipe ~5% busy),
+// and the per-chunk operand staging makes it slower than the SIMT Gram.
+static bool zeta_tc_enabled(int N) {
+    if (N < 32) return false;
+    const char* env = getenv("HERMES_ZETA_TC");
+    return env && env[0] == '1';
+}
+
 template <int N>
 static int zeta_blocks_impl() {
     const int lines = N * N;
-    return lines < 296 ? lines : 296;
+    const int cap = zeta_tc_enabled(N) ? 148 : 296;  // the tensor-core kernel keeps one CTA per SM
+    return lines < cap ? lines : cap;
 }
 
 int zeta_z_blocks(int N) {
@@ -273,12 +518,11 @@ int zeta_z_blocks(int N) {
 
 template <int N>
 static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                             const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr) {
+                             const Tables& tb, double* gram_part, unsigned* err, cudaStream_t st, const Tracer& tr) {
     using C = ZCfg<N>;
     cudaError_t e;
     if ((e = allow_smem_z(k_zeta_x<N>, C::SMEM_X)) != cudaSuccess) return e;
     if ((e = allow_smem_z(k_zeta_y<N>, C::SMEM_X)) != cudaSuccess) return e;
-    if ((e = allow_smem_z(k_zeta_z_gram<N>, C::SMEM_Z)) != cudaSuccess) return e;
     dim3 g1(N / C::W, N, 1);
     tr(K_ZETA_X, 0, st);
     k_zeta_x<N><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hb, tb);
@@ -287,6 +531,17 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     tr(K_ZETA_Y, 0, st);
     k_zeta_y<N><<<g2, C::TS, C::SMEM_X, st>>>(fields, tb.tw);
     tr(K_ZETA_Y, 1, st);
+    if constexpr (N >= 32) {
+        if (zeta_tc_enabled(N)) {
+            if ((e = allow_smem_z(k_zeta_z_gram_tc<N>, ZTcCfg<N>::SMEM)) != cudaSuccess) return e;
+            tr(K_ZETA_Z_GRAM_TC, 0, st);
+            k_zeta_z_gram_tc<N><<<zeta_blocks_impl<N>(), C::ZT, ZTcCfg<N>::SMEM, st>>>(fields, hb.S, delta, tb.tw,
+                                                                                    gram_part, err);
+            tr(K_ZETA_Z_GRAM_TC, 1, st);
+            return cudaGetLastError();
+        }
+    }
+    if ((e = allow_smem_z(k_zeta_z_gram<N>, C::SMEM_Z)) != cudaSuccess) return e;
     tr(K_ZETA_Z_GRAM, 0, st);
     k_zeta_z_gram<N><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw, gram_part);
     tr(K_ZETA_Z_GRAM, 1, st);
@@ -294,16 +549,16 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
 }
 
 cudaError_t launch_zeta_lm(int N, const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
-                           const Tables& tb, double* gram_part, cudaStream_t st, const Tracer& tr) {
+                           const Tables& tb, double* gram_part, unsigned* err, cudaStream_t st, const Tracer& tr) {
     if (hb.S < 1 || hb.S > 16) return cudaErrorInvalidValue;
     switch (N) {
-        case 16: return zeta_impl<16>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 32: return zeta_impl<32>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 64: return zeta_impl<64>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 128: return zeta_impl<128>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 256: return zeta_impl<256>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 512: return zeta_impl<512>(spec, fields, delta, hb, tb, gram_part, st, tr);
-        case 1024: return zeta_impl<1024>(spec, fields, delta, hb, tb, gram_part, st, tr);
+        case 16: return zeta_impl<16>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 32: return zeta_impl<32>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 64: return zeta_impl<64>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 128: return zeta_impl<128>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 256: return zeta_impl<256>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 512: return zeta_impl<512>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
+        case 1024: return zeta_impl<1024>(spec, fields, delta, hb, tb, gram_part, err, st, tr);
     }
     return cudaErrorInvalidValue;
 }

@@ -255,3 +255,26 @@ def test_fused_yz_pass_matches_three_pass_path(N, L, n, monkeypatch):
     np.testing.assert_allclose(res["1"], res["0"], rtol=2e-5, atol=1e-7)
     if N <= 64:
         _close(res["1"], O.xi_multipoles(pos, None, N, L, 4, edges, ells=(0, 2))["xi"])
+
+
+@pytest.mark.parametrize("N,nb", [(32, 16), (64, 7), (128, 16)])
+def test_zeta_tensor_core_gram_matches_simt_and_oracle(N, nb, monkeypatch):
+    # the tcgen05 split-TF32 Gram (opt-in) against the float32 SIMT Gram (default),
+    # and both against the oracle at 32^3
+    H = _hermes()
+    L, p, l_max = 3.0 * N, 4, 3
+    pos = S.mixed_poisson_sp(8000, L, seed=N + 3 * nb)
+    edges = np.linspace(L / 40, L / 3, nb + 1)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HERMES_ZETA_TC", flag)
+        with H.Context(L, N, p) as ctx:
+            ctx.assign(pos)
+            ctx.window_shells(edges, l_max=l_max)
+            res[flag] = ctx.zeta_multipoles()
+    _close(res["1"], res["0"], rel=1e-4, ab=1e-7)
+    if N == 32:
+        eps, sw, _ = O.assign(pos, None, N, L, p)
+        ref, _ = O.zeta_multipoles(O.delta_from_eps(eps, sw), N, L, p, edges, l_max)
+        _close(res["1"], ref)
+        _close(res["0"], ref)
