@@ -21,6 +21,7 @@
 //      fields never return to HBM.
 #include "kernels.h"
 #include "fft_core.cuh"
+#include "async_copy.cuh"
 
 #include <cooperative_groups.h>
 #include <cstdlib>
@@ -38,6 +39,7 @@ struct Cfg {
     static constexpr int ZTHREADS = TZ * LZ;
     static constexpr size_t SMEM_STRIDED = (size_t)SmemStrided<W>::words(N) * sizeof(float2);
     static constexpr size_t SMEM_Z = (size_t)LZ * LinePad<MZ>::value * sizeof(float2);
+    static constexpr size_t SMEM_Z3 = SMEM_Z + (size_t)2 * LZ * (N / 2) * sizeof(float2);  // + double stage
 };
 
 template <class K>
@@ -260,22 +262,49 @@ template <int N>
 __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(const float2* __restrict__ work, int S,
                                                                              const float* __restrict__ delta,
                                                                              const float2* __restrict__ tw,
-                                                                             double* __restrict__ dd_part) {
+                                                                             double* __restrict__ dd_part,
+                                                                             unsigned* __restrict__ err) {
     using C = Cfg<N>;
-    constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value, H = N / 2;
+    constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value, H = N / 2, LZ = C::LZ;
     constexpr int NW = C::ZTHREADS / 32;
-    extern __shared__ float2 smem[];
+    constexpr uint32_t STAGE = (uint32_t)(LZ * H * sizeof(float2));  // the block's LZ lines of one window
+    // Window s+1 is fetched by one bulk copy (the LZ lines are contiguous) into
+    // the other half of a double buffer while window s is transformed.
+    extern __shared__ __align__(16) float2 smem[];
+    float2* stage = smem;                  // [2][LZ * H], dense
+    float2* lines = smem + 2 * LZ * H;     // LZ padded lines for the FFT exchanges
+    __shared__ __align__(8) uint64_t full[2];
     __shared__ float wdd[NW][MAX_BATCH];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemLine<M> sm{smem + li * LP};
+    const size_t line0 = (size_t)blockIdx.x * LZ;
+    const size_t line = line0 + li;
+    const SmemLine<M> sm{lines + li * LP};
+    if (threadIdx.x == 0) {
+        ac::mbar_init(&full[0], 1);
+        ac::mbar_init(&full[1], 1);
+        ac::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && S > 0) {
+        ac::mbar_expect_tx(&full[0], STAGE);
+        ac::bulk_g2s(stage, work + line0 * H, STAGE, &full[0]);
+    }
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
     float2 d2[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) d2[i] = dl[t + i * T];
+    bool late = false;
     for (int s = 0; s < S; ++s) {
-        const float2* X = work + (size_t)s * N * N * H + line * H;
+        __syncthreads();  // every thread is done with the buffer that the next copy overwrites
+        if (threadIdx.x == 0 && s + 1 < S) {
+            ac::fence_proxy_async();
+            ac::mbar_expect_tx(&full[(s + 1) & 1], STAGE);
+            ac::bulk_g2s(stage + ((s + 1) & 1) * LZ * H, work + (size_t)(s + 1) * N * N * H + line0 * H, STAGE,
+                         &full[(s + 1) & 1]);
+        }
+        if (!ac::mbar_wait(&full[s & 1], (s >> 1) & 1)) late = true;
+        const float2* X = stage + (s & 1) * LZ * H + li * H;
         float2 v[8], xm[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = X[t + i * T];
@@ -291,14 +320,10 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
                 for (int i = 1; i < 8; ++i) xm[i] = v[8 - i];
             }
         } else {
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
-            __syncthreads();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int k = t + i * T;
-                xm[i] = (k == 0) ? make_float2(0.f, 0.f) : sm.ld(M - k);
+                xm[i] = (k == 0) ? make_float2(0.f, 0.f) : X[M - k];
             }
         }
 #pragma unroll
@@ -319,6 +344,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) wdd[wid][s] = acc;
     }
+    if (late) atomicOr(err, 4u);
     __syncthreads();
     if (threadIdx.x < S) {
         double tot = 0.0;
@@ -532,13 +558,13 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 
 template <int N>
 static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                                const Tables& tb, int P, double* sn_part, double* dd_part, cudaStream_t st,
-                                const Tracer& tr) {
+                                const Tables& tb, int P, double* sn_part, double* dd_part, unsigned* err,
+                                cudaStream_t st, const Tracer& tr) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_inv_x_window<N>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z3)) != cudaSuccess) return e;
     const long long H = N / 2;
     dim3 g1(H / C::W, N, 1);
     tr(K_INV_X_WINDOW, 0, st);
@@ -557,7 +583,8 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
-    k_inv_z_c2r_contract<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(work, wb.S, delta, tb.tw, dd_part);
+    k_inv_z_c2r_contract<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw, dd_part,
+                                                                            err);
     tr(K_INV_Z_C2R_CONTRACT, 1, st);
     return cudaGetLastError();
 }
@@ -589,8 +616,9 @@ cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double*
 }
 
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                              const Tables& tb, double* sn_part, double* dd_part, cudaStream_t st, const Tracer& tr) {
-#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, st, tr)
+                              const Tables& tb, double* sn_part, double* dd_part, unsigned* err, cudaStream_t st,
+                              const Tracer& tr) {
+#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, err, st, tr)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }

@@ -608,7 +608,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     }
     DeviceGuard g(c->device);
     cudaStream_t st = c->stream;
-    const int N = c->N, H = c->H, nb = c->n_bins, LM = c->l_max + 1;
+    const int N = c->N, H = c->H, nb = c->n_bins;
     const int nwin = n_ells * nb;
     const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
     // windows per launch: up to 16 within an 8 GiB work buffer, a multiple of 4
@@ -621,6 +621,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     CK(grow_doubles(c->part, c->part_cap, (size_t)S * (xb + zb)), "partials");
     CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
     const Tables tb = tables_of(c);
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     // batches never cross an order: bins b0 .. b0+S-1 of one l (b0 a multiple of S)
     for (int a = 0; a < n_ells; ++a) {
         const int ell = ells[a];
@@ -634,15 +635,19 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
             const int w0 = a * nb + b0;
             double* sn_part = c->part;
             double* dd_part = c->part + (size_t)wb.S * xb;
-            CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, st, c->tracer),
+            CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, c->err, st,
+                                 c->tracer),
                "inverse passes");
             CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st, c->tracer), "reduce self-pair sums");
             CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
         }
     }
-    CK(ensure_host(c, (size_t)2 * nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(ensure_host(c, (size_t)2 * nwin + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
     CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
     CK(cudaStreamSynchronize(st), "xi");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
     const double n3 = (double)N * N * N;
     const double n6 = n3 * n3;
     const double eps_bar = c->sum_w / n3;

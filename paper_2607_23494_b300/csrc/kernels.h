@@ -70,7 +70,7 @@ int inv_x_blocks(int N);
 int inv_z_blocks(int N);
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta,
                               const WinBatch& wb, const Tables& tb, double* sn_part, double* dd_part,
-                              cudaStream_t st, const Tracer& tr);
+                              unsigned* err, cudaStream_t st, const Tracer& tr);
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr);
 

@@ -16,6 +16,7 @@
 // negative m recovered by conjugation as in Sec. 4.4).
 #include "kernels.h"
 #include "fft_core.cuh"
+#include "async_copy.cuh"
 
 #include <cstdlib>
 
@@ -33,7 +34,10 @@ struct ZCfg {
     static constexpr int ZPER = N / NZS;                  // z values per slice
     static constexpr int LPZ = LinePad<N>::value + 4;     // line stride: +8 words skew per line
     static constexpr size_t SMEM_X = (size_t)SmemStrided<W>::words(N) * sizeof(float2);
-    static constexpr size_t SMEM_Z = (size_t)16 * LPZ * sizeof(float2) + (size_t)N * sizeof(float);
+    // z pass: 16 padded bin lines, two delta lines and (N <= 512) a stage for the next line's bins
+    static constexpr bool PREFETCH = N <= 512;
+    static constexpr size_t SMEM_Z = (size_t)16 * LPZ * sizeof(float2) + (size_t)2 * N * sizeof(float) +
+                                     (PREFETCH ? (size_t)16 * N * sizeof(float2) : 0);
 };
 static_assert(ZCfg<16>::ZPER >= 1 && ZCfg<1024>::NZS == 32, "z-pass layout");
 
@@ -157,12 +161,17 @@ template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __restrict__ fields, int S,
                                                               const float* __restrict__ delta,
                                                               const float2* __restrict__ tw,
-                                                              double* __restrict__ part) {
+                                                              double* __restrict__ part,
+                                                              unsigned* __restrict__ err) {
     using C = ZCfg<N>;
     constexpr int T = C::T, GB = C::GB, LPZ = C::LPZ, ZPER = C::ZPER;
-    extern __shared__ float2 smem[];
+    constexpr bool PREF = C::PREFETCH;
+    extern __shared__ __align__(16) float2 smem[];
     __shared__ double tot[256];
-    float* dsm = reinterpret_cast<float*>(smem + 16 * LPZ);
+    __shared__ __align__(8) uint64_t full;
+    float* dsm2 = reinterpret_cast<float*>(smem + 16 * LPZ);      // [2][N] delta lines
+    float2* stage = reinterpret_cast<float2*>(dsm2 + 2 * N);       // [16][N] bin lines of the next line
+    bool late = false;
     const size_t n3 = (size_t)N * N * N;
     const int tid = threadIdx.x;
     const int bb = tid / T, t = tid % T;
@@ -180,14 +189,37 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
         }
     const int rounds = (S + GB - 1) / GB;
     int since_flush = 0;
-    for (size_t line = blockIdx.x; line < (size_t)N * N; line += gridDim.x) {
+    // fetch the S bin lines and the delta line of `line` by bulk copies
+    auto fetch = [&](size_t ln, int slot) {
+        ac::mbar_expect_tx(&full, (uint32_t)(S * N * sizeof(float2) + N * sizeof(float)));
+        for (int b = 0; b < S; ++b) ac::bulk_g2s(stage + b * N, fields + (size_t)b * n3 + ln * N, N * sizeof(float2), &full);
+        ac::bulk_g2s(dsm2 + slot * N, delta + ln * N, N * sizeof(float), &full);
+    };
+    if constexpr (PREF) {
+        if (tid == 0) {
+            ac::mbar_init(&full, 1);
+            ac::mbar_init_fence();
+        }
+        __syncthreads();
+        if (tid == 0 && blockIdx.x < (size_t)N * N) fetch(blockIdx.x, 0);
+    }
+    int it = 0;
+    for (size_t line = blockIdx.x; line < (size_t)N * N; line += gridDim.x, ++it) {
+        if constexpr (PREF) {
+            if (!ac::mbar_wait(&full, it & 1)) late = true;
+        }
         for (int r = 0; r < rounds; ++r) {
             const int b = r * GB + bb;
             float2 v[8];
             if (b < S) {
-                const float2* src = fields + (size_t)b * n3 + line * N;
+                if constexpr (PREF) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = src[t + i * T];
+                    for (int i = 0; i < 8; ++i) v[i] = stage[b * N + t + i * T];
+                } else {
+                    const float2* src = fields + (size_t)b * n3 + line * N;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = src[t + i * T];
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
@@ -197,8 +229,17 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
 #pragma unroll
             for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
         }
-        for (int z = tid; z < N; z += blockDim.x) dsm[z] = delta[line * N + z];
-        __syncthreads();
+        float* dsm = dsm2 + (PREF ? (it & 1) * N : 0);
+        if constexpr (!PREF) {
+            for (int z = tid; z < N; z += blockDim.x) dsm[z] = delta[line * N + z];
+        }
+        __syncthreads();  // the stage has been read: fetch the next line during the Gram phase
+        if constexpr (PREF) {
+            if (tid == 0 && line + gridDim.x < (size_t)N * N) {
+                ac::fence_proxy_async();
+                fetch(line + gridDim.x, (it + 1) & 1);
+            }
+        }
         if (active) {
             const int z0 = zs * ZPER;
             for (int z = z0; z < z0 + ZPER; ++z) {
@@ -252,6 +293,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
         __syncthreads();
     }
     for (int e = tid; e < 256; e += blockDim.x) part[(size_t)e * gridDim.x + blockIdx.x] = tot[e];
+    if (late && (tid & 31) == 0) atomicOr(err, 4u);
 }
 
 // Z3 on the tensor cores ---------------------------------------------------
@@ -543,7 +585,7 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     }
     if ((e = allow_smem_z(k_zeta_z_gram<N>, C::SMEM_Z)) != cudaSuccess) return e;
     tr(K_ZETA_Z_GRAM, 0, st);
-    k_zeta_z_gram<N><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw, gram_part);
+    k_zeta_z_gram<N><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw, gram_part, err);
     tr(K_ZETA_Z_GRAM, 1, st);
     return cudaGetLastError();
 }
