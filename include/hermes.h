@@ -152,6 +152,19 @@ int hermes_xi(hermes_ctx *ctx, double *out);
 int hermes_xi_multipoles(hermes_ctx *ctx, const int *ells, int n_ells, double *out);
 
 /*
+ * The same statistics as hermes_xi_multipoles, evaluated in Fourier space by
+ * Parseval's theorem (Eq. pair-counting-kspace): one pass over the half spectrum
+ * accumulates, per order l, the float64 histogram over |n|^2 of
+ * w_z Phi^(n) L_l(k_z/k) (|delta^_n|^2 - S^(n)/eps_bar^2), then
+ * xi_{b,l} = (2l+1) i^l sum_q <j_l>_b(q) A_l(q) / N^6.  No inverse transform is
+ * run, so the cost is one read of delta^ for all windows.  The self-pair term is
+ * subtracted exactly as in hermes_xi_multipoles; the results agree to rounding.
+ *   ells: 1..8 even orders <= l_max; out: [n_ells][n_bins] float64.
+ * Errors: as hermes_xi_multipoles.
+ */
+int hermes_xi_multipoles_kspace(hermes_ctx *ctx, const int *ells, int n_ells, double *out);
+
+/*
  * 3PCF Legendre multipoles zeta_l(r_b1, r_b2), 0 <= l <= l_max, from the
  * harmonic shell fields a_{b,lm} = iFFT[delta^ 4 pi i^l <j_l>_b Y_lm Phi^]
  * (Eq. multipole-window, Eq. iFFT-multipoleSFC):

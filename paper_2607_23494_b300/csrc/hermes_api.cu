@@ -659,6 +659,37 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     return HERMES_OK;
 }
 
+int hermes_xi_multipoles_kspace(hermes_ctx* c, const int* ells, int n_ells, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!ells || !out || n_ells < 1 || n_ells > 8) return fail(c, HERMES_ERR_ARG, "ells/out NULL or n_ells not in 1..8");
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
+    KsOrders ko;
+    ko.n = n_ells;
+    for (int a = 0; a < n_ells; ++a) {
+        if (ells[a] < 0 || ells[a] > c->l_max)
+            return fail(c, HERMES_ERR_ARG, "l = %d outside 0..l_max = %d", ells[a], c->l_max);
+        if (ells[a] & 1) return fail(c, HERMES_ERR_ARG, "odd l = %d vanishes for an auto-correlation", ells[a]);
+        ko.ell[a] = ells[a];
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int nb = c->n_bins;
+    const size_t nh = (size_t)n_ells * c->Q;
+    CK(grow_doubles(c->part, c->part_cap, nh), "histogram");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)n_ells * nb), "reduction buffer");
+    CK(cudaMemsetAsync(c->part, 0, nh * sizeof(double), st), "clear histogram");
+    CK(launch_kspace_hist(c->N, c->spec, tables_of(c), c->p, c->scal, ko, c->part, c->Q, st, c->tracer),
+       "k-space histogram");
+    CK(launch_kspace_contract(c->rad, c->nbp, c->Q, ko, c->part, c->N, c->red, nb, st, c->tracer), "k-space sums");
+    CK(ensure_host(c, (size_t)n_ells * nb) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)n_ells * nb * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
+    CK(cudaStreamSynchronize(st), "xi (k-space)");
+    for (int i = 0; i < n_ells * nb; ++i) out[i] = c->host_buf[i];
+    return HERMES_OK;
+}
+
 int hermes_xi(hermes_ctx* c, double* out) {
     const int zero = 0;
     return hermes_xi_multipoles(c, &zero, 1, out);
@@ -754,6 +785,8 @@ int hermes_debug_set_delta(hermes_ctx* c, const float* host_delta) {
     CK(cudaMemcpyAsync(c->grid, host_delta, n3 * sizeof(float), cudaMemcpyDefault, c->stream), "write delta");
     CK(cudaMemsetAsync(c->stab_f, 0, 512 * sizeof(float), c->stream), "clear self-pair");
     CK(cudaMemsetAsync(c->stab_d, 0, 512 * sizeof(double), c->stream), "clear self-pair");
+    const double scal_host[3] = {(double)n3, 0.0, 1.0};  // sum w = N^3, eps_bar = 1
+    CK(cudaMemcpyAsync(c->scal, scal_host, sizeof(scal_host), cudaMemcpyHostToDevice, c->stream), "field scalars");
     CK(launch_delta_to_spec(c->N, c->grid, c->spec, c->scal, tables_of(c), c->stream, c->tracer), "forward FFT");
     CK(cudaStreamSynchronize(c->stream), "set delta");
     c->sum_w = (double)n3;  // eps_bar = 1
@@ -796,7 +829,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;

@@ -10,7 +10,7 @@ constexpr int MAX_BATCH = 32;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -45,6 +45,12 @@ struct HarmBatch {
     float ylm_norm;  // N_lm (-1)^m (2m-1)!!  times 4 pi
 };
 
+// Orders of one k-space evaluation (even l, at most 8).
+struct KsOrders {
+    int n;
+    int ell[8];
+};
+
 struct Tables {
     const float2* tw;     // twiddle tables, layout in fft_core.cuh
     const float* phi;     // [N]  sinc^{2p}(pi n / N), FFT order
@@ -73,6 +79,12 @@ cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, co
                               unsigned* err, cudaStream_t st, const Tracer& tr);
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr);
+
+// kspace.cu
+cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int P, const double* scal,
+                               const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
+                                   int N, double* out, int nb, cudaStream_t st, const Tracer& tr);
 
 // zeta.cu
 int zeta_z_blocks(int N);

@@ -49,6 +49,7 @@ def _load() -> C.CDLL:
         "hermes_window_shells": (i32, [vp, dp, i32, i32]),
         "hermes_xi": (i32, [vp, dp]),
         "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
+        "hermes_xi_multipoles_kspace": (i32, [vp, C.POINTER(i32), i32, dp]),
         "hermes_zeta_multipoles": (i32, [vp, dp]),
         "hermes_last_error": (C.c_char_p, [vp]),
         "hermes_debug_get_delta": (i32, [vp, fp]),
@@ -188,6 +189,13 @@ class Context:
         out = np.empty((len(ea), self.n_bins), dtype=np.float64)
         self._check(_lib.hermes_xi_multipoles(self._h, ea.ctypes.data_as(C.POINTER(C.c_int)), len(ea), _dptr(out)),
                     "hermes_xi_multipoles")
+        return out
+
+    def xi_multipoles_kspace(self, ells: Sequence[int]) -> np.ndarray:
+        ea = np.ascontiguousarray(ells, dtype=np.int32)
+        out = np.empty((len(ea), self.n_bins), dtype=np.float64)
+        self._check(_lib.hermes_xi_multipoles_kspace(self._h, ea.ctypes.data_as(C.POINTER(C.c_int)), len(ea),
+                                                     _dptr(out)), "hermes_xi_multipoles_kspace")
         return out
 
     def zeta_multipoles(self) -> np.ndarray:

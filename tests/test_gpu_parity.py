@@ -278,3 +278,47 @@ def test_zeta_tensor_core_gram_matches_simt_and_oracle(N, nb, monkeypatch):
         ref, _ = O.zeta_multipoles(O.delta_from_eps(eps, sw), N, L, p, edges, l_max)
         _close(res["1"], ref)
         _close(res["0"], ref)
+
+
+@pytest.mark.parametrize("N,p,L,ells", [(64, 4, 300.0, (0, 2, 4)), (16, 2, 50.0, (0,)), (128, 6, 400.0, (2, 0))])
+def test_kspace_route_matches_oracle_and_real_space_path(N, p, L, ells):
+    # Eq. pair-counting-kspace: the Parseval sum over the half spectrum gives the
+    # same xi_l as the inverse-FFT cell contraction (and the oracle's full-spectrum sum)
+    H = _hermes()
+    pos = S.lognormal_catalogue(30000, L, seed=N + 5, n_grid=N)
+    mass = S.lognormal_masses(pos.shape[0], seed=N + 6)
+    edges = np.linspace(L / 60, L / 4, 12)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=max(ells))
+        ctx.assign(pos, mass)
+        got = ctx.xi_multipoles_kspace(ells)
+        real = ctx.xi_multipoles(ells)
+    ref = O.xi_multipoles(pos, mass, N, L, p, edges, ells=ells)["xi"]
+    assert got.shape == (len(ells), len(edges) - 1)
+    _close(got, ref)
+    _close(got, real)
+
+
+def test_kspace_route_planted_mode_and_errors():
+    # delta = cos(2 pi n0.x / N): |delta^|^2 = (N^3/2)^2 at +-n0, so
+    # xi_{b,l} = K_{b,l}(n0) / 2 with no self-pair term (the field has no catalogue)
+    H = _hermes()
+    L, N, p = 100.0, 32, 3
+    n0 = (3, -2, 5)
+    x = np.arange(N)
+    ph = 2 * np.pi * (n0[0] * x[:, None, None] + n0[1] * x[None, :, None] + n0[2] * x[None, None, :]) / N
+    delta = np.cos(ph).astype(np.float32)
+    edges = np.array([3.0, 9.0, 15.0, 25.0])
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=4)
+        ctx.set_delta(delta)
+        got = ctx.xi_multipoles_kspace([0, 2, 4])
+        for bad in ([1], [6], [], list(range(0, 18, 2))):
+            with pytest.raises(H.HermesError) as ei:
+                ctx.xi_multipoles_kspace(bad)
+            assert ei.value.code == H.ERR_ARG
+    for a, ell in enumerate((0, 2, 4)):
+        for b in range(3):
+            K = O.window_xi(N, L, p, edges[b], edges[b + 1], ell)
+            ref = 0.5 * K[n0[0] % N, n0[1] % N, n0[2] % N]
+            assert abs(got[a, b] - ref) <= max(2e-5 * abs(ref), 1e-7), (ell, b, got[a, b], ref)
