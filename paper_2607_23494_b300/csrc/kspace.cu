@@ -32,7 +32,23 @@ __device__ __forceinline__ float legendre_k(int ell, float mu) {
     return p1;
 }
 
-// Block (k_z chunk, k_y); thread (col, tx) walks k_x = tx, tx + TX, ...
+// Exact float32 -> float64 widening done with integer instructions (IEEE 754
+// binary32 -> binary64: re-bias the exponent by 1023 - 127 = 896 and left-align
+// the 23-bit fraction in the 52-bit one).  Subnormal inputs flush to signed
+// zero (|v| < 1.2e-38 is far below any histogram entry that matters); Inf/NaN
+// keep their class.  This keeps the conversion off the float64 pipe.
+__device__ __forceinline__ double widen_f32(float v) {
+    const unsigned u = __float_as_uint(v);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned e64 = (e == 0xffu) ? 0x7ffu : e + 896u;
+    return __hiloint2double((int)(sign | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// Block (k_z chunk, k_y in [0, N/2)); thread (col, tx) walks k_x = tx, tx + TX, ... < N/2.
+// The mirror modes (+-n_x, +-n_y) share |n|^2, Phi^ and S^ (both even in every
+// component), so a thread sums |delta^|^2 over the up to four of them that are
+// stored and issues one atomic per order instead of four.
 template <int N>
 __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2* __restrict__ spec, const Tables tb,
                                                                    int P, const double* __restrict__ scal,
@@ -42,8 +58,8 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
     constexpr int W = C::W, TX = C::TX, H = N / 2;
     const int col = threadIdx.x % W, tx = threadIdx.x / W;
     const int ky = blockIdx.y, kz = blockIdx.x * W + col;
-    if (ky == H) return;  // Nyquist plane: K = 0 for every window
-    const int ny = signed_freq(ky, N), nz = kz;
+    const int ky2 = (N - ky) & (N - 1);  // mirror row (== ky for ky = 0)
+    const int ny = ky, nz = kz;
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
     const double inv_eps2 = scal[2] * scal[2];  // scal[2] = N^3 / sum w = 1 / eps_bar
     // self-pair transform S^(n) = sum_a C(k_x, a) U[a], U[a] = sum_{b,c} S(a,b,c) C(k_y,b) C(k_z,c)
@@ -70,41 +86,92 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
         }
         U[a] = u;
     }
-    const double wz = (kz == 0) ? 1.0 : 2.0;
-    for (int kx = tx; kx < N; kx += TX) {
-        if (kx == H) continue;
-        const int nx = signed_freq(kx, N);
-        const int q = nx * nx + ny * ny + nz * nz;
-        const float2 d = spec[((size_t)kx * N + ky) * H + kz];
+    // Per-mode arithmetic in float32 (B300's float64 issue rate is a small
+    // fraction of float32's); only the histogram accumulates in float64.
+    const float wz = (kz == 0) ? 1.0f : 2.0f;
+    const float ny_cnt = (ky == 0) ? 1.0f : 2.0f;
+    const float inv_e2 = (float)inv_eps2;
+    for (int kx = tx; kx < H; kx += TX) {
+        const int kx2 = (N - kx) & (N - 1);
+        const int q = kx * kx + ny * ny + nz * nz;
+        const float2 d00 = spec[((size_t)kx * N + ky) * H + kz];
+        float pw = fmaf(d00.x, d00.x, d00.y * d00.y);
+        if (ky) {
+            const float2 d = spec[((size_t)kx * N + ky2) * H + kz];
+            pw += fmaf(d.x, d.x, d.y * d.y);
+        }
+        if (kx) {
+            const float2 d = spec[((size_t)kx2 * N + ky) * H + kz];
+            pw += fmaf(d.x, d.x, d.y * d.y);
+            if (ky) {
+                const float2 e = spec[((size_t)kx2 * N + ky2) * H + kz];
+                pw += fmaf(e.x, e.x, e.y * e.y);
+            }
+        }
         float sh = 0.0f;
 #pragma unroll
         for (int a = 0; a < 8; ++a)
             if (a < P) sh = fmaf((a == 0) ? 1.0f : 2.0f * __ldg(tb.tw + N + ((kx * a) & (N - 1))).x, U[a], sh);
-        const double pw = (double)d.x * d.x + (double)d.y * d.y - (double)sh * inv_eps2;
-        const double base = wz * (double)(__ldg(tb.phi + kx) * phyz) * pw;
+        const float cnt = ny_cnt * ((kx == 0) ? 1.0f : 2.0f);
+        pw = fmaf(-cnt * sh, inv_e2, pw);
+        const float base = wz * (__ldg(tb.phi + kx) * phyz) * pw;
         const float mu = q > 0 ? (float)nz * rsqrtf((float)q) : 0.0f;
         for (int o = 0; o < ko.n; ++o) {
-            const double v = ko.ell[o] == 0 ? base : base * (double)legendre_k(ko.ell[o], mu);
-            atomicAdd(hist + (size_t)o * Q + q, v);
+            const float v = ko.ell[o] == 0 ? base : base * legendre_k(ko.ell[o], mu);
+            atomicAdd(hist + (size_t)o * Q + q, widen_f32(v));
         }
     }
 }
 
-// xi[o][b] = c_l sum_q T[(l*Q + q)*nbp + b] * hist[o*Q + q] / N^6; one block per (o, b).
-__global__ void __launch_bounds__(256) k_kspace_contract(const float* __restrict__ rad, int nbp, int64_t Q,
-                                                         KsOrders ko, const double* __restrict__ hist, double n6,
-                                                         double* __restrict__ out, int nb) {
-    __shared__ double red[8];
-    const int o = blockIdx.x / nb, b = blockIdx.x % nb;
+// out[o][b] += c_l sum_q T[(l*Q + q)*nbp + b] * hist[o*Q + q] / N^6 (out zeroed first).
+// Grid (q slices, 32-bin chunks, orders); lane = bin within the chunk, so every
+// warp reads table rows contiguously.  A warp takes 32 consecutive q at a time:
+// each lane narrows one histogram entry to float32 and the warp shares them by
+// shuffles; the 32 products accumulate in float32 and each group of 32 is added
+// into a float64 sum, so float64 work is one add per 32 table entries.
+constexpr int KC_THREADS = 256;
+__global__ void __launch_bounds__(KC_THREADS) k_kspace_contract(const float* __restrict__ rad, int nbp, int64_t Q,
+                                                                KsOrders ko, const double* __restrict__ hist,
+                                                                double n6, double* __restrict__ out, int nb) {
+    __shared__ double part[KC_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int o = blockIdx.z, b = blockIdx.y * 32 + lane;
     const int ell = ko.ell[o];
-    const float* tab = rad + (size_t)ell * Q * nbp + b;
+    const bool live = b < nb;
+    const float* tab = rad + (size_t)ell * Q * nbp + (live ? b : 0);
     const double* h = hist + (size_t)o * Q;
+    const int64_t ngroups = (Q + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * (KC_THREADS / 32);
     double s = 0.0;
-    for (int64_t q = threadIdx.x; q < Q; q += blockDim.x) s += (double)tab[(size_t)q * nbp] * h[q];
-    s = block_sum_double(s, red);
-    if (threadIdx.x == 0) {
-        const double c = (double)(2 * ell + 1) * (((ell / 2) & 1) ? -1.0 : 1.0);
-        out[blockIdx.x] = c * s / n6;
+    for (int64_t g = (int64_t)blockIdx.x * (KC_THREADS / 32) + wid; g < ngroups; g += nwarps) {
+        const int64_t q0 = g * 32;
+        const int64_t qn = (Q - q0) < 32 ? (Q - q0) : 32;
+        const float hl = lane < qn ? (float)__ldg(h + q0 + lane) : 0.0f;
+        float acc = 0.0f;
+        if (qn == 32) {
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const float hj = __shfl_sync(0xffffffffu, hl, j);
+                acc = fmaf(__ldg(tab + (size_t)(q0 + j) * nbp), hj, acc);
+            }
+        } else {
+            for (int j = 0; j < qn; ++j) {
+                const float hj = __shfl_sync(0xffffffffu, hl, j);
+                acc = fmaf(__ldg(tab + (size_t)(q0 + j) * nbp), hj, acc);
+            }
+        }
+        s += (double)acc;
+    }
+    part[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < KC_THREADS / 32; ++w) t += part[w][lane];
+        if (live) {
+            const double c = (double)(2 * ell + 1) * (((ell / 2) & 1) ? -1.0 : 1.0);
+            atomicAdd(out + (size_t)o * nb + b, c * t / n6);
+        }
     }
 }
 
@@ -112,7 +179,7 @@ template <int N>
 static cudaError_t kspace_impl(const float2* spec, const Tables& tb, int P, const double* scal, const KsOrders& ko,
                                double* hist, int64_t Q, cudaStream_t st, const Tracer& tr) {
     using C = KsCfg<N>;
-    dim3 g((N / 2) / C::W, N, 1);
+    dim3 g((N / 2) / C::W, N / 2, 1);
     tr(K_KSPACE_HIST, 0, st);
     k_kspace_hist<N><<<g, C::THREADS, 0, st>>>(spec, tb, P, scal, ko, hist, Q);
     tr(K_KSPACE_HIST, 1, st);
@@ -136,8 +203,16 @@ cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int 
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
                                    int N, double* out, int nb, cudaStream_t st, const Tracer& tr) {
     const double n3 = (double)N * N * N;
+    const int chunks = (nb + 31) / 32;
+    // about four blocks per SM in total, but at least one group of 32 q per warp
+    const int64_t groups = (Q + 31) / 32;
+    const int64_t most = (groups + KC_THREADS / 32 - 1) / (KC_THREADS / 32);
+    int64_t want = (4 * 148 + chunks * ko.n - 1) / (chunks * ko.n);
+    const int slices = (int)(want < most ? want : most);
     tr(K_KSPACE_CONTRACT, 0, st);
-    k_kspace_contract<<<ko.n * nb, 256, 0, st>>>(rad, nbp, Q, ko, hist, n3 * n3, out, nb);
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)ko.n * nb * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_kspace_contract<<<dim3(slices, chunks, ko.n), KC_THREADS, 0, st>>>(rad, nbp, Q, ko, hist, n3 * n3, out, nb);
     tr(K_KSPACE_CONTRACT, 1, st);
     return cudaGetLastError();
 }
