@@ -241,12 +241,19 @@ def run_hermes(args, rank, world, local_rank):
 
     # the k-space (Parseval) route on the resident marked field: same xi_l, no inverse FFTs
     ks = run_kspace(ctx, stream, res[1])
+    plain = None
+    if not args.no_plain:
+        ctx.close()
+        ctx = None
+        plain = run_plain_fp32(pos_d, mass_d, res)
+        plain["speedup"] = round(value / world / plain["value"], 2)
 
     zeta = None
     if not args.no_zeta:
         zeta = run_zeta(args, dev, stream, rank)
 
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     out = None
     if rank == 0:
         out = {
@@ -267,6 +274,8 @@ def run_hermes(args, rank, world, local_rank):
             "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
         }
         out["kspace"] = ks
+        if plain:
+            out["vs_plain_fp32"] = plain
         if zeta:
             out["zeta"] = zeta
     return out, pos
@@ -301,6 +310,104 @@ def run_kspace(ctx, stream, real):
             "hist_GBps": round(spec_b / (hist_ms / 1e3) / 1e9, 1) if hist_ms else None,
             "diff_vs_real_space_in_tolerances": round(tol_units, 4),
             "kernels": {k: {"ms": round(v[0] / reps, 3), "launches": v[1] // reps} for k, v in tr.items()}}
+
+
+def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
+    """The plain one-request-at-a-time FP32 pipeline on the same GPU, for the ratio
+    the metric asks for: torch ops and cuFFT only (index_add_ B-spline scatter,
+    rfftn, then per window: build K on the device, multiply, irfftn, cell dot
+    product, self-pair term).  The per-catalogue part is timed on both fields, the
+    per-window part on n_win windows of each field (every window costs the same);
+    the step estimate is 2 * catalogue + 240 * window.  Comparison arm only."""
+    import torch
+    from paper_2607_23494_b300.hermes import shell_table_host
+    dev = pos_d.device
+    N, L, p = N2, L2, P2
+    H = N // 2
+    nb = len(EDGES2) - 1
+    T = torch.from_numpy(shell_table_host(L, N, EDGES2, max(ELLS2)).astype(np.float32)).to(dev)
+    fxy = torch.fft.fftfreq(N, d=1.0 / N, device=dev).round().to(torch.int64)
+    fz = torch.arange(H + 1, device=dev, dtype=torch.int64)
+    q = (fxy[:, None, None] ** 2 + fxy[None, :, None] ** 2 + fz[None, None, :] ** 2)
+    ph1 = torch.sinc(fxy.double() / N) ** (2 * p)
+    ph1z = torch.sinc(fz.double() / N) ** (2 * p)
+    keep = ((fxy.abs() != H)[:, None, None] & (fxy.abs() != H)[None, :, None] & (fz != H)[None, None, :])
+    phi = (ph1[:, None, None] * ph1[None, :, None] * ph1z[None, None, :]).float() * keep
+    q = torch.where(keep, q, torch.zeros((), device=dev, dtype=q.dtype))  # tables stop below the Nyquist planes
+    mu = torch.where(q > 0, fz[None, None, :].float() / q.float().clamp(min=1).sqrt(), torch.zeros((), device=dev))
+    leg = {0: torch.ones_like(mu), 2: 0.5 * (3 * mu ** 2 - 1), 4: (35 * mu ** 4 - 30 * mu ** 2 + 3) / 8}
+    wz = torch.full((H + 1,), 2.0, device=dev)
+    wz[0] = 1.0
+    wz[H] = 1.0
+    cxy = torch.stack([torch.ones(N, device=dev, dtype=torch.float64)] +
+                      [2 * torch.cos(2 * np.pi * fxy.double() * a / N) for a in range(1, p)], 1)
+    cz = torch.stack([torch.ones(H + 1, device=dev, dtype=torch.float64)] +
+                     [2 * torch.cos(2 * np.pi * fz.double() * a / N) for a in range(1, p)], 1)
+
+    def mp(x):  # centred cubic B-spline
+        ax = x.abs()
+        return torch.where(ax < 1, 2.0 / 3 - ax ** 2 + 0.5 * ax ** 3,
+                           torch.where(ax < 2, (2 - ax) ** 3 / 6, torch.zeros_like(ax)))
+
+    def catalogue(pos, w):
+        grid = torch.zeros(N ** 3, device=dev, dtype=torch.float32)
+        S = torch.zeros(p, p, p, device=dev, dtype=torch.float64)
+        sw = torch.zeros((), device=dev, dtype=torch.float64)
+        for c0 in range(0, pos.shape[0], 2_000_000):
+            x = pos[c0:c0 + 2_000_000]
+            ww = torch.ones(x.shape[0], device=dev) if w is None else w[c0:c0 + 2_000_000]
+            u = x * np.float32(N / L)
+            i = torch.floor(u)
+            t = u - i
+            j = torch.arange(p, device=dev, dtype=torch.float32)
+            wts = mp(t[:, :, None] + 1 - j)                               # [n, 3, 4]
+            nodes = (i.long()[:, :, None] - 1 + j.long()) % N              # [n, 3, 4]
+            flat = (nodes[:, 0, :, None, None] * N + nodes[:, 1, None, :, None]) * N + nodes[:, 2, None, None, :]
+            val = ww[:, None, None, None] * wts[:, 0, :, None, None] * wts[:, 1, None, :, None] * wts[:, 2, None, None, :]
+            grid.index_add_(0, flat.reshape(-1), val.reshape(-1))
+            sw += ww.double().sum()
+            sd = torch.stack([(wts[..., :p - d] * wts[..., d:]).sum(-1) for d in range(p)], -1).double()
+            S += torch.einsum("n,na,nb,nc->abc", ww.double() ** 2, sd[:, 0], sd[:, 1], sd[:, 2])
+        ebar = sw / N ** 3
+        delta = grid.view(N, N, N) / ebar.float() - 1
+        dh = torch.fft.rfftn(delta)
+        dh[0, 0, 0] = 0
+        shat = torch.einsum("abc,xa,yb,zc->xyz", S, cxy, cxy, cz).float()
+        snw = shat * wz / float(N) ** 6 / ebar.float() ** 2  # K carries Phi^ already
+        return delta, dh, snw
+
+    def window(delta, dh, snw, b, ell):
+        c = (2 * ell + 1) * (-1) ** (ell // 2)
+        K = c * T[b, ell][q] * phi * leg[ell]
+        dt = torch.fft.irfftn(dh * K, s=(N, N, N))
+        return (delta * dt).sum(dtype=torch.float64) / N ** 3 - (K * snw).sum(dtype=torch.float64)
+
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    catalogue(pos_d, None)  # warm-up (cuFFT plans, allocator)
+    torch.cuda.synchronize()
+    e[0].record()
+    fields = [catalogue(pos_d, None), catalogue(pos_d, mass_d)]
+    e[1].record()
+    picks = [(b, ELLS2[k % len(ELLS2)]) for k, b in enumerate(np.linspace(0, nb - 1, n_win).astype(int))]
+    window(*fields[0], 0, 0)
+    e[2].record()
+    got = [[float(window(*fields[f], b, ell)) for (b, ell) in picks] for f in range(2)]
+    e[3].record()
+    torch.cuda.synchronize()
+    cat_ms = e[0].elapsed_time(e[1]) / 2
+    win_ms = e[2].elapsed_time(e[3]) / (2 * n_win)
+    step_ms = 2 * cat_ms + 2 * len(ELLS2) * nb * win_ms
+    worst = 0.0
+    for f in range(2):
+        for (b, ell), g in zip(picks, got[f]):
+            r = float(real_res[f][ELLS2.index(ell)][b])
+            worst = max(worst, abs(g - r) / max(1e-4 * abs(r), 1e-6))
+    del fields, q, phi, mu, leg, keep
+    torch.cuda.empty_cache()
+    return {"value": round(N ** 3 * 2 * len(ELLS2) * nb / (step_ms / 1e3), 1), "unit": UNIT,
+            "ms_per_step": round(step_ms, 2), "ms_per_catalogue": round(cat_ms, 3), "ms_per_window": round(win_ms, 3),
+            "windows_timed": 2 * n_win, "what": "torch index_add_ scatter + cuFFT rfftn/irfftn, one window at a time",
+            "diff_vs_hermes_in_tolerances": round(worst, 3)}
 
 
 def run_zeta(args, dev, stream, rank):
@@ -431,6 +538,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hermes", choices=["hermes", "reference"])
     ap.add_argument("--no-zeta", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain torch/cuFFT comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
