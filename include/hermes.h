@@ -48,6 +48,7 @@ extern "C" {
 /* flags of hermes_assign */
 #define HERMES_DEVICE_PTR 1u /* pos / w are device pointers on the context's GPU   */
 #define HERMES_WRAP 2u       /* wrap coordinates periodically instead of rejecting */
+#define HERMES_EAGER 4u      /* batched calls: launch directly, no CUDA graph       */
 
 typedef struct hermes_ctx hermes_ctx;
 
@@ -163,6 +164,50 @@ int hermes_xi_multipoles(hermes_ctx *ctx, const int *ells, int n_ells, double *o
  * Errors: as hermes_xi_multipoles.
  */
 int hermes_xi_multipoles_kspace(hermes_ctx *ctx, const int *ells, int n_ells, double *out);
+
+/*
+ * xi_l of many catalogues in one call (the estimator of Eq. 2rdEs and its
+ * multipole form, Sec. 3, applied to each catalogue separately): catalogue k is
+ * points [offsets[k], offsets[k+1]) of pos (n x 3 float32) and w (n float32 or
+ * NULL = unit weights), gridded on this context's N^3 grid and measured with
+ * its shells.  Each catalogue gets its own mean density, self-pair table and
+ * fields; the context's single resident field (hermes_assign) is untouched.
+ * Every pass runs as one launch over a chunk of catalogues; the whole
+ * measurement is captured into a CUDA graph on the context's stream and
+ * replayed by later calls of the same shape (same n_cat, total points, weights
+ * present or not, orders and plan); HERMES_EAGER (or the legacy default stream)
+ * launches the same kernels directly instead.
+ *   offsets: host array of n_cat + 1 int64, offsets[0] = 0, strictly increasing
+ *            (no empty catalogue); n = offsets[n_cat].
+ *   n_cat:   1..1024.  ells: 1..8 even orders <= l_max.
+ *   flags:   HERMES_DEVICE_PTR (pos, w are device memory of this device),
+ *            HERMES_WRAP, HERMES_EAGER.  Inputs are copied into the context
+ *            during the call.
+ *   out:     [n_cat][n_ells][n_bins] float64, host.
+ * Windows per launch S and catalogues per launch C come from
+ * hermes_batch_set_plan, else from a process-wide cache for this shape, else
+ * from timing candidates on the first call (the autotuner).
+ * Errors: as hermes_assign and hermes_xi_multipoles; HERMES_ERR_RANGE names the
+ * catalogue whose weights do not sum to a positive number.
+ */
+int hermes_xi_multipoles_batch(hermes_ctx *ctx, const float *pos, const float *w, const int64_t *offsets,
+                               int n_cat, const int *ells, int n_ells, unsigned flags, double *out);
+
+/*
+ * Fixes the batch plan: S windows per launch (multiple of 4, <= 32) and C
+ * catalogues per launch (1..1024); S = C = 0 returns to autotuning.
+ * Errors: HERMES_ERR_ARG.
+ */
+int hermes_batch_set_plan(hermes_ctx *ctx, int S, int C);
+
+/*
+ * The plan of the last batched call and its graph: S, C, kernels in the graph,
+ * graph replays so far, and the autotuner's timings as triples
+ * {S, C, ms per catalogue-window} (up to tune_cap triples; *n_tune = count).
+ * Any pointer may be NULL.  Errors: HERMES_ERR_ARG.
+ */
+int hermes_batch_info(hermes_ctx *ctx, int *S, int *C, int64_t *graph_kernels, int64_t *graph_replays,
+                      double *tune, int tune_cap, int *n_tune);
 
 /*
  * 3PCF Legendre multipoles zeta_l(r_b1, r_b2), 0 <= l <= l_max, from the

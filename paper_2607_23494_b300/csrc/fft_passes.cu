@@ -63,6 +63,12 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
     const SmemLine<M> sm{smem + li * LP};
+    {  // batched launch: blockIdx.y = catalogue
+        const size_t cat = blockIdx.y;
+        grid += cat * N * N * N;
+        spec += cat * N * N * (N / 2);
+        scal += cat * SCAL_STRIDE;
+    }
     float2* g = reinterpret_cast<float2*>(grid + line * N);
     const float inv_mean = convert ? (float)scal[2] : 1.0f;
     float2 v[8];
@@ -154,6 +160,13 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
     const size_t nblk = (size_t)gridDim.x * gridDim.y;
     const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     const size_t xstride = (size_t)N * H;
+    {  // batched launch: blockIdx.z = catalogue
+        const size_t cat = blockIdx.z;
+        spec += cat * N * N * H;
+        work += cat * wb.S * N * N * H;
+        sn_part += cat * wb.S * nblk;
+    }
+    const float* stab = tb.stab + (size_t)blockIdx.z * STAB_STRIDE;
     const float2* src = spec + (size_t)ky * H + kz;
     float2 v0[8];
 #pragma unroll
@@ -179,7 +192,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
                     float ub = 0.0f;
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
-                        if (c < P) ub = fmaf(__ldg(tb.stab + (a * P + b) * P + c), cz[c], ub);
+                        if (c < P) ub = fmaf(__ldg(stab + (a * P + b) * P + c), cz[c], ub);
                     u = fmaf(ub, cy[b], u);
                 }
             }
@@ -280,6 +293,12 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
     const size_t line0 = (size_t)blockIdx.x * LZ;
     const size_t line = line0 + li;
     const SmemLine<M> sm{lines + li * LP};
+    {  // batched launch: blockIdx.y = catalogue
+        const size_t cat = blockIdx.y;
+        work += cat * S * N * N * H;
+        delta += cat * N * N * N;
+        dd_part += cat * S * gridDim.x;
+    }
     if (threadIdx.x == 0) {
         ac::mbar_init(&full[0], 1);
         ac::mbar_init(&full[1], 1);
@@ -535,23 +554,24 @@ static cudaError_t launch_yz(const float2* work, int S, const float* delta, cons
 
 template <int N>
 static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, int convert, const Tables& tb,
-                                cudaStream_t st, const Tracer& tr) {
+                                cudaStream_t st, const Tracer& tr, int ncat) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_fwd_z_r2c<N>, C::SMEM_Z)) != cudaSuccess) return e;
     if ((e = allow_smem(k_strided<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     tr(K_FWD_Z_R2C, 0, st);
-    k_fwd_z_r2c<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(grid, spec, scal, convert, tb.tw);
+    k_fwd_z_r2c<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z, st>>>(grid, spec, scal, convert, tb.tw);
     tr(K_FWD_Z_R2C, 1, st);
     const long long H = N / 2;
-    dim3 g(H / C::W, N, 1);
+    const long long cat_stride = (long long)N * N * H;  // one spectrum per catalogue (blockIdx.z)
+    dim3 g(H / C::W, N, ncat);
     // along y: pos stride H, blockIdx.y = x
     tr(K_FWD_Y, 0, st);
-    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, H, (long long)N * H, 0, 0, tb.tw);
+    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, H, (long long)N * H, cat_stride, 0, tb.tw);
     tr(K_FWD_Y, 1, st);
     // along x: pos stride N*H, blockIdx.y = y, delta^(0) := 0
     tr(K_FWD_X, 0, st);
-    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, 0, 1, tb.tw);
+    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, cat_stride, 1, tb.tw);
     tr(K_FWD_X, 1, st);
     return cudaGetLastError();
 }
@@ -559,32 +579,32 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 template <int N>
 static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
                                 const Tables& tb, int P, double* sn_part, double* dd_part, unsigned* err,
-                                cudaStream_t st, const Tracer& tr) {
+                                cudaStream_t st, const Tracer& tr, int ncat) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_inv_x_window<N>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z3)) != cudaSuccess) return e;
     const long long H = N / 2;
-    dim3 g1(H / C::W, N, 1);
+    dim3 g1(H / C::W, N, ncat);
     tr(K_INV_X_WINDOW, 0, st);
     k_inv_x_window<N><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb, P, sn_part);
     tr(K_INV_X_WINDOW, 1, st);
     if constexpr (N <= 512) {
-        if (yz_fused_ok<N>()) {
+        if (ncat == 1 && yz_fused_ok<N>()) {
             tr(K_INV_YZ_CONTRACT, 0, st);
             e = launch_yz<N>(work, wb.S, delta, tb.tw, dd_part, st);
             tr(K_INV_YZ_CONTRACT, 1, st);
             return e != cudaSuccess ? e : cudaGetLastError();
         }
     }
-    dim3 g2(H / C::W, N, wb.S);
+    dim3 g2(H / C::W, N, wb.S * ncat);  // windows of all catalogues are consecutive in work
     tr(K_INV_Y, 0, st);
     k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
-    k_inv_z_c2r_contract<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw, dd_part,
-                                                                            err);
+    k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw,
+                                                                                        dd_part, err);
     tr(K_INV_Z_C2R_CONTRACT, 1, st);
     return cudaGetLastError();
 }
@@ -602,23 +622,25 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     }
 
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb, cudaStream_t st,
-                           const Tracer& tr) {
-#define F(n) forward_impl<n>(grid, spec, scal, 1, tb, st, tr)
+                           const Tracer& tr, int ncat) {
+    if (ncat < 1 || ncat > MAX_CATALOGUES) return cudaErrorInvalidValue;
+#define F(n) forward_impl<n>(grid, spec, scal, 1, tb, st, tr, ncat)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }
 
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr) {
-#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st, tr)
+#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st, tr, 1)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }
 
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
                               const Tables& tb, double* sn_part, double* dd_part, unsigned* err, cudaStream_t st,
-                              const Tracer& tr) {
-#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, err, st, tr)
+                              const Tracer& tr, int ncat) {
+    if (ncat < 1 || ncat > MAX_CATALOGUES || (size_t)wb.S * ncat > 65535) return cudaErrorInvalidValue;
+#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, err, st, tr, ncat)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }
@@ -647,6 +669,8 @@ static int z_blocks_of(int N) {
     }
     return 0;
 }
+
+int inv_z_blocks_plain(int N) { return z_blocks_of(N); }
 int inv_x_blocks(int N) { return x_blocks_of(N); }
 int inv_z_blocks(int N) {
     switch (N) {

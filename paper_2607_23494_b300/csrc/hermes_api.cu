@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <cmath>
 #include <complex>
@@ -20,6 +21,9 @@
 #include "fft_core.cuh"
 
 using namespace hermes;
+
+struct BatchState;  // batched measurements (defined with hermes_xi_multipoles_batch)
+void batch_free(BatchState* b);
 
 struct hermes_ctx {
     double L = 0;
@@ -72,6 +76,7 @@ struct hermes_ctx {
     double trace_ms[K_COUNT] = {0};
     int64_t trace_n[K_COUNT] = {0};
     Tracer tracer{nullptr, nullptr};
+    BatchState* batch = nullptr;
 };
 
 namespace {
@@ -331,6 +336,7 @@ void trace_collect(hermes_ctx* c) {
 int ensure_host(hermes_ctx* c, size_t n) {
     if (n <= c->host_cap) return HERMES_OK;
     if (c->host_buf) cudaFreeHost(c->host_buf);
+    batch_free(c->batch);
     c->host_buf = nullptr;
     c->host_cap = 0;
     if (cudaMallocHost((void**)&c->host_buf, n * sizeof(double)) != cudaSuccess) {
@@ -829,7 +835,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -965,5 +971,464 @@ extern "C" int hermes_assign_noalloc(hermes_ctx* c, const float* pos, const floa
     CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st, tr), "forward FFT");
     CK(cudaStreamSynchronize(st), "forward FFT");
     c->have_field = true;
+    return HERMES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched measurements: many catalogues on the same grid and windows.
+//
+// Every pass is one launch over all catalogues of a chunk (the catalogue is a
+// grid dimension of each kernel); the whole measurement (scatter .. final xi)
+// is captured once into a CUDA graph per shape and replayed on later calls.
+// Windows per launch (S) and catalogues per launch (C) are chosen by timing the
+// inverse passes on the live spectra the first time a shape is seen; the
+// choice is cached for the process.
+
+struct BatchPlan {
+    int S = 0, C = 0;
+};
+
+struct BatchState {
+    float* pos = nullptr;
+    float* w = nullptr;
+    size_t pts_cap = 0;                // points
+    int64_t* offs = nullptr;           // [MAX_CATALOGUES + 1]
+    float* grid = nullptr;             // [cat][N^3]
+    float2* spec = nullptr;            // [cat][N*N*H]
+    int cat_cap = 0;
+    double* scal = nullptr;            // [cat][SCAL_STRIDE]
+    float* stab_f = nullptr;           // [cat][STAB_STRIDE]
+    double* sums = nullptr;            // [cat][2]
+    double* sp = nullptr;              // [cat][512]
+    double* part = nullptr;
+    size_t part_cap = 0;               // doubles
+    double* res = nullptr;             // dd, sn, xi: [3][cat][nwin]
+    size_t res_cap = 0;                // doubles
+    float2* work = nullptr;
+    size_t work_bytes = 0;
+    BatchPlan forced, last;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> key;
+    int64_t graph_kernels = 0;
+    int64_t graph_launches = 0;        // replays of the cached graph (for tests)
+    std::vector<double> tune_ms;       // [candidate] = {S, C, ms per catalogue-window}
+};
+
+void batch_free(BatchState* b) {
+    if (!b) return;
+    cudaFree(b->pos);
+    cudaFree(b->w);
+    cudaFree(b->offs);
+    cudaFree(b->grid);
+    cudaFree(b->spec);
+    cudaFree(b->scal);
+    cudaFree(b->stab_f);
+    cudaFree(b->sums);
+    cudaFree(b->sp);
+    cudaFree(b->part);
+    cudaFree(b->res);
+    cudaFree(b->work);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaGetLastError();
+    delete b;
+}
+
+namespace {
+
+std::mutex g_plan_mu;
+std::map<std::vector<int64_t>, BatchPlan> g_plans;  // (device, N, p, ncat, nb, n_ells) -> plan
+
+struct BatchJob {
+    int ncat;
+    int64_t n_total;
+    bool has_w, wrap;
+    std::vector<int> ells;
+    BatchPlan plan;
+};
+
+int batch_nblk(int ncat) { return std::max(8, std::min(592, 2048 / ncat)); }
+
+size_t batch_work_limit(const hermes_ctx* c) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return (size_t)8 << 30;
+    }
+    size_t have = free_b + c->batch->work_bytes;
+    return std::min<size_t>((size_t)32 << 30, have / 3);
+}
+
+// Partials of the inverse passes for C catalogues x S windows.
+size_t batch_part_need(int N, int S, int C) {
+    return (size_t)C * S * ((size_t)inv_x_blocks(N) + std::max(inv_z_blocks(N), inv_z_blocks_plain(N)));
+}
+
+cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
+    BatchState* b = c->batch;
+    const int N = c->N;
+    const size_t n3 = (size_t)N * N * N;
+    cudaError_t e;
+    if ((size_t)j.n_total > b->pts_cap) {
+        cudaFree(b->pos);
+        cudaFree(b->w);
+        b->pos = nullptr;
+        b->w = nullptr;
+        b->pts_cap = 0;
+        if ((e = cudaMalloc((void**)&b->pos, (size_t)j.n_total * 3 * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->w, (size_t)j.n_total * sizeof(float))) != cudaSuccess) return e;
+        b->pts_cap = (size_t)j.n_total;
+    }
+    if (!b->offs && (e = cudaMalloc((void**)&b->offs, (MAX_CATALOGUES + 1) * sizeof(int64_t))) != cudaSuccess) return e;
+    if (j.ncat > b->cat_cap) {
+        cudaFree(b->grid);
+        cudaFree(b->spec);
+        cudaFree(b->scal);
+        cudaFree(b->stab_f);
+        cudaFree(b->sums);
+        cudaFree(b->sp);
+        b->grid = nullptr;
+        b->spec = nullptr;
+        b->scal = nullptr;
+        b->stab_f = nullptr;
+        b->sums = nullptr;
+        b->sp = nullptr;
+        b->cat_cap = 0;
+        const size_t k = (size_t)j.ncat;
+        if ((e = cudaMalloc((void**)&b->grid, k * n3 * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->spec, k * (size_t)N * N * (N / 2) * sizeof(float2))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->scal, k * SCAL_STRIDE * sizeof(double))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->stab_f, k * STAB_STRIDE * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->sums, k * 2 * sizeof(double))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&b->sp, k * 512 * sizeof(double))) != cudaSuccess) return e;
+        b->cat_cap = j.ncat;
+    }
+    const int p3 = c->p * c->p * c->p;
+    const size_t nblk = (size_t)batch_nblk(j.ncat);
+    size_t part_need = std::max<size_t>((size_t)j.ncat * std::max(2, p3) * nblk, batch_part_need(N, S_max, C_max));
+    if ((e = grow_doubles(b->part, b->part_cap, part_need)) != cudaSuccess) return e;
+    const size_t nwin = j.ells.size() * (size_t)c->n_bins;
+    if ((e = grow_doubles(b->res, b->res_cap, 3 * (size_t)j.ncat * nwin)) != cudaSuccess) return e;
+    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
+    return grow(b->work, b->work_bytes, (size_t)S_max * C_max * win_bytes);
+}
+
+// Scatter, sums, self-pair tables and forward transforms of every catalogue.
+cudaError_t batch_enqueue_assign(hermes_ctx* c, const BatchJob& j, cudaStream_t st, const Tracer& tr) {
+    BatchState* b = c->batch;
+    const int N = c->N, p = c->p, p3 = p * p * p;
+    const size_t n3 = (size_t)N * N * N;
+    const int nblk = batch_nblk(j.ncat);
+    const float s = (float)((double)N / c->L);
+    const float* w = j.has_w ? b->w : nullptr;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->grid, 0, (size_t)j.ncat * n3 * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+    if ((e = launch_scatter_batch(N, p, b->pos, w, b->offs, j.ncat, j.n_total, b->grid, s, j.wrap ? 1 : 0, c->err, st,
+                                  tr)) != cudaSuccess)
+        return e;
+    if ((e = launch_weight_sums(w, j.n_total, b->part, nblk, st, tr, b->offs, j.ncat)) != cudaSuccess) return e;
+    if ((e = launch_reduce_rows(b->part, j.ncat * 2, nblk, b->sums, st, tr)) != cudaSuccess) return e;
+    if ((e = launch_selfpair(N, p, b->pos, w, j.n_total, s, b->part, nblk, st, tr, b->offs, j.ncat)) != cudaSuccess)
+        return e;
+    if ((e = launch_reduce_rows(b->part, j.ncat * p3, nblk, b->sp, st, tr)) != cudaSuccess) return e;
+    if ((e = launch_finish_batch(b->sums, b->sp, p3, b->stab_f, N, b->scal, j.ncat, st, tr)) != cudaSuccess) return e;
+    Tables tb = tables_of(c);
+    tb.stab = b->stab_f;
+    return launch_forward(N, b->grid, b->spec, b->scal, tb, st, tr, j.ncat);
+}
+
+// Windows w0 .. of order index o, bins b0 .. b0+S-1, catalogues c0 .. c0+C-1.
+cudaError_t batch_enqueue_window_block(hermes_ctx* c, const BatchJob& j, int o, int b0, int S, int c0, int C,
+                                       cudaStream_t st, const Tracer& tr) {
+    BatchState* b = c->batch;
+    const int N = c->N, nb = c->n_bins, H = N / 2;
+    const int ell = j.ells[o];
+    const size_t n3 = (size_t)N * N * N;
+    const int nwin = (int)j.ells.size() * nb;
+    WinBatch wb;
+    wb.S = S;
+    wb.tab = c->rad + (size_t)ell * c->Q * c->nbp + b0;
+    wb.nbp = c->nbp;
+    wb.ell = ell;
+    wb.scale = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));
+    Tables tb = tables_of(c);
+    tb.stab = b->stab_f + (size_t)c0 * STAB_STRIDE;
+    const int xb = inv_x_blocks(N);
+    const int zb = (C == 1) ? inv_z_blocks(N) : inv_z_blocks_plain(N);
+    double* sn_part = b->part;
+    double* dd_part = b->part + (size_t)C * S * xb;
+    cudaError_t e = launch_inverse_xi(N, c->p, b->spec + (size_t)c0 * N * N * H, b->work, b->grid + (size_t)c0 * n3,
+                                      wb, tb, sn_part, dd_part, c->err, st, tr, C);
+    if (e != cudaSuccess) return e;
+    double* dd = b->res;
+    double* sn = b->res + (size_t)j.ncat * nwin;
+    const size_t at = (size_t)c0 * nwin + (size_t)o * nb + b0;
+    if ((e = launch_reduce_rows_strided(sn_part, C * S, xb, S, sn + at, nwin, st, tr)) != cudaSuccess) return e;
+    return launch_reduce_rows_strided(dd_part, C * S, zb, S, dd + at, nwin, st, tr);
+}
+
+cudaError_t batch_enqueue_windows(hermes_ctx* c, const BatchJob& j, cudaStream_t st, const Tracer& tr) {
+    BatchState* b = c->batch;
+    const int nb = c->n_bins;
+    const int nwin = (int)j.ells.size() * nb;
+    const int S = j.plan.S, C = j.plan.C;
+    cudaError_t e;
+    for (int o = 0; o < (int)j.ells.size(); ++o)
+        for (int b0 = 0; b0 < nb; b0 += S)
+            for (int c0 = 0; c0 < j.ncat; c0 += C)
+                if ((e = batch_enqueue_window_block(c, j, o, b0, std::min(S, nb - b0), c0, std::min(C, j.ncat - c0),
+                                                    st, tr)) != cudaSuccess)
+                    return e;
+    double* dd = b->res;
+    double* sn = b->res + (size_t)j.ncat * nwin;
+    return launch_xi_batch_finish(dd, sn, b->scal, j.ncat, nwin, c->N, b->res + 2 * (size_t)j.ncat * nwin, st, tr);
+}
+
+}  // namespace
+
+namespace {
+
+// Candidate plans, timed on the live spectra with CUDA events: first S (windows
+// per launch) at a middle C, then C (catalogues per launch) at the best S.  A
+// candidate costs ms per catalogue-window; the cheapest wins.  Work-buffer size
+// bounds both.
+int batch_autotune(hermes_ctx* c, BatchJob& j, cudaStream_t st) {
+    BatchState* b = c->batch;
+    const int N = c->N, nb = c->n_bins;
+    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
+    const size_t limit = batch_work_limit(c);
+    const int nb4 = (nb + 3) & ~3;
+    std::vector<int> Ss, Cs;
+    for (int S : {4, 8, 16, 32})
+        if (S <= std::max(4, nb4)) Ss.push_back(S);
+    for (int C = 1; C <= j.ncat; C *= 2) Cs.push_back(C);
+    if (Cs.back() != j.ncat) Cs.push_back(j.ncat);
+    auto fits = [&](int S, int C) { return (size_t)S * C * win_bytes <= limit; };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "tuning event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, cudaErrorMemoryAllocation, "tuning event");
+    }
+    const Tracer quiet{c, count_only_mark};
+    b->tune_ms.clear();
+    auto trial = [&](int S, int C, double& ms_out) -> cudaError_t {
+        const int Se = std::min(S, nb), Ce = std::min(C, j.ncat);
+        cudaError_t e = batch_grow(c, j, Se, Ce);
+        if (e != cudaSuccess) return e;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
+            if ((e = batch_enqueue_window_block(c, j, 0, 0, Se, 0, Ce, st, quiet)) != cudaSuccess) return e;
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+            if (rep > 0) best = std::min(best, ms);
+        }
+        ms_out = best / ((double)Se * Ce);
+        b->tune_ms.insert(b->tune_ms.end(), {(double)S, (double)C, ms_out});
+        return cudaSuccess;
+    };
+    int rc = HERMES_OK;
+    BatchPlan best;
+    double best_ms = 1e300;
+    const int C_mid = std::min(j.ncat, 8);
+    for (int S : Ss) {
+        if (!fits(S, C_mid)) continue;
+        double ms;
+        cudaError_t e = trial(S, C_mid, ms);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(c, e, "autotune (windows per launch)");
+            break;
+        }
+        if (ms < best_ms) best_ms = ms, best.S = S, best.C = C_mid;
+    }
+    if (rc == HERMES_OK && best.S == 0) rc = fail(c, HERMES_ERR_NOMEM, "no batch plan fits the free device memory");
+    if (rc == HERMES_OK) {
+        const int S = best.S;
+        for (int C : Cs) {
+            if (C == C_mid || !fits(S, C)) continue;
+            double ms;
+            cudaError_t e = trial(S, C, ms);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(c, e, "autotune (catalogues per launch)");
+                break;
+            }
+            if (ms < best_ms) best_ms = ms, best.C = C;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == HERMES_OK) j.plan = best;
+    return rc;
+}
+
+std::vector<int64_t> batch_key(const hermes_ctx* c, const BatchJob& j) {
+    const BatchState* b = c->batch;
+    std::vector<int64_t> k = {c->N, c->p, j.ncat, j.n_total, j.has_w, j.wrap, c->n_bins, j.plan.S, j.plan.C,
+                              (int64_t)(intptr_t)c->rad, (int64_t)(intptr_t)b->pos, (int64_t)(intptr_t)b->grid,
+                              (int64_t)(intptr_t)b->part, (int64_t)(intptr_t)b->res, (int64_t)(intptr_t)b->work,
+                              (int64_t)(intptr_t)c->stream};
+    for (int e : j.ells) k.push_back(e);
+    return k;
+}
+
+void counting_mark(void* vc, int, int phase, cudaStream_t) {
+    if (phase == 0) ++((BatchState*)vc)->graph_kernels;
+}
+
+}  // namespace
+
+extern "C" int hermes_batch_set_plan(hermes_ctx* c, int S, int C) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if ((S == 0) != (C == 0)) return fail(c, HERMES_ERR_ARG, "S and C are both 0 (autotune) or both positive");
+    if (S < 0 || C < 0 || (S && (S % 4 || S > MAX_BATCH)) || C > MAX_CATALOGUES)
+        return fail(c, HERMES_ERR_ARG, "S must be a multiple of 4 in 4..%d and C in 1..%d", MAX_BATCH,
+                    MAX_CATALOGUES);
+    if (!c->batch) c->batch = new BatchState;
+    c->batch->forced = BatchPlan{S, C};
+    return HERMES_OK;
+}
+
+extern "C" int hermes_batch_info(hermes_ctx* c, int* S, int* C, int64_t* graph_kernels, int64_t* graph_replays,
+                                 double* tune, int tune_cap, int* n_tune) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    const BatchState* b = c->batch;
+    if (S) *S = b ? b->last.S : 0;
+    if (C) *C = b ? b->last.C : 0;
+    if (graph_kernels) *graph_kernels = b ? b->graph_kernels : 0;
+    if (graph_replays) *graph_replays = b ? b->graph_launches : 0;
+    const int n = b ? (int)(b->tune_ms.size() / 3) : 0;
+    if (n_tune) *n_tune = n;
+    if (tune)
+        for (int i = 0; i < std::min(n, tune_cap) * 3; ++i) tune[i] = b->tune_ms[i];
+    return HERMES_OK;
+}
+
+extern "C" int hermes_xi_multipoles_batch(hermes_ctx* c, const float* pos, const float* w, const int64_t* offsets,
+                                          int n_cat, const int* ells, int n_ells, unsigned flags, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!pos || !offsets || !ells || !out) return fail(c, HERMES_ERR_ARG, "pos/offsets/ells/out is NULL");
+    if (n_cat < 1 || n_cat > MAX_CATALOGUES)
+        return fail(c, HERMES_ERR_ARG, "n_cat = %d outside 1..%d", n_cat, MAX_CATALOGUES);
+    if (n_ells < 1 || n_ells > 8) return fail(c, HERMES_ERR_ARG, "n_ells = %d outside 1..8", n_ells);
+    if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP | HERMES_EAGER))
+        return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
+    if (offsets[0] != 0) return fail(c, HERMES_ERR_ARG, "offsets[0] = %lld, must be 0", (long long)offsets[0]);
+    for (int k = 0; k < n_cat; ++k)
+        if (offsets[k + 1] <= offsets[k])
+            return fail(c, HERMES_ERR_ARG, "catalogue %d is empty or offsets decrease (the density contrast of an "
+                                           "empty catalogue is undefined)", k);
+    BatchJob j;
+    j.ncat = n_cat;
+    j.n_total = offsets[n_cat];
+    j.has_w = w != nullptr;
+    j.wrap = (flags & HERMES_WRAP) != 0;
+    for (int a = 0; a < n_ells; ++a) {
+        if (ells[a] < 0 || ells[a] > c->l_max)
+            return fail(c, HERMES_ERR_ARG, "l = %d outside 0..l_max = %d", ells[a], c->l_max);
+        if (ells[a] & 1) return fail(c, HERMES_ERR_ARG, "odd l = %d vanishes for an auto-correlation", ells[a]);
+        j.ells.push_back(ells[a]);
+    }
+    DeviceGuard g(c->device);
+    if (flags & HERMES_DEVICE_PTR) {
+        int r = check_device_ptr(c, pos, "pos");
+        if (r) return r;
+        if (w && (r = check_device_ptr(c, w, "w"))) return r;
+    }
+    if (!c->batch) c->batch = new BatchState;
+    BatchState* b = c->batch;
+    cudaStream_t st = c->stream;
+    const int nb = c->n_bins;
+    // plan: forced, cached for this shape, or tuned below
+    j.plan = b->forced;
+    const std::vector<int64_t> pkey = {c->device, c->N, c->p, n_cat, nb, n_ells};
+    bool tune = false;
+    if (j.plan.S == 0) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(pkey);
+        if (it != g_plans.end()) j.plan = it->second;
+        else tune = true;
+    }
+    const int S0 = tune ? 4 : std::min(j.plan.S, nb), C0 = tune ? 1 : std::min(j.plan.C, n_cat);
+    CK(batch_grow(c, j, S0, C0), "batch buffers");
+    // inputs go to fixed device buffers, so a captured graph stays valid across calls
+    const cudaMemcpyKind kind = (flags & HERMES_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(b->pos, pos, (size_t)j.n_total * 3 * sizeof(float), kind, st), "copy positions");
+    if (w) CK(cudaMemcpyAsync(b->w, w, (size_t)j.n_total * sizeof(float), kind, st), "copy weights");
+    CK(cudaMemcpyAsync(b->offs, offsets, (size_t)(n_cat + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st),
+       "copy offsets");
+    if (tune) {
+        CK(batch_enqueue_assign(c, j, st, c->tracer), "batch fields for tuning");
+        int r = batch_autotune(c, j, st);
+        if (r) return r;
+        {
+            std::lock_guard<std::mutex> lk(g_plan_mu);
+            g_plans[pkey] = j.plan;
+        }
+        CK(batch_grow(c, j, std::min(j.plan.S, nb), std::min(j.plan.C, n_cat)), "batch buffers");
+    }
+    const bool graphable =
+        !(flags & HERMES_EAGER) && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    if (graphable) {
+        const std::vector<int64_t> key = batch_key(c, j);
+        if (!b->exec || key != b->key) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            if (b->graph) cudaGraphDestroy(b->graph);
+            b->exec = nullptr;
+            b->graph = nullptr;
+            b->key.clear();
+            b->graph_kernels = 0;
+            const Tracer counting{b, counting_mark};
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin graph capture");
+            cudaError_t e = batch_enqueue_assign(c, j, st, counting);
+            if (e == cudaSuccess) e = batch_enqueue_windows(c, j, st, counting);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(c, e != cudaSuccess ? e : e2, "capture of the batch graph");
+            }
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                b->exec = nullptr;
+                return cuda_fail(c, e, "instantiate the batch graph");
+            }
+            b->graph = graph;
+            b->key = key;
+        }
+        c->tracer(K_BATCH_GRAPH, 0, st);
+        CK(cudaGraphLaunch(b->exec, st), "launch the batch graph");
+        c->tracer(K_BATCH_GRAPH, 1, st);
+        c->launches += b->graph_kernels - 1;  // the tracer counted the graph as one launch
+        ++b->graph_launches;
+    } else {
+        CK(batch_enqueue_assign(c, j, st, c->tracer), "batch fields");
+        CK(batch_enqueue_windows(c, j, st, c->tracer), "batch windows");
+    }
+    const size_t nwin = (size_t)n_ells * nb;
+    const size_t nres = (size_t)n_cat * nwin, nsc = (size_t)n_cat * SCAL_STRIDE;
+    CK(ensure_host(c, nres + nsc + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, b->res + 2 * nres, nres * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    CK(cudaMemcpyAsync(c->host_buf + nres, b->scal, nsc * sizeof(double), cudaMemcpyDeviceToHost, st), "read sums");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + nres + nsc);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "batch");
+    b->last = j.plan;
+    if (*hflag & 1u)
+        return fail(c, HERMES_ERR_RANGE, "a coordinate is outside [0, L] (u = x*N/L outside [0, N]) or a weight is "
+                                         "not finite; use HERMES_WRAP to wrap");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
+    for (int k = 0; k < n_cat; ++k) {
+        const double sw = c->host_buf[nres + (size_t)k * SCAL_STRIDE];
+        if (!(sw > 0.0) || !std::isfinite(sw))
+            return fail(c, HERMES_ERR_RANGE, "catalogue %d: sum of weights is %g; it must be positive", k, sw);
+    }
+    std::memcpy(out, c->host_buf, nres * sizeof(double));
     return HERMES_OK;
 }

@@ -5,12 +5,18 @@
 
 namespace hermes {
 
-constexpr int MAX_BATCH = 32;
+constexpr int MAX_BATCH = 32;  // windows evaluated per launch of the first inverse pass (upper bound)
+
+// Batched measurements: catalogues per call, and the per-catalogue strides of
+// the field scalars (sum w, sum w^2, N^3/sum w, ...) and of the float self-pair tables.
+constexpr int MAX_CATALOGUES = 1024;
+constexpr int SCAL_STRIDE = 8;
+constexpr int STAB_STRIDE = 512;
 
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -20,7 +26,7 @@ struct Tracer {
     void operator()(int id, int phase, cudaStream_t st) const {
         if (mark) mark(ctx, id, phase, st);
     }
-};  // windows evaluated per launch of the first inverse pass
+};
 
 // Radial tables are stored bin-fastest: rad[(l*Q + q)*nbp + b], nbp a multiple
 // of 4, so one 16-byte load returns the values of 4 consecutive bins at |n|^2 = q.
@@ -54,29 +60,45 @@ struct KsOrders {
 struct Tables {
     const float2* tw;     // twiddle tables, layout in fft_core.cuh
     const float* phi;     // [N]  sinc^{2p}(pi n / N), FFT order
-    const float* stab;    // [p^3] self-pair table (float)
+    const float* stab;    // [p^3] self-pair table (float); batched: catalogue c at stab + c*STAB_STRIDE
 };
 
 // scatter.cu
 cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
                            int wrap, unsigned* err, cudaStream_t st, const Tracer& tr);
+// catalogue c: points [offs[c], offs[c+1]) (device offsets), grid + c*N^3
+cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int ncat,
+                                 int64_t n, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
+                                 const Tracer& tr);
 cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
                          unsigned* err, cudaStream_t st, const Tracer& tr);
-cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr);
+// offs != nullptr: per-catalogue partials, [ncat][2][nblk] (sums) and [ncat][p^3][nblk] (self-pair)
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr,
+                               const int64_t* offs = nullptr, int ncat = 1);
 cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
-                            int nblk, cudaStream_t st, const Tracer& tr);
+                            int nblk, cudaStream_t st, const Tracer& tr, const int64_t* offs = nullptr,
+                            int ncat = 1);
 cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* out, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_reduce_rows_strided(const double* part, int rows, int cols, int S, double* out, int out_stride,
+                                       cudaStream_t st, const Tracer& tr);
 cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3, float* stab_f, int N,
                                 double* scal, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_finish_batch(const double* sums, const double* sp, int p3, float* stab_f, int N, double* scal,
+                                int ncat, cudaStream_t st, const Tracer& tr);
+cudaError_t launch_xi_batch_finish(const double* dd, const double* sn, const double* scal, int ncat, int nwin, int N,
+                                   double* out, cudaStream_t st, const Tracer& tr);
 
-// fft_passes.cu
+// fft_passes.cu.  ncat > 1: catalogue c uses grid + c*N^3, spec + c*N*N*(N/2),
+// scal + c*SCAL_STRIDE; the inverse work buffer is [ncat][S][N][N][N/2] and the
+// partials are [ncat][S][blocks].
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
-                           cudaStream_t st, const Tracer& tr);
+                           cudaStream_t st, const Tracer& tr, int ncat = 1);
 int inv_x_blocks(int N);
-int inv_z_blocks(int N);
+int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
+int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)
 cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta,
                               const WinBatch& wb, const Tables& tb, double* sn_part, double* dd_part,
-                              unsigned* err, cudaStream_t st, const Tracer& tr);
+                              unsigned* err, cudaStream_t st, const Tracer& tr, int ncat = 1);
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr);
 

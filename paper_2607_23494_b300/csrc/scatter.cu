@@ -83,36 +83,70 @@ __device__ __forceinline__ void add_run(float* row, int z0, int N, float w, cons
     }
 }
 
+// One point's p^3 contributions (err bit 1 on a rejected coordinate or weight).
+template <int P>
+__device__ __forceinline__ void scatter_point(float x, float y, float z, float wi, float* __restrict__ grid, float s,
+                                              int N, int wrap, unsigned* __restrict__ err) {
+    const int msk = N - 1;
+    float bx[P], by[P], bz[P];
+    int fx, fy, fz;
+    bool ok = node_rule<P>(x, s, N, wrap, fx, bx) & node_rule<P>(y, s, N, wrap, fy, by) &
+              node_rule<P>(z, s, N, wrap, fz, bz);
+    if (!ok || !isfinite(wi)) {
+        atomicOr(err, 1u);
+        return;
+    }
+    const int z0 = fz & msk;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const int ix = (fx + a) & msk;
+        const float wa = wi * bx[a];
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const int iy = (fy + b) & msk;
+            const float wab = wa * by[b];
+            float* row = grid + ((size_t)ix * N + iy) * N;
+            add_run<P>(row, z0, N, wab, bz);
+        }
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, const float* __restrict__ w,
                                                  int64_t n, float* __restrict__ grid, float s, int N, int wrap,
                                                  unsigned* __restrict__ err) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int msk = N - 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float x = __ldg(pos + 3 * i), y = __ldg(pos + 3 * i + 1), z = __ldg(pos + 3 * i + 2);
         const float wi = w ? __ldg(w + i) : 1.0f;
-        float bx[P], by[P], bz[P];
-        int fx, fy, fz;
-        bool ok = node_rule<P>(x, s, N, wrap, fx, bx) & node_rule<P>(y, s, N, wrap, fy, by) &
-                  node_rule<P>(z, s, N, wrap, fz, bz);
-        if (!ok || !isfinite(wi)) {
-            atomicOr(err, 1u);
-            continue;
+        scatter_point<P>(x, y, z, wi, grid, s, N, wrap, err);
+    }
+}
+
+// Batched scatter: catalogue c owns points [offs[c], offs[c+1]) of one
+// concatenated array and grid c (N^3 floats, consecutive grids).  The grid
+// stride runs over all points, so uneven catalogues share the GPU evenly; each
+// point finds its catalogue by bisection over the offsets held in shared memory.
+template <int P>
+__global__ void __launch_bounds__(256) k_scatter_batch(const float* __restrict__ pos, const float* __restrict__ w,
+                                                       const int64_t* __restrict__ offs, int ncat, int64_t n,
+                                                       float* __restrict__ grid, float s, int N, int wrap,
+                                                       unsigned* __restrict__ err) {
+    __shared__ int64_t so[MAX_CATALOGUES + 1];
+    for (int c = threadIdx.x; c <= ncat; c += blockDim.x) so[c] = offs[c];
+    __syncthreads();
+    const size_t n3 = (size_t)N * N * N;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = ncat;  // so[lo] <= i < so[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (so[mid] <= i) lo = mid;
+            else hi = mid;
         }
-        const int z0 = fz & msk;
-#pragma unroll
-        for (int a = 0; a < P; ++a) {
-            const int ix = (fx + a) & msk;
-            const float wa = wi * bx[a];
-#pragma unroll
-            for (int b = 0; b < P; ++b) {
-                const int iy = (fy + b) & msk;
-                const float wab = wa * by[b];
-                float* row = grid + ((size_t)ix * N + iy) * N;
-                add_run<P>(row, z0, N, wab, bz);
-            }
-        }
+        const float x = __ldg(pos + 3 * i), y = __ldg(pos + 3 * i + 1), z = __ldg(pos + 3 * i + 2);
+        const float wi = w ? __ldg(w + i) : 1.0f;
+        scatter_point<P>(x, y, z, wi, grid + (size_t)lo * n3, s, N, wrap, err);
     }
 }
 
@@ -136,9 +170,17 @@ __global__ void __launch_bounds__(256) k_nodes(const float* __restrict__ pos, in
     }
 }
 
+// offs == nullptr: one catalogue of n points.  Otherwise blockIdx.y = catalogue
+// c over points [offs[c], offs[c+1]), partials at part + c * 2 * gridDim.x.
 __global__ void __launch_bounds__(256) k_weight_sums(const float* __restrict__ w, int64_t n,
-                                                     double* __restrict__ part) {
+                                                     const int64_t* __restrict__ offs, double* __restrict__ part) {
     __shared__ double red[8];
+    if (offs) {
+        const int64_t lo = offs[blockIdx.y];
+        n = offs[blockIdx.y + 1] - lo;
+        if (w) w += lo;
+        part += (size_t)blockIdx.y * 2 * gridDim.x;
+    }
     double s1 = 0.0, s2 = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -159,8 +201,16 @@ __global__ void __launch_bounds__(256) k_weight_sums(const float* __restrict__ w
 // them over the staged points (float32), then the block sums in float64.
 template <int P>
 __global__ void __launch_bounds__(256) k_selfpair(const float* __restrict__ pos, const float* __restrict__ w,
-                                                  int64_t n, float s, int N, double* __restrict__ part) {
+                                                  int64_t n, const int64_t* __restrict__ offs, float s, int N,
+                                                  double* __restrict__ part) {
     constexpr int P3 = P * P * P;
+    if (offs) {  // batched: blockIdx.y = catalogue, as k_weight_sums
+        const int64_t lo = offs[blockIdx.y];
+        n = offs[blockIdx.y + 1] - lo;
+        pos += 3 * lo;
+        if (w) w += lo;
+        part += (size_t)blockIdx.y * P3 * gridDim.x;
+    }
     constexpr int E = (P3 + 31) / 32;
     constexpr int STRIDE = 3 * P + 1;
     __shared__ float stage[8][32][STRIDE];
@@ -240,6 +290,47 @@ __global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ 
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
+// Row r of part (cols wide) summed into out[(r / S) * out_stride + r % S]: the
+// rows of a batched launch are [catalogue][window] and land in a [catalogue][...]
+// result array.
+__global__ void __launch_bounds__(256) k_reduce_rows_strided(const double* __restrict__ part, int cols, int S,
+                                                             double* __restrict__ out, int out_stride) {
+    __shared__ double red[8];
+    const double* row = part + (size_t)blockIdx.x * cols;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += row[c];
+    s = block_sum_double(s, red);
+    if (threadIdx.x == 0) out[(size_t)(blockIdx.x / S) * out_stride + blockIdx.x % S] = s;
+}
+
+// Per catalogue c (one block each): scal[c*SCAL_STRIDE + 0..2] = sum w, sum w^2,
+// N^3 / sum w; float copy of its self-pair table at stab_f + c*STAB_STRIDE.
+__global__ void __launch_bounds__(256) k_finish_batch(const double* __restrict__ sums, const double* __restrict__ sp,
+                                                      int p3, float* __restrict__ stab_f, int N,
+                                                      double* __restrict__ scal) {
+    const int c = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const double sw = sums[2 * c];
+        scal[(size_t)c * SCAL_STRIDE + 0] = sw;
+        scal[(size_t)c * SCAL_STRIDE + 1] = sums[2 * c + 1];
+        scal[(size_t)c * SCAL_STRIDE + 2] = (double)N * (double)N * (double)N / sw;
+    }
+    for (int e = threadIdx.x; e < p3; e += blockDim.x) stab_f[(size_t)c * STAB_STRIDE + e] = (float)sp[(size_t)c * p3 + e];
+}
+
+// xi of every (catalogue, window): out[c*nwin + w] = dd/N^6 - sn/(N^6 eps_bar_c^2),
+// eps_bar_c = sum w_c / N^3 (dd, sn laid out like out).
+__global__ void __launch_bounds__(256) k_xi_batch_finish(const double* __restrict__ dd, const double* __restrict__ sn,
+                                                         const double* __restrict__ scal, int ncat, int nwin, int N,
+                                                         double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncat * nwin) return;
+    const int c = i / nwin;
+    const double n3 = (double)N * N * N, n6 = n3 * n3;
+    const double eb = scal[(size_t)c * SCAL_STRIDE] / n3;
+    out[i] = dd[i] / n6 - sn[i] / (n6 * eb * eb);
+}
+
 // scal[0] = sum w, scal[1] = sum w^2, scal[2] = N^3 / sum w (the inverse mean);
 // float copy of the self-pair table for the window kernels.
 __global__ void k_finish_field(const double* __restrict__ sums, const double* __restrict__ stab_d, int p3,
@@ -291,19 +382,39 @@ cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr) {
+cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int ncat,
+                                 int64_t n, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
+                                 const Tracer& tr) {
+    if (n == 0) return cudaSuccess;
+    if (ncat < 1 || ncat > MAX_CATALOGUES) return cudaErrorInvalidValue;
+    const int nb = nblocks_for(n, 256, 148 * 32);
+    tr(K_SCATTER, 0, st);
+    switch (p) {
+#define HERMES_SC(P) \
+    case P: k_scatter_batch<P><<<nb, 256, 0, st>>>(pos, w, offs, ncat, n, grid, s, N, wrap, err); break;
+        HERMES_SC(1) HERMES_SC(2) HERMES_SC(3) HERMES_SC(4) HERMES_SC(5) HERMES_SC(6) HERMES_SC(7) HERMES_SC(8)
+#undef HERMES_SC
+        default: return cudaErrorInvalidValue;
+    }
+    tr(K_SCATTER, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weight_sums(const float* w, int64_t n, double* part, int nblk, cudaStream_t st, const Tracer& tr,
+                               const int64_t* offs, int ncat) {
     tr(K_WEIGHT_SUMS, 0, st);
-    k_weight_sums<<<nblk, 256, 0, st>>>(w, n, part);
+    k_weight_sums<<<dim3(nblk, offs ? ncat : 1), 256, 0, st>>>(w, n, offs, part);
     tr(K_WEIGHT_SUMS, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int64_t n, float s, double* part,
-                            int nblk, cudaStream_t st, const Tracer& tr) {
+                            int nblk, cudaStream_t st, const Tracer& tr, const int64_t* offs, int ncat) {
     tr(K_SELFPAIR, 0, st);
+    const dim3 g(nblk, offs ? ncat : 1);
     switch (p) {
 #define HERMES_SP(P) \
-    case P: k_selfpair<P><<<nblk, 256, 0, st>>>(pos, w, n, s, N, part); break;
+    case P: k_selfpair<P><<<g, 256, 0, st>>>(pos, w, n, offs, s, N, part); break;
         HERMES_SP(1) HERMES_SP(2) HERMES_SP(3) HERMES_SP(4) HERMES_SP(5) HERMES_SP(6) HERMES_SP(7) HERMES_SP(8)
 #undef HERMES_SP
         default: return cudaErrorInvalidValue;
@@ -325,6 +436,32 @@ cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3
                                 double* scal, cudaStream_t st, const Tracer& tr) {
     tr(K_FINISH, 0, st);
     k_finish_field<<<1, 256, 0, st>>>(sums, stab_d, p3, stab_f, N, scal);
+    tr(K_FINISH, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rows_strided(const double* part, int rows, int cols, int S, double* out, int out_stride,
+                                       cudaStream_t st, const Tracer& tr) {
+    if (rows <= 0) return cudaSuccess;
+    tr(K_REDUCE, 0, st);
+    k_reduce_rows_strided<<<rows, 256, 0, st>>>(part, cols, S, out, out_stride);
+    tr(K_REDUCE, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_batch(const double* sums, const double* sp, int p3, float* stab_f, int N, double* scal,
+                                int ncat, cudaStream_t st, const Tracer& tr) {
+    tr(K_FINISH, 0, st);
+    k_finish_batch<<<ncat, 256, 0, st>>>(sums, sp, p3, stab_f, N, scal);
+    tr(K_FINISH, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xi_batch_finish(const double* dd, const double* sn, const double* scal, int ncat, int nwin, int N,
+                                   double* out, cudaStream_t st, const Tracer& tr) {
+    const int n = ncat * nwin;
+    tr(K_FINISH, 0, st);
+    k_xi_batch_finish<<<(n + 255) / 256, 256, 0, st>>>(dd, sn, scal, ncat, nwin, N, out);
     tr(K_FINISH, 1, st);
     return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ ERR_TIMEOUT = -5
 ERR_STATE = -6
 DEVICE_PTR = 1
 WRAP = 2
+EAGER = 4
 
 _NAMES = {ERR_ARG: "HERMES_ERR_ARG", ERR_RANGE: "HERMES_ERR_RANGE", ERR_NOMEM: "HERMES_ERR_NOMEM",
           ERR_CUDA: "HERMES_ERR_CUDA", ERR_TIMEOUT: "HERMES_ERR_TIMEOUT", ERR_STATE: "HERMES_ERR_STATE"}
@@ -50,6 +51,11 @@ def _load() -> C.CDLL:
         "hermes_xi": (i32, [vp, dp]),
         "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
         "hermes_xi_multipoles_kspace": (i32, [vp, C.POINTER(i32), i32, dp]),
+        "hermes_xi_multipoles_batch": (i32, [vp, vp, vp, C.POINTER(C.c_int64), i32, C.POINTER(i32), i32, C.c_uint,
+                                             dp]),
+        "hermes_batch_set_plan": (i32, [vp, i32, i32]),
+        "hermes_batch_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64), dp, i32, C.POINTER(i32)]),
         "hermes_zeta_multipoles": (i32, [vp, dp]),
         "hermes_last_error": (C.c_char_p, [vp]),
         "hermes_debug_get_delta": (i32, [vp, fp]),
@@ -197,6 +203,56 @@ class Context:
         self._check(_lib.hermes_xi_multipoles_kspace(self._h, ea.ctypes.data_as(C.POINTER(C.c_int)), len(ea),
                                                      _dptr(out)), "hermes_xi_multipoles_kspace")
         return out
+
+    def xi_multipoles_batch(self, pos, w, offsets, ells: Sequence[int], wrap: bool = False,
+                            graph: bool = True) -> np.ndarray:
+        """xi_l of every catalogue: catalogue k is rows offsets[k]:offsets[k+1] of pos (n,3) and w (n,) or None.
+        pos / w: float32 numpy arrays or torch tensors (CUDA tensors are read in place).
+        Returns [n_cat, len(ells), n_bins]."""
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        n_cat = len(offs) - 1
+        ea = np.ascontiguousarray(ells, dtype=np.int32)
+        flags = (WRAP if wrap else 0) | (0 if graph else EAGER)
+        keep = []
+        if hasattr(pos, "data_ptr"):
+            import torch
+            assert pos.dtype == torch.float32 and pos.is_contiguous() and pos.dim() == 2 and pos.shape[1] == 3
+            if w is not None:
+                assert w.dtype == torch.float32 and w.is_contiguous() and w.is_cuda == pos.is_cuda
+            if pos.is_cuda:
+                flags |= DEVICE_PTR
+            pp, wp = pos.data_ptr(), (None if w is None else w.data_ptr())
+        else:
+            pos = np.ascontiguousarray(pos, dtype=np.float32)
+            if pos.ndim != 2 or pos.shape[1] != 3:
+                raise ValueError("pos must have shape (n, 3)")
+            keep.append(pos)
+            pp = pos.ctypes.data
+            wp = None
+            if w is not None:
+                w = np.ascontiguousarray(w, dtype=np.float32)
+                keep.append(w)
+                wp = w.ctypes.data
+        if n_cat >= 1 and offs[-1] != pos.shape[0]:
+            raise ValueError(f"offsets[-1] = {offs[-1]} but pos has {pos.shape[0]} rows")
+        out = np.empty((max(n_cat, 0), len(ea), self.n_bins), dtype=np.float64)
+        rc = _lib.hermes_xi_multipoles_batch(self._h, pp, wp, offs.ctypes.data_as(C.POINTER(C.c_int64)), n_cat,
+                                             ea.ctypes.data_as(C.POINTER(C.c_int)), len(ea), flags, _dptr(out))
+        self._check(rc, "hermes_xi_multipoles_batch")
+        return out
+
+    def batch_set_plan(self, S: int = 0, C_: int = 0) -> None:
+        self._check(_lib.hermes_batch_set_plan(self._h, int(S), int(C_)), "hermes_batch_set_plan")
+
+    def batch_info(self) -> dict:
+        S, Cc, n_t = C.c_int(), C.c_int(), C.c_int()
+        gk, gr = C.c_int64(), C.c_int64()
+        tune = np.zeros(3 * 64, dtype=np.float64)
+        self._check(_lib.hermes_batch_info(self._h, C.byref(S), C.byref(Cc), C.byref(gk), C.byref(gr), _dptr(tune),
+                                           64, C.byref(n_t)), "hermes_batch_info")
+        n = min(n_t.value, 64)
+        return {"S": S.value, "C": Cc.value, "graph_kernels": gk.value, "graph_replays": gr.value,
+                "tuning": [tuple(tune[3 * i:3 * i + 3]) for i in range(n)]}
 
     def zeta_multipoles(self) -> np.ndarray:
         out = np.empty((self.l_max + 1, self.n_bins, self.n_bins), dtype=np.float64)
