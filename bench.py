@@ -42,6 +42,9 @@ UNIT = "cell-window/s"
 L2, N2, P2, NPTS2 = 1000.0, 512, 4, 10_000_000
 EDGES2 = np.linspace(2.0, 202.0, 41)
 ELLS2 = (0, 2, 4)
+# batched configuration
+L4, N4, NCAT4 = 500.0, 256, 64
+EDGES4 = np.linspace(5.0, 155.0, 31)
 # 3PCF multipoles configuration
 L3, N3, NPTS3 = 500.0, 512, 2_000_000
 EDGES3 = np.linspace(10.0, 170.0, 17)
@@ -248,6 +251,10 @@ def run_hermes(args, rank, world, local_rank):
         plain = run_plain_fp32(pos_d, mass_d, res)
         plain["speedup"] = round(value / world / plain["value"], 2)
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, dev, stream, rank)
+
     zeta = None
     if not args.no_zeta:
         zeta = run_zeta(args, dev, stream, rank)
@@ -276,6 +283,8 @@ def run_hermes(args, rank, world, local_rank):
         out["kspace"] = ks
         if plain:
             out["vs_plain_fp32"] = plain
+        if batch:
+            out["batch"] = batch
         if zeta:
             out["zeta"] = zeta
     return out, pos
@@ -312,44 +321,45 @@ def run_kspace(ctx, stream, real):
             "kernels": {k: {"ms": round(v[0] / reps, 3), "launches": v[1] // reps} for k, v in tr.items()}}
 
 
-def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
+class PlainPipeline:
     """The plain one-request-at-a-time FP32 pipeline on the same GPU, for the ratio
     the metric asks for: torch ops and cuFFT only (index_add_ B-spline scatter,
     rfftn, then per window: build K on the device, multiply, irfftn, cell dot
-    product, self-pair term).  The per-catalogue part is timed on both fields, the
-    per-window part on n_win windows of each field (every window costs the same);
-    the step estimate is 2 * catalogue + 240 * window.  Comparison arm only."""
-    import torch
-    from paper_2607_23494_b300.hermes import shell_table_host
-    dev = pos_d.device
-    N, L, p = N2, L2, P2
-    H = N // 2
-    nb = len(EDGES2) - 1
-    T = torch.from_numpy(shell_table_host(L, N, EDGES2, max(ELLS2)).astype(np.float32)).to(dev)
-    fxy = torch.fft.fftfreq(N, d=1.0 / N, device=dev).round().to(torch.int64)
-    fz = torch.arange(H + 1, device=dev, dtype=torch.int64)
-    q = (fxy[:, None, None] ** 2 + fxy[None, :, None] ** 2 + fz[None, None, :] ** 2)
-    ph1 = torch.sinc(fxy.double() / N) ** (2 * p)
-    ph1z = torch.sinc(fz.double() / N) ** (2 * p)
-    keep = ((fxy.abs() != H)[:, None, None] & (fxy.abs() != H)[None, :, None] & (fz != H)[None, None, :])
-    phi = (ph1[:, None, None] * ph1[None, :, None] * ph1z[None, None, :]).float() * keep
-    q = torch.where(keep, q, torch.zeros((), device=dev, dtype=q.dtype))  # tables stop below the Nyquist planes
-    mu = torch.where(q > 0, fz[None, None, :].float() / q.float().clamp(min=1).sqrt(), torch.zeros((), device=dev))
-    leg = {0: torch.ones_like(mu), 2: 0.5 * (3 * mu ** 2 - 1), 4: (35 * mu ** 4 - 30 * mu ** 2 + 3) / 8}
-    wz = torch.full((H + 1,), 2.0, device=dev)
-    wz[0] = 1.0
-    wz[H] = 1.0
-    cxy = torch.stack([torch.ones(N, device=dev, dtype=torch.float64)] +
-                      [2 * torch.cos(2 * np.pi * fxy.double() * a / N) for a in range(1, p)], 1)
-    cz = torch.stack([torch.ones(H + 1, device=dev, dtype=torch.float64)] +
-                     [2 * torch.cos(2 * np.pi * fz.double() * a / N) for a in range(1, p)], 1)
+    product, self-pair term).  Comparison arm only; cubic B-spline (p = 4)."""
 
-    def mp(x):  # centred cubic B-spline
+    def __init__(self, N, L, edges, ells, dev):
+        import torch
+        from paper_2607_23494_b300.hermes import shell_table_host
+        self.N, self.L, self.p, self.dev, self.torch = N, L, 4, dev, torch
+        p, H = self.p, N // 2
+        self.T = torch.from_numpy(shell_table_host(L, N, edges, max(ells)).astype(np.float32)).to(dev)
+        fxy = torch.fft.fftfreq(N, d=1.0 / N, device=dev).round().to(torch.int64)
+        fz = torch.arange(H + 1, device=dev, dtype=torch.int64)
+        q = (fxy[:, None, None] ** 2 + fxy[None, :, None] ** 2 + fz[None, None, :] ** 2)
+        ph1 = torch.sinc(fxy.double() / N) ** (2 * p)
+        ph1z = torch.sinc(fz.double() / N) ** (2 * p)
+        keep = ((fxy.abs() != H)[:, None, None] & (fxy.abs() != H)[None, :, None] & (fz != H)[None, None, :])
+        self.phi = (ph1[:, None, None] * ph1[None, :, None] * ph1z[None, None, :]).float() * keep
+        self.q = torch.where(keep, q, torch.zeros((), device=dev, dtype=q.dtype))  # tables stop below Nyquist
+        mu = torch.where(q > 0, fz[None, None, :].float() / q.float().clamp(min=1).sqrt(), torch.zeros((), device=dev))
+        self.leg = {0: torch.ones_like(mu), 2: 0.5 * (3 * mu ** 2 - 1), 4: (35 * mu ** 4 - 30 * mu ** 2 + 3) / 8}
+        self.wz = torch.full((H + 1,), 2.0, device=dev)
+        self.wz[0] = 1.0
+        self.wz[H] = 1.0
+        self.cxy = torch.stack([torch.ones(N, device=dev, dtype=torch.float64)] +
+                               [2 * torch.cos(2 * np.pi * fxy.double() * a / N) for a in range(1, p)], 1)
+        self.cz = torch.stack([torch.ones(H + 1, device=dev, dtype=torch.float64)] +
+                              [2 * torch.cos(2 * np.pi * fz.double() * a / N) for a in range(1, p)], 1)
+
+    @staticmethod
+    def _mp(x):  # centred cubic B-spline
+        import torch
         ax = x.abs()
         return torch.where(ax < 1, 2.0 / 3 - ax ** 2 + 0.5 * ax ** 3,
                            torch.where(ax < 2, (2 - ax) ** 3 / 6, torch.zeros_like(ax)))
 
-    def catalogue(pos, w):
+    def catalogue(self, pos, w):
+        torch, N, L, p, dev = self.torch, self.N, self.L, self.p, self.dev
         grid = torch.zeros(N ** 3, device=dev, dtype=torch.float32)
         S = torch.zeros(p, p, p, device=dev, dtype=torch.float64)
         sw = torch.zeros((), device=dev, dtype=torch.float64)
@@ -360,8 +370,8 @@ def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
             i = torch.floor(u)
             t = u - i
             j = torch.arange(p, device=dev, dtype=torch.float32)
-            wts = mp(t[:, :, None] + 1 - j)                               # [n, 3, 4]
-            nodes = (i.long()[:, :, None] - 1 + j.long()) % N              # [n, 3, 4]
+            wts = self._mp(t[:, :, None] + 1 - j)                          # [n, 3, 4]
+            nodes = (i.long()[:, :, None] - 1 + j.long()) % N             # [n, 3, 4]
             flat = (nodes[:, 0, :, None, None] * N + nodes[:, 1, None, :, None]) * N + nodes[:, 2, None, None, :]
             val = ww[:, None, None, None] * wts[:, 0, :, None, None] * wts[:, 1, None, :, None] * wts[:, 2, None, None, :]
             grid.index_add_(0, flat.reshape(-1), val.reshape(-1))
@@ -372,26 +382,36 @@ def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
         delta = grid.view(N, N, N) / ebar.float() - 1
         dh = torch.fft.rfftn(delta)
         dh[0, 0, 0] = 0
-        shat = torch.einsum("abc,xa,yb,zc->xyz", S, cxy, cxy, cz).float()
-        snw = shat * wz / float(N) ** 6 / ebar.float() ** 2  # K carries Phi^ already
+        shat = torch.einsum("abc,xa,yb,zc->xyz", S, self.cxy, self.cxy, self.cz).float()
+        snw = shat * self.wz / float(N) ** 6 / ebar.float() ** 2  # K carries Phi^ already
         return delta, dh, snw
 
-    def window(delta, dh, snw, b, ell):
+    def window(self, field, b, ell):
+        torch, N = self.torch, self.N
+        delta, dh, snw = field
         c = (2 * ell + 1) * (-1) ** (ell // 2)
-        K = c * T[b, ell][q] * phi * leg[ell]
+        K = c * self.T[b, ell][self.q] * self.phi * self.leg[ell]
         dt = torch.fft.irfftn(dh * K, s=(N, N, N))
         return (delta * dt).sum(dtype=torch.float64) / N ** 3 - (K * snw).sum(dtype=torch.float64)
 
+
+def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
+    """Plain pipeline on the 512^3 workload: the per-catalogue part is timed on both
+    fields, the per-window part on n_win windows of each field (every window costs
+    the same); the step estimate is 2 * catalogue + 240 * window."""
+    import torch
+    nb = len(EDGES2) - 1
+    pp = PlainPipeline(N2, L2, EDGES2, ELLS2, pos_d.device)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    catalogue(pos_d, None)  # warm-up (cuFFT plans, allocator)
+    pp.catalogue(pos_d, None)  # warm-up (cuFFT plans, allocator)
     torch.cuda.synchronize()
     e[0].record()
-    fields = [catalogue(pos_d, None), catalogue(pos_d, mass_d)]
+    fields = [pp.catalogue(pos_d, None), pp.catalogue(pos_d, mass_d)]
     e[1].record()
     picks = [(b, ELLS2[k % len(ELLS2)]) for k, b in enumerate(np.linspace(0, nb - 1, n_win).astype(int))]
-    window(*fields[0], 0, 0)
+    pp.window(fields[0], 0, 0)
     e[2].record()
-    got = [[float(window(*fields[f], b, ell)) for (b, ell) in picks] for f in range(2)]
+    got = [[float(pp.window(fields[f], b, ell)) for (b, ell) in picks] for f in range(2)]
     e[3].record()
     torch.cuda.synchronize()
     cat_ms = e[0].elapsed_time(e[1]) / 2
@@ -402,12 +422,94 @@ def run_plain_fp32(pos_d, mass_d, real_res, n_win=6):
         for (b, ell), g in zip(picks, got[f]):
             r = float(real_res[f][ELLS2.index(ell)][b])
             worst = max(worst, abs(g - r) / max(1e-4 * abs(r), 1e-6))
-    del fields, q, phi, mu, leg, keep
+    del fields, pp
     torch.cuda.empty_cache()
-    return {"value": round(N ** 3 * 2 * len(ELLS2) * nb / (step_ms / 1e3), 1), "unit": UNIT,
+    return {"value": round(N2 ** 3 * 2 * len(ELLS2) * nb / (step_ms / 1e3), 1), "unit": UNIT,
             "ms_per_step": round(step_ms, 2), "ms_per_catalogue": round(cat_ms, 3), "ms_per_window": round(win_ms, 3),
             "windows_timed": 2 * n_win, "what": "torch index_add_ scatter + cuFFT rfftn/irfftn, one window at a time",
             "diff_vs_hermes_in_tolerances": round(worst, 3)}
+
+
+def gen_batch(seed: int):
+    """64 lognormal catalogues, sizes log-uniform in [1e5, 5e6], one seed each."""
+    from synthetic import catalogues as S
+    sizes = S.batched_catalogue_sizes(NCAT4, 1e5, 5e6, seed=seed)
+    cats = [S.lognormal_catalogue(int(n), L4, seed=seed + 1 + k, n_grid=128) for k, n in enumerate(sizes)]
+    offs = np.concatenate([[0], np.cumsum([c.shape[0] for c in cats])]).astype(np.int64)
+    return np.concatenate(cats).astype(np.float32), offs
+
+
+def run_batch(args, dev, stream, rank):
+    """The batched configuration: 64 uneven catalogues, 256^3, 30 shells, l = 0.
+    Three arms on the same catalogues: the batched call (graph replay, autotuned
+    plan), the same library one catalogue at a time, and the plain FP32 pipeline."""
+    import torch
+    from paper_2607_23494_b300 import Context
+    pos, offs = gen_batch(777 + 17 * rank)
+    pos_d = torch.from_numpy(pos).to(dev)
+    ncat, nb = len(offs) - 1, len(EDGES4) - 1
+    cw = float(N4) ** 3 * nb * ncat  # cell-window evaluations per batch
+    ctx = Context(L4, N4, 4)
+    ctx.set_stream(stream)
+    ctx.window_shells(EDGES4, l_max=0)
+    t0 = time.time()
+    ref = ctx.xi_multipoles_batch(pos_d, None, offs, (0,))  # tunes, captures the graph
+    first_s = time.time() - t0
+    reps = max(2, min(args.steps, 5))
+    ctx.xi_multipoles_batch(pos_d, None, offs, (0,))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
+    e0.record(stream)
+    for _ in range(reps):
+        got = ctx.xi_multipoles_batch(pos_d, None, offs, (0,))
+    e1.record(stream)
+    stream.synchronize()
+    b_ms = e0.elapsed_time(e1) / reps
+    launches = (ctx.launch_count() - l0) // reps
+    info = ctx.batch_info()
+    # one catalogue at a time through hermes_assign + hermes_xi_multipoles
+    seq = np.empty_like(got)
+    e0.record(stream)
+    for k in range(ncat):
+        ctx.assign(pos_d[offs[k]:offs[k + 1]])
+        seq[k] = ctx.xi_multipoles((0,))
+    e1.record(stream)
+    stream.synchronize()
+    s_ms = e0.elapsed_time(e1)
+    ctx.close()
+    diff = float(np.max(np.abs(got - seq) / np.maximum(1e-4 * np.abs(seq), 1e-6)))
+    # plain FP32 pipeline, every catalogue and window
+    pp = PlainPipeline(N4, L4, EDGES4, (0,), dev)
+    pp.catalogue(pos_d[:offs[1]], None)
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    plain_vals = []
+    for k in range(ncat):
+        f = pp.catalogue(pos_d[offs[k]:offs[k + 1]], None)
+        plain_vals.append([pp.window(f, b, 0) for b in range(nb)])
+        del f
+    plain_vals = np.array([[float(v) for v in row] for row in plain_vals])
+    e3.record()
+    torch.cuda.synchronize()
+    p_ms = e2.elapsed_time(e3)
+    pdiff = float(np.max(np.abs(plain_vals - got[:, 0, :]) / np.maximum(1e-4 * np.abs(got[:, 0, :]), 1e-6)))
+    del pp
+    torch.cuda.empty_cache()
+    return {"workload": f"{ncat} lognormal catalogues, {int(offs[-1])} points (log-uniform sizes in [1e5, 5e6]), "
+                        f"L={L4:g}, {N4}^3, p=4, {nb} shells [5,155), l=0",
+            "batched": {"value": round(cw / (b_ms / 1e3), 1), "unit": UNIT, "ms_per_batch": round(b_ms, 2),
+                        "plan": {"S": info["S"], "C": info["C"]}, "graph_kernels": info["graph_kernels"],
+                        "gpu_launches_per_batch": launches, "first_call_s_incl_tuning": round(first_s, 2),
+                        "tuning": [[int(a), int(b), round(c, 4)] for a, b, c in info["tuning"]]},
+            "one_at_a_time": {"value": round(cw / (s_ms / 1e3), 1), "ms_per_batch": round(s_ms, 2),
+                              "diff_vs_batched_in_tolerances": round(diff, 4)},
+            "plain_fp32": {"value": round(cw / (p_ms / 1e3), 1), "ms_per_batch": round(p_ms, 2),
+                           "diff_vs_batched_in_tolerances": round(pdiff, 4)},
+            "speedup_vs_plain": round(p_ms / b_ms, 2), "speedup_vs_one_at_a_time": round(s_ms / b_ms, 2)}
 
 
 def run_zeta(args, dev, stream, rank):
@@ -539,6 +641,7 @@ def main():
     ap.add_argument("--impl", default="hermes", choices=["hermes", "reference"])
     ap.add_argument("--no-zeta", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain torch/cuFFT comparison arm")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-catalogue measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")

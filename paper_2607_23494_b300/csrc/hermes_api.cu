@@ -336,7 +336,6 @@ void trace_collect(hermes_ctx* c) {
 int ensure_host(hermes_ctx* c, size_t n) {
     if (n <= c->host_cap) return HERMES_OK;
     if (c->host_buf) cudaFreeHost(c->host_buf);
-    batch_free(c->batch);
     c->host_buf = nullptr;
     c->host_cap = 0;
     if (cudaMallocHost((void**)&c->host_buf, n * sizeof(double)) != cudaSuccess) {
@@ -443,6 +442,8 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->stage_pos);
     cudaFree(c->stage_w);
     cudaFree(c->rad);
+    batch_free(c->batch);
+    c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
     for (auto& p : c->pending) {
         cudaEventDestroy(p.a);
@@ -1123,11 +1124,19 @@ cudaError_t batch_enqueue_assign(hermes_ctx* c, const BatchJob& j, cudaStream_t 
     const float s = (float)((double)N / c->L);
     const float* w = j.has_w ? b->w : nullptr;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(b->grid, 0, (size_t)j.ncat * n3 * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-    if ((e = launch_scatter_batch(N, p, b->pos, w, b->offs, j.ncat, j.n_total, b->grid, s, j.wrap ? 1 : 0, c->err, st,
-                                  tr)) != cudaSuccess)
-        return e;
+    // groups of catalogues whose grids share about half of L2: each group's
+    // clear and scatter atomics then stay on chip
+    const size_t grid_bytes = n3 * sizeof(float);
+    const int group = (int)std::max<size_t>(1, ((size_t)48 << 20) / grid_bytes);
+    for (int c0 = 0; c0 < j.ncat; c0 += group) {
+        const int c1 = std::min(j.ncat, c0 + group);
+        if ((e = cudaMemsetAsync(b->grid + (size_t)c0 * n3, 0, (size_t)(c1 - c0) * grid_bytes, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_scatter_batch(N, p, b->pos, w, b->offs, c0, c1, j.n_total, b->grid, s, j.wrap ? 1 : 0, c->err,
+                                      st, tr)) != cudaSuccess)
+            return e;
+    }
     if ((e = launch_weight_sums(w, j.n_total, b->part, nblk, st, tr, b->offs, j.ncat)) != cudaSuccess) return e;
     if ((e = launch_reduce_rows(b->part, j.ncat * 2, nblk, b->sums, st, tr)) != cudaSuccess) return e;
     if ((e = launch_selfpair(N, p, b->pos, w, j.n_total, s, b->part, nblk, st, tr, b->offs, j.ncat)) != cudaSuccess)

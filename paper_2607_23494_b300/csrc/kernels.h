@@ -66,9 +66,10 @@ struct Tables {
 // scatter.cu
 cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
                            int wrap, unsigned* err, cudaStream_t st, const Tracer& tr);
-// catalogue c: points [offs[c], offs[c+1]) (device offsets), grid + c*N^3
-cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int ncat,
-                                 int64_t n, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
+// catalogues c0 .. c1-1; catalogue c: points [offs[c], offs[c+1]) (device
+// offsets), grid + c*N^3; n_max bounds the points of the group (sizes the grid)
+cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int c0, int c1,
+                                 int64_t n_max, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
                                  const Tracer& tr);
 cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int wrap, int* first, float* wts,
                          unsigned* err, cudaStream_t st, const Tracer& tr);

@@ -123,21 +123,27 @@ __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ pos, 
     }
 }
 
-// Batched scatter: catalogue c owns points [offs[c], offs[c+1]) of one
-// concatenated array and grid c (N^3 floats, consecutive grids).  The grid
-// stride runs over all points, so uneven catalogues share the GPU evenly; each
-// point finds its catalogue by bisection over the offsets held in shared memory.
+// Batched scatter of catalogues c0 .. c1-1: catalogue c owns points
+// [offs[c], offs[c+1]) of one concatenated array and grid c (N^3 floats,
+// consecutive grids).  The point range is read from the device offsets, so one
+// launch configuration serves any split of the points.  The grid stride runs
+// over the whole range, so uneven catalogues share the GPU evenly; each point
+// finds its catalogue by bisection over the offsets held in shared memory.
+// The host launches groups of catalogues whose grids fit in L2 together, so the
+// atomics resolve in L2 instead of DRAM.
 template <int P>
 __global__ void __launch_bounds__(256) k_scatter_batch(const float* __restrict__ pos, const float* __restrict__ w,
-                                                       const int64_t* __restrict__ offs, int ncat, int64_t n,
+                                                       const int64_t* __restrict__ offs, int c0, int c1,
                                                        float* __restrict__ grid, float s, int N, int wrap,
                                                        unsigned* __restrict__ err) {
     __shared__ int64_t so[MAX_CATALOGUES + 1];
-    for (int c = threadIdx.x; c <= ncat; c += blockDim.x) so[c] = offs[c];
+    const int ncat = c1 - c0;
+    for (int c = threadIdx.x; c <= ncat; c += blockDim.x) so[c] = offs[c0 + c];
     __syncthreads();
     const size_t n3 = (size_t)N * N * N;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    grid += (size_t)c0 * n3;
+    for (int64_t i = so[0] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < so[ncat]; i += stride) {
         int lo = 0, hi = ncat;  // so[lo] <= i < so[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -382,16 +388,15 @@ cudaError_t launch_nodes(int N, int p, const float* pos, int64_t n, float s, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int ncat,
-                                 int64_t n, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
+cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int c0, int c1,
+                                 int64_t n_max, float* grid, float s, int wrap, unsigned* err, cudaStream_t st,
                                  const Tracer& tr) {
-    if (n == 0) return cudaSuccess;
-    if (ncat < 1 || ncat > MAX_CATALOGUES) return cudaErrorInvalidValue;
-    const int nb = nblocks_for(n, 256, 148 * 32);
+    if (c0 < 0 || c1 <= c0 || c1 - c0 > MAX_CATALOGUES) return cudaErrorInvalidValue;
+    const int nb = nblocks_for(n_max, 256, 148 * 32);
     tr(K_SCATTER, 0, st);
     switch (p) {
 #define HERMES_SC(P) \
-    case P: k_scatter_batch<P><<<nb, 256, 0, st>>>(pos, w, offs, ncat, n, grid, s, N, wrap, err); break;
+    case P: k_scatter_batch<P><<<nb, 256, 0, st>>>(pos, w, offs, c0, c1, grid, s, N, wrap, err); break;
         HERMES_SC(1) HERMES_SC(2) HERMES_SC(3) HERMES_SC(4) HERMES_SC(5) HERMES_SC(6) HERMES_SC(7) HERMES_SC(8)
 #undef HERMES_SC
         default: return cudaErrorInvalidValue;

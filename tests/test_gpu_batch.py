@@ -193,3 +193,26 @@ def test_batch_argument_and_range_errors():
         assert ei.value.code == H.ERR_RANGE and "catalogue 1" in str(ei.value)
         got = ctx.xi_multipoles_batch(pos, w, offs, (0, 2))  # the context still works
         assert np.all(np.isfinite(got))
+
+
+def test_batch_many_small_catalogues_grow_the_result_buffers():
+    # 40 catalogues x 2 orders x 20 bins: results and sums outgrow the context's
+    # initial pinned read-back buffer; the batch state must survive the growth
+    torch, H = _hermes()
+    L, N, p = 80.0, 16, 4
+    edges = np.linspace(2.0, 38.0, 21)
+    sizes = S.batched_catalogue_sizes(40, 50, 600, seed=9)
+    cats = [S.poisson_uniform(int(n), L, seed=200 + k) for k, n in enumerate(sizes)]
+    offs = np.concatenate([[0], np.cumsum([c.shape[0] for c in cats])]).astype(np.int64)
+    pos = np.concatenate(cats).astype(np.float32)
+    with H.Context(L, N, p) as ctx:
+        ctx.set_stream(torch.cuda.Stream())
+        ctx.window_shells(edges, l_max=2)
+        ctx.batch_set_plan(8, 16)
+        a = ctx.xi_multipoles_batch(pos, None, offs, (0, 2))
+        b = ctx.xi_multipoles_batch(pos, None, offs, (0, 2))
+        assert ctx.batch_info()["graph_replays"] == 2
+    assert a.shape == (40, 2, 20)
+    ref = _single(H, L, N, p, edges, 2, pos, None, offs, (0, 2))
+    _close(a, ref)
+    _close(b, ref)
