@@ -286,6 +286,85 @@ int hermes_shell_table_host(double L, int N, const double *r_edges, int n_edges,
 /* Number of table entries Q for a grid of N cells per axis. */
 int64_t hermes_shell_table_len(int N);
 
+/* ------------------------------------------------------------------------
+ * Device-memory accounting.
+ *
+ * hermes_device_bytes: bytes of device memory the context holds now (fields,
+ * window tables, work and staging buffers, batched state); -1 for NULL.
+ * hermes_estimate_bytes: what a context would hold after one request of the
+ * given kind (stat as in hermes_request, n_bins shells, windows up to l_max,
+ * n_points points, copied from host memory when host_inputs != 0); -1 on a
+ * bad argument.  No device is needed.
+ */
+int64_t hermes_device_bytes(const hermes_ctx *ctx);
+int64_t hermes_estimate_bytes(int N, int stat, int n_bins, int l_max, int64_t n_points, int host_inputs);
+
+/* ------------------------------------------------------------------------
+ * Request server: measurement requests of any grid size, catalogue size and
+ * statistic, served with continuous batching on one GPU.
+ *
+ * Worker threads (n_streams, each with its own CUDA stream) take queued
+ * requests as soon as a worker is free and the request's device footprint
+ * (hermes_estimate_bytes) fits in hbm_budget next to the requests in flight
+ * and the idle resident contexts; idle contexts are evicted least recently
+ * used first.  A request passed over by 8 later ones blocks further
+ * admissions until it fits.  Fields stay resident: a request whose field_id
+ * (>= 0) names a field resident for the same L, N, p skips the scatter and the
+ * forward transform and may pass pos = NULL, n = 0; requests for a field that
+ * is being used wait for it.  Each result equals what the same calls on a
+ * context of its own would give, to the rounding of float atomics.
+ */
+#define HERMES_STAT_XI 0
+#define HERMES_STAT_XI_MULTIPOLES 1
+#define HERMES_STAT_ZETA 2
+
+typedef struct hermes_request {
+    double L;                /* box side */
+    int N, p;                /* grid (power of two, 16..1024) and B-spline order */
+    int stat;                /* HERMES_STAT_* */
+    const double *r_edges;   /* shells, as hermes_window_shells; copied at submit */
+    int n_edges;
+    const int *ells;         /* HERMES_STAT_XI_MULTIPOLES: orders; copied at submit */
+    int n_ells;
+    int l_max;               /* HERMES_STAT_ZETA: l_max */
+    const float *pos;        /* as hermes_assign; must stay valid until the wait returns */
+    const float *w;
+    int64_t n;
+    unsigned flags;
+    int64_t field_id;        /* catalogue identity for reuse, or -1 */
+    double *out;             /* result, caller-owned, written before the wait returns:
+                                xi [n_bins]; xi_l [n_ells][n_bins]; zeta [l_max+1][n_bins][n_bins] */
+} hermes_request;
+
+typedef struct hermes_result {
+    int status;              /* HERMES_OK or the error of the failing call */
+    int reused_field;        /* 1 if a resident field served the request */
+    double queue_ms;         /* submit -> start on a worker */
+    double latency_ms;       /* submit -> result written */
+    int64_t device_bytes;    /* the serving context's footprint afterwards */
+    char msg[256];           /* error text */
+} hermes_result;
+
+typedef struct hermes_server hermes_server;
+
+/* Errors: HERMES_ERR_ARG (bad device, n_streams outside 1..64, budget <= 0),
+ * HERMES_ERR_CUDA (no GPU). */
+int hermes_server_create(int device, int64_t hbm_budget, int n_streams, hermes_server **out);
+/* Queues a request; *ticket identifies it.  Errors: HERMES_ERR_ARG (malformed
+ * request), HERMES_ERR_STATE (server stopping).  Requests larger than the
+ * whole budget complete with HERMES_ERR_NOMEM. */
+int hermes_server_submit(hermes_server *srv, const hermes_request *req, int64_t *ticket);
+/* Blocks until the request completes and returns its result (once per ticket).
+ * Errors: HERMES_ERR_ARG (unknown ticket). */
+int hermes_server_wait(hermes_server *srv, int64_t ticket, hermes_result *res);
+/* stats[0..8] = completed, in flight, queued, bytes reserved, peak bytes
+ * reserved, peak requests in flight, requests served from a resident field,
+ * resident contexts, contexts evicted (the first n are written). */
+int hermes_server_stats(hermes_server *srv, int64_t *stats, int n);
+/* Fails queued requests with HERMES_ERR_STATE, lets running ones finish,
+ * frees everything. */
+int hermes_server_destroy(hermes_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

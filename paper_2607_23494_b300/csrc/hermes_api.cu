@@ -275,6 +275,16 @@ int64_t table_len(int N) {
 
 bool valid_N(int N) { return N >= 16 && N <= 1024 && (N & (N - 1)) == 0; }
 
+// Windows per launch of the inverse passes: up to 16 within an 8 GiB work
+// buffer, a multiple of 4 (bin offsets b0 = 0, S, 2S, ... must stay 16-byte
+// aligned in the tables), at least 4, and one batch per order when the bins fit.
+size_t xi_window_S(int N, int nb) {
+    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
+    int S = (int)std::min<size_t>(16, ((size_t)8 << 30) / win_bytes) & ~3;
+    S = std::max(S, 4);
+    return (size_t)std::min(S, std::max(nb, 1));
+}
+
 Tables tables_of(const hermes_ctx* c) {
     Tables t;
     t.tw = c->tw;
@@ -618,11 +628,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     const int N = c->N, H = c->H, nb = c->n_bins;
     const int nwin = n_ells * nb;
     const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
-    // windows per launch: up to 16 within an 8 GiB work buffer, a multiple of 4
-    // (bin offsets b0 = 0, S, 2S, ... must stay 16-byte aligned in the tables), at least 4
-    int S = (int)std::min<size_t>(16, ((size_t)8 << 30) / win_bytes) & ~3;
-    S = std::max(S, 4);
-    S = std::min(S, std::max(nb, 1));  // one batch per order when the bins fit
+    const int S = (int)xi_window_S(N, nb);
     CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
     const int xb = inv_x_blocks(N), zb = inv_z_blocks(N);
     CK(grow_doubles(c->part, c->part_cap, (size_t)S * (xb + zb)), "partials");
@@ -1440,4 +1446,44 @@ extern "C" int hermes_xi_multipoles_batch(hermes_ctx* c, const float* pos, const
     }
     std::memcpy(out, c->host_buf, nres * sizeof(double));
     return HERMES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-memory accounting (used by the request server's admission control).
+
+extern "C" int64_t hermes_device_bytes(const hermes_ctx* c) {
+    if (!c) return -1;
+    const size_t N = (size_t)c->N, n3 = N * N * N;
+    size_t b = n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2);  // grid, spectrum
+    b += TW_ENTRIES * sizeof(float2) + N * sizeof(float) + 8 * sizeof(double) + 512 * (sizeof(double) + sizeof(float));
+    b += c->work_bytes + c->zfields_bytes + (c->part_cap + c->red_cap) * sizeof(double);
+    b += c->stage_cap * 4 * sizeof(float);
+    if (c->rad) b += (size_t)c->nbp * (c->l_max + 1) * c->Q * sizeof(float);
+    if (c->batch) {
+        const BatchState* s = c->batch;
+        b += s->pts_cap * 4 * sizeof(float) + (size_t)s->cat_cap * (n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2));
+        b += s->work_bytes + (s->part_cap + s->res_cap) * sizeof(double);
+    }
+    return (int64_t)b;
+}
+
+extern "C" int64_t hermes_estimate_bytes(int N, int stat, int n_bins, int l_max, int64_t n_points, int host_inputs) {
+    if (!valid_N(N) || n_bins < 1 || l_max < 0 || n_points < 0 || stat < 0 || stat > 2) return -1;
+    const size_t n = (size_t)N, n3 = n * n * n;
+    size_t b = n3 * sizeof(float) + n * n * (n / 2) * sizeof(float2);
+    b += TW_ENTRIES * sizeof(float2) + n * sizeof(float) + 8 * sizeof(double) + 512 * (sizeof(double) + sizeof(float));
+    const size_t nbp = (size_t)((n_bins + 3) & ~3);
+    b += nbp * (size_t)(l_max + 1) * (size_t)table_len(N) * sizeof(float);
+    if (host_inputs) b += (size_t)n_points * 4 * sizeof(float);
+    b += (size_t)std::max(2, 512) * 592 * sizeof(double) + 1024 * sizeof(double);  // assign partials
+    if (stat == 2) {
+        b += (size_t)n_bins * n3 * sizeof(float2) + (size_t)256 * zeta_z_blocks(N) * sizeof(double);
+        b += (size_t)256 * (l_max + 1) * (l_max + 2) / 2 * sizeof(double);
+    } else {
+        const size_t S = xi_window_S(N, n_bins);
+        b += S * n * n * (n / 2) * sizeof(float2);
+        b += S * ((size_t)inv_x_blocks(N) + (size_t)std::max(inv_z_blocks(N), inv_z_blocks_plain(N))) * sizeof(double);
+        b += (size_t)2 * (l_max + 1) * n_bins * sizeof(double);
+    }
+    return (int64_t)b;
 }

@@ -36,6 +36,24 @@ class HermesError(RuntimeError):
         self.code = code
 
 
+STAT_XI, STAT_XI_MULTIPOLES, STAT_ZETA = 0, 1, 2
+
+
+class Request(C.Structure):
+    """hermes_request (include/hermes.h)."""
+    _fields_ = [("L", C.c_double), ("N", C.c_int), ("p", C.c_int), ("stat", C.c_int),
+                ("r_edges", C.POINTER(C.c_double)), ("n_edges", C.c_int),
+                ("ells", C.POINTER(C.c_int)), ("n_ells", C.c_int), ("l_max", C.c_int),
+                ("pos", C.c_void_p), ("w", C.c_void_p), ("n", C.c_int64), ("flags", C.c_uint),
+                ("field_id", C.c_int64), ("out", C.POINTER(C.c_double))]
+
+
+class Result(C.Structure):
+    """hermes_result (include/hermes.h)."""
+    _fields_ = [("status", C.c_int), ("reused_field", C.c_int), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double), ("device_bytes", C.c_int64), ("msg", C.c_char * 256)]
+
+
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhermes.so not built at {LIB_PATH}; run `python paper_2607_23494_b300/build.py`")
@@ -69,6 +87,13 @@ def _load() -> C.CDLL:
         "hermes_trace_read": (i32, [vp, dp, C.POINTER(i64), i32]),
         "hermes_kernel_name": (C.c_char_p, [i32]),
         "hermes_launch_count": (i64, [vp]),
+        "hermes_device_bytes": (i64, [vp]),
+        "hermes_estimate_bytes": (i64, [i32, i32, i32, i32, i64, i32]),
+        "hermes_server_create": (i32, [i32, i64, i32, C.POINTER(vp)]),
+        "hermes_server_submit": (i32, [vp, C.POINTER(Request), C.POINTER(i64)]),
+        "hermes_server_wait": (i32, [vp, i64, C.POINTER(Result)]),
+        "hermes_server_stats": (i32, [vp, C.POINTER(i64), i32]),
+        "hermes_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -306,3 +331,103 @@ class Context:
         t = np.empty(self.p ** 3, dtype=np.float64)
         self._check(_lib.hermes_debug_get_sums(self._h, _dptr(s), _dptr(t)), "hermes_debug_get_sums")
         return s, t.reshape(self.p, self.p, self.p)
+
+
+def estimate_bytes(N: int, stat: int, n_bins: int, l_max: int, n_points: int, host_inputs: bool = True) -> int:
+    """hermes_estimate_bytes: device footprint of one request of this kind (-1 on a bad argument)."""
+    return int(_lib.hermes_estimate_bytes(int(N), int(stat), int(n_bins), int(l_max), int(n_points),
+                                          1 if host_inputs else 0))
+
+
+class Server:
+    """hermes_server_*: continuous-batching request server on one GPU.
+
+    submit() returns a ticket; the arrays it was given (positions, weights) are
+    kept referenced until wait() returns the (result array, hermes_result) pair."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 64 << 30, n_streams: int = 4):
+        h = C.c_void_p()
+        rc = _lib.hermes_server_create(int(device), int(hbm_budget), int(n_streams), C.byref(h))
+        if rc != OK:
+            raise HermesError(rc, f"hermes_server_create(device={device}, budget={hbm_budget}, "
+                                  f"streams={n_streams})")
+        self._h = h
+        self._live = {}
+
+    def submit(self, L: float, N: int, p: int, stat: int, r_edges, pos=None, w=None, ells=None, l_max: int = 0,
+               field_id: int = -1, wrap: bool = False) -> int:
+        edges = np.ascontiguousarray(r_edges, dtype=np.float64)
+        nb = len(edges) - 1
+        keep = [edges]
+        flags = WRAP if wrap else 0
+        n = 0
+        pp = wp = None
+        if pos is not None:
+            if hasattr(pos, "data_ptr"):
+                if pos.is_cuda:
+                    flags |= DEVICE_PTR
+                pp, n = pos.data_ptr(), pos.shape[0]
+                wp = None if w is None else w.data_ptr()
+                keep += [pos, w]
+            else:
+                pos = np.ascontiguousarray(pos, dtype=np.float32)
+                pp, n = pos.ctypes.data, pos.shape[0]
+                keep.append(pos)
+                if w is not None:
+                    w = np.ascontiguousarray(w, dtype=np.float32)
+                    wp = w.ctypes.data
+                    keep.append(w)
+        ea = None
+        if stat == STAT_XI:
+            shape = (nb,)
+        elif stat == STAT_XI_MULTIPOLES:
+            ea = np.ascontiguousarray(ells, dtype=np.int32)
+            keep.append(ea)
+            shape = (len(ea), nb)
+        else:
+            shape = (l_max + 1, nb, nb)
+        out = np.zeros(shape, dtype=np.float64)
+        req = Request(L=float(L), N=int(N), p=int(p), stat=int(stat), r_edges=_dptr(edges), n_edges=len(edges),
+                      ells=None if ea is None else ea.ctypes.data_as(C.POINTER(C.c_int)),
+                      n_ells=0 if ea is None else len(ea), l_max=int(l_max), pos=pp, w=wp, n=int(n),
+                      flags=flags, field_id=int(field_id), out=_dptr(out))
+        t = C.c_int64()
+        rc = _lib.hermes_server_submit(self._h, C.byref(req), C.byref(t))
+        if rc != OK:
+            raise HermesError(rc, "hermes_server_submit")
+        self._live[t.value] = (out, keep)
+        return t.value
+
+    def wait(self, ticket: int):
+        res = Result()
+        rc = _lib.hermes_server_wait(self._h, int(ticket), C.byref(res))
+        if rc != OK:
+            raise HermesError(rc, f"hermes_server_wait({ticket})")
+        out, _ = self._live.pop(ticket)
+        return out, {"status": res.status, "reused_field": bool(res.reused_field), "queue_ms": res.queue_ms,
+                     "latency_ms": res.latency_ms, "device_bytes": res.device_bytes,
+                     "msg": res.msg.decode(errors="replace")}
+
+    def stats(self) -> dict:
+        v = (C.c_int64 * 9)()
+        _lib.hermes_server_stats(self._h, v, 9)
+        keys = ["completed", "in_flight", "queued", "bytes_reserved", "peak_bytes_reserved", "peak_in_flight",
+                "reused_fields", "resident_contexts", "evicted"]
+        return dict(zip(keys, list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hermes_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -78,3 +78,38 @@ def test_host_tables_reject_bad_edges():
         H.shell_table_host(100.0, 32, [5.0, 5.0, 10.0], 0)
     with pytest.raises(H.HermesError):
         H.shell_table_host(100.0, 32, [-1.0, 5.0], 0)
+
+
+def test_server_and_accounting_entry_points_without_a_gpu():
+    import torch
+    from paper_2607_23494_b300 import hermes as H
+    lib = H.lib()
+    h = ctypes.c_void_p()
+    assert lib.hermes_server_create(0, 1 << 30, 0, ctypes.byref(h)) == H.ERR_ARG     # no worker
+    assert lib.hermes_server_create(0, 0, 2, ctypes.byref(h)) == H.ERR_ARG           # no budget
+    assert lib.hermes_server_create(0, 1 << 30, 2, None) == H.ERR_ARG
+    assert lib.hermes_server_destroy(None) == H.OK
+    assert lib.hermes_device_bytes(None) == -1
+    if not torch.cuda.is_available():
+        assert lib.hermes_server_create(0, 1 << 30, 2, ctypes.byref(h)) == H.ERR_CUDA
+        assert not h.value
+
+
+def test_footprint_estimate_follows_the_allocation_rules():
+    from paper_2607_23494_b300.hermes import STAT_XI, STAT_XI_MULTIPOLES, STAT_ZETA, estimate_bytes
+    assert estimate_bytes(48, STAT_XI, 10, 0, 1000) == -1
+    assert estimate_bytes(64, 3, 10, 0, 1000) == -1
+    assert estimate_bytes(64, STAT_XI, 0, 0, 1000) == -1
+    for N in (64, 256, 1024):
+        n3 = N ** 3
+        xi = estimate_bytes(N, STAT_XI, 40, 0, 10 ** 6, host_inputs=False)
+        # grid (4 B) + half spectrum (4 B) + at least four windows of work (4 B each) per cell
+        assert 24 * n3 <= xi < 24 * n3 + 72 * n3 + (1 << 26)
+        # zeta keeps n_bins full complex fields (8 B per cell each)
+        z = estimate_bytes(N, STAT_ZETA, 12, 4, 10 ** 6, host_inputs=False)
+        assert z >= 8 * n3 + 12 * 8 * n3
+        # host inputs are staged: 16 B per point
+        assert estimate_bytes(N, STAT_XI, 40, 0, 10 ** 6, host_inputs=True) - xi == 16 * 10 ** 6
+        # more orders only enlarge the tables
+        assert estimate_bytes(N, STAT_XI_MULTIPOLES, 40, 4, 10 ** 6, host_inputs=False) > xi
+    assert estimate_bytes(512, STAT_XI, 40, 0, 0) > estimate_bytes(256, STAT_XI, 40, 0, 0)
