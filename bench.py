@@ -45,6 +45,8 @@ ELLS2 = (0, 2, 4)
 # batched configuration
 L4, N4, NCAT4 = 500.0, 256, 64
 EDGES4 = np.linspace(5.0, 155.0, 31)
+# serving configuration
+L5, NPOOL5 = 1000.0, 6
 # 3PCF multipoles configuration
 L3, N3, NPTS3 = 500.0, 512, 2_000_000
 EDGES3 = np.linspace(10.0, 170.0, 17)
@@ -255,6 +257,10 @@ def run_hermes(args, rank, world, local_rank):
     if not args.no_batch:
         batch = run_batch(args, dev, stream, rank)
 
+    serve = None
+    if not args.no_serve and args.serve_requests > 0:
+        serve = run_serve(args, dev, rank)
+
     zeta = None
     if not args.no_zeta:
         zeta = run_zeta(args, dev, stream, rank)
@@ -285,6 +291,8 @@ def run_hermes(args, rank, world, local_rank):
             out["vs_plain_fp32"] = plain
         if batch:
             out["batch"] = batch
+        if serve:
+            out["serve"] = serve
         if zeta:
             out["zeta"] = zeta
     return out, pos
@@ -512,6 +520,84 @@ def run_batch(args, dev, stream, rank):
             "speedup_vs_plain": round(p_ms / b_ms, 2), "speedup_vs_one_at_a_time": round(s_ms / b_ms, 2)}
 
 
+def gen_serve_pool(seed: int):
+    """Catalogues the serving trace draws from: sizes log-uniform in [1e5, 2e7], L = 1000."""
+    from synthetic import catalogues as S
+    sizes = S.batched_catalogue_sizes(NPOOL5, 1e5, 2e7, seed=seed)
+    return [S.lognormal_catalogue(int(n), L5, seed=seed + 1 + k, n_grid=128) for k, n in enumerate(sizes)]
+
+
+def serve_trace(n_req: int, rate: float, n_pool: int, seed: int):
+    """Poisson arrivals; grid 128/256/512/1024^3 with probability .4/.3/.2/.1; statistic
+    xi (40 shells), xi_l (l <= 4, 40 shells) or zeta_l (l_max 4, 12 shells) uniformly;
+    catalogue uniform over the pool (its field id, so fields can be reused)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_req)) if rate > 0 else np.zeros(n_req)
+    grids = rng.choice([128, 256, 512, 1024], size=n_req, p=[0.4, 0.3, 0.2, 0.1])
+    stats = rng.integers(0, 3, size=n_req)
+    cats = rng.integers(0, n_pool, size=n_req)
+    return [(float(t[i]), int(grids[i]), int(stats[i]), int(cats[i])) for i in range(n_req)]
+
+
+def run_serve_trace(H, pool_d, trace, n_streams, budget):
+    edges_xi = np.linspace(2.0, 202.0, 41)
+    edges_z = np.linspace(10.0, 130.0, 13)
+    t_wall0 = time.time()
+    with H.Server(0, hbm_budget=budget, n_streams=n_streams) as srv:
+        tickets = []
+        t0 = time.time()
+        for (ta, N, stat, k) in trace:
+            dt = ta - (time.time() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            if stat == H.STAT_XI:
+                tk = srv.submit(L5, N, 4, stat, edges_xi, pos=pool_d[k], field_id=k)
+            elif stat == H.STAT_XI_MULTIPOLES:
+                tk = srv.submit(L5, N, 4, stat, edges_xi, pos=pool_d[k], ells=(0, 2, 4), field_id=k)
+            else:
+                tk = srv.submit(L5, N, 4, stat, edges_z, pos=pool_d[k], l_max=4, field_id=k)
+            tickets.append(tk)
+        res = [srv.wait(tk) for tk in tickets]
+        wall = time.time() - t0
+        st = srv.stats()
+    lat = np.array([r[1]["latency_ms"] for r in res])
+    ok = sum(1 for r in res if r[1]["status"] == H.OK)
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "mean_ms": round(float(lat.mean()), 1), "requests_per_s": round(len(trace) / wall, 3),
+            "ok": ok, "peak_in_flight": st["peak_in_flight"], "reused_fields": st["reused_fields"],
+            "evicted": st["evicted"], "peak_reserved_GB": round(st["peak_bytes_reserved"] / 2 ** 30, 1),
+            "wall_s": round(wall, 1), "setup_s": round(t0 - t_wall0, 2)}, [r[0] for r in res]
+
+
+def run_serve(args, dev, rank):
+    """Serving: a Poisson-arrival trace of mixed requests at 0.75 x the measured
+    one-at-a-time capacity, served by 4 concurrent workers and by 1 (the same
+    library one request at a time); p50/p99 latency and throughput of both."""
+    import torch
+    from paper_2607_23494_b300 import hermes as H
+    pool = gen_serve_pool(4242 + 17 * rank)
+    pool_d = [torch.from_numpy(c).to(dev) for c in pool]
+    budget = 200 << 30
+    # capacity of the one-at-a-time server on a calibration trace (back to back)
+    cal = serve_trace(min(12, args.serve_requests), 0.0, len(pool), seed=99)
+    run_serve_trace(H, pool_d, cal[:3], 1, budget)  # warm-up (module load, cuFFT-free path, allocator)
+    c1, _ = run_serve_trace(H, pool_d, cal, 1, budget)
+    capacity = c1["requests_per_s"]
+    rate = 0.75 * capacity
+    trace = serve_trace(args.serve_requests, rate, len(pool), seed=7)
+    cont, out_c = run_serve_trace(H, pool_d, trace, 4, budget)
+    one, out_1 = run_serve_trace(H, pool_d, trace, 1, budget)
+    worst = 0.0
+    for a, b in zip(out_c, out_1):
+        worst = max(worst, float(np.max(np.abs(a - b) / np.maximum(1e-4 * np.abs(b), 1e-6))))
+    return {"workload": f"{len(trace)} Poisson-arrival requests at {rate:.2f}/s (0.75 x measured one-at-a-time "
+                        f"capacity {capacity:.2f}/s); grids 128/256/512/1024^3 (p .4/.3/.2/.1), L={L5:g}, p=4; "
+                        f"xi 40 shells / xi_l l<=4 / zeta_l l_max 4 12 shells; {len(pool)} resident catalogues "
+                        f"of {min(len(c) for c in pool)}..{max(len(c) for c in pool)} points (device inputs)",
+            "continuous_4_streams": cont, "one_at_a_time": one,
+            "results_mix_vs_alone_in_tolerances": round(worst, 4)}
+
+
 def run_zeta(args, dev, stream, rank):
     import torch
     from paper_2607_23494_b300 import Context
@@ -642,6 +728,8 @@ def main():
     ap.add_argument("--no-zeta", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain torch/cuFFT comparison arm")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-catalogue measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests in the serving trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <cmath>
 #include <complex>
@@ -564,6 +565,51 @@ int hermes_shell_table_host(double L, int N, const double* r_edges, int n_edges,
     return HERMES_OK;
 }
 
+namespace {
+// Process-wide cache of built window tables in the device layout
+// [(l*Q + q)*nbp + b], keyed by (L, N, edges); an entry built for a larger
+// l_max serves a smaller one (the orders are the leading blocks).  Bounded in
+// host memory, least recently used first out.
+struct TableEntry {
+    double L;
+    int N;
+    std::vector<double> edges;
+    int l_max;
+    std::shared_ptr<const std::vector<float>> data;
+    uint64_t stamp;
+};
+std::mutex g_tab_mu;
+std::vector<TableEntry> g_tabs;
+uint64_t g_tab_clock = 0;
+constexpr size_t kTableCacheBytes = (size_t)8 << 30;
+
+std::shared_ptr<const std::vector<float>> table_lookup(double L, int N, const double* e, int ne, int l_max) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    TableEntry* best = nullptr;
+    for (auto& t : g_tabs)
+        if (t.L == L && t.N == N && t.l_max >= l_max && (int)t.edges.size() == ne &&
+            std::equal(t.edges.begin(), t.edges.end(), e) && (!best || t.l_max < best->l_max))
+            best = &t;
+    if (!best) return nullptr;
+    best->stamp = ++g_tab_clock;
+    return best->data;
+}
+
+void table_insert(double L, int N, const double* e, int ne, int l_max, std::shared_ptr<const std::vector<float>> d) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    size_t total = d->size() * sizeof(float);
+    for (auto& t : g_tabs) total += t.data->size() * sizeof(float);
+    while (total > kTableCacheBytes && !g_tabs.empty()) {
+        auto old = std::min_element(g_tabs.begin(), g_tabs.end(),
+                                    [](const TableEntry& a, const TableEntry& b) { return a.stamp < b.stamp; });
+        total -= old->data->size() * sizeof(float);
+        g_tabs.erase(old);
+    }
+    if (d->size() * sizeof(float) <= kTableCacheBytes)
+        g_tabs.push_back(TableEntry{L, N, std::vector<double>(e, e + ne), l_max, std::move(d), ++g_tab_clock});
+}
+}  // namespace
+
 int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int l_max) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!r_edges) return fail(c, HERMES_ERR_ARG, "r_edges is NULL");
@@ -583,28 +629,34 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     const int nbp = (nb + 3) & ~3;
     const size_t count = (size_t)nb * (l_max + 1) * Q;
     const size_t count_dev = (size_t)nbp * (l_max + 1) * Q;
-    std::vector<double> host;
-    std::vector<float> host32;
-    try {
-        host.resize(count);
-        host32.assign(count_dev, 0.0f);
-    } catch (...) {
-        return fail(c, HERMES_ERR_NOMEM, "host table of %zu entries", count);
-    }
-    build_shell_tables(c->L, Q, r_edges, n_edges, l_max, host.data());
-    // device layout bin-fastest: [(l*Q + q)*nbp + b]
-    for (int b = 0; b < nb; ++b)
-        for (int l = 0; l <= l_max; ++l) {
-            const double* src = host.data() + ((size_t)b * (l_max + 1) + l) * Q;
-            float* dst = host32.data() + (size_t)l * Q * nbp + b;
-            for (int64_t q = 0; q < Q; ++q) dst[(size_t)q * nbp] = (float)src[q];
+    std::shared_ptr<const std::vector<float>> tab = table_lookup(c->L, c->N, r_edges, n_edges, l_max);
+    if (!tab) {
+        std::shared_ptr<std::vector<float>> host32;
+        std::vector<double> host;
+        try {
+            host.resize(count);
+            host32 = std::make_shared<std::vector<float>>(count_dev, 0.0f);
+        } catch (...) {
+            return fail(c, HERMES_ERR_NOMEM, "host table of %zu entries", count);
         }
+        build_shell_tables(c->L, Q, r_edges, n_edges, l_max, host.data());
+        // device layout bin-fastest: [(l*Q + q)*nbp + b]
+        for (int b = 0; b < nb; ++b)
+            for (int l = 0; l <= l_max; ++l) {
+                const double* src = host.data() + ((size_t)b * (l_max + 1) + l) * Q;
+                float* dst = host32->data() + (size_t)l * Q * nbp + b;
+                for (int64_t q = 0; q < Q; ++q) dst[(size_t)q * nbp] = (float)src[q];
+            }
+        tab = host32;
+        table_insert(c->L, c->N, r_edges, n_edges, l_max, host32);
+    }
     cudaStreamSynchronize(c->stream);
     cudaFree(c->rad);
     c->rad = nullptr;
     c->n_bins = 0;
     CK(cudaMalloc((void**)&c->rad, count_dev * sizeof(float)), "window tables");
-    CK(cudaMemcpy(c->rad, host32.data(), count_dev * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
+    // the orders 0..l_max are the leading blocks of a cached table built for a larger l_max
+    CK(cudaMemcpy(c->rad, tab->data(), count_dev * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
     c->edges.assign(r_edges, r_edges + n_edges);
     c->n_bins = nb;
     c->l_max = l_max;

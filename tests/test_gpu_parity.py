@@ -322,3 +322,24 @@ def test_kspace_route_planted_mode_and_errors():
             K = O.window_xi(N, L, p, edges[b], edges[b + 1], ell)
             ref = 0.5 * K[n0[0] % N, n0[1] % N, n0[2] % N]
             assert abs(got[a, b] - ref) <= max(2e-5 * abs(ref), 1e-7), (ell, b, got[a, b], ref)
+
+
+def test_cached_window_tables_serve_smaller_orders():
+    # a table built for l_max = 4 is reused (its leading blocks) by later
+    # contexts asking l_max = 0 or 2 with the same L, N and shells
+    H = _hermes()
+    L, N, p = 180.0, 32, 4
+    edges = np.linspace(3.0, 60.0, 10)
+    pos = S.mixed_poisson_sp(6000, L, seed=91)
+    with H.Context(L, N, p) as c4:
+        c4.window_shells(edges, l_max=4)
+        c4.assign(pos)
+        x4 = c4.xi_multipoles([0, 2, 4])
+    for lm, ells in ((0, [0]), (2, [0, 2])):
+        with H.Context(L, N, p) as c:
+            c.window_shells(edges, l_max=lm)
+            c.assign(pos)
+            got = c.xi_multipoles(ells)
+        np.testing.assert_allclose(got, x4[:len(ells)], rtol=1e-6, atol=1e-9)
+    ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2, 4))["xi"]
+    _close(x4, ref)
