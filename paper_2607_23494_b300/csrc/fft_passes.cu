@@ -42,6 +42,16 @@ struct Cfg {
     static constexpr size_t SMEM_Z3 = SMEM_Z + (size_t)2 * LZ * (N / 2) * sizeof(float2);  // + double stage
 };
 
+// Dynamic shared memory a block may use next to the kernels' static arrays.
+constexpr size_t kMaxDynSmem = 220 * 1024;
+
+// The shared-table window pass is the default; HERMES_X_GATHER=1 selects the
+// per-element global gathers instead (kept for comparison).
+static bool stab_x_enabled() {
+    const char* env = getenv("HERMES_X_GATHER");
+    return !(env && env[0] == '1');
+}
+
 template <class K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -143,127 +153,102 @@ __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
 
 // ---------------------------------------------------------------------------
 // I1: first inverse pass (along x) with the window multiply of a batch of S
-// windows fused in.  Also accumulates sum_n K_s(n) S^(n) over the full
-// spectrum (the half-spectrum sum doubles k_z > 0), where
-// S^(n) = sum_{a,b,c} S(a,b,c) C(n_x,a) C(n_y,b) C(n_z,c), C(n,0) = 1,
-// C(n,a>0) = 2 cos(2 pi n a / N), is the Fourier transform of the even
-// self-pair overlap table.
-template <int N>
-__global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __restrict__ spec, float2* __restrict__ work,
-                                                              const WinBatch wb, const Tables tb, int P,
-                                                              double* __restrict__ sn_part) {
+// windows fused in: K_s(n) = scale * T_s(|n|^2) * Phi^(n) * L_l(k_z/k), all
+// windows of the batch sharing the order l (Phi^, L_l and scale are applied to
+// the input once).  The self-pair term of each window is not summed here: it
+// is the radial contraction of the self-pair histogram (kspace.cu).
+//
+// STAB: the block first copies the radial factors it needs into shared memory
+// (its columns see |n|^2 = a^2 + n_y^2 + n_z^2 for a = |n_x| only, so H rows per
+// column cover every element, the +-n_x pair included), with asynchronous
+// 16-byte copies issued before the spectrum is read; otherwise every element
+// gathers them from the global table (16-byte loads of 4 bins).
+
+// Row stride (floats) of the shared radial table: S rounded up to 4, plus 4
+// when that is a multiple of 8, so the 16-byte reads of a warp (32 rows at
+// consecutive (|n_x|, column)) spread over all banks.
+__host__ __device__ constexpr int stab_row_stride(int S) {
+    return ((S + 3) & ~3) + ((((S + 3) >> 2) & 1) ? 0 : 4);
+}
+
+template <int N, bool STAB>
+__global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __restrict__ spec,
+                                                              float2* __restrict__ work, const WinBatch wb,
+                                                              const Tables tb) {
     using C = Cfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
+    float* ttab = reinterpret_cast<float*>(smem + SmemStrided<W>::words(N));  // [a][col][RS] (STAB)
+    const int RS = stab_row_stride(wb.S);
     const int col = threadIdx.x % W, t = threadIdx.x / W;
     const int ky = blockIdx.y, kz = blockIdx.x * W + col;
-    const size_t nblk = (size_t)gridDim.x * gridDim.y;
-    const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     const size_t xstride = (size_t)N * H;
     {  // batched launch: blockIdx.z = catalogue
         const size_t cat = blockIdx.z;
         spec += cat * N * N * H;
         work += cat * wb.S * N * N * H;
-        sn_part += cat * wb.S * nblk;
     }
-    const float* stab = tb.stab + (size_t)blockIdx.z * STAB_STRIDE;
+    const int ny = signed_freq(ky, N), nz = kz;
+    const bool nyq_y = (ky == H);
+    if constexpr (STAB) {
+        // rows of S4 16-byte pieces per (a, column); consecutive threads copy one row's pieces
+        const int S4 = (wb.S + 3) >> 2;
+        const int total = H * W * S4;
+        const int ny2 = nyq_y ? 0 : ny * ny;
+        for (int e = threadIdx.x; e < total; e += C::TS) {
+            const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
+            const int nzc = blockIdx.x * W + c;
+            const int qq = nyq_y ? 0 : a * a + ny2 + nzc * nzc;
+            ac::cp_async16(ttab + (a * W + c) * RS + 4 * s4,
+                           reinterpret_cast<const float4*>(wb.tab + (size_t)qq * wb.nbp) + s4);
+        }
+        ac::cp_async_commit();
+    }
     const float2* src = spec + (size_t)ky * H + kz;
     float2 v0[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v0[i] = src[(size_t)(t + i * T) * xstride];
-
-    const int ny = signed_freq(ky, N), nz = kz;
-    const bool nyq_y = (ky == H);
+    // Phi^, the Nyquist mask, scale and L_l(k_z/k) are folded into the input once,
+    // so per window v = v0 * T_s(|n|^2)
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
-    // self-pair transform: U[a] = sum_{b,c} S(a,b,c) C(ky,b) C(kz,c)
-    float cy[8], cz[8], U[8];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        cy[a] = (a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, ky * a);
-        cz[a] = (a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, kz * a);
-    }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        float u = 0.0f;
-        if (a < P) {
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                if (b < P) {
-                    float ub = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (c < P) ub = fmaf(__ldg(stab + (a * P + b) * P + c), cz[c], ub);
-                    u = fmaf(ub, cy[b], u);
-                }
-            }
-        }
-        U[a] = u;
-    }
-    // Phi^ and the Nyquist mask are folded into the spectrum and the self-pair
-    // transform once, so per window K' = scale * table[q] * L_l(mu) only:
-    //   v = (delta^ Phi^) K',  sn += K' (S^ Phi^)
-    float shat[8];
-    int q[8];
+    int q[8];  // |n|^2, or the shared-table row offset (a*W + col)*RS under STAB
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int kx = t + i * T;
         const int nx = signed_freq(kx, N);
         const bool nyq = nyq_y || (kx == H);
-        q[i] = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
+        const int qq = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
         const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
-        v0[i] = cscale(v0[i], ph);
-        float sh = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-            if (a < P) sh = fmaf((a == 0) ? 1.0f : 2.0f * cos_tab<N>(tb.tw, kx * a), U[a], sh);
-        shat[i] = sh * ph;
+        const float a = wb.scale * legendre(wb.ell, qq > 0 ? (float)nz * rsqrtf((float)qq) : 0.0f);
+        v0[i] = cscale(v0[i], ph * a);
+        const int ax = (kx < H) ? kx : (kx == H ? 0 : N - kx);  // |n_x|; the Nyquist lane reads row 0
+        q[i] = STAB ? (ax * W + col) * RS : qq;
     }
-    const float wz = (kz == 0) ? 1.0f : 2.0f;
-    // per-warp partial self-pair sums; one float64 reduction per window at the end
-    constexpr int NW = (C::TS + 31) / 32;
-    constexpr unsigned MASK = C::TS >= 32 ? 0xffffffffu : ((1u << C::TS) - 1u);
-    __shared__ float wsn[NW][MAX_BATCH];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // the batch shares one order l: fold scale * L_l(k_z/k) into the inputs once
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float a = wb.scale * legendre(wb.ell, q[i] > 0 ? (float)nz * rsqrtf((float)q[i]) : 0.0f);
-        v0[i] = cscale(v0[i], a);
-        shat[i] *= a;
+    if constexpr (STAB) {
+        ac::cp_async_wait_all();
+        __syncthreads();
     }
     const int nbp = wb.nbp;
     for (int g = 0; g < wb.S; g += 4) {
         // radial factors of windows g..g+3 at every element: one 16-byte load each
         float4 tv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) tv[i] = __ldg(reinterpret_cast<const float4*>(wb.tab + (size_t)q[i] * nbp + g));
+        for (int i = 0; i < 8; ++i)
+            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + q[i] + g)
+                         : __ldg(reinterpret_cast<const float4*>(wb.tab + (size_t)q[i] * nbp + g));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int s = g + j;
             if (s >= wb.S) break;  // uniform across the block
-            float sn = 0.0f;
             float2 v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float K = j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w));
-                sn = fmaf(K, shat[i], sn);
-                v[i] = cscale(v0[i], K);
-            }
+            for (int i = 0; i < 8; ++i)
+                v[i] = cscale(v0[i], j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
             fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
             float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
 #pragma unroll
             for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
-            sn *= wz;
-#pragma unroll
-            for (int o = (C::TS >= 32 ? 16 : C::TS / 2); o > 0; o >>= 1) sn += __shfl_xor_sync(MASK, sn, o);
-            if (lane == 0) wsn[wid][s] = sn;
         }
-    }
-    __syncthreads();
-    if (threadIdx.x < wb.S) {
-        double tot = 0.0;
-        for (int w = 0; w < NW; ++w) tot += (double)wsn[w][threadIdx.x];
-        sn_part[(size_t)threadIdx.x * nblk + blk] = tot;
     }
 }
 
@@ -578,17 +563,22 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 
 template <int N>
 static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                                const Tables& tb, int P, double* sn_part, double* dd_part, unsigned* err,
-                                cudaStream_t st, const Tracer& tr, int ncat) {
+                                const Tables& tb, double* dd_part, unsigned* err, cudaStream_t st, const Tracer& tr,
+                                int ncat) {
     using C = Cfg<N>;
     cudaError_t e;
-    if ((e = allow_smem(k_inv_x_window<N>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    // radial factors staged in shared memory when they fit next to the FFT tile
+    const size_t stab_bytes = C::SMEM_STRIDED + (size_t)(N / 2) * C::W * stab_row_stride(wb.S) * sizeof(float);
+    const bool use_stab = stab_bytes <= kMaxDynSmem && stab_x_enabled();
+    if ((e = allow_smem(k_inv_x_window<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    if (use_stab && (e = allow_smem(k_inv_x_window<N, true>, stab_bytes)) != cudaSuccess) return e;
     if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z3)) != cudaSuccess) return e;
     const long long H = N / 2;
     dim3 g1(H / C::W, N, ncat);
     tr(K_INV_X_WINDOW, 0, st);
-    k_inv_x_window<N><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb, P, sn_part);
+    if (use_stab) k_inv_x_window<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, work, wb, tb);
+    else k_inv_x_window<N, false><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb);
     tr(K_INV_X_WINDOW, 1, st);
     if constexpr (N <= 512) {
         if (ncat == 1 && yz_fused_ok<N>()) {
@@ -636,11 +626,11 @@ cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double*
 #undef F
 }
 
-cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
-                              const Tables& tb, double* sn_part, double* dd_part, unsigned* err, cudaStream_t st,
-                              const Tracer& tr, int ncat) {
+cudaError_t launch_inverse_xi(int N, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
+                              const Tables& tb, double* dd_part, unsigned* err, cudaStream_t st, const Tracer& tr,
+                              int ncat) {
     if (ncat < 1 || ncat > MAX_CATALOGUES || (size_t)wb.S * ncat > 65535) return cudaErrorInvalidValue;
-#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, p, sn_part, dd_part, err, st, tr, ncat)
+#define F(n) inverse_impl<n>(spec, work, delta, wb, tb, dd_part, err, st, tr, ncat)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }

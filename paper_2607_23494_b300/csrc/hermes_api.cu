@@ -665,6 +665,29 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     return HERMES_OK;
 }
 
+namespace {
+// Self-pair term of every window (order index a, bin b) into out[a*nb + b]:
+// c_l sum_q T_{b,l}(q) B_l(q) / N^6 with B_l the self-pair histogram of the
+// field whose float table is tb.stab (divide by eps_bar^2 for SN_b).  hist
+// holds min(n_ells, 8) * Q doubles.
+cudaError_t enqueue_selfpair_terms(hermes_ctx* c, const Tables& tb, const int* ells, int n_ells, double* hist,
+                                   double* out, cudaStream_t st, const Tracer& tr) {
+    for (int a0 = 0; a0 < n_ells; a0 += 8) {
+        KsOrders ko;
+        ko.n = std::min(8, n_ells - a0);
+        for (int k = 0; k < ko.n; ++k) ko.ell[k] = ells[a0 + k];
+        cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ko.n * c->Q * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+        if ((e = launch_kspace_hist(c->N, nullptr, tb, c->p, nullptr, ko, hist, c->Q, st, tr, 1)) != cudaSuccess)
+            return e;
+        if ((e = launch_kspace_contract(c->rad, c->nbp, c->Q, ko, hist, c->N, out + (size_t)a0 * c->n_bins, c->n_bins,
+                                        st, tr, K_SN_CONTRACT)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
 int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!ells || !out || n_ells < 1) return fail(c, HERMES_ERR_ARG, "ells/out NULL or n_ells < 1");
@@ -682,11 +705,13 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
     const int S = (int)xi_window_S(N, nb);
     CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
-    const int xb = inv_x_blocks(N), zb = inv_z_blocks(N);
-    CK(grow_doubles(c->part, c->part_cap, (size_t)S * (xb + zb)), "partials");
+    const int zb = inv_z_blocks(N);
+    CK(grow_doubles(c->part, c->part_cap, std::max((size_t)S * zb, (size_t)std::min(n_ells, 8) * c->Q)), "partials");
     CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
     const Tables tb = tables_of(c);
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    // self-pair terms of all windows first (the histogram lives in the partials buffer)
+    CK(enqueue_selfpair_terms(c, tb, ells, n_ells, c->part, c->red + nwin, st, c->tracer), "self-pair terms");
     // batches never cross an order: bins b0 .. b0+S-1 of one l (b0 a multiple of S)
     for (int a = 0; a < n_ells; ++a) {
         const int ell = ells[a];
@@ -698,12 +723,9 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
             wb.ell = ell;
             wb.scale = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));  // (2l+1) i^l, l even
             const int w0 = a * nb + b0;
-            double* sn_part = c->part;
-            double* dd_part = c->part + (size_t)wb.S * xb;
-            CK(launch_inverse_xi(N, c->p, c->spec, c->work, c->grid, wb, tb, sn_part, dd_part, c->err, st,
-                                 c->tracer),
+            double* dd_part = c->part;
+            CK(launch_inverse_xi(N, c->spec, c->work, c->grid, wb, tb, dd_part, c->err, st, c->tracer),
                "inverse passes");
-            CK(launch_reduce_rows(sn_part, wb.S, xb, c->red + nwin + w0, st, c->tracer), "reduce self-pair sums");
             CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
         }
     }
@@ -718,7 +740,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     const double eps_bar = c->sum_w / n3;
     for (int widx = 0; widx < nwin; ++widx) {
         const double dd = c->host_buf[widx] / n6;
-        const double sn = c->host_buf[nwin + widx] / (n6 * eps_bar * eps_bar);
+        const double sn = c->host_buf[nwin + widx] / (eps_bar * eps_bar);  // already / N^6
         out[widx] = dd - sn;
     }
     return HERMES_OK;
@@ -894,7 +916,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -1121,7 +1143,7 @@ size_t batch_work_limit(const hermes_ctx* c) {
 
 // Partials of the inverse passes for C catalogues x S windows.
 size_t batch_part_need(int N, int S, int C) {
-    return (size_t)C * S * ((size_t)inv_x_blocks(N) + std::max(inv_z_blocks(N), inv_z_blocks_plain(N)));
+    return (size_t)C * S * (size_t)std::max(inv_z_blocks(N), inv_z_blocks_plain(N));
 }
 
 cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
@@ -1166,6 +1188,7 @@ cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
     const int p3 = c->p * c->p * c->p;
     const size_t nblk = (size_t)batch_nblk(j.ncat);
     size_t part_need = std::max<size_t>((size_t)j.ncat * std::max(2, p3) * nblk, batch_part_need(N, S_max, C_max));
+    part_need = std::max(part_need, (size_t)std::min<size_t>(j.ells.size(), 8) * c->Q);  // self-pair histogram
     if ((e = grow_doubles(b->part, b->part_cap, part_need)) != cudaSuccess) return e;
     const size_t nwin = j.ells.size() * (size_t)c->n_bins;
     if ((e = grow_doubles(b->res, b->res_cap, 3 * (size_t)j.ncat * nwin)) != cudaSuccess) return e;
@@ -1220,19 +1243,14 @@ cudaError_t batch_enqueue_window_block(hermes_ctx* c, const BatchJob& j, int o, 
     wb.nbp = c->nbp;
     wb.ell = ell;
     wb.scale = (float)((2 * ell + 1) * (((ell / 2) & 1) ? -1 : 1));
-    Tables tb = tables_of(c);
-    tb.stab = b->stab_f + (size_t)c0 * STAB_STRIDE;
-    const int xb = inv_x_blocks(N);
+    const Tables tb = tables_of(c);
     const int zb = (C == 1) ? inv_z_blocks(N) : inv_z_blocks_plain(N);
-    double* sn_part = b->part;
-    double* dd_part = b->part + (size_t)C * S * xb;
-    cudaError_t e = launch_inverse_xi(N, c->p, b->spec + (size_t)c0 * N * N * H, b->work, b->grid + (size_t)c0 * n3,
-                                      wb, tb, sn_part, dd_part, c->err, st, tr, C);
+    double* dd_part = b->part;
+    cudaError_t e = launch_inverse_xi(N, b->spec + (size_t)c0 * N * N * H, b->work, b->grid + (size_t)c0 * n3, wb, tb,
+                                      dd_part, c->err, st, tr, C);
     if (e != cudaSuccess) return e;
     double* dd = b->res;
-    double* sn = b->res + (size_t)j.ncat * nwin;
     const size_t at = (size_t)c0 * nwin + (size_t)o * nb + b0;
-    if ((e = launch_reduce_rows_strided(sn_part, C * S, xb, S, sn + at, nwin, st, tr)) != cudaSuccess) return e;
     return launch_reduce_rows_strided(dd_part, C * S, zb, S, dd + at, nwin, st, tr);
 }
 
@@ -1242,6 +1260,14 @@ cudaError_t batch_enqueue_windows(hermes_ctx* c, const BatchJob& j, cudaStream_t
     const int nwin = (int)j.ells.size() * nb;
     const int S = j.plan.S, C = j.plan.C;
     cudaError_t e;
+    // self-pair terms, catalogue by catalogue (the histogram lives in the partials buffer)
+    for (int k = 0; k < j.ncat; ++k) {
+        Tables tb = tables_of(c);
+        tb.stab = b->stab_f + (size_t)k * STAB_STRIDE;
+        if ((e = enqueue_selfpair_terms(c, tb, j.ells.data(), (int)j.ells.size(), b->part,
+                                        b->res + (size_t)j.ncat * nwin + (size_t)k * nwin, st, tr)) != cudaSuccess)
+            return e;
+    }
     for (int o = 0; o < (int)j.ells.size(); ++o)
         for (int b0 = 0; b0 < nb; b0 += S)
             for (int c0 = 0; c0 < j.ncat; c0 += C)

@@ -16,7 +16,7 @@ constexpr int STAB_STRIDE = 512;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -97,17 +97,24 @@ cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal,
 int inv_x_blocks(int N);
 int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
 int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)
-cudaError_t launch_inverse_xi(int N, int p, const float2* spec, float2* work, const float* delta,
-                              const WinBatch& wb, const Tables& tb, double* sn_part, double* dd_part,
-                              unsigned* err, cudaStream_t st, const Tracer& tr, int ncat = 1);
+// window multiply + inverse transforms + cell contraction of one window batch;
+// dd_part: [ncat][S][blocks] partial sums of delta * filtered field
+cudaError_t launch_inverse_xi(int N, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
+                              const Tables& tb, double* dd_part, unsigned* err, cudaStream_t st, const Tracer& tr,
+                              int ncat = 1);
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr);
 
 // kspace.cu
+// self_only = 0: A_l(q) of the Parseval route; self_only = 1: the self-pair
+// histogram B_l(q) = sum_{|n|^2=q} w_z Phi^ L_l S^ alone (spec and scal unused)
 cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int P, const double* scal,
-                               const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr);
+                               const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr,
+                               int self_only = 0);
+// out[o*nb + b] = c_l sum_q T_{b,l}(q) hist[o*Q + q] / N^6, c_l = (2l+1) i^l
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
-                                   int N, double* out, int nb, cudaStream_t st, const Tracer& tr);
+                                   int N, double* out, int nb, cudaStream_t st, const Tracer& tr,
+                                   int trace_id = K_KSPACE_CONTRACT);
 
 // zeta.cu
 int zeta_z_blocks(int N);

@@ -49,7 +49,9 @@ __device__ __forceinline__ double widen_f32(float v) {
 // The mirror modes (+-n_x, +-n_y) share |n|^2, Phi^ and S^ (both even in every
 // component), so a thread sums |delta^|^2 over the up to four of them that are
 // stored and issues one atomic per order instead of four.
-template <int N>
+// SELF: only the self-pair part, B_l(q) = sum_{|n|^2=q} w_z Phi^(n) L_l(mu) S^(n)
+// (positive, not divided by eps_bar^2; the spectrum is not read).
+template <int N, bool SELF>
 __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2* __restrict__ spec, const Tables tb,
                                                                    int P, const double* __restrict__ scal,
                                                                    KsOrders ko, double* __restrict__ hist,
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
     const int ky2 = (N - ky) & (N - 1);  // mirror row (== ky for ky = 0)
     const int ny = ky, nz = kz;
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
-    const double inv_eps2 = scal[2] * scal[2];  // scal[2] = N^3 / sum w = 1 / eps_bar
+    const double inv_eps2 = SELF ? 0.0 : scal[2] * scal[2];  // scal[2] = N^3 / sum w = 1 / eps_bar
     // self-pair transform S^(n) = sum_a C(k_x, a) U[a], U[a] = sum_{b,c} S(a,b,c) C(k_y,b) C(k_z,c)
     float cy[8], cz[8], U[8];
 #pragma unroll
@@ -94,18 +96,21 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
     for (int kx = tx; kx < H; kx += TX) {
         const int kx2 = (N - kx) & (N - 1);
         const int q = kx * kx + ny * ny + nz * nz;
-        const float2 d00 = spec[((size_t)kx * N + ky) * H + kz];
-        float pw = fmaf(d00.x, d00.x, d00.y * d00.y);
-        if (ky) {
-            const float2 d = spec[((size_t)kx * N + ky2) * H + kz];
-            pw += fmaf(d.x, d.x, d.y * d.y);
-        }
-        if (kx) {
-            const float2 d = spec[((size_t)kx2 * N + ky) * H + kz];
-            pw += fmaf(d.x, d.x, d.y * d.y);
+        float pw = 0.0f;
+        if constexpr (!SELF) {
+            const float2 d00 = spec[((size_t)kx * N + ky) * H + kz];
+            pw = fmaf(d00.x, d00.x, d00.y * d00.y);
             if (ky) {
-                const float2 e = spec[((size_t)kx2 * N + ky2) * H + kz];
-                pw += fmaf(e.x, e.x, e.y * e.y);
+                const float2 d = spec[((size_t)kx * N + ky2) * H + kz];
+                pw += fmaf(d.x, d.x, d.y * d.y);
+            }
+            if (kx) {
+                const float2 d = spec[((size_t)kx2 * N + ky) * H + kz];
+                pw += fmaf(d.x, d.x, d.y * d.y);
+                if (ky) {
+                    const float2 e = spec[((size_t)kx2 * N + ky2) * H + kz];
+                    pw += fmaf(e.x, e.x, e.y * e.y);
+                }
             }
         }
         float sh = 0.0f;
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
         for (int a = 0; a < 8; ++a)
             if (a < P) sh = fmaf((a == 0) ? 1.0f : 2.0f * __ldg(tb.tw + N + ((kx * a) & (N - 1))).x, U[a], sh);
         const float cnt = ny_cnt * ((kx == 0) ? 1.0f : 2.0f);
-        pw = fmaf(-cnt * sh, inv_e2, pw);
+        pw = SELF ? cnt * sh : fmaf(-cnt * sh, inv_e2, pw);
         const float base = wz * (__ldg(tb.phi + kx) * phyz) * pw;
         const float mu = q > 0 ? (float)nz * rsqrtf((float)q) : 0.0f;
         for (int o = 0; o < ko.n; ++o) {
@@ -177,31 +182,33 @@ __global__ void __launch_bounds__(KC_THREADS) k_kspace_contract(const float* __r
 
 template <int N>
 static cudaError_t kspace_impl(const float2* spec, const Tables& tb, int P, const double* scal, const KsOrders& ko,
-                               double* hist, int64_t Q, cudaStream_t st, const Tracer& tr) {
+                               double* hist, int64_t Q, cudaStream_t st, const Tracer& tr, int self_only) {
     using C = KsCfg<N>;
     dim3 g((N / 2) / C::W, N / 2, 1);
-    tr(K_KSPACE_HIST, 0, st);
-    k_kspace_hist<N><<<g, C::THREADS, 0, st>>>(spec, tb, P, scal, ko, hist, Q);
-    tr(K_KSPACE_HIST, 1, st);
+    tr(self_only ? K_SN_HIST : K_KSPACE_HIST, 0, st);
+    if (self_only) k_kspace_hist<N, true><<<g, C::THREADS, 0, st>>>(spec, tb, P, scal, ko, hist, Q);
+    else k_kspace_hist<N, false><<<g, C::THREADS, 0, st>>>(spec, tb, P, scal, ko, hist, Q);
+    tr(self_only ? K_SN_HIST : K_KSPACE_HIST, 1, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int P, const double* scal,
-                               const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr) {
+                               const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr,
+                               int self_only) {
     switch (N) {
-        case 16: return kspace_impl<16>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 32: return kspace_impl<32>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 64: return kspace_impl<64>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 128: return kspace_impl<128>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 256: return kspace_impl<256>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 512: return kspace_impl<512>(spec, tb, P, scal, ko, hist, Q, st, tr);
-        case 1024: return kspace_impl<1024>(spec, tb, P, scal, ko, hist, Q, st, tr);
+        case 16: return kspace_impl<16>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 32: return kspace_impl<32>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 64: return kspace_impl<64>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 128: return kspace_impl<128>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 256: return kspace_impl<256>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 512: return kspace_impl<512>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
+        case 1024: return kspace_impl<1024>(spec, tb, P, scal, ko, hist, Q, st, tr, self_only);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
-                                   int N, double* out, int nb, cudaStream_t st, const Tracer& tr) {
+                                   int N, double* out, int nb, cudaStream_t st, const Tracer& tr, int trace_id) {
     const double n3 = (double)N * N * N;
     const int chunks = (nb + 31) / 32;
     // about four blocks per SM in total, but at least one group of 32 q per warp
@@ -209,11 +216,11 @@ cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const K
     const int64_t most = (groups + KC_THREADS / 32 - 1) / (KC_THREADS / 32);
     int64_t want = (4 * 148 + chunks * ko.n - 1) / (chunks * ko.n);
     const int slices = (int)(want < most ? want : most);
-    tr(K_KSPACE_CONTRACT, 0, st);
+    tr(trace_id, 0, st);
     cudaError_t e = cudaMemsetAsync(out, 0, (size_t)ko.n * nb * sizeof(double), st);
     if (e != cudaSuccess) return e;
     k_kspace_contract<<<dim3(slices, chunks, ko.n), KC_THREADS, 0, st>>>(rad, nbp, Q, ko, hist, n3 * n3, out, nb);
-    tr(K_KSPACE_CONTRACT, 1, st);
+    tr(trace_id, 1, st);
     return cudaGetLastError();
 }
 

@@ -324,8 +324,8 @@ __global__ void __launch_bounds__(256) k_finish_batch(const double* __restrict__
     for (int e = threadIdx.x; e < p3; e += blockDim.x) stab_f[(size_t)c * STAB_STRIDE + e] = (float)sp[(size_t)c * p3 + e];
 }
 
-// xi of every (catalogue, window): out[c*nwin + w] = dd/N^6 - sn/(N^6 eps_bar_c^2),
-// eps_bar_c = sum w_c / N^3 (dd, sn laid out like out).
+// xi of every (catalogue, window): out[c*nwin + w] = dd/N^6 - sn/eps_bar_c^2,
+// eps_bar_c = sum w_c / N^3 (dd, sn laid out like out; sn is already / N^6).
 __global__ void __launch_bounds__(256) k_xi_batch_finish(const double* __restrict__ dd, const double* __restrict__ sn,
                                                          const double* __restrict__ scal, int ncat, int nwin, int N,
                                                          double* __restrict__ out) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_xi_batch_finish(const double* __restric
     const int c = i / nwin;
     const double n3 = (double)N * N * N, n6 = n3 * n3;
     const double eb = scal[(size_t)c * SCAL_STRIDE] / n3;
-    out[i] = dd[i] / n6 - sn[i] / (n6 * eb * eb);
+    out[i] = dd[i] / n6 - sn[i] / (eb * eb);
 }
 
 // scal[0] = sum w, scal[1] = sum w^2, scal[2] = N^3 / sum w (the inverse mean);
