@@ -120,6 +120,21 @@ def gen_catalogue3(seed: int):
     return S.lognormal_catalogue(NPTS3, L3, seed=seed, n_grid=512)
 
 
+# DRAM bytes measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the inverse
+# passes at 512^3 on a 5-window launch of the current kernels (summary and command in
+# profiles/xi_512_inverse_passes_ncu.md): bytes per launch (read once per launch) and per window.
+NCU_TRAFFIC_512 = {
+    "inv_x_window": {"per_launch": 0.562242e9, "per_window": 2.651025e9 / 5},
+    "inv_y": {"per_launch": 0.0, "per_window": (2.684539e9 + 2.630558e9) / 5},
+    "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221751e9 + 0.005018e9) / 5},
+}
+
+
+def ncu_traffic(name: str, windows_per_launch: float) -> float | None:
+    t = NCU_TRAFFIC_512.get(name)
+    return None if t is None else t["per_launch"] + t["per_window"] * windows_per_launch
+
+
 def alg_bytes(name: str, launches: int, n_windows: int, n_batches: int, n_pts_bytes: float) -> float | None:
     """Algorithmic HBM bytes of one kernel class over the timed region (N = 512)."""
     n3 = float(N2) ** 3
@@ -238,10 +253,15 @@ def run_hermes(args, rank, world, local_rank):
     dom_b = alg_bytes(dom, trace[dom][1], windows_per_step * args.steps, batches_per_step * args.steps,
                       (12 * n + 16 * n) * args.steps)
     achieved = dom_b / (trace[dom][0] / 1e3) / 1e9 if dom_b else None
+    traffic = ncu_traffic(dom, windows_per_step / batches_per_step)  # per launch, scaled from ncu
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
             "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
-            "traffic": None, "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured"
+            "traffic": round(traffic) if traffic else None,
+            "alg_bytes_per_launch": round(dom_b / trace[dom][1]) if dom_b else None,
+            "traffic_source": "ncu dram bytes of a 5-window launch at 512^3 scaled to this launch's windows "
+                              "(profiles/xi_512_inverse_passes_ncu.md)",
+            "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured"
             else "fallback 6.4 TB/s"}
 
     # the k-space (Parseval) route on the resident marked field: same xi_l, no inverse FFTs
