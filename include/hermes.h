@@ -210,6 +210,39 @@ int hermes_batch_info(hermes_ctx *ctx, int *S, int *C, int64_t *graph_kernels, i
                       double *tune, int tune_cap, int *n_tune);
 
 /*
+ * Axisymmetric windows for the redshift-space 2PCF xi(r_perp, r_par), line of
+ * sight z (Sec. 3.4.4, the finite-bin ring window; Table A1 rows (f)-(i)):
+ *   K_{j,i}(n) = <J_0(k_perp rho)>_i exp(-k_perp^2 sigma_perp^2 / 2)
+ *                * <cos(k_par z)>_j * Phi^(n),
+ * <J_0>_i the area average over the annulus perp_edges[i] <= rho < perp_edges[i+1]
+ * (a first edge 0 gives the disk 2 J_1(kR)/(kR)), <cos>_j the average over the slab
+ * pair par_edges[j] <= |z| < par_edges[j+1] (a first edge 0 gives the filled slab
+ * sin(kH)/(kH)); sigma_perp > 0 multiplies the Gaussian transverse smoothing of
+ * the Gaussian ring.  Tables are built on the host in float64 (closed forms with
+ * J_1) and stored on the device as float32, indexed exactly by
+ * q_perp = n_x^2 + n_y^2 and |n_z|.  Replaces earlier cylindrical bins.
+ *   edges: 2..4097 per axis, >= 0, strictly increasing, <= L/2.
+ * Errors: HERMES_ERR_ARG, HERMES_ERR_RANGE, HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ */
+int hermes_window_cylinders(hermes_ctx *ctx, const double *perp_edges, int n_perp_edges, const double *par_edges,
+                            int n_par_edges, double sigma_perp);
+
+/*
+ * xi(r_perp, r_par) of the resident field with the cylindrical bins: the window
+ * multiply, inverse transforms and cell contraction of hermes_xi_multipoles with
+ * K_{j,i}, minus the exact self-pair term, normalised by the uniform RR (= 1 in
+ * delta units, K(0) = 1).  out: [n_par][n_perp] float64.
+ * Errors: HERMES_ERR_STATE (no field or no cylindrical bins), HERMES_ERR_TIMEOUT,
+ * HERMES_ERR_CUDA, HERMES_ERR_NOMEM.
+ */
+int hermes_xi_cylinders(hermes_ctx *ctx, double *out);
+
+/* The same by Parseval's theorem (Eq. pair-counting-kspace): one pass over delta^
+ * histograms (|delta^|^2 - S^/eps_bar^2) Phi^ <cos>_j over q_perp, contracted with
+ * the transverse table.  Errors: as hermes_xi_cylinders. */
+int hermes_xi_cylinders_kspace(hermes_ctx *ctx, double *out);
+
+/*
  * 3PCF Legendre multipoles zeta_l(r_b1, r_b2), 0 <= l <= l_max, from the
  * harmonic shell fields a_{b,lm} = iFFT[delta^ 4 pi i^l <j_l>_b Y_lm Phi^]
  * (Eq. multipole-window, Eq. iFFT-multipoleSFC):

@@ -155,7 +155,8 @@ __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
 // I1: first inverse pass (along x) with the window multiply of a batch of S
 // windows fused in: K_s(n) = scale * T_s(|n|^2) * Phi^(n) * L_l(k_z/k), all
 // windows of the batch sharing the order l (Phi^, L_l and scale are applied to
-// the input once).  The self-pair term of each window is not summed here: it
+// the input once); for axisymmetric windows K_s(n) = T_perp_s(n_x^2 + n_y^2) *
+// T_par_j(|n_z|) * Phi^(n), the batch sharing the line-of-sight bin j.  The self-pair term of each window is not summed here: it
 // is the radial contraction of the self-pair histogram (kspace.cu).
 //
 // STAB: the block first copies the radial factors it needs into shared memory
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         for (int e = threadIdx.x; e < total; e += C::TS) {
             const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
             const int nzc = blockIdx.x * W + c;
-            const int qq = nyq_y ? 0 : a * a + ny2 + nzc * nzc;
+            const int qq = nyq_y ? 0 : a * a + ny2 + (wb.cyl ? 0 : nzc * nzc);
             ac::cp_async16(ttab + (a * W + c) * RS + 4 * s4,
                            reinterpret_cast<const float4*>(wb.tab + (size_t)qq * wb.nbp) + s4);
         }
@@ -217,10 +218,13 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         const int kx = t + i * T;
         const int nx = signed_freq(kx, N);
         const bool nyq = nyq_y || (kx == H);
-        const int qq = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
+        const int qi = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
         const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
-        const float a = wb.scale * legendre(wb.ell, qq > 0 ? (float)nz * rsqrtf((float)qq) : 0.0f);
+        // the window's factor that does not depend on the bin: scale * L_l(k_z/k), or T_par_j(|n_z|)
+        const float a = wb.cyl ? __ldg(wb.par + nz)
+                               : wb.scale * legendre(wb.ell, qi > 0 ? (float)nz * rsqrtf((float)qi) : 0.0f);
         v0[i] = cscale(v0[i], ph * a);
+        const int qq = (wb.cyl && !nyq) ? nx * nx + ny * ny : qi;
         const int ax = (kx < H) ? kx : (kx == H ? 0 : N - kx);  // |n_x|; the Nyquist lane reads row 0
         q[i] = STAB ? (ax * W + col) * RS : qq;
     }

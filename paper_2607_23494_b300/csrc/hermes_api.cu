@@ -60,6 +60,11 @@ struct hermes_ctx {
     int nbp = 0;                 // bins padded to a multiple of 4
     std::vector<double> edges;
     float* rad = nullptr;        // [(l*Q + q)*nbp + b]
+    // axisymmetric windows: transverse table [q_perp*cyl_nbp + i], line-of-sight [j*H + |n_z|]
+    float* cyl_perp = nullptr;
+    float* cyl_par = nullptr;
+    int cyl_nperp = 0, cyl_npar = 0, cyl_nbp = 0;
+    int64_t cyl_Q = 0;
     // state
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
@@ -453,6 +458,8 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->stage_pos);
     cudaFree(c->stage_w);
     cudaFree(c->rad);
+    cudaFree(c->cyl_perp);
+    cudaFree(c->cyl_par);
     batch_free(c->batch);
     c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -666,25 +673,41 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
 }
 
 namespace {
-// Self-pair term of every window (order index a, bin b) into out[a*nb + b]:
-// c_l sum_q T_{b,l}(q) B_l(q) / N^6 with B_l the self-pair histogram of the
-// field whose float table is tb.stab (divide by eps_bar^2 for SN_b).  hist
-// holds min(n_ells, 8) * Q doubles.
-cudaError_t enqueue_selfpair_terms(hermes_ctx* c, const Tables& tb, const int* ells, int n_ells, double* hist,
-                                   double* out, cudaStream_t st, const Tracer& tr) {
-    for (int a0 = 0; a0 < n_ells; a0 += 8) {
+// Radial-histogram terms of every window (entry a of idx, bin b) into
+// out[a*nb + b] = c sum_q T_b(q) H_a(q) / N^6 (Eq. pair-counting-kspace):
+//   self_only = 1: H is the self-pair histogram of the field whose float table is
+//                  tb.stab (divide by eps_bar^2 for SN_b);
+//   self_only = 0: H is the Parseval histogram (|delta^|^2 - S^/eps_bar^2), so out is xi.
+// cyl = 0: idx are even orders l over the isotropic tables; cyl = 1: idx are
+// line-of-sight bins j over the axisymmetric tables.  hist holds
+// min(n, 8) * Q doubles.
+cudaError_t enqueue_hist_terms(hermes_ctx* c, const Tables& tb, const double* scal, const int* idx, int n, int cyl,
+                               int self_only, double* hist, double* out, cudaStream_t st, const Tracer& tr) {
+    const float* rad = cyl ? c->cyl_perp : c->rad;
+    const int nbp = cyl ? c->cyl_nbp : c->nbp;
+    const int64_t Q = cyl ? c->cyl_Q : c->Q;
+    const int nb = cyl ? c->cyl_nperp : c->n_bins;
+    for (int a0 = 0; a0 < n; a0 += 8) {
         KsOrders ko;
-        ko.n = std::min(8, n_ells - a0);
-        for (int k = 0; k < ko.n; ++k) ko.ell[k] = ells[a0 + k];
-        cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ko.n * c->Q * sizeof(double), st);
+        ko.n = std::min(8, n - a0);
+        for (int k = 0; k < ko.n; ++k) ko.ell[k] = idx[a0 + k];
+        ko.cyl = cyl;
+        ko.par = c->cyl_par;
+        cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ko.n * Q * sizeof(double), st);
         if (e != cudaSuccess) return e;
-        if ((e = launch_kspace_hist(c->N, nullptr, tb, c->p, nullptr, ko, hist, c->Q, st, tr, 1)) != cudaSuccess)
+        if ((e = launch_kspace_hist(c->N, self_only ? nullptr : c->spec, tb, c->p, scal, ko, hist, Q, st, tr,
+                                    self_only)) != cudaSuccess)
             return e;
-        if ((e = launch_kspace_contract(c->rad, c->nbp, c->Q, ko, hist, c->N, out + (size_t)a0 * c->n_bins, c->n_bins,
-                                        st, tr, K_SN_CONTRACT)) != cudaSuccess)
+        if ((e = launch_kspace_contract(rad, nbp, Q, ko, hist, c->N, out + (size_t)a0 * nb, nb, st, tr,
+                                        self_only ? K_SN_CONTRACT : K_KSPACE_CONTRACT)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t enqueue_selfpair_terms(hermes_ctx* c, const Tables& tb, const int* ells, int n_ells, double* hist,
+                                   double* out, cudaStream_t st, const Tracer& tr) {
+    return enqueue_hist_terms(c, tb, nullptr, ells, n_ells, 0, 1, hist, out, st, tr);
 }
 }  // namespace
 
@@ -1537,6 +1560,7 @@ extern "C" int64_t hermes_device_bytes(const hermes_ctx* c) {
     b += c->work_bytes + c->zfields_bytes + (c->part_cap + c->red_cap) * sizeof(double);
     b += c->stage_cap * 4 * sizeof(float);
     if (c->rad) b += (size_t)c->nbp * (c->l_max + 1) * c->Q * sizeof(float);
+    if (c->cyl_perp) b += ((size_t)c->cyl_nbp * c->cyl_Q + (size_t)c->cyl_npar * (N / 2)) * sizeof(float);
     if (c->batch) {
         const BatchState* s = c->batch;
         b += s->pts_cap * 4 * sizeof(float) + (size_t)s->cat_cap * (n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2));
@@ -1564,4 +1588,165 @@ extern "C" int64_t hermes_estimate_bytes(int N, int stat, int n_bins, int l_max,
         b += (size_t)2 * (l_max + 1) * n_bins * sizeof(double);
     }
     return (int64_t)b;
+}
+
+// ---------------------------------------------------------------------------
+// Axisymmetric windows: xi(r_perp, r_par) with finite transverse annuli and
+// line-of-sight slab pairs (Sec. 3.4.4; Table A1 rows (f)-(i) as limits).
+
+namespace {
+
+// Area average of J_0(k rho) over a <= rho < b: [b J_1(kb) - a J_1(ka)] / (k (b^2 - a^2) / 2),
+// from int_0^r rho J_0(k rho) d rho = r J_1(k r) / k; 1 at k = 0.
+double annulus_j0(double k, double a, double b) {
+    if (k == 0.0) return 1.0;
+    const double jb = b * std::cyl_bessel_j(1.0, k * b);
+    const double ja = a > 0.0 ? a * std::cyl_bessel_j(1.0, k * a) : 0.0;
+    return (jb - ja) / (k * 0.5 * (b * b - a * a));
+}
+
+// Average of cos(k z) over a <= |z| < b: [sin(kb) - sin(ka)] / (k (b - a)); 1 at k = 0.
+double slab_cos(double k, double a, double b) {
+    if (k == 0.0) return 1.0;
+    return (std::sin(k * b) - std::sin(k * a)) / (k * (b - a));
+}
+
+}  // namespace
+
+extern "C" int hermes_window_cylinders(hermes_ctx* c, const double* perp_edges, int n_perp_edges,
+                                       const double* par_edges, int n_par_edges, double sigma_perp) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!perp_edges || !par_edges) return fail(c, HERMES_ERR_ARG, "edges are NULL");
+    if (n_perp_edges < 2 || n_perp_edges > 4097 || n_par_edges < 2 || n_par_edges > 4097)
+        return fail(c, HERMES_ERR_ARG, "need 2..4097 edges per axis (have %d transverse, %d line-of-sight)",
+                    n_perp_edges, n_par_edges);
+    if (!std::isfinite(sigma_perp) || sigma_perp < 0.0)
+        return fail(c, HERMES_ERR_RANGE, "sigma_perp = %g must be finite and >= 0", sigma_perp);
+    for (const auto& ax : {std::make_pair(perp_edges, n_perp_edges), std::make_pair(par_edges, n_par_edges)}) {
+        for (int e = 0; e < ax.second; ++e) {
+            if (!std::isfinite(ax.first[e]) || ax.first[e] < 0.0)
+                return fail(c, HERMES_ERR_RANGE, "edge %d = %g is negative or not finite", e, ax.first[e]);
+            if (e > 0 && !(ax.first[e] > ax.first[e - 1]))
+                return fail(c, HERMES_ERR_RANGE, "edges must increase strictly (index %d)", e);
+        }
+        if (ax.first[ax.second - 1] > 0.5 * c->L)
+            return fail(c, HERMES_ERR_RANGE, "largest edge %g exceeds L/2 = %g", ax.first[ax.second - 1], 0.5 * c->L);
+    }
+    DeviceGuard g(c->device);
+    const int N = c->N, H = N / 2;
+    const int np = n_perp_edges - 1, nz = n_par_edges - 1;
+    const int nbp = (np + 3) & ~3;
+    const int64_t Qp = 2 * (int64_t)(H - 1) * (H - 1) + 1;  // q_perp = n_x^2 + n_y^2 off the Nyquist planes
+    const double kf = 2.0 * M_PI / c->L;
+    std::vector<float> perp, par;
+    try {
+        perp.assign((size_t)Qp * nbp, 0.0f);
+        par.assign((size_t)nz * H, 0.0f);
+    } catch (...) {
+        return fail(c, HERMES_ERR_NOMEM, "host tables");
+    }
+    // transverse table by threads over q_perp (J_1 at every edge once per q)
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nt; ++w)
+        th.emplace_back([&, w] {
+            std::vector<double> rj(n_perp_edges);
+            for (int64_t q = w; q < Qp; q += nt) {
+                const double k = kf * std::sqrt((double)q);
+                const double gs = std::exp(-0.5 * k * k * sigma_perp * sigma_perp);
+                for (int i = 0; i < np; ++i)
+                    perp[(size_t)q * nbp + i] = (float)(annulus_j0(k, perp_edges[i], perp_edges[i + 1]) * gs);
+            }
+        });
+    for (auto& t : th) t.join();
+    for (int j = 0; j < nz; ++j)
+        for (int a = 0; a < H; ++a) par[(size_t)j * H + a] = (float)slab_cos(kf * a, par_edges[j], par_edges[j + 1]);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->cyl_perp);
+    cudaFree(c->cyl_par);
+    c->cyl_perp = nullptr;
+    c->cyl_par = nullptr;
+    c->cyl_nperp = c->cyl_npar = 0;
+    CK(cudaMalloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "transverse table");
+    CK(cudaMalloc((void**)&c->cyl_par, par.size() * sizeof(float)), "line-of-sight table");
+    CK(cudaMemcpy(c->cyl_perp, perp.data(), perp.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    CK(cudaMemcpy(c->cyl_par, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    c->cyl_nperp = np;
+    c->cyl_npar = nz;
+    c->cyl_nbp = nbp;
+    c->cyl_Q = Qp;
+    return HERMES_OK;
+}
+
+namespace {
+int check_cyl(hermes_ctx* c, double* out) {
+    if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->cyl_nperp < 1) return fail(c, HERMES_ERR_STATE, "no cylindrical bins: call hermes_window_cylinders first");
+    return HERMES_OK;
+}
+}  // namespace
+
+extern "C" int hermes_xi_cylinders(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (int r = check_cyl(c, out)) return r;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, H = N / 2, np = c->cyl_nperp, nz = c->cyl_npar;
+    const int nwin = np * nz;
+    const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
+    const int S = (int)xi_window_S(N, np);
+    CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
+    const int zb = inv_z_blocks(N);
+    CK(grow_doubles(c->part, c->part_cap, std::max((size_t)S * zb, (size_t)std::min(nz, 8) * c->cyl_Q)), "partials");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
+    const Tables tb = tables_of(c);
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    std::vector<int> js(nz);
+    for (int j = 0; j < nz; ++j) js[j] = j;
+    CK(enqueue_hist_terms(c, tb, nullptr, js.data(), nz, 1, 1, c->part, c->red + nwin, st, c->tracer),
+       "self-pair terms");
+    for (int j = 0; j < nz; ++j)
+        for (int b0 = 0; b0 < np; b0 += S) {
+            WinBatch wb;
+            wb.S = std::min(S, np - b0);
+            wb.tab = c->cyl_perp + b0;
+            wb.nbp = c->cyl_nbp;
+            wb.ell = 0;
+            wb.scale = 1.0f;
+            wb.cyl = 1;
+            wb.par = c->cyl_par + (size_t)j * H;
+            CK(launch_inverse_xi(N, c->spec, c->work, c->grid, wb, tb, c->part, c->err, st, c->tracer),
+               "inverse passes");
+            CK(launch_reduce_rows(c->part, wb.S, zb, c->red + (size_t)j * np + b0, st, c->tracer),
+               "reduce contractions");
+        }
+    CK(ensure_host(c, (size_t)2 * nwin + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "xi(r_perp, r_par)");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
+    const double n3 = (double)N * N * N, n6 = n3 * n3, eb = c->sum_w / n3;
+    for (int w = 0; w < nwin; ++w) out[w] = c->host_buf[w] / n6 - c->host_buf[nwin + w] / (eb * eb);
+    return HERMES_OK;
+}
+
+extern "C" int hermes_xi_cylinders_kspace(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (int r = check_cyl(c, out)) return r;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int np = c->cyl_nperp, nz = c->cyl_npar, nwin = np * nz;
+    CK(grow_doubles(c->part, c->part_cap, (size_t)std::min(nz, 8) * c->cyl_Q), "histogram");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)nwin), "reduction buffer");
+    std::vector<int> js(nz);
+    for (int j = 0; j < nz; ++j) js[j] = j;
+    CK(enqueue_hist_terms(c, tables_of(c), c->scal, js.data(), nz, 1, 0, c->part, c->red, st, c->tracer),
+       "k-space histogram");
+    CK(ensure_host(c, (size_t)nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    CK(cudaStreamSynchronize(st), "xi(r_perp, r_par) (k-space)");
+    std::memcpy(out, c->host_buf, (size_t)nwin * sizeof(double));
+    return HERMES_OK;
 }

@@ -33,12 +33,19 @@ struct Tracer {
 
 // One batch of real (xi / xi_l) windows: consecutive bins b0 .. b0+S-1 of one
 // even order l.  tab = rad + l*Q*nbp + b0; window s uses tab[q*nbp + s].
+//
+// Axisymmetric (cylindrical) windows, cyl = 1: K_{j,i}(n) = T_perp_i(n_x^2 + n_y^2)
+// * T_par_j(|n_z|) * Phi^(n); tab is the transverse table indexed by q_perp =
+// n_x^2 + n_y^2 (bin fastest), par = T_par_j over |n_z| in [0, N/2) for the
+// batch's line-of-sight bin j; ell and scale are unused.
 struct WinBatch {
     const float* tab;
     int nbp;
     int S;
     int ell;
     float scale;  // (2l+1) i^l, real for even l
+    int cyl = 0;
+    const float* par = nullptr;
 };
 
 // One batch of complex harmonic windows: all bins of a fixed (l, m).
@@ -51,10 +58,15 @@ struct HarmBatch {
     float ylm_norm;  // N_lm (-1)^m (2m-1)!!  times 4 pi
 };
 
-// Orders of one k-space evaluation (even l, at most 8).
+// Orders of one k-space evaluation (even l, at most 8).  cyl = 1: the entries
+// are line-of-sight bins j of an axisymmetric window instead, each weighting a
+// mode by par[j*(N/2) + |n_z|], the histogram is indexed by q_perp = n_x^2 + n_y^2
+// and the contraction constant is 1.
 struct KsOrders {
     int n;
     int ell[8];
+    int cyl = 0;
+    const float* par = nullptr;
 };
 
 struct Tables {

@@ -1,4 +1,5 @@
-// k-space (Parseval) route for xi and xi_l, Eq. (pair-counting-kspace):
+// k-space (Parseval) route for xi, xi_l and the axisymmetric xi(r_perp, r_par),
+// Eq. (pair-counting-kspace):
 //   (1/N^3) sum_x delta delta~_b = (1/N^6) sum_n |delta^_n|^2 K_b(n),
 // and the self-pair term (1/(N^6 eps_bar^2)) sum_n K_b(n) S^(n).  Every window
 // of this library has K_{b,l}(n) = c_l T_{b,l}(|n|^2) Phi^(n) L_l(k_z/k), so one
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
     const float inv_e2 = (float)inv_eps2;
     for (int kx = tx; kx < H; kx += TX) {
         const int kx2 = (N - kx) & (N - 1);
-        const int q = kx * kx + ny * ny + nz * nz;
+        const int qp = kx * kx + ny * ny;  // mirrors share n_x^2 + n_y^2 and |n_z|
+        const int q = qp + nz * nz;
         float pw = 0.0f;
         if constexpr (!SELF) {
             const float2 d00 = spec[((size_t)kx * N + ky) * H + kz];
@@ -122,8 +124,10 @@ __global__ void __launch_bounds__(KsCfg<N>::THREADS) k_kspace_hist(const float2*
         const float base = wz * (__ldg(tb.phi + kx) * phyz) * pw;
         const float mu = q > 0 ? (float)nz * rsqrtf((float)q) : 0.0f;
         for (int o = 0; o < ko.n; ++o) {
-            const float v = ko.ell[o] == 0 ? base : base * legendre_k(ko.ell[o], mu);
-            atomicAdd(hist + (size_t)o * Q + q, widen_f32(v));
+            const float f = ko.cyl ? __ldg(ko.par + ko.ell[o] * H + nz)
+                                   : (ko.ell[o] == 0 ? 1.0f : legendre_k(ko.ell[o], mu));
+            const float v = base * f;
+            atomicAdd(hist + (size_t)o * Q + (ko.cyl ? qp : q), widen_f32(v));
         }
     }
 }
@@ -143,7 +147,8 @@ __global__ void __launch_bounds__(KC_THREADS) k_kspace_contract(const float* __r
     const int o = blockIdx.z, b = blockIdx.y * 32 + lane;
     const int ell = ko.ell[o];
     const bool live = b < nb;
-    const float* tab = rad + (size_t)ell * Q * nbp + (live ? b : 0);
+    // isotropic: the table block of order l; axisymmetric: the one transverse table
+    const float* tab = rad + (ko.cyl ? 0 : (size_t)ell * Q * nbp) + (live ? b : 0);
     const double* h = hist + (size_t)o * Q;
     const int64_t ngroups = (Q + 31) / 32;
     const int64_t nwarps = (int64_t)gridDim.x * (KC_THREADS / 32);
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(KC_THREADS) k_kspace_contract(const float* __r
 #pragma unroll
         for (int w = 0; w < KC_THREADS / 32; ++w) t += part[w][lane];
         if (live) {
-            const double c = (double)(2 * ell + 1) * (((ell / 2) & 1) ? -1.0 : 1.0);
+            const double c = ko.cyl ? 1.0 : (double)(2 * ell + 1) * (((ell / 2) & 1) ? -1.0 : 1.0);
             atomicAdd(out + (size_t)o * nb + b, c * t / n6);
         }
     }

@@ -75,6 +75,9 @@ def _load() -> C.CDLL:
         "hermes_batch_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64), dp, i32, C.POINTER(i32)]),
         "hermes_zeta_multipoles": (i32, [vp, dp]),
+        "hermes_window_cylinders": (i32, [vp, dp, i32, dp, i32, C.c_double]),
+        "hermes_xi_cylinders": (i32, [vp, dp]),
+        "hermes_xi_cylinders_kspace": (i32, [vp, dp]),
         "hermes_last_error": (C.c_char_p, [vp]),
         "hermes_debug_get_delta": (i32, [vp, fp]),
         "hermes_debug_get_spectrum": (i32, [vp, fp]),
@@ -278,6 +281,21 @@ class Context:
         n = min(n_t.value, 64)
         return {"S": S.value, "C": Cc.value, "graph_kernels": gk.value, "graph_replays": gr.value,
                 "tuning": [tuple(tune[3 * i:3 * i + 3]) for i in range(n)]}
+
+    def window_cylinders(self, perp_edges: Sequence[float], par_edges: Sequence[float],
+                         sigma_perp: float = 0.0) -> None:
+        pe = np.ascontiguousarray(perp_edges, dtype=np.float64)
+        ze = np.ascontiguousarray(par_edges, dtype=np.float64)
+        self._check(_lib.hermes_window_cylinders(self._h, _dptr(pe), len(pe), _dptr(ze), len(ze), float(sigma_perp)),
+                    "hermes_window_cylinders")
+        self.n_perp, self.n_par = len(pe) - 1, len(ze) - 1
+
+    def xi_cylinders(self, kspace: bool = False) -> np.ndarray:
+        """xi(r_perp, r_par) as [n_par, n_perp]; kspace=True uses the Parseval route."""
+        out = np.empty((self.n_par, self.n_perp), dtype=np.float64)
+        f = _lib.hermes_xi_cylinders_kspace if kspace else _lib.hermes_xi_cylinders
+        self._check(f(self._h, _dptr(out)), "hermes_xi_cylinders" + ("_kspace" if kspace else ""))
+        return out
 
     def zeta_multipoles(self) -> np.ndarray:
         out = np.empty((self.l_max + 1, self.n_bins, self.n_bins), dtype=np.float64)

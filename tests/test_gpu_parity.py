@@ -343,3 +343,53 @@ def test_cached_window_tables_serve_smaller_orders():
         np.testing.assert_allclose(got, x4[:len(ells)], rtol=1e-6, atol=1e-9)
     ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2, 4))["xi"]
     _close(x4, ref)
+
+
+@pytest.mark.parametrize("N,p,L,sigma", [(64, 4, 240.0, 0.0), (32, 3, 100.0, 4.0), (16, 2, 60.0, 0.0)])
+def test_cylinder_windows_match_oracle_both_routes(N, p, L, sigma):
+    # xi(r_perp, r_par): 7 transverse annuli (the first a disk) x 5 line-of-sight slab pairs
+    # (the first a filled slab); S = 4 window batches leave a ragged tail of 3
+    H = _hermes()
+    pos = S.lognormal_catalogue(25000, L, seed=N + 11, n_grid=N)
+    mass = S.lognormal_masses(pos.shape[0], seed=N + 12)
+    rperp = np.concatenate([[0.0], np.linspace(L / 40, L / 5, 7)])
+    rpar = np.linspace(0.0, L / 6, 6)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_cylinders(rperp, rpar, sigma_perp=sigma)
+        ctx.assign(pos, mass)
+        got = ctx.xi_cylinders()
+        gk = ctx.xi_cylinders(kspace=True)
+    ref = O.xi_cylinders(pos, mass, N, L, p, rperp, rpar, sigma_perp=sigma)
+    assert got.shape == (5, 7)
+    _close(got, ref)
+    _close(gk, ref)
+
+
+def test_cylinder_planted_mode_and_errors():
+    # delta = cos(2 pi n0.x / N) gives xi_{j,i} = K_{j,i}(n0) / 2 exactly
+    H = _hermes()
+    L, N, p = 90.0, 32, 4
+    n0 = (2, -3, 4)
+    x = np.arange(N)
+    ph = 2 * np.pi * (n0[0] * x[:, None, None] + n0[1] * x[None, :, None] + n0[2] * x[None, None, :]) / N
+    rperp, rpar = [1.0, 6.0, 15.0], [0.0, 5.0, 12.0]
+    with H.Context(L, N, p) as ctx:
+        with pytest.raises(H.HermesError) as ei:
+            ctx.window_cylinders([3.0, 2.0], rpar)
+        assert ei.value.code == H.ERR_RANGE
+        with pytest.raises(H.HermesError) as ei:
+            ctx.window_cylinders(rperp, [0.0, L])
+        assert ei.value.code == H.ERR_RANGE
+        ctx.window_cylinders(rperp, rpar)
+        with pytest.raises(H.HermesError) as ei:
+            ctx.xi_cylinders()
+        assert ei.value.code == H.ERR_STATE
+        ctx.set_delta(np.cos(ph).astype(np.float32))
+        got = ctx.xi_cylinders()
+        gk = ctx.xi_cylinders(kspace=True)
+    for j in range(2):
+        for i in range(2):
+            K = O.window_cyl(N, L, p, rperp[i], rperp[i + 1], rpar[j], rpar[j + 1])
+            ref = 0.5 * K[n0[0] % N, n0[1] % N, n0[2] % N]
+            assert abs(got[j, i] - ref) <= max(2e-5 * abs(ref), 1e-7), (j, i, got[j, i], ref)
+            assert abs(gk[j, i] - ref) <= max(2e-5 * abs(ref), 1e-7), (j, i, gk[j, i], ref)
