@@ -266,6 +266,7 @@ def run_hermes(args, rank, world, local_rank):
 
     # the k-space (Parseval) route on the resident marked field: same xi_l, no inverse FFTs
     ks = run_kspace(ctx, stream, res[1])
+    cyl = run_cylinders(ctx, stream)
     plain = None
     if not args.no_plain:
         ctx.close()
@@ -307,6 +308,7 @@ def run_hermes(args, rank, world, local_rank):
             "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
         }
         out["kspace"] = ks
+        out["cylinders"] = cyl
         if plain:
             out["vs_plain_fp32"] = plain
         if batch:
@@ -316,6 +318,31 @@ def run_hermes(args, rank, world, local_rank):
         if zeta:
             out["zeta"] = zeta
     return out, pos
+
+
+def run_cylinders(ctx, stream):
+    """xi(r_perp, r_par) of the resident marked 512^3 field: 20 transverse annuli x 20
+    line-of-sight slab pairs in [0, 100) Mpc/h (400 windows), by inverse transforms
+    and by the Parseval route."""
+    import torch
+    ctx.window_cylinders(np.linspace(0.0, 100.0, 21), np.linspace(0.0, 100.0, 21))
+    out = {}
+    for route, ks in (("inverse_fft", False), ("kspace", True)):
+        ctx.xi_cylinders(kspace=ks)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = ctx.xi_cylinders(kspace=ks)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[route] = {"ms": round(ms, 2), "cell_window_evals_per_s": round(float(N2) ** 3 * 400 / (ms / 1e3), 1)}
+        out[route + "_xi"] = got
+    a, b = out.pop("inverse_fft_xi"), out.pop("kspace_xi")
+    out["diff_between_routes_in_tolerances"] = round(float(np.max(np.abs(a - b) / np.maximum(1e-4 * np.abs(b), 1e-6))), 4)
+    out["workload"] = "xi(r_perp, r_par), marked 1e7-point field, 512^3, 20 x 20 bins in [0, 100) Mpc/h"
+    return out
 
 
 def run_kspace(ctx, stream, real):
