@@ -21,6 +21,8 @@ float64, by the plainest route that follows the paper:
   xi via cell contraction       Eq. (pair-counting), Eq. (2rdEs)
   Landy-Szalay with uniform R   Eq. (xi-deltaDD-over-RR)
   zeta_l                        Eq. (2-fold-translation), Eq. (particle_nfold)
+  explicit randoms (LS)         Sec. 3.3 estimator: Delta = D - R, xi = Delta DD / RR,
+                                Eq. (xi-deltaDD-over-RR) with a random field
   anisotropic xi(r_perp, r_par) Sec. 3.4.4 ring window with finite bins; Table A1 rows
                                 (f)-(i): separable transverse x line-of-sight windows
 
@@ -52,7 +54,7 @@ __all__ = [
     "window_zeta", "xi_parseval", "xi_cell_contraction", "self_pair_table",
     "kappa_from_K", "shot_noise", "xi_multipoles", "zeta_multipoles", "lm_modes",
     "keff_pair_direct", "xi_brute_force", "direct_convolution", "annulus_avg_j0", "slab_avg_cos",
-    "window_cyl", "xi_cylinders",
+    "window_cyl", "xi_cylinders", "xi_randoms",
 ]
 
 
@@ -492,6 +494,46 @@ def xi_multipoles(pos, w, N, L, p, r_edges, ells=(0,), route="parseval"):
                 raw[a, b] = xi_cell_contraction(delta, dh, K)
             sn[a, b] = shot_noise(S, K, N, sw)
     return dict(xi=raw - sn, sn=sn, raw=raw, delta=delta, delta_hat=dh)
+
+
+def xi_randoms(pos, w, pos_r, w_r, N, L, p, r_edges, ells=(0,), cyl=None):
+    """Landy-Szalay with an explicit random catalogue, in the field language of Sec. 3.3:
+    Delta = D - alpha R (alpha = sum w_D / sum w_R), both in units of the mean data
+    density, xi[W] = Delta DD[W] / RR[W] (Eq. xi-deltaDD-over-RR) with the self pairs of
+    D and R removed from the products (SN terms with the tables S_D + alpha^2 S_R and
+    alpha^2 S_R).  Multipoles divide by RR of the l = 0 window of the same bin.
+    cyl = (perp_edges, par_edges) measures xi(r_perp, r_par) instead ([n_par][n_perp]).
+    Parseval on the full spectrum; the random field keeps its k = 0 mode."""
+    eps_d, swd, _ = assign(pos, w, N, L, p)
+    eps_r, swr, _ = assign(pos_r, w_r, N, L, p)
+    alpha = swd / swr
+    ebar = swd / N ** 3
+    hd = forward((eps_d - alpha * eps_r) / ebar)    # its mean is 0 by the choice of alpha
+    hr = np.fft.fftn(alpha * eps_r / ebar)           # the k = 0 mode carries most of RR
+    s_d = self_pair_table(pos, w, N, L, p)
+    s_r = self_pair_table(pos_r, w_r, N, L, p)
+
+    def ratio(K, K0):
+        num = xi_parseval(hd, K) - shot_noise(s_d + alpha * alpha * s_r, K, N, swd)
+        rr = xi_parseval(hr, K0) - shot_noise(alpha * alpha * s_r, K0, N, swd)
+        return num / rr
+
+    if cyl is not None:
+        pe, ze = cyl
+        out = np.zeros((len(ze) - 1, len(pe) - 1))
+        for j in range(len(ze) - 1):
+            for i in range(len(pe) - 1):
+                K = window_cyl(N, L, p, pe[i], pe[i + 1], ze[j], ze[j + 1])
+                out[j, i] = ratio(K, K)
+        return out
+    nb = len(r_edges) - 1
+    out = np.zeros((len(ells), nb))
+    for b in range(nb):
+        K0 = window_xi(N, L, p, r_edges[b], r_edges[b + 1], 0)
+        for a, ell in enumerate(ells):
+            K = K0 if ell == 0 else window_xi(N, L, p, r_edges[b], r_edges[b + 1], ell)
+            out[a, b] = ratio(K, K0)
+    return out
 
 
 def lm_modes(l_max: int):
