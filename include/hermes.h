@@ -210,6 +210,25 @@ int hermes_batch_info(hermes_ctx *ctx, int *S, int *C, int64_t *graph_kernels, i
                       double *tune, int tune_cap, int *n_tune);
 
 /*
+ * Explicit random catalogue for the Landy-Szalay estimator in the field language
+ * (Sec. 3.3, Eq. xi-deltaDD-over-RR): xi[W] = Delta DD[W] / RR[W] with
+ * Delta = D - alpha R, alpha = sum w_D / sum w_R, both fields in units of the mean
+ * data density, and the self pairs of D and R removed from both products.
+ * The random field, its transform (k = 0 mode kept) and its self-pair table stay
+ * on the device; the next hermes_assign builds Delta from the data and them, and
+ * hermes_xi / hermes_xi_multipoles / hermes_xi_cylinders (and the k-space forms)
+ * then divide by RR (xi_l by the RR of the l = 0 window of each bin; RR by
+ * Parseval on the random field).  Without randoms RR = 1 (analytic uniform randoms).
+ * Arguments as hermes_assign.  Invalidates the resident field (assign the data
+ * again).  zeta_l and hermes_assign_noalloc refuse to run while randoms are set
+ * (HERMES_ERR_STATE); batched calls use analytic randoms.
+ * Errors: as hermes_assign.
+ */
+int hermes_assign_randoms(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
+/* Back to analytic uniform randoms (invalidates a resident difference field). */
+int hermes_clear_randoms(hermes_ctx *ctx);
+
+/*
  * Axisymmetric windows for the redshift-space 2PCF xi(r_perp, r_par), line of
  * sight z (Sec. 3.4.4, the finite-bin ring window; Table A1 rows (f)-(i)):
  *   K_{j,i}(n) = <J_0(k_perp rho)>_i exp(-k_perp^2 sigma_perp^2 / 2)

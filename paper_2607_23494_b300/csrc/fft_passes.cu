@@ -543,7 +543,7 @@ static cudaError_t launch_yz(const float2* work, int S, const float* delta, cons
 
 template <int N>
 static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, int convert, const Tables& tb,
-                                cudaStream_t st, const Tracer& tr, int ncat) {
+                                cudaStream_t st, const Tracer& tr, int ncat, int keep_dc = 0) {
     using C = Cfg<N>;
     cudaError_t e;
     if ((e = allow_smem(k_fwd_z_r2c<N>, C::SMEM_Z)) != cudaSuccess) return e;
@@ -560,7 +560,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
     tr(K_FWD_Y, 1, st);
     // along x: pos stride N*H, blockIdx.y = y, delta^(0) := 0
     tr(K_FWD_X, 0, st);
-    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, cat_stride, 1, tb.tw);
+    k_strided<N, false><<<g, C::TS, C::SMEM_STRIDED, st>>>(spec, (long long)N * H, H, cat_stride, keep_dc ? 0 : 1,
+                                                            tb.tw);
     tr(K_FWD_X, 1, st);
     return cudaGetLastError();
 }
@@ -624,8 +625,8 @@ cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal,
 }
 
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
-                                 cudaStream_t st, const Tracer& tr) {
-#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st, tr, 1)
+                                 cudaStream_t st, const Tracer& tr, int keep_dc) {
+#define F(n) forward_impl<n>(grid, spec, scal, 0, tb, st, tr, 1, keep_dc)
     HERMES_DISPATCH_N(N, F)
 #undef F
 }

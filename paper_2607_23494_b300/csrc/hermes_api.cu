@@ -65,6 +65,15 @@ struct hermes_ctx {
     float* cyl_par = nullptr;
     int cyl_nperp = 0, cyl_npar = 0, cyl_nbp = 0;
     int64_t cyl_Q = 0;
+    // explicit random catalogue (Landy-Szalay): raw field, its transform (k = 0 kept),
+    // self-pair table; rscal[2] = 1 so the histogram kernel subtracts S^ unscaled
+    float* rgrid = nullptr;
+    float2* rspec = nullptr;
+    double* rstab_d = nullptr;
+    float* rstab_f = nullptr;
+    double* rscal = nullptr;
+    double sum_wr = 0;
+    bool have_randoms = false;
     // state
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
@@ -460,6 +469,11 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->rad);
     cudaFree(c->cyl_perp);
     cudaFree(c->cyl_par);
+    cudaFree(c->rgrid);
+    cudaFree(c->rspec);
+    cudaFree(c->rstab_d);
+    cudaFree(c->rstab_f);
+    cudaFree(c->rscal);
     batch_free(c->batch);
     c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -552,7 +566,17 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
     c->sum_w2 = c->host_buf[1];
     if (!(c->sum_w > 0.0) || !std::isfinite(c->sum_w))
         return fail(c, HERMES_ERR_RANGE, "sum of weights is %g; it must be positive", c->sum_w);
-    CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st, c->tracer), "forward FFT");
+    if (c->have_randoms) {
+        // Delta = (eps_D - alpha eps_R) / eps_bar_D, alpha = sum w_D / sum w_R; SN table S_D + alpha^2 S_R
+        const double alpha = c->sum_w / c->sum_wr;
+        const double inv_ebar = (double)n3 / c->sum_w;
+        CK(launch_combine_randoms(c->grid, c->rgrid, n3, (float)alpha, (float)inv_ebar, c->stab_d, c->rstab_d,
+                                  alpha * alpha, c->stab_f, p3, st, c->tracer),
+           "difference field");
+        CK(launch_delta_to_spec(N, c->grid, c->spec, c->scal, tables_of(c), st, c->tracer), "forward FFT");
+    } else {
+        CK(launch_forward(N, c->grid, c->spec, c->scal, tables_of(c), st, c->tracer), "forward FFT");
+    }
     CK(cudaStreamSynchronize(st), "forward FFT");
     c->have_field = true;
     return HERMES_OK;
@@ -682,7 +706,8 @@ namespace {
 // line-of-sight bins j over the axisymmetric tables.  hist holds
 // min(n, 8) * Q doubles.
 cudaError_t enqueue_hist_terms(hermes_ctx* c, const Tables& tb, const double* scal, const int* idx, int n, int cyl,
-                               int self_only, double* hist, double* out, cudaStream_t st, const Tracer& tr) {
+                               int self_only, double* hist, double* out, cudaStream_t st, const Tracer& tr,
+                               const float2* spec_override = nullptr) {
     const float* rad = cyl ? c->cyl_perp : c->rad;
     const int nbp = cyl ? c->cyl_nbp : c->nbp;
     const int64_t Q = cyl ? c->cyl_Q : c->Q;
@@ -695,8 +720,8 @@ cudaError_t enqueue_hist_terms(hermes_ctx* c, const Tables& tb, const double* sc
         ko.par = c->cyl_par;
         cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ko.n * Q * sizeof(double), st);
         if (e != cudaSuccess) return e;
-        if ((e = launch_kspace_hist(c->N, self_only ? nullptr : c->spec, tb, c->p, scal, ko, hist, Q, st, tr,
-                                    self_only)) != cudaSuccess)
+        const float2* spec = self_only ? nullptr : (spec_override ? spec_override : c->spec);
+        if ((e = launch_kspace_hist(c->N, spec, tb, c->p, scal, ko, hist, Q, st, tr, self_only)) != cudaSuccess)
             return e;
         if ((e = launch_kspace_contract(rad, nbp, Q, ko, hist, c->N, out + (size_t)a0 * nb, nb, st, tr,
                                         self_only ? K_SN_CONTRACT : K_KSPACE_CONTRACT)) != cudaSuccess)
@@ -708,6 +733,17 @@ cudaError_t enqueue_hist_terms(hermes_ctx* c, const Tables& tb, const double* sc
 cudaError_t enqueue_selfpair_terms(hermes_ctx* c, const Tables& tb, const int* ells, int n_ells, double* hist,
                                    double* out, cudaStream_t st, const Tracer& tr) {
     return enqueue_hist_terms(c, tb, nullptr, ells, n_ells, 0, 1, hist, out, st, tr);
+}
+
+// RR of the random field for windows idx (isotropic orders or line-of-sight bins), by
+// Parseval on its transform: out[a*nb + b] = c sum_q T_b(q) H_a(q) / N^6 with
+// H the histogram of |eps^_R|^2 - S^_R (the randoms' self pairs removed); the caller
+// scales by (N^3 / sum w_R)^2, which turns eps_R into alpha eps_R / eps_bar_D.
+cudaError_t enqueue_rr_terms(hermes_ctx* c, const int* idx, int n, int cyl, double* hist, double* out,
+                             cudaStream_t st, const Tracer& tr) {
+    Tables tb = tables_of(c);
+    tb.stab = c->rstab_f;
+    return enqueue_hist_terms(c, tb, c->rscal, idx, n, cyl, 0, hist, out, st, tr, c->rspec);
 }
 }  // namespace
 
@@ -730,7 +766,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
     CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
     const int zb = inv_z_blocks(N);
     CK(grow_doubles(c->part, c->part_cap, std::max((size_t)S * zb, (size_t)std::min(n_ells, 8) * c->Q)), "partials");
-    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin + nb), "reduction buffer");
     const Tables tb = tables_of(c);
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     // self-pair terms of all windows first (the histogram lives in the partials buffer)
@@ -752,19 +788,29 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
             CK(launch_reduce_rows(dd_part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
         }
     }
-    CK(ensure_host(c, (size_t)2 * nwin + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
-    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin);
+    const int nrr = c->have_randoms ? nb : 0;  // RR of the l = 0 window of every bin
+    if (nrr) {
+        const int zero = 0;
+        CK(enqueue_rr_terms(c, &zero, 1, 0, c->part, c->red + 2 * nwin, st, c->tracer), "random pairs");
+    }
+    CK(ensure_host(c, (size_t)2 * nwin + nrr + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation,
+       "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(2 * nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin + nrr);
     CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
     CK(cudaStreamSynchronize(st), "xi");
     if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
     const double n3 = (double)N * N * N;
     const double n6 = n3 * n3;
     const double eps_bar = c->sum_w / n3;
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
     for (int widx = 0; widx < nwin; ++widx) {
         const double dd = c->host_buf[widx] / n6;
         const double sn = c->host_buf[nwin + widx] / (eps_bar * eps_bar);  // already / N^6
-        out[widx] = dd - sn;
+        // Eq. xi-deltaDD-over-RR: RR = 1 for analytic uniform randoms; xi_l divides by RR_0
+        const double rr = nrr ? c->host_buf[2 * nwin + widx % nb] * rr_scale : 1.0;
+        out[widx] = (dd - sn) / rr;
     }
     return HERMES_OK;
 }
@@ -787,16 +833,26 @@ int hermes_xi_multipoles_kspace(hermes_ctx* c, const int* ells, int n_ells, doub
     const int nb = c->n_bins;
     const size_t nh = (size_t)n_ells * c->Q;
     CK(grow_doubles(c->part, c->part_cap, nh), "histogram");
-    CK(grow_doubles(c->red, c->red_cap, (size_t)n_ells * nb), "reduction buffer");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)n_ells * nb + nb), "reduction buffer");  // + RR per bin
     CK(cudaMemsetAsync(c->part, 0, nh * sizeof(double), st), "clear histogram");
     CK(launch_kspace_hist(c->N, c->spec, tables_of(c), c->p, c->scal, ko, c->part, c->Q, st, c->tracer),
        "k-space histogram");
     CK(launch_kspace_contract(c->rad, c->nbp, c->Q, ko, c->part, c->N, c->red, nb, st, c->tracer), "k-space sums");
-    CK(ensure_host(c, (size_t)n_ells * nb) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)n_ells * nb * sizeof(double), cudaMemcpyDeviceToHost, st),
+    const int nrr = c->have_randoms ? nb : 0;
+    if (nrr) {
+        const int zero = 0;
+        CK(enqueue_rr_terms(c, &zero, 1, 0, c->part, c->red + (size_t)n_ells * nb, st, c->tracer), "random pairs");
+    }
+    CK(ensure_host(c, (size_t)n_ells * nb + nrr) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation,
+       "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(n_ells * nb + nrr) * sizeof(double), cudaMemcpyDeviceToHost,
+                       st),
        "read xi");
     CK(cudaStreamSynchronize(st), "xi (k-space)");
-    for (int i = 0; i < n_ells * nb; ++i) out[i] = c->host_buf[i];
+    const double n3 = (double)c->N * c->N * c->N;
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
+    for (int i = 0; i < n_ells * nb; ++i)
+        out[i] = c->host_buf[i] / (nrr ? c->host_buf[n_ells * nb + i % nb] * rr_scale : 1.0);
     return HERMES_OK;
 }
 
@@ -808,6 +864,9 @@ int hermes_xi(hermes_ctx* c, double* out) {
 int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
+    if (c->have_randoms)
+        return fail(c, HERMES_ERR_STATE, "zeta_l uses analytic uniform randoms: call hermes_clear_randoms and "
+                                         "hermes_assign first");
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
     if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
     if (c->n_bins > 16) return fail(c, HERMES_ERR_ARG, "zeta_l supports at most 16 bins (have %d)", c->n_bins);
@@ -939,7 +998,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -1033,6 +1092,9 @@ extern "C" int hermes_assign_noalloc(hermes_ctx* c, const float* pos, const floa
     if (n < 1) return fail(c, HERMES_ERR_ARG, "empty catalogue (n = %lld): the density contrast is undefined",
                            (long long)n);
     if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    if (c->have_randoms)
+        return fail(c, HERMES_ERR_STATE, "hermes_assign_noalloc builds analytic-random fields only; "
+                                         "use hermes_assign with explicit randoms");
     const int N = c->N, p = c->p;
     const int p3 = p * p * p;
     const size_t need = 2 + (size_t)std::max(2, p3) * kNoallocBlocks;
@@ -1561,6 +1623,7 @@ extern "C" int64_t hermes_device_bytes(const hermes_ctx* c) {
     b += c->stage_cap * 4 * sizeof(float);
     if (c->rad) b += (size_t)c->nbp * (c->l_max + 1) * c->Q * sizeof(float);
     if (c->cyl_perp) b += ((size_t)c->cyl_nbp * c->cyl_Q + (size_t)c->cyl_npar * (N / 2)) * sizeof(float);
+    if (c->rgrid) b += n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2);
     if (c->batch) {
         const BatchState* s = c->batch;
         b += s->pts_cap * 4 * sizeof(float) + (size_t)s->cat_cap * (n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2));
@@ -1699,7 +1762,7 @@ extern "C" int hermes_xi_cylinders(hermes_ctx* c, double* out) {
     CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
     const int zb = inv_z_blocks(N);
     CK(grow_doubles(c->part, c->part_cap, std::max((size_t)S * zb, (size_t)std::min(nz, 8) * c->cyl_Q)), "partials");
-    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)3 * nwin), "reduction buffer");  // dd, sn, RR
     const Tables tb = tables_of(c);
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     std::vector<int> js(nz);
@@ -1721,14 +1784,21 @@ extern "C" int hermes_xi_cylinders(hermes_ctx* c, double* out) {
             CK(launch_reduce_rows(c->part, wb.S, zb, c->red + (size_t)j * np + b0, st, c->tracer),
                "reduce contractions");
         }
-    CK(ensure_host(c, (size_t)2 * nwin + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)2 * nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
-    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin);
+    const int nrr = c->have_randoms ? nwin : 0;
+    if (nrr) CK(enqueue_rr_terms(c, js.data(), nz, 1, c->part, c->red + 2 * nwin, st, c->tracer), "random pairs");
+    CK(ensure_host(c, (size_t)2 * nwin + nrr + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation,
+       "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(2 * nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin + nrr);
     CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
     CK(cudaStreamSynchronize(st), "xi(r_perp, r_par)");
     if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
     const double n3 = (double)N * N * N, n6 = n3 * n3, eb = c->sum_w / n3;
-    for (int w = 0; w < nwin; ++w) out[w] = c->host_buf[w] / n6 - c->host_buf[nwin + w] / (eb * eb);
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
+    for (int w = 0; w < nwin; ++w)
+        out[w] = (c->host_buf[w] / n6 - c->host_buf[nwin + w] / (eb * eb)) /
+                 (nrr ? c->host_buf[2 * nwin + w] * rr_scale : 1.0);
     return HERMES_OK;
 }
 
@@ -1739,14 +1809,99 @@ extern "C" int hermes_xi_cylinders_kspace(hermes_ctx* c, double* out) {
     cudaStream_t st = c->stream;
     const int np = c->cyl_nperp, nz = c->cyl_npar, nwin = np * nz;
     CK(grow_doubles(c->part, c->part_cap, (size_t)std::min(nz, 8) * c->cyl_Q), "histogram");
-    CK(grow_doubles(c->red, c->red_cap, (size_t)nwin), "reduction buffer");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");  // xi numerators, RR
     std::vector<int> js(nz);
     for (int j = 0; j < nz; ++j) js[j] = j;
     CK(enqueue_hist_terms(c, tables_of(c), c->scal, js.data(), nz, 1, 0, c->part, c->red, st, c->tracer),
        "k-space histogram");
-    CK(ensure_host(c, (size_t)nwin) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)nwin * sizeof(double), cudaMemcpyDeviceToHost, st), "read xi");
+    const int nrr = c->have_randoms ? nwin : 0;
+    if (nrr) CK(enqueue_rr_terms(c, js.data(), nz, 1, c->part, c->red + nwin, st, c->tracer), "random pairs");
+    CK(ensure_host(c, (size_t)nwin + nrr) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
     CK(cudaStreamSynchronize(st), "xi(r_perp, r_par) (k-space)");
-    std::memcpy(out, c->host_buf, (size_t)nwin * sizeof(double));
+    const double n3 = (double)c->N * c->N * c->N;
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
+    for (int w = 0; w < nwin; ++w) out[w] = c->host_buf[w] / (nrr ? c->host_buf[nwin + w] * rr_scale : 1.0);
+    return HERMES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit random catalogue (Landy-Szalay in the field language, Sec. 3.3).
+
+extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const float* w, int64_t n, unsigned flags) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!pos) return fail(c, HERMES_ERR_ARG, "pos is NULL");
+    if (n < 1) return fail(c, HERMES_ERR_ARG, "empty random catalogue");
+    if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, p = c->p, p3 = p * p * p;
+    const size_t n3 = (size_t)N * N * N;
+    const float* dpos = pos;
+    const float* dw = w;
+    if (flags & HERMES_DEVICE_PTR) {
+        int r = check_device_ptr(c, pos, "pos");
+        if (r) return r;
+        if (w && (r = check_device_ptr(c, w, "w"))) return r;
+    } else {
+        if ((size_t)n > c->stage_cap) {
+            cudaFree(c->stage_pos);
+            cudaFree(c->stage_w);
+            c->stage_pos = nullptr;
+            c->stage_w = nullptr;
+            c->stage_cap = 0;
+            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
+            c->stage_cap = (size_t)n;
+        }
+        CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
+        if (w) CK(cudaMemcpyAsync(c->stage_w, w, (size_t)n * sizeof(float), cudaMemcpyDefault, st), "copy weights");
+        dpos = c->stage_pos;
+        dw = w ? c->stage_w : nullptr;
+    }
+    if (!c->rgrid) CK(cudaMalloc((void**)&c->rgrid, n3 * sizeof(float)), "random field");
+    if (!c->rspec) CK(cudaMalloc((void**)&c->rspec, (size_t)N * N * (N / 2) * sizeof(float2)), "random spectrum");
+    if (!c->rstab_d) CK(cudaMalloc((void**)&c->rstab_d, 512 * sizeof(double)), "random self-pair table");
+    if (!c->rstab_f) CK(cudaMalloc((void**)&c->rstab_f, 512 * sizeof(float)), "random self-pair table");
+    if (!c->rscal) {
+        CK(cudaMalloc((void**)&c->rscal, 8 * sizeof(double)), "random scalars");
+        const double one[8] = {0, 0, 1, 0, 0, 0, 0, 0};
+        CK(cudaMemcpy(c->rscal, one, sizeof(one), cudaMemcpyHostToDevice), "random scalars");
+    }
+    c->have_field = false;  // the data field must be rebuilt against the new randoms
+    c->have_randoms = false;
+    const int nblk = 592;
+    CK(grow_doubles(c->part, c->part_cap, (size_t)std::max(2, p3) * nblk), "partials");
+    CK(grow_doubles(c->red, c->red_cap, 1024), "reduction buffer");
+    CK(cudaMemsetAsync(c->rgrid, 0, n3 * sizeof(float), st), "clear random field");
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    const float s = (float)((double)N / c->L);
+    CK(launch_scatter(N, p, dpos, dw, n, c->rgrid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st, c->tracer),
+       "scatter randoms");
+    CK(launch_weight_sums(dw, n, c->part, nblk, st, c->tracer), "weight sums");
+    CK(launch_reduce_rows(c->part, 2, nblk, c->red, st, c->tracer), "reduce sums");
+    CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st, c->tracer), "self-pair table");
+    CK(launch_reduce_rows(c->part, p3, nblk, c->rstab_d, st, c->tracer), "reduce self-pair");
+    // float copy of the table (the scalars land in scratch)
+    CK(launch_finish_field(c->red, c->rstab_d, p3, c->rstab_f, N, c->red + 8, st, c->tracer), "random table");
+    CK(launch_delta_to_spec(N, c->rgrid, c->rspec, nullptr, tables_of(c), st, c->tracer, 1), "random spectrum");
+    CK(ensure_host(c, 4) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "read sums");
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "assign randoms");
+    if (herr) return fail(c, HERMES_ERR_RANGE, "a random coordinate is outside [0, L] or a weight is not finite");
+    c->sum_wr = c->host_buf[0];
+    if (!(c->sum_wr > 0.0) || !std::isfinite(c->sum_wr))
+        return fail(c, HERMES_ERR_RANGE, "sum of random weights is %g; it must be positive", c->sum_wr);
+    c->have_randoms = true;
+    return HERMES_OK;
+}
+
+extern "C" int hermes_clear_randoms(hermes_ctx* c) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (c->have_randoms) c->have_field = false;  // the resident field is a difference field
+    c->have_randoms = false;
     return HERMES_OK;
 }

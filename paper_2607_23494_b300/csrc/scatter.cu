@@ -445,6 +445,33 @@ cudaError_t launch_finish_field(const double* sums, const double* stab_d, int p3
     return cudaGetLastError();
 }
 
+// Delta = (eps_D - alpha eps_R) / eps_bar_D in place, 4 cells per thread (n is a
+// multiple of 4: N^3 with N >= 16); block 0 also writes the combined self-pair table.
+__global__ void __launch_bounds__(256) k_combine_randoms(float4* __restrict__ grid, const float4* __restrict__ rgrid,
+                                                         size_t n4, float alpha, float inv_ebar,
+                                                         const double* __restrict__ stab_d,
+                                                         const double* __restrict__ rstab_d, double alpha2,
+                                                         float* __restrict__ stab_f, int p3) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 d = grid[i], r = __ldg(rgrid + i);
+        grid[i] = make_float4(fmaf(-alpha, r.x, d.x) * inv_ebar, fmaf(-alpha, r.y, d.y) * inv_ebar,
+                              fmaf(-alpha, r.z, d.z) * inv_ebar, fmaf(-alpha, r.w, d.w) * inv_ebar);
+    }
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < p3; e += blockDim.x) stab_f[e] = (float)(stab_d[e] + alpha2 * rstab_d[e]);
+}
+
+cudaError_t launch_combine_randoms(float* grid, const float* rgrid, size_t n, float alpha, float inv_ebar,
+                                   const double* stab_d, const double* rstab_d, double alpha2, float* stab_f, int p3,
+                                   cudaStream_t st, const Tracer& tr) {
+    tr(K_COMBINE, 0, st);
+    k_combine_randoms<<<148 * 8, 256, 0, st>>>(reinterpret_cast<float4*>(grid), reinterpret_cast<const float4*>(rgrid),
+                                               n / 4, alpha, inv_ebar, stab_d, rstab_d, alpha2, stab_f, p3);
+    tr(K_COMBINE, 1, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_rows_strided(const double* part, int rows, int cols, int S, double* out, int out_stride,
                                        cudaStream_t st, const Tracer& tr) {
     if (rows <= 0) return cudaSuccess;

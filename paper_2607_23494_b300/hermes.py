@@ -65,6 +65,8 @@ def _load() -> C.CDLL:
         "hermes_set_stream": (i32, [vp, vp]),
         "hermes_assign": (i32, [vp, fp, fp, i64, u32]),
         "hermes_assign_noalloc": (i32, [vp, fp, fp, i64, u32]),
+        "hermes_assign_randoms": (i32, [vp, fp, fp, i64, u32]),
+        "hermes_clear_randoms": (i32, [vp]),
         "hermes_window_shells": (i32, [vp, dp, i32, i32]),
         "hermes_xi": (i32, [vp, dp]),
         "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
@@ -199,6 +201,35 @@ class Context:
                 wp = w.ctypes.data
             rc = _lib.hermes_assign(self._h, pos.ctypes.data if n else None, wp, n, flags)
         self._check(rc, "hermes_assign")
+
+    def _points(self, pos, w):
+        """(pos pointer, w pointer, n, device flag, keep-alive) for numpy arrays or torch tensors."""
+        if hasattr(pos, "data_ptr"):
+            import torch
+            assert pos.dtype == torch.float32 and pos.is_contiguous() and pos.dim() == 2 and pos.shape[1] == 3
+            if w is not None:
+                assert w.dtype == torch.float32 and w.is_contiguous() and w.is_cuda == pos.is_cuda
+            return pos.data_ptr(), (None if w is None else w.data_ptr()), pos.shape[0], \
+                (DEVICE_PTR if pos.is_cuda else 0), (pos, w)
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+        if pos.ndim != 2 or pos.shape[1] != 3:
+            raise ValueError("pos must have shape (n, 3)")
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            if w.shape != (pos.shape[0],):
+                raise ValueError("w must have shape (n,)")
+        return pos.ctypes.data if pos.shape[0] else None, (None if w is None else w.ctypes.data), pos.shape[0], 0, \
+            (pos, w)
+
+    def assign_randoms(self, pos, w=None, wrap: bool = False) -> None:
+        """hermes_assign_randoms: an explicit random catalogue for the Landy-Szalay estimator;
+        call assign() with the data afterwards."""
+        pp, wp, n, flags, _keep = self._points(pos, w)
+        self._check(_lib.hermes_assign_randoms(self._h, pp, wp, n, flags | (WRAP if wrap else 0)),
+                    "hermes_assign_randoms")
+
+    def clear_randoms(self) -> None:
+        self._check(_lib.hermes_clear_randoms(self._h), "hermes_clear_randoms")
 
     def assign_noalloc(self, pos, w=None, wrap: bool = False) -> None:
         """hermes_assign_noalloc: pos / w are CUDA tensors; no device memory is allocated."""

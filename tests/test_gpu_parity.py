@@ -393,3 +393,41 @@ def test_cylinder_planted_mode_and_errors():
             ref = 0.5 * K[n0[0] % N, n0[1] % N, n0[2] % N]
             assert abs(got[j, i] - ref) <= max(2e-5 * abs(ref), 1e-7), (j, i, got[j, i], ref)
             assert abs(gk[j, i] - ref) <= max(2e-5 * abs(ref), 1e-7), (j, i, gk[j, i], ref)
+
+
+@pytest.mark.parametrize("N,p,L", [(32, 4, 100.0), (64, 3, 200.0)])
+def test_explicit_randoms_landy_szalay_matches_oracle(N, p, L):
+    # data: clustered catalogue with masses; randoms: 3x as many weighted uniform points;
+    # xi_l over RR_0 by inverse transforms and by Parseval, xi(r_perp, r_par) over RR
+    H = _hermes()
+    pd = S.lognormal_catalogue(8000, L, seed=N + 21, n_grid=N)
+    wd = S.lognormal_masses(pd.shape[0], seed=N + 22)
+    pr = S.poisson_uniform(24000, L, seed=N + 23)
+    wr = (0.5 + np.random.default_rng(N).random(pr.shape[0])).astype(np.float32)
+    edges = np.linspace(L / 25, L / 4, 8)
+    rperp, rpar = np.linspace(0.0, L / 5, 5), np.linspace(0.0, L / 6, 4)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=2)
+        ctx.window_cylinders(rperp, rpar)
+        ctx.assign_randoms(pr, wr)
+        with pytest.raises(H.HermesError) as ei:  # the data field must be rebuilt
+            ctx.xi_multipoles([0])
+        assert ei.value.code == H.ERR_STATE
+        ctx.assign(pd, wd)
+        got = ctx.xi_multipoles([0, 2])
+        gk = ctx.xi_multipoles_kspace([0, 2])
+        gc = ctx.xi_cylinders()
+        gck = ctx.xi_cylinders(kspace=True)
+        with pytest.raises(H.HermesError) as ei:
+            ctx.zeta_multipoles()
+        assert ei.value.code == H.ERR_STATE
+        ctx.clear_randoms()
+        ctx.assign(pd, wd)
+        plain = ctx.xi_multipoles([0, 2])
+    ref = O.xi_randoms(pd, wd, pr, wr, N, L, p, edges, ells=(0, 2))
+    refc = O.xi_randoms(pd, wd, pr, wr, N, L, p, None, cyl=(rperp, rpar))
+    _close(got, ref)
+    _close(gk, ref)
+    _close(gc, refc)
+    _close(gck, refc)
+    _close(plain, O.xi_multipoles(pd, wd, N, L, p, edges, ells=(0, 2))["xi"])
