@@ -21,6 +21,9 @@ float64, by the plainest route that follows the paper:
   xi via cell contraction       Eq. (pair-counting), Eq. (2rdEs)
   Landy-Szalay with uniform R   Eq. (xi-deltaDD-over-RR)
   zeta_l                        Eq. (2-fold-translation), Eq. (particle_nfold)
+  density-dependent marks       Sec. 3.3: smoothed density read at the particles (the
+                                adjoint of the scatter), Eq. (power-law-mark),
+                                Eq. (inverse-density-mark)
   explicit randoms (LS)         Sec. 3.3 estimator: Delta = D - R, xi = Delta DD / RR,
                                 Eq. (xi-deltaDD-over-RR) with a random field
   anisotropic xi(r_perp, r_par) Sec. 3.4.4 ring window with finite bins; Table A1 rows
@@ -54,7 +57,7 @@ __all__ = [
     "window_zeta", "xi_parseval", "xi_cell_contraction", "self_pair_table",
     "kappa_from_K", "shot_noise", "xi_multipoles", "zeta_multipoles", "lm_modes",
     "keff_pair_direct", "xi_brute_force", "direct_convolution", "annulus_avg_j0", "slab_avg_cos",
-    "window_cyl", "xi_cylinders", "xi_randoms",
+    "window_cyl", "xi_cylinders", "xi_randoms", "smoothing_window", "density_at", "density_marks",
 ]
 
 
@@ -534,6 +537,51 @@ def xi_randoms(pos, w, pos_r, w_r, N, L, p, r_edges, ells=(0,), cyl=None):
             K = K0 if ell == 0 else window_xi(N, L, p, r_edges[b], r_edges[b + 1], ell)
             out[a, b] = ratio(K, K0)
     return out
+
+
+def smoothing_window(N: int, L: float, p: int, kind: str, R: float) -> np.ndarray:
+    """K(n) = W^(k) Phi^(n) on the full grid, Nyquist = 0: Table A1 row (b) sphere
+    3 (sin x - x cos x) / x^3 or row (c) Gaussian exp(-x^2 / 2), x = k R."""
+    nx, ny, nz, q, k, nyq = _mode_grid(N, L)
+    if kind == "sphere":
+        W = _sphere_hat(k * R)
+    elif kind == "gauss":
+        W = np.exp(-0.5 * (k * R) ** 2)
+    else:
+        raise ValueError(kind)
+    ph = phi_hat_1d(N, p)
+    K = W * ph[:, None, None] * ph[None, :, None] * ph[None, None, :]
+    K[nyq] = 0.0
+    return K
+
+
+def density_at(pos_eval, pos, w, N, L, p, kind, R):
+    """1 + delta_W(x) at every evaluation point: the field filtered with K (its coefficients
+    delta~ = iFT(delta^ K)) read back through the same basis, sum_l phi_l(x) delta~_l, plus 1
+    (the mean, K(0) = 1).  Equals sum_j w_j K_eff(x, x_j) / eps_bar."""
+    eps, sw, _ = assign(pos, w, N, L, p)
+    dt = np.fft.ifftn(forward(delta_from_eps(eps, sw)) * smoothing_window(N, L, p, kind, R)).real
+    first, m = node_weights(np.asarray(pos_eval), N, L, p)
+    o = np.arange(p)
+    ix = (first[:, 0, None] + o) % N
+    iy = (first[:, 1, None] + o) % N
+    iz = (first[:, 2, None] + o) % N
+    vals = dt[ix[:, :, None, None], iy[:, None, :, None], iz[:, None, None, :]]
+    wts = m[:, 0, :, None, None] * m[:, 1, None, :, None] * m[:, 2, None, None, :]
+    return 1.0 + np.sum(vals * wts, axis=(1, 2, 3))
+
+
+def density_marks(rho, kind: str, a: float, b: float, self_count: float = 0.0):
+    """Marks from densities rho in units of the mean (density_at).  The self count (one
+    object per window volume, in units of the mean) is removed and the result clipped at
+    0 first.  "power": Eq. (power-law-mark) (rho + b)^a, b the regulariser epsilon;
+    "inverse": Eq. (inverse-density-mark) ((b + 1) / (b + rho))^a, b = rho_* / rho_bar."""
+    r = np.maximum(np.asarray(rho, dtype=np.float64) - self_count, 0.0)
+    if kind == "power":
+        return (r + b) ** a
+    if kind == "inverse":
+        return ((b + 1.0) / (b + r)) ** a
+    raise ValueError(kind)
 
 
 def lm_modes(l_max: int):
