@@ -210,6 +210,31 @@ int hermes_batch_info(hermes_ctx *ctx, int *S, int *C, int64_t *graph_kernels, i
                       double *tune, int tune_cap, int *n_tune);
 
 /*
+ * Density-dependent marks (Sec. 3.3, Eq. power-law-mark, Eq. inverse-density-mark).
+ * The resident field is smoothed with a window (HERMES_SMOOTH_SPHERE: Table A1 row
+ * (b), radius R; HERMES_SMOOTH_GAUSS: row (c), width R), K = W^ Phi^, and read back
+ * at each of the n positions through the same basis as the scatter (its adjoint):
+ *   rho_i = 1 + sum_l phi_l(x_i) delta~_l,  delta~ = iFT(delta^ K),
+ * the smoothed density in units of the mean sum w / L^3 (it equals
+ * sum_j w_j K_eff(x_i, x_j) / eps_bar).  With remove_self, one object per window
+ * volume (4 pi R^3 / 3, or (2 pi)^{3/2} R^3) is subtracted, r = max(rho - self, 0):
+ *   HERMES_MARK_DENSITY   out_i = rho_i
+ *   HERMES_MARK_POWER     out_i = (r + b)^a        (b the regulariser epsilon, a = alpha)
+ *   HERMES_MARK_INVERSE   out_i = ((b + 1) / (b + r))^a  (b = rho_* / rho_bar, a = p).
+ * Pass the marks to hermes_assign as weights for the marked statistics.
+ *   pos: n x 3 float32 (host, or device with HERMES_DEVICE_PTR, like out: n float32).
+ * Errors: HERMES_ERR_ARG, HERMES_ERR_RANGE (bad R or a coordinate outside [0, L]),
+ * HERMES_ERR_STATE (no field, or explicit randoms set), HERMES_ERR_CUDA, HERMES_ERR_NOMEM.
+ */
+#define HERMES_SMOOTH_SPHERE 0
+#define HERMES_SMOOTH_GAUSS 1
+#define HERMES_MARK_DENSITY 0
+#define HERMES_MARK_POWER 1
+#define HERMES_MARK_INVERSE 2
+int hermes_density_marks(hermes_ctx *ctx, int window, double R, int kind, double a, double b, int remove_self,
+                         const float *pos, int64_t n, unsigned flags, float *out);
+
+/*
  * Explicit random catalogue for the Landy-Szalay estimator in the field language
  * (Sec. 3.3, Eq. xi-deltaDD-over-RR): xi[W] = Delta DD[W] / RR[W] with
  * Delta = D - alpha R, alpha = sum w_D / sum w_R, both fields in units of the mean

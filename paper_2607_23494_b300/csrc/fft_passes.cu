@@ -362,6 +362,61 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
 }
 
 // ---------------------------------------------------------------------------
+// c2r along z of one filtered spectrum, written out as a real field (no
+// contraction): out[line*N + 2j] = scale * Re z_j, out[line*N + 2j+1] = scale * Im z_j,
+// with the same split of the half spectrum as I3.  Used to read a smoothed
+// density back at the particles.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_store(const float2* __restrict__ work,
+                                                                      float* __restrict__ out, float scale,
+                                                                      const float2* __restrict__ tw) {
+    using C = Cfg<N>;
+    constexpr int M = C::MZ, T = C::TZ, LP = LinePad<M>::value, H = N / 2;
+    extern __shared__ float2 smem[];
+    const int t = threadIdx.x % T, li = threadIdx.x / T;
+    const size_t line = (size_t)blockIdx.x * C::LZ + li;
+    const SmemLine<M> sm{smem + li * LP};
+    const float2* X = work + line * H;
+    float2 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = t + i * T;
+        const float2 xk = X[k];
+        const float2 xc = cconj(k == 0 ? make_float2(0.f, 0.f) : X[M - k]);
+        const float2 a = cadd(xk, xc);
+        const float2 w = cconj(__ldg(tw + N + k));  // e^{+2 pi i k / N}
+        const float2 c = cmul(w, csub(xk, xc));
+        v[i] = make_float2(a.x - c.y, a.y + c.x);
+    }
+    fft_line<M, true>(v, t, tw, sm);
+    float2* o = reinterpret_cast<float2*>(out + line * N);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[t + i * T] = cscale(v[i], scale);
+}
+
+template <int N>
+static cudaError_t smooth_impl(const float2* spec, float2* work, float* out, const WinBatch& wb, const Tables& tb,
+                               cudaStream_t st, const Tracer& tr) {
+    using C = Cfg<N>;
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_x_window<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_inv_z_c2r_store<N>, C::SMEM_Z)) != cudaSuccess) return e;
+    const long long H = N / 2;
+    tr(K_INV_X_WINDOW, 0, st);
+    k_inv_x_window<N, false><<<dim3(H / C::W, N, 1), C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb);
+    tr(K_INV_X_WINDOW, 1, st);
+    tr(K_INV_Y, 0, st);
+    k_strided<N, true><<<dim3(H / C::W, N, 1), C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, 0, 0, tb.tw);
+    tr(K_INV_Y, 1, st);
+    tr(K_INV_Z_STORE, 0, st);
+    const float scale = 1.0f / ((float)N * (float)N * (float)N);
+    k_inv_z_c2r_store<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(work, out, scale, tb.tw);
+    tr(K_INV_Z_STORE, 1, st);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Fused I2 + I3 on a thread-block cluster.  The (y, k_z) plane of one x and one
 // window (N x N/2 complex, 1 MiB at N = 512) is split over CL CTAs:
 //   y phase : CTA c holds the k_z slab [c*KZ, (c+1)*KZ) for every y and runs the
@@ -615,6 +670,14 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
         case 1024: return CALL(1024);     \
         default: return cudaErrorInvalidValue; \
     }
+
+cudaError_t launch_smooth_field(int N, const float2* spec, float2* work, float* out, const WinBatch& wb,
+                                const Tables& tb, cudaStream_t st, const Tracer& tr) {
+    if (wb.S != 1) return cudaErrorInvalidValue;
+#define F(n) smooth_impl<n>(spec, work, out, wb, tb, st, tr)
+    HERMES_DISPATCH_N(N, F)
+#undef F
+}
 
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb, cudaStream_t st,
                            const Tracer& tr, int ncat) {

@@ -74,6 +74,7 @@ struct hermes_ctx {
     double* rscal = nullptr;
     double sum_wr = 0;
     bool have_randoms = false;
+    float* smooth_tab = nullptr;  // one-bin smoothing table [q*4] (density marks)
     // state
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
@@ -474,6 +475,7 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->rstab_d);
     cudaFree(c->rstab_f);
     cudaFree(c->rscal);
+    cudaFree(c->smooth_tab);
     batch_free(c->batch);
     c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -998,7 +1000,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms", "inv_z_store", "gather_marks"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -1903,5 +1905,93 @@ extern "C" int hermes_clear_randoms(hermes_ctx* c) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (c->have_randoms) c->have_field = false;  // the resident field is a difference field
     c->have_randoms = false;
+    return HERMES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Density-dependent marks (Sec. 3.3): smoothed density read at the particles.
+
+extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kind, double a, double b,
+                                    int remove_self, const float* pos, int64_t n, unsigned flags, float* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!pos || !out || n < 1) return fail(c, HERMES_ERR_ARG, "pos/out NULL or n < 1");
+    if (window != HERMES_SMOOTH_SPHERE && window != HERMES_SMOOTH_GAUSS)
+        return fail(c, HERMES_ERR_ARG, "unknown smoothing window %d", window);
+    if (kind < HERMES_MARK_DENSITY || kind > HERMES_MARK_INVERSE) return fail(c, HERMES_ERR_ARG, "unknown mark %d", kind);
+    if (!(R > 0.0) || !std::isfinite(R) || R > 0.5 * c->L)
+        return fail(c, HERMES_ERR_RANGE, "smoothing radius %g outside (0, L/2]", R);
+    if (!std::isfinite(a) || !std::isfinite(b)) return fail(c, HERMES_ERR_ARG, "mark parameters must be finite");
+    if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->have_randoms)
+        return fail(c, HERMES_ERR_STATE, "the resident field is a difference field (explicit randoms); "
+                                         "call hermes_clear_randoms and hermes_assign first");
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, H = N / 2;
+    const size_t n3 = (size_t)N * N * N;
+    const float* dpos = pos;
+    float* dout = out;
+    if (flags & HERMES_DEVICE_PTR) {
+        int r = check_device_ptr(c, pos, "pos");
+        if (r) return r;
+        if ((r = check_device_ptr(c, out, "out"))) return r;
+    } else {
+        if ((size_t)n > c->stage_cap) {
+            cudaFree(c->stage_pos);
+            cudaFree(c->stage_w);
+            c->stage_pos = nullptr;
+            c->stage_w = nullptr;
+            c->stage_cap = 0;
+            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging marks");
+            c->stage_cap = (size_t)n;
+        }
+        CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
+        dpos = c->stage_pos;
+        dout = c->stage_w;
+    }
+    // one-bin table W^(k_q) for q = |n|^2 (Table A1 rows (b), (c)), float64 on the host
+    const int64_t Q = table_len(N);
+    std::vector<float> tab((size_t)Q * 4, 0.0f);
+    const double kf = 2.0 * M_PI / c->L;
+    for (int64_t q = 0; q < Q; ++q) {
+        const double x = kf * std::sqrt((double)q) * R;
+        double wv;
+        if (window == HERMES_SMOOTH_GAUSS) wv = std::exp(-0.5 * x * x);
+        else if (x < 1e-2) wv = 1.0 - x * x / 10.0 + x * x * x * x / 280.0;
+        else wv = 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
+        tab[(size_t)q * 4] = (float)wv;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(c->smooth_tab);
+    c->smooth_tab = nullptr;
+    CK(cudaMalloc((void**)&c->smooth_tab, tab.size() * sizeof(float)), "smoothing table");
+    CK(cudaMemcpy(c->smooth_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice), "upload table");
+    // work: one half spectrum, then the real smoothed field (N^3 floats) behind it
+    const size_t spec_bytes = (size_t)N * N * H * sizeof(float2);
+    CK(grow(c->work, c->work_bytes, spec_bytes + n3 * sizeof(float)), "work buffer");
+    float* field = reinterpret_cast<float*>(reinterpret_cast<char*>(c->work) + spec_bytes);
+    WinBatch wb;
+    wb.tab = c->smooth_tab;
+    wb.nbp = 4;
+    wb.S = 1;
+    wb.ell = 0;
+    wb.scale = 1.0f;
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    CK(launch_smooth_field(N, c->spec, c->work, field, wb, tables_of(c), st, c->tracer), "smoothing");
+    // one object per window volume, in units of the mean density sum w / L^3
+    const double vol = window == HERMES_SMOOTH_GAUSS ? std::pow(2.0 * M_PI, 1.5) * R * R * R : 4.0 * M_PI * R * R * R / 3.0;
+    const double self = remove_self ? c->L * c->L * c->L / (vol * c->sum_w) : 0.0;
+    const float s = (float)((double)N / c->L);
+    CK(launch_gather_marks(N, c->p, dpos, n, field, s, (flags & HERMES_WRAP) ? 1 : 0, kind, (float)a, (float)b,
+                           (float)self, dout, c->err, st, c->tracer),
+       "gather");
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    if (!(flags & HERMES_DEVICE_PTR))
+        CK(cudaMemcpyAsync(out, dout, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st), "read marks");
+    CK(cudaStreamSynchronize(st), "density marks");
+    if (herr) return fail(c, HERMES_ERR_RANGE, "a coordinate is outside [0, L]; use HERMES_WRAP to wrap");
     return HERMES_OK;
 }

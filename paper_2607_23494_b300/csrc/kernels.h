@@ -16,7 +16,7 @@ constexpr int STAB_STRIDE = 512;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_INV_Z_STORE, K_GATHER, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -114,10 +114,20 @@ int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used
 cudaError_t launch_inverse_xi(int N, const float2* spec, float2* work, const float* delta, const WinBatch& wb,
                               const Tables& tb, double* dd_part, unsigned* err, cudaStream_t st, const Tracer& tr,
                               int ncat = 1);
+// delta~ = iFT(spec * K) / N^3 written to out (N^3 floats) for one window (wb.S = 1);
+// work holds one half spectrum
+cudaError_t launch_smooth_field(int N, const float2* spec, float2* work, float* out, const WinBatch& wb,
+                                const Tables& tb, cudaStream_t st, const Tracer& tr);
 // forward transform of a field as it is (no eps -> delta conversion); keep_dc = 1
 // keeps the k = 0 mode (otherwise it is set to 0)
 cudaError_t launch_delta_to_spec(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                                  cudaStream_t st, const Tracer& tr, int keep_dc = 0);
+// Smoothed density at points: rho_i = 1 + sum_l phi_l(x_i) field_l (the scatter's node
+// rule and weights), then the mark: kind 0 rho; 1 (max(rho - self, 0) + b)^a;
+// 2 ((b + 1) / (b + max(rho - self, 0)))^a.  err bit 1 marks a rejected coordinate.
+cudaError_t launch_gather_marks(int N, int p, const float* pos, int64_t n, const float* field, float s, int wrap,
+                                int kind, float a, float b, float self, float* out, unsigned* err, cudaStream_t st,
+                                const Tracer& tr);
 // Landy-Szalay difference field: grid <- (grid - alpha * rgrid) * inv_ebar (n cells), and the
 // combined float self-pair table stab_f[e] = stab_d[e] + alpha^2 rstab_d[e] (p3 entries)
 cudaError_t launch_combine_randoms(float* grid, const float* rgrid, size_t n, float alpha, float inv_ebar,

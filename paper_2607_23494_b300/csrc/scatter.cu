@@ -156,6 +156,45 @@ __global__ void __launch_bounds__(256) k_scatter_batch(const float* __restrict__
     }
 }
 
+// Adjoint of the scatter: read a field at the points through the same basis, then
+// apply the density mark (see launch_gather_marks).
+template <int P>
+__global__ void __launch_bounds__(256) k_gather_marks(const float* __restrict__ pos, int64_t n,
+                                                      const float* __restrict__ field, float s, int N, int wrap,
+                                                      int kind, float ma, float mb, float self,
+                                                      float* __restrict__ out, unsigned* __restrict__ err) {
+    const int msk = N - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float bx[P], by[P], bz[P];
+        int fx, fy, fz;
+        const bool ok = node_rule<P>(__ldg(pos + 3 * i), s, N, wrap, fx, bx) &
+                        node_rule<P>(__ldg(pos + 3 * i + 1), s, N, wrap, fy, by) &
+                        node_rule<P>(__ldg(pos + 3 * i + 2), s, N, wrap, fz, bz);
+        if (!ok) {
+            atomicOr(err, 1u);
+            out[i] = 0.0f;
+            continue;
+        }
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const int ix = (fx + a) & msk;
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const float* row = field + ((size_t)ix * N + ((fy + b) & msk)) * N;
+                float r = 0.0f;
+#pragma unroll
+                for (int c = 0; c < P; ++c) r = fmaf(bz[c], __ldg(row + ((fz + c) & msk)), r);
+                acc = fmaf(bx[a] * by[b], r, acc);
+            }
+        }
+        const float rho = 1.0f + acc;
+        const float r = fmaxf(rho - self, 0.0f);
+        out[i] = kind == 0 ? rho : (kind == 1 ? powf(r + mb, ma) : powf((mb + 1.0f) / (mb + r), ma));
+    }
+}
+
 // Node rule of every point, for inspection: first node (mod N) and the p basis
 // values per axis; err bit 1 marks a rejected coordinate.
 template <int P>
@@ -495,6 +534,23 @@ cudaError_t launch_xi_batch_finish(const double* dd, const double* sn, const dou
     tr(K_FINISH, 0, st);
     k_xi_batch_finish<<<(n + 255) / 256, 256, 0, st>>>(dd, sn, scal, ncat, nwin, N, out);
     tr(K_FINISH, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_marks(int N, int p, const float* pos, int64_t n, const float* field, float s, int wrap,
+                                int kind, float a, float b, float self, float* out, unsigned* err, cudaStream_t st,
+                                const Tracer& tr) {
+    if (n == 0) return cudaSuccess;
+    const int nb = nblocks_for(n, 256, 148 * 16);
+    tr(K_GATHER, 0, st);
+    switch (p) {
+#define HERMES_GM(P) \
+    case P: k_gather_marks<P><<<nb, 256, 0, st>>>(pos, n, field, s, N, wrap, kind, a, b, self, out, err); break;
+        HERMES_GM(1) HERMES_GM(2) HERMES_GM(3) HERMES_GM(4) HERMES_GM(5) HERMES_GM(6) HERMES_GM(7) HERMES_GM(8)
+#undef HERMES_GM
+        default: return cudaErrorInvalidValue;
+    }
+    tr(K_GATHER, 1, st);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ ERR_STATE = -6
 DEVICE_PTR = 1
 WRAP = 2
 EAGER = 4
+SMOOTH_SPHERE, SMOOTH_GAUSS = 0, 1
+MARK_DENSITY, MARK_POWER, MARK_INVERSE = 0, 1, 2
 
 _NAMES = {ERR_ARG: "HERMES_ERR_ARG", ERR_RANGE: "HERMES_ERR_RANGE", ERR_NOMEM: "HERMES_ERR_NOMEM",
           ERR_CUDA: "HERMES_ERR_CUDA", ERR_TIMEOUT: "HERMES_ERR_TIMEOUT", ERR_STATE: "HERMES_ERR_STATE"}
@@ -67,6 +69,7 @@ def _load() -> C.CDLL:
         "hermes_assign_noalloc": (i32, [vp, fp, fp, i64, u32]),
         "hermes_assign_randoms": (i32, [vp, fp, fp, i64, u32]),
         "hermes_clear_randoms": (i32, [vp]),
+        "hermes_density_marks": (i32, [vp, i32, C.c_double, i32, C.c_double, C.c_double, i32, fp, i64, u32, fp]),
         "hermes_window_shells": (i32, [vp, dp, i32, i32]),
         "hermes_xi": (i32, [vp, dp]),
         "hermes_xi_multipoles": (i32, [vp, C.POINTER(i32), i32, dp]),
@@ -227,6 +230,24 @@ class Context:
         pp, wp, n, flags, _keep = self._points(pos, w)
         self._check(_lib.hermes_assign_randoms(self._h, pp, wp, n, flags | (WRAP if wrap else 0)),
                     "hermes_assign_randoms")
+
+    def density_marks(self, pos, window: str = "sphere", R: float = 8.0, kind: str = "density", a: float = 1.0,
+                      b: float = 0.0, remove_self: bool = False, wrap: bool = False):
+        """hermes_density_marks: smoothed density (kind "density") or the "power" / "inverse" mark at
+        every position; numpy in, numpy out (CUDA tensor in, CUDA tensor out)."""
+        win = {"sphere": SMOOTH_SPHERE, "gauss": SMOOTH_GAUSS}[window]
+        kd = {"density": MARK_DENSITY, "power": MARK_POWER, "inverse": MARK_INVERSE}[kind]
+        pp, _, n, flags, keep = self._points(pos, None)
+        if flags & DEVICE_PTR:
+            import torch
+            out = torch.empty(n, dtype=torch.float32, device=pos.device)
+            op = out.data_ptr()
+        else:
+            out = np.empty(n, dtype=np.float32)
+            op = out.ctypes.data
+        self._check(_lib.hermes_density_marks(self._h, win, float(R), kd, float(a), float(b), int(remove_self), pp, n,
+                                              flags | (WRAP if wrap else 0), op), "hermes_density_marks")
+        return out
 
     def clear_randoms(self) -> None:
         self._check(_lib.hermes_clear_randoms(self._h), "hermes_clear_randoms")

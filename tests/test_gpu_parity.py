@@ -431,3 +431,35 @@ def test_explicit_randoms_landy_szalay_matches_oracle(N, p, L):
     _close(gc, refc)
     _close(gck, refc)
     _close(plain, O.xi_multipoles(pd, wd, N, L, p, edges, ells=(0, 2))["xi"])
+
+
+def test_density_marks_match_oracle_and_feed_the_marked_xi():
+    import torch
+    H = _hermes()
+    L, N, p = 120.0, 64, 4
+    pos = S.lognormal_catalogue(20000, L, seed=61, n_grid=64)
+    n = pos.shape[0]
+    edges = np.linspace(3.0, 40.0, 8)
+    with H.Context(L, N, p) as ctx:
+        ctx.assign(pos)
+        rho = ctx.density_marks(pos, "sphere", 8.0, "density")
+        mpl = ctx.density_marks(pos, "sphere", 8.0, "power", a=0.5, b=0.1, remove_self=True)
+        minv = ctx.density_marks(pos, "gauss", 5.0, "inverse", a=1.0, b=1.0)
+        dev = ctx.density_marks(torch.from_numpy(pos).cuda(), "sphere", 8.0, "power", a=0.5, b=0.1,
+                                remove_self=True)
+        with pytest.raises(H.HermesError) as ei:
+            ctx.density_marks(pos, "sphere", 0.7 * L, "density")
+        assert ei.value.code == H.ERR_RANGE
+        ctx.window_shells(edges, l_max=2)
+        ctx.assign(pos, mpl)
+        xi_m = ctx.xi_multipoles([0, 2])
+    ref_rho = O.density_at(pos, pos, None, N, L, p, "sphere", 8.0)
+    ref_g = O.density_at(pos, pos, None, N, L, p, "gauss", 5.0)
+    self_count = L ** 3 / (4.0 * np.pi * 8.0 ** 3 / 3.0 * n)
+    tol = 2e-5 * max(1.0, np.abs(ref_rho).max())
+    np.testing.assert_allclose(rho, ref_rho, rtol=0, atol=tol)
+    np.testing.assert_allclose(mpl, O.density_marks(ref_rho, "power", 0.5, 0.1, self_count), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(minv, O.density_marks(ref_g, "inverse", 1.0, 1.0), rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(dev.cpu().numpy(), mpl, rtol=0, atol=1e-6)
+    # the marks are the weights of the marked field: same xi_l as the oracle given those marks
+    _close(xi_m, O.xi_multipoles(pos, mpl.astype(np.float64), N, L, p, edges, ells=(0, 2))["xi"])
