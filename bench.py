@@ -108,6 +108,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_seeds(rank: int) -> dict:
+    """Seeds of each replica's independent catalogues (one set per rank)."""
+    return {"xi": 1234 + 17 * rank, "batch": 777 + 17 * rank, "serve": 4242 + 17 * rank, "zeta": 4321 + 17 * rank}
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time: all_reduce(MAX) over the process group (nccl on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(cells: float, windows_per_step: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas: every rank's cell-windows over the slowest rank's time."""
+    return world * cells * windows_per_step * steps / (ms_max / 1e3)
+
+
 def gen_catalogue(seed: int):
     from synthetic import catalogues as S
     pos = S.lognormal_catalogue(NPTS2, L2, seed=seed, n_grid=512)
@@ -168,7 +188,7 @@ def run_hermes(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
 
-    pos, mass = gen_catalogue(1234 + 17 * rank)
+    pos, mass = gen_catalogue(rank_seeds(rank)["xi"])
     n = pos.shape[0]
     pos_d = torch.from_numpy(pos).to(dev)
     mass_d = torch.from_numpy(mass).to(dev)
@@ -210,13 +230,10 @@ def run_hermes(args, rank, world, local_rank):
     trace = ctx.trace_read()
     ctx.trace(False)
     clk = clocks.stop()
-    ms_t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(dev_ms, world, dev)
     ms_per_step = ms_max / args.steps
     cells = float(N2) ** 3
-    value = world * cells * windows_per_step * args.steps / (ms_max / 1e3)
+    value = replica_value(cells, windows_per_step, args.steps, ms_max, world)
 
     # end to end through host buffers (pinned), host->device copies inside the timed region
     pos_h = torch.from_numpy(pos).pin_memory().numpy()
@@ -232,11 +249,8 @@ def run_hermes(args, rank, world, local_rank):
     e1.record(stream)
     stream.synchronize()
     barrier()
-    e2e_t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
-    e2e_value = world * cells * windows_per_step * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e_value = replica_value(cells, windows_per_step, args.steps, e2e_ms, world)
     h2d = 12 * n + (12 * n + 4 * n)
     d2h = 2 * 20 + 2 * 16 * (len(ELLS2) * nb)
 
@@ -500,7 +514,7 @@ def run_batch(args, dev, stream, rank):
     plan), the same library one catalogue at a time, and the plain FP32 pipeline."""
     import torch
     from paper_2607_23494_b300 import Context
-    pos, offs = gen_batch(777 + 17 * rank)
+    pos, offs = gen_batch(rank_seeds(rank)["batch"])
     pos_d = torch.from_numpy(pos).to(dev)
     ncat, nb = len(offs) - 1, len(EDGES4) - 1
     cw = float(N4) ** 3 * nb * ncat  # cell-window evaluations per batch
@@ -622,7 +636,7 @@ def run_serve(args, dev, rank):
     library one request at a time); p50/p99 latency and throughput of both."""
     import torch
     from paper_2607_23494_b300 import hermes as H
-    pool = gen_serve_pool(4242 + 17 * rank)
+    pool = gen_serve_pool(rank_seeds(rank)["serve"])
     pool_d = [torch.from_numpy(c).to(dev) for c in pool]
     budget = 200 << 30
     # capacity of the one-at-a-time server on a calibration trace (back to back)
@@ -648,7 +662,7 @@ def run_serve(args, dev, rank):
 def run_zeta(args, dev, stream, rank):
     import torch
     from paper_2607_23494_b300 import Context
-    pos = gen_catalogue3(4321 + 17 * rank)
+    pos = gen_catalogue3(rank_seeds(rank)["zeta"])
     pos_d = torch.from_numpy(pos).to(dev)
     ctx = Context(L3, N3, 4)
     ctx.set_stream(stream)

@@ -24,6 +24,7 @@
 #include "async_copy.cuh"
 
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <cstdlib>
 
 namespace hermes {
@@ -131,6 +132,59 @@ __global__ void __launch_bounds__(Cfg<N>::TS) k_strided(float2* __restrict__ dat
     if (zero_dc && blockIdx.x == 0 && blockIdx.y == 0 && col == 0 && t == 0) v[0] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < 8; ++i) base[(size_t)(t + i * T) * pos_stride] = v[i];
+}
+
+// Persistent form of k_strided for long batches (the inverse y pass over S
+// windows of C catalogues): each CTA walks tiles tile0, tile0 + gridDim.x, ...
+// (tile = (column chunk, y, z) with the chunk fastest, as the plain grid) and
+// issues the loads of its next tile before the current tile's FFT, so they are
+// in flight across the shared-memory exchanges.  Tile coordinates advance by
+// carries; no division in the loop.
+template <int N, bool INV>
+__global__ void __launch_bounds__(Cfg<N>::TS, 2) k_strided_pf(float2* __restrict__ data, int pos_stride,
+                                                             int ystride, long long zstride, int nxt, int nyt,
+                                                             int ntiles, const float2* __restrict__ tw) {
+    constexpr int W = Cfg<N>::W, T = N / 8;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    int bx = tile % nxt, by = (tile / nxt) % nyt, bz = tile / nxt / nyt;
+    const int dx = gridDim.x % nxt, dy = (gridDim.x / nxt) % nyt, dz = gridDim.x / nxt / nyt;
+    auto base_of = [&](int x, int y, int z) {
+        return data + (size_t)z * zstride + (size_t)y * ystride + x * W + col;
+    };
+    float2 v[8], vn[8];
+    {
+        const float2* b = base_of(bx, by, bz);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = b[(t + i * T) * pos_stride];
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        int nx_ = bx + dx, ny_ = by + dy, nz_ = bz + dz;
+        if (nx_ >= nxt) {
+            nx_ -= nxt;
+            ++ny_;
+        }
+        if (ny_ >= nyt) {
+            ny_ -= nyt;
+            ++nz_;
+        }
+        if (tile + (int)gridDim.x < ntiles) {
+            const float2* b = base_of(nx_, ny_, nz_);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) vn[i] = b[(t + i * T) * pos_stride];
+        }
+        fft_line<N, INV>(v, t, tw, SmemStrided<W>{smem, col});
+        float2* b = base_of(bx, by, bz);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[(t + i * T) * pos_stride] = v[i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = vn[i];
+        bx = nx_;
+        by = ny_;
+        bz = nz_;
+    }
 }
 
 // Legendre polynomial L_l(mu) by the three-term recurrence.
@@ -648,9 +702,21 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
             return e != cudaSuccess ? e : cudaGetLastError();
         }
     }
-    dim3 g2(H / C::W, N, wb.S * ncat);  // windows of all catalogues are consecutive in work
+    // windows of all catalogues are consecutive in work: tiles (column chunk, x, window)
+    const int nxt = (int)(H / C::W);
+    const long long ntiles = (long long)nxt * N * wb.S * ncat;
     tr(K_INV_Y, 0, st);
-    k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tb.tw);
+    if constexpr (N <= 512) {  // two 512-thread blocks per SM at 64 registers; 1024^3 keeps the plain pass
+        if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if ((e = allow_smem(k_strided_pf<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+        const int nblk = (int)std::min<long long>(ntiles, 2LL * 148);
+        k_strided_pf<N, true><<<nblk, C::TS, C::SMEM_STRIDED, st>>>(work, (int)H, (int)(N * H), (long long)N * N * H,
+                                                                    nxt, N, (int)ntiles, tb.tw);
+    } else {
+        dim3 g2(nxt, N, wb.S * ncat);
+        k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0,
+                                                               tb.tw);
+    }
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
     k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw,
