@@ -81,17 +81,41 @@ __device__ __forceinline__ float2 ylm_unnorm(int ell, int m, int nx, int ny, int
 }
 
 // Z1 ------------------------------------------------------------------------
-template <int N>
+// Shared radial-table row stride: bins rounded up to 4, plus 4 when that is a
+// multiple of 8 (bank skew for the 16-byte reads of a warp).
+__host__ __device__ constexpr int zstab_row_stride(int S) {
+    return ((S + 3) & ~3) + ((((S + 3) >> 2) & 1) ? 0 : 4);
+}
+
+// STAB: the radial factors of the block's columns are first copied into shared
+// memory (rows (|n_x|, column), 16-byte asynchronous copies; layout and bank
+// skew as the window pass I1), otherwise each element gathers them from the table.
+template <int N, bool STAB>
 __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restrict__ spec, float2* __restrict__ fields,
                                                          const HarmBatch hb, const Tables tb) {
     using C = ZCfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
+    float* ttab = reinterpret_cast<float*>(smem + SmemStrided<W>::words(N));  // [a][col][RS] (STAB)
+    const int RS = zstab_row_stride(hb.S);
     const int col = threadIdx.x % W, t = threadIdx.x / W;
     const int ky = blockIdx.y, kz = blockIdx.x * W + col;
     const int ny = signed_freq(ky, N), nz = signed_freq(kz, N);
     const size_t xs = (size_t)N * H;
     const size_t n3 = (size_t)N * N * N;
+    if constexpr (STAB) {
+        const int S4 = (hb.S + 3) >> 2;
+        const int total = H * W * S4;
+        for (int e = threadIdx.x; e < total; e += C::TS) {
+            const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
+            const int kzc = blockIdx.x * W + c, nzc = signed_freq(kzc, N);
+            // Nyquist rows and columns carry K = 0: read row 0, which is always in range
+            const int qq = (ky == H || kzc == H) ? 0 : a * a + ny * ny + nzc * nzc;
+            ac::cp_async16(ttab + (a * W + c) * RS + 4 * s4,
+                           reinterpret_cast<const float4*>(hb.tab + (size_t)qq * hb.nbp) + s4);
+        }
+        ac::cp_async_commit();
+    }
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
     float2 v0[8];
     int q[8];
@@ -109,16 +133,23 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
         }
         const bool nyq = (kx == H) || (ky == H) || (kz == H);
         const int qq = nx * nx + ny * ny + nz * nz;
-        q[i] = nyq ? 0 : qq;  // table index stays in range on Nyquist lanes
+        const int ax = (kx < H) ? kx : (kx == H ? 0 : N - kx);  // |n_x|; the Nyquist lane reads row 0
+        q[i] = STAB ? (ax * W + col) * RS : (nyq ? 0 : qq);    // table index stays in range on Nyquist lanes
         const float2 y = ylm_unnorm(hb.ell, hb.m, nx, ny, nz, qq);
         const float2 ang = mul_ipow(cscale(y, hb.ylm_norm * __ldg(tb.phi + kx) * phyz), hb.ell);
         v0[i] = nyq ? make_float2(0.f, 0.f) : cmul(d, ang);
+    }
+    if constexpr (STAB) {
+        ac::cp_async_wait_all();
+        __syncthreads();
     }
     const int nbp = hb.nbp;
     for (int g = 0; g < hb.S; g += 4) {
         float4 tv[8];  // radial factors of bins g..g+3: one 16-byte load per element
 #pragma unroll
-        for (int i = 0; i < 8; ++i) tv[i] = __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
+        for (int i = 0; i < 8; ++i)
+            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + q[i] + g)
+                         : __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int b = g + j;
@@ -563,11 +594,15 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
                              const Tables& tb, double* gram_part, unsigned* err, cudaStream_t st, const Tracer& tr) {
     using C = ZCfg<N>;
     cudaError_t e;
-    if ((e = allow_smem_z(k_zeta_x<N>, C::SMEM_X)) != cudaSuccess) return e;
+    const size_t stab_bytes = C::SMEM_X + (size_t)(N / 2) * C::W * zstab_row_stride(hb.S) * sizeof(float);
+    const bool use_stab = stab_bytes <= 220 * 1024;
+    if ((e = allow_smem_z(k_zeta_x<N, false>, C::SMEM_X)) != cudaSuccess) return e;
+    if (use_stab && (e = allow_smem_z(k_zeta_x<N, true>, stab_bytes)) != cudaSuccess) return e;
     if ((e = allow_smem_z(k_zeta_y<N>, C::SMEM_X)) != cudaSuccess) return e;
     dim3 g1(N / C::W, N, 1);
     tr(K_ZETA_X, 0, st);
-    k_zeta_x<N><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hb, tb);
+    if (use_stab) k_zeta_x<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, fields, hb, tb);
+    else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hb, tb);
     tr(K_ZETA_X, 1, st);
     dim3 g2(N / C::W, N, hb.S);
     tr(K_ZETA_Y, 0, st);
