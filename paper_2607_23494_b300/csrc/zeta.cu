@@ -184,9 +184,11 @@ __global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_y(float2* __restrict__ fie
 }
 
 // Z3 ------------------------------------------------------------------------
+// The 10 tiles (ti, tj), ti <= tj, of a symmetric 16x16 Gram in 4x4 tiles (tile = 4 ti + tj).
+__constant__ int kGramTiles[10] = {0, 1, 2, 3, 5, 6, 7, 10, 11, 15};
 // Persistent over (x, y) lines.  Per line: GB bin lines per round are inverse
-// transformed along z (T threads each) into shared memory; then 16 tiles of
-// 4x4 bins x NZS z-slices accumulate the Gram, float32 per line, flushed to
+// transformed along z (T threads each) into shared memory; then the 10 upper
+// 4x4 bin tiles x 3 z-slices per warp accumulate the Gram, float32 per line, flushed to
 // float64 registers every 8 lines.  Partial Gram per block: part[(b1*16+b2)*nblk + blk].
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __restrict__ fields, int S,
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
                                                               double* __restrict__ part,
                                                               unsigned* __restrict__ err) {
     using C = ZCfg<N>;
-    constexpr int T = C::T, GB = C::GB, LPZ = C::LPZ, ZPER = C::ZPER;
+    constexpr int T = C::T, GB = C::GB, LPZ = C::LPZ;
     constexpr bool PREF = C::PREFETCH;
     extern __shared__ __align__(16) float2 smem[];
     __shared__ double tot[256];
@@ -206,9 +208,15 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     const size_t n3 = (size_t)N * N * N;
     const int tid = threadIdx.x;
     const int bb = tid / T, t = tid % T;
-    const int tile = tid & 15, zs = tid >> 4;
+    // Gram phase: lane l < 30 of warp w owns 4x4 tile kActive[l % 10] (one of the 10 tiles with
+    // ti <= tj of the symmetric 16x16 Gram) and z-slice s = 3w + l / 10, z = s, s + NS, ...
+    // (lanes 30, 31 idle).  The 12 addresses a warp reads per z fall on distinct bank pairs.
+    const int lane_g = tid & 31, sub = lane_g / 10;
+    const bool active = lane_g < 30;
+    const int tile = active ? kGramTiles[lane_g % 10] : 0;
     const int ti = tile >> 2, tj = tile & 3;
-    const bool active = ti <= tj;
+    const int NS = (int)(blockDim.x >> 5) * 3;
+    const int zs = (tid >> 5) * 3 + sub;
     float acc[4][4];
     double acc64[4][4];
 #pragma unroll
@@ -272,8 +280,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
             }
         }
         if (active) {
-            const int z0 = zs * ZPER;
-            for (int z = z0; z < z0 + ZPER; ++z) {
+            for (int z = zs; z < N; z += NS) {
                 const float d = dsm[z];
                 const int zp = SmemLine<N>::at(z);
                 float2 a1[4], a2[4];
@@ -306,16 +313,20 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc64[a][b] += (double)acc[a][b];
-    // lanes l and l^16 hold the same tile: merge, then warps add in turn
+    // lanes l, l + 10, l + 20 hold the same tile: merge onto lane l, then warps add in turn
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc64[a][b] += __shfl_xor_sync(0xffffffffu, acc64[a][b], 16);
+        for (int b = 0; b < 4; ++b) {
+            const double v10 = __shfl_down_sync(0xffffffffu, acc64[a][b], 10);
+            const double v20 = __shfl_down_sync(0xffffffffu, acc64[a][b], 20);
+            acc64[a][b] += v10 + v20;
+        }
     for (int e = tid; e < 256; e += blockDim.x) tot[e] = 0.0;
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int w = 0; w < nw; ++w) {
-        if (wid == w && lane < 16 && active) {
+        if (wid == w && lane < 10) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
