@@ -75,6 +75,14 @@ struct hermes_ctx {
     double sum_wr = 0;
     bool have_randoms = false;
     float* smooth_tab = nullptr;  // one-bin smoothing table [q*4] (density marks)
+    // tiled scatter scratch: per-point tile and permutation, per-tile counts / offsets /
+    // cursors, and the per-tile deposit regions
+    int* ts_tile_of = nullptr;
+    int* ts_perm = nullptr;
+    size_t ts_pts_cap = 0;
+    int* ts_tiles = nullptr;      // [counts | offs (+1) | cursor]
+    float* ts_regions = nullptr;
+    size_t ts_regions_cap = 0;    // floats
     // state
     bool have_field = false;
     double sum_w = 0, sum_w2 = 0;
@@ -372,6 +380,47 @@ int ensure_host(hermes_ctx* c, size_t n) {
     return HERMES_OK;
 }
 
+// Grows the tiled-scatter scratch for n points (tile tables and regions are sized once).
+cudaError_t tiled_scratch(hermes_ctx* c, int64_t n) {
+    cudaError_t e;
+    if ((size_t)n > c->ts_pts_cap) {
+        cudaFree(c->ts_tile_of);
+        cudaFree(c->ts_perm);
+        c->ts_tile_of = nullptr;
+        c->ts_perm = nullptr;
+        c->ts_pts_cap = 0;
+        if ((e = cudaMalloc((void**)&c->ts_tile_of, (size_t)n * sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void**)&c->ts_perm, (size_t)n * sizeof(int))) != cudaSuccess) return e;
+        c->ts_pts_cap = (size_t)n;
+    }
+    if (!c->ts_tiles) {
+        const size_t nt = (size_t)scatter_tiled_tiles(c->N);
+        if ((e = cudaMalloc((void**)&c->ts_tiles, (3 * nt + 1) * sizeof(int))) != cudaSuccess) return e;
+    }
+    const size_t rf = scatter_tiled_region_floats(c->N, c->p);
+    if (rf > c->ts_regions_cap) {
+        cudaFree(c->ts_regions);
+        c->ts_regions = nullptr;
+        c->ts_regions_cap = 0;
+        if ((e = cudaMalloc((void**)&c->ts_regions, rf * sizeof(float))) != cudaSuccess) return e;
+        c->ts_regions_cap = rf;
+    }
+    return cudaSuccess;
+}
+
+// The shared-memory scatter of n points into dst (an N^3 grid; no clearing needed).
+cudaError_t scatter_tiled(hermes_ctx* c, const float* pos, const float* w, int64_t n, float* dst, float s, int wrap,
+                          cudaStream_t st) {
+    cudaError_t e = tiled_scratch(c, n);
+    if (e != cudaSuccess) return e;
+    const size_t nt = (size_t)scatter_tiled_tiles(c->N);
+    int* counts = c->ts_tiles;
+    int* offs = counts + nt;
+    int* cursor = offs + nt + 1;
+    return launch_scatter_tiled(c->N, c->p, pos, w, n, dst, s, wrap, c->err, c->ts_tile_of, c->ts_perm, counts, offs,
+                                cursor, c->ts_regions, st, c->tracer);
+}
+
 int check_ctx(hermes_ctx* c) {
     if (!c) return HERMES_ERR_ARG;
     c->msg.clear();
@@ -476,6 +525,10 @@ int hermes_destroy(hermes_ctx* c) {
     cudaFree(c->rstab_f);
     cudaFree(c->rscal);
     cudaFree(c->smooth_tab);
+    cudaFree(c->ts_tile_of);
+    cudaFree(c->ts_perm);
+    cudaFree(c->ts_tiles);
+    cudaFree(c->ts_regions);
     batch_free(c->batch);
     c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -549,10 +602,9 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
     const int nblk = 592;
     CK(grow_doubles(c->part, c->part_cap, (size_t)std::max(2, p3) * nblk), "partials");
     CK(grow_doubles(c->red, c->red_cap, 1024), "reduction buffer");
-    CK(cudaMemsetAsync(c->grid, 0, n3 * sizeof(float), st), "clear grid");
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     const float s = (float)((double)N / c->L);
-    CK(launch_scatter(N, p, dpos, dw, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st, c->tracer), "scatter");
+    CK(scatter_tiled(c, dpos, dw, n, c->grid, s, (flags & HERMES_WRAP) ? 1 : 0, st), "scatter");
     CK(launch_weight_sums(dw, n, c->part, nblk, st, c->tracer), "weight sums");
     CK(launch_reduce_rows(c->part, 2, nblk, c->red, st, c->tracer), "reduce sums");
     CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st, c->tracer), "self-pair table");
@@ -1623,6 +1675,8 @@ extern "C" int64_t hermes_device_bytes(const hermes_ctx* c) {
     b += TW_ENTRIES * sizeof(float2) + N * sizeof(float) + 8 * sizeof(double) + 512 * (sizeof(double) + sizeof(float));
     b += c->work_bytes + c->zfields_bytes + (c->part_cap + c->red_cap) * sizeof(double);
     b += c->stage_cap * 4 * sizeof(float);
+    b += c->ts_pts_cap * 2 * sizeof(int) + c->ts_regions_cap * sizeof(float);
+    if (c->ts_tiles) b += (3 * (size_t)scatter_tiled_tiles(c->N) + 1) * sizeof(int);
     if (c->rad) b += (size_t)c->nbp * (c->l_max + 1) * c->Q * sizeof(float);
     if (c->cyl_perp) b += ((size_t)c->cyl_nbp * c->cyl_Q + (size_t)c->cyl_npar * (N / 2)) * sizeof(float);
     if (c->rgrid) b += n3 * sizeof(float) + N * N * (N / 2) * sizeof(float2);
@@ -1642,6 +1696,9 @@ extern "C" int64_t hermes_estimate_bytes(int N, int stat, int n_bins, int l_max,
     const size_t nbp = (size_t)((n_bins + 3) & ~3);
     b += nbp * (size_t)(l_max + 1) * (size_t)table_len(N) * sizeof(float);
     if (host_inputs) b += (size_t)n_points * 4 * sizeof(float);
+    // tiled scatter: per-point tile and permutation, per-tile tables, deposit regions (order p <= 8)
+    b += (size_t)n_points * 2 * sizeof(int) + (3 * (size_t)scatter_tiled_tiles(N) + 1) * sizeof(int) +
+         scatter_tiled_region_floats(N, 8) * sizeof(float);
     b += (size_t)std::max(2, 512) * 592 * sizeof(double) + 1024 * sizeof(double);  // assign partials
     if (stat == 2) {
         b += (size_t)n_bins * n3 * sizeof(float2) + (size_t)256 * zeta_z_blocks(N) * sizeof(double);
@@ -1876,11 +1933,9 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
     const int nblk = 592;
     CK(grow_doubles(c->part, c->part_cap, (size_t)std::max(2, p3) * nblk), "partials");
     CK(grow_doubles(c->red, c->red_cap, 1024), "reduction buffer");
-    CK(cudaMemsetAsync(c->rgrid, 0, n3 * sizeof(float), st), "clear random field");
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     const float s = (float)((double)N / c->L);
-    CK(launch_scatter(N, p, dpos, dw, n, c->rgrid, s, (flags & HERMES_WRAP) ? 1 : 0, c->err, st, c->tracer),
-       "scatter randoms");
+    CK(scatter_tiled(c, dpos, dw, n, c->rgrid, s, (flags & HERMES_WRAP) ? 1 : 0, st), "scatter randoms");
     CK(launch_weight_sums(dw, n, c->part, nblk, st, c->tracer), "weight sums");
     CK(launch_reduce_rows(c->part, 2, nblk, c->red, st, c->tracer), "reduce sums");
     CK(launch_selfpair(N, p, dpos, dw, n, s, c->part, nblk, st, c->tracer), "self-pair table");

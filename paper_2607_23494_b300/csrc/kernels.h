@@ -78,6 +78,14 @@ struct Tables {
 // scatter.cu
 cudaError_t launch_scatter(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
                            int wrap, unsigned* err, cudaStream_t st, const Tracer& tr);
+// Shared-memory-privatised scatter into grid (no clearing needed; no global
+// atomics on the grid).  Scratch: tile_of, perm [n] ints; counts, cursor
+// [ntiles] ints, offs [ntiles + 1] ints; regions [scatter_tiled_region_floats] floats.
+size_t scatter_tiled_region_floats(int N, int p);
+int scatter_tiled_tiles(int N);
+cudaError_t launch_scatter_tiled(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
+                                 int wrap, unsigned* err, int* tile_of, int* perm, int* counts, int* offs,
+                                 int* cursor, float* regions, cudaStream_t st, const Tracer& tr);
 // catalogues c0 .. c1-1; catalogue c: points [offs[c], offs[c+1]) (device
 // offsets), grid + c*N^3; n_max bounds the points of the group (sizes the grid)
 cudaError_t launch_scatter_batch(int N, int p, const float* pos, const float* w, const int64_t* offs, int c0, int c1,

@@ -195,6 +195,152 @@ __global__ void __launch_bounds__(256) k_gather_marks(const float* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled scatter: shared-memory privatisation of the B-spline deposit.
+//   1. each point's tile is the tile of its first node (tiles of SB^3 cells, NT
+//      per axis); points are counted per tile,
+//   2. an exclusive scan of the counts gives each tile's range of a permutation,
+//      filled by a second pass,
+//   3. one block per tile deposits its points into a shared region of
+//      RB^3 = (SB + P - 1)^3 cells (the tile and the P - 1 cells its points reach
+//      beyond it) with shared-memory atomics and writes the region out,
+//   4. every grid cell sums the (up to 2 per axis) regions that cover it, with a
+//      plain store; the grid needs no clearing and sees no global atomics.
+constexpr int SB = 16;
+
+__device__ __forceinline__ int tile_of_first(int fx, int fy, int fz, int N, int NT) {
+    const int msk = N - 1;
+    return (((fx & msk) / SB) * NT + (fy & msk) / SB) * NT + (fz & msk) / SB;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_tile_count(const float* __restrict__ pos, const float* __restrict__ w,
+                                                    int64_t n, float s, int N, int wrap, int NT,
+                                                    int* __restrict__ counts, int* __restrict__ tile_of,
+                                                    unsigned* __restrict__ err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float bx[P], by[P], bz[P];
+        int fx, fy, fz;
+        const bool ok = node_rule<P>(__ldg(pos + 3 * i), s, N, wrap, fx, bx) &
+                        node_rule<P>(__ldg(pos + 3 * i + 1), s, N, wrap, fy, by) &
+                        node_rule<P>(__ldg(pos + 3 * i + 2), s, N, wrap, fz, bz);
+        const float wi = w ? __ldg(w + i) : 1.0f;
+        if (!ok || !isfinite(wi)) {
+            atomicOr(err, 1u);
+            tile_of[i] = -1;
+            continue;
+        }
+        const int t = tile_of_first(fx, fy, fz, N, NT);
+        tile_of[i] = t;
+        atomicAdd(counts + t, 1);
+    }
+}
+
+// Exclusive scan of n counts by one block of 1024 threads; offs[n] = total.
+__global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ counts, int n, int* __restrict__ offs,
+                                                    int* __restrict__ cursor) {
+    __shared__ int part[1024];
+    const int per = (n + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(n, lo + per);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += counts[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
+        const int v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int i = lo; i < hi; ++i) {
+        offs[i] = run;
+        cursor[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 1023) offs[n] = part[1023];
+}
+
+__global__ void __launch_bounds__(256) k_tile_fill(const int* __restrict__ tile_of, int64_t n,
+                                                   int* __restrict__ cursor, int* __restrict__ perm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int t = tile_of[i];
+        if (t >= 0) perm[atomicAdd(cursor + t, 1)] = (int)i;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_tile_deposit(const float* __restrict__ pos, const float* __restrict__ w,
+                                                      const int* __restrict__ perm, const int* __restrict__ offs,
+                                                      float s, int N, int wrap, int NT, float* __restrict__ regions) {
+    constexpr int RB = SB + P - 1, R3 = RB * RB * RB;
+    __shared__ float reg[R3];
+    const int t = blockIdx.x;
+    const int tx = t / (NT * NT), ty = (t / NT) % NT, tz = t % NT;
+    const int msk = N - 1;
+    for (int e = threadIdx.x; e < R3; e += blockDim.x) reg[e] = 0.0f;
+    __syncthreads();
+    const int lo = offs[t], hi = offs[t + 1];
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const int i = perm[k];
+        float bx[P], by[P], bz[P];
+        int fx, fy, fz;
+        node_rule<P>(__ldg(pos + 3 * i), s, N, wrap, fx, bx);
+        node_rule<P>(__ldg(pos + 3 * i + 1), s, N, wrap, fy, by);
+        node_rule<P>(__ldg(pos + 3 * i + 2), s, N, wrap, fz, bz);
+        const float wi = w ? __ldg(w + i) : 1.0f;
+        const int lx = (fx & msk) - tx * SB, ly = (fy & msk) - ty * SB, lz = (fz & msk) - tz * SB;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const float wa = wi * bx[a];
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const float wab = wa * by[b];
+                float* row = reg + ((lx + a) * RB + (ly + b)) * RB + lz;
+#pragma unroll
+                for (int c = 0; c < P; ++c) atomicAdd(row + c, wab * bz[c]);
+            }
+        }
+    }
+    __syncthreads();
+    float* out = regions + (size_t)t * R3;
+    for (int e = threadIdx.x; e < R3; e += blockDim.x) out[e] = reg[e];
+}
+
+// grid[x,y,z] = sum over the regions covering the cell: per axis the cell's own tile
+// (local l = x % SB) and the previous tile (local l + SB, when l + SB < RB).
+template <int P>
+__global__ void __launch_bounds__(256) k_tile_gather(const float* __restrict__ regions, int N, int NT,
+                                                     float* __restrict__ grid) {
+    constexpr int RB = SB + P - 1, R3 = RB * RB * RB;
+    const size_t n3 = (size_t)N * N * N;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += stride) {
+        const int z = (int)(c % N), y = (int)((c / N) % N), x = (int)(c / ((size_t)N * N));
+        const int X[2] = {x / SB, (x / SB + NT - 1) % NT}, LX[2] = {x % SB, x % SB + SB};
+        const int Y[2] = {y / SB, (y / SB + NT - 1) % NT}, LY[2] = {y % SB, y % SB + SB};
+        const int Z[2] = {z / SB, (z / SB + NT - 1) % NT}, LZ[2] = {z % SB, z % SB + SB};
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (LX[a] >= RB) continue;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (LY[b] >= RB) continue;
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    if (LZ[d] >= RB) continue;
+                    const size_t t = ((size_t)X[a] * NT + Y[b]) * NT + Z[d];
+                    acc += __ldg(regions + t * R3 + ((size_t)LX[a] * RB + LY[b]) * RB + LZ[d]);
+                }
+            }
+        }
+        grid[c] = acc;
+    }
+}
+
 // Node rule of every point, for inspection: first node (mod N) and the p basis
 // values per axis; err bit 1 marks a rejected coordinate.
 template <int P>
@@ -551,6 +697,43 @@ cudaError_t launch_gather_marks(int N, int p, const float* pos, int64_t n, const
         default: return cudaErrorInvalidValue;
     }
     tr(K_GATHER, 1, st);
+    return cudaGetLastError();
+}
+
+size_t scatter_tiled_region_floats(int N, int p) {
+    const int NT = N / SB, RB = SB + p - 1;
+    return (size_t)NT * NT * NT * RB * RB * RB;
+}
+int scatter_tiled_tiles(int N) { return (N / SB) * (N / SB) * (N / SB); }
+
+cudaError_t launch_scatter_tiled(int N, int p, const float* pos, const float* w, int64_t n, float* grid, float s,
+                                 int wrap, unsigned* err, int* tile_of, int* perm, int* counts, int* offs,
+                                 int* cursor, float* regions, cudaStream_t st, const Tracer& tr) {
+    if (N < SB || p < 1 || p > 8 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int NT = N / SB, ntiles = NT * NT * NT;
+    cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)ntiles * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int nb = nblocks_for(n, 256, 148 * 16);
+    tr(K_SCATTER, 0, st);
+    switch (p) {
+#define HERMES_TC(P) \
+    case P: k_tile_count<P><<<nb, 256, 0, st>>>(pos, w, n, s, N, wrap, NT, counts, tile_of, err); break;
+        HERMES_TC(1) HERMES_TC(2) HERMES_TC(3) HERMES_TC(4) HERMES_TC(5) HERMES_TC(6) HERMES_TC(7) HERMES_TC(8)
+#undef HERMES_TC
+    }
+    k_tile_scan<<<1, 1024, 0, st>>>(counts, ntiles, offs, cursor);
+    k_tile_fill<<<nb, 256, 0, st>>>(tile_of, n, cursor, perm);
+    const int ng = nblocks_for((int64_t)N * N * N, 256, 148 * 32);
+    switch (p) {
+#define HERMES_TD(P)                                                                                    \
+    case P:                                                                                             \
+        k_tile_deposit<P><<<ntiles, 256, 0, st>>>(pos, w, perm, offs, s, N, wrap, NT, regions);         \
+        k_tile_gather<P><<<ng, 256, 0, st>>>(regions, N, NT, grid);                                     \
+        break;
+        HERMES_TD(1) HERMES_TD(2) HERMES_TD(3) HERMES_TD(4) HERMES_TD(5) HERMES_TD(6) HERMES_TD(7) HERMES_TD(8)
+#undef HERMES_TD
+    }
+    tr(K_SCATTER, 1, st);
     return cudaGetLastError();
 }
 

@@ -327,20 +327,26 @@ def test_kspace_route_planted_mode_and_errors():
 def test_cached_window_tables_serve_smaller_orders():
     # a table built for l_max = 4 is reused (its leading blocks) by later
     # contexts asking l_max = 0 or 2 with the same L, N and shells
+    # (the same field is set directly in every context, so only the tables can differ;
+    # two scatters of one catalogue differ by float-atomic order)
     H = _hermes()
     L, N, p = 180.0, 32, 4
     edges = np.linspace(3.0, 60.0, 10)
     pos = S.mixed_poisson_sp(6000, L, seed=91)
+    eps, sw, _ = O.assign(pos, None, N, L, p)
+    delta = O.delta_from_eps(eps, sw).astype(np.float32)
     with H.Context(L, N, p) as c4:
         c4.window_shells(edges, l_max=4)
         c4.assign(pos)
         x4 = c4.xi_multipoles([0, 2, 4])
+        c4.set_delta(delta)
+        d4 = c4.xi_multipoles([0, 2, 4])
     for lm, ells in ((0, [0]), (2, [0, 2])):
         with H.Context(L, N, p) as c:
             c.window_shells(edges, l_max=lm)
-            c.assign(pos)
+            c.set_delta(delta)
             got = c.xi_multipoles(ells)
-        np.testing.assert_allclose(got, x4[:len(ells)], rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(got, d4[:len(ells)], rtol=1e-9, atol=1e-12)
     ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=(0, 2, 4))["xi"]
     _close(x4, ref)
 
