@@ -12,6 +12,7 @@
 // host in float64 and laid out so each load is coalesced; the inverse uses
 // conjugates.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace hermes {
@@ -107,6 +108,7 @@ struct SmemStrided {
     __device__ __forceinline__ int at(int pos) const { return pos * W + col + (pos >> 3) * 4; }
     __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
     __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }  // a tile spans the block
 };
 // Contiguous line of length M with one padding slot every 2^SH elements.
 constexpr int line_shift(int m) { return m >= 128 ? 4 : (m == 32 ? 2 : 3); }
@@ -117,7 +119,18 @@ struct SmemLine {
     __device__ __forceinline__ static int at(int pos) { return pos + (pos >> SH); }
     __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
     __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
 };
+// The same line when its M/8 threads are consecutive threads of one warp
+// (line li = threadIdx.x / T, T = M/8 <= 32): its exchanges then only need the
+// warp, and the other lines of the block run on without waiting.
+template <int M>
+struct SmemWarpLine : SmemLine<M> {
+    static_assert(M / 8 <= 32, "a warp-synchronised line has at most 32 threads");
+    __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
+template <int M>
+using SmemZLine = std::conditional_t<(M / 8 <= 32), SmemWarpLine<M>, SmemLine<M>>;
 template <int M>
 struct LinePad {
     static constexpr int value = M + (M >> line_shift(M)) + 1;
@@ -158,7 +171,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = out[i];
     } else {
-        __syncthreads();  // everyone finished reading the previous contents
+        sm.sync();  // everyone finished reading the previous contents
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int b = t + u * T;
@@ -166,7 +179,7 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
 #pragma unroll
             for (int r = 0; r < R; ++r) sm.st(base + r * NS, out[u + r * U]);
         }
-        __syncthreads();
+        sm.sync();
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = sm.ld(t + i * T);
     }
@@ -181,8 +194,9 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* 
 
 // In-register/shared FFT of length M (8 <= M <= TW).  Precondition: v[i] =
 // x[t + i*M/8].  Postcondition: v[i] = X[t + i*M/8], X_k = sum_n x_n
-// e^{-+2 pi i k n / M} (unnormalised).  All threads of the block must call it
-// the same number of times (it contains __syncthreads when M > 8).
+// e^{-+2 pi i k n / M} (unnormalised).  All threads that share the layout's
+// synchronisation (the block, or the warp of a SmemWarpLine) must call it the
+// same number of times (it synchronises them when M > 8).
 template <int M, bool INV, class S>
 __device__ __forceinline__ void fft_line(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
     static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");

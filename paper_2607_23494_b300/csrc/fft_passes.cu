@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
     extern __shared__ float2 smem[];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemLine<M> sm{smem + li * LP};
+    const SmemZLine<M> sm{smem + li * LP};
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         grid += cat * N * N * N;
@@ -94,10 +94,10 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
         v[i] = e;
     }
     fft_line<M, false>(v, t, tw, sm);
-    __syncthreads();
+    sm.sync();
 #pragma unroll
     for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
-    __syncthreads();
+    sm.sync();  // the partner k' = M - k lies in the same line
     float2* out = spec + line * (N / 2);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line0 = (size_t)blockIdx.x * LZ;
     const size_t line = line0 + li;
-    const SmemLine<M> sm{lines + li * LP};
+    const SmemZLine<M> sm{lines + li * LP};
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         work += cat * S * N * N * H;
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_store(const floa
     extern __shared__ float2 smem[];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemLine<M> sm{smem + li * LP};
+    const SmemZLine<M> sm{smem + li * LP};
     const float2* X = work + line * H;
     float2 v[8];
 #pragma unroll

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
             }
-            const SmemLine<N> sm{smem + b * LPZ};
+            const SmemZLine<N> sm{smem + b * LPZ};  // one warp per bin line when N <= 256
             fft_line<N, true>(v, t, tw, sm);
 #pragma unroll
             for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
