@@ -121,16 +121,19 @@ struct SmemLine {
     __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
     __device__ __forceinline__ static void sync() { __syncthreads(); }
 };
-// The same line when its M/8 threads are consecutive threads of one warp
-// (line li = threadIdx.x / T, T = M/8 <= 32): its exchanges then only need the
-// warp, and the other lines of the block run on without waiting.
+// A contiguous line whose M/8 threads are consecutive (thread group g =
+// threadIdx.x / (M/8) of the block): its exchanges only wait for that group,
+// so the other lines of the block run on.  Up to 32 threads that is their
+// warp; above, named barrier 1 + g over the group's warps (at most 15 groups
+// per block; barrier 0 stays the block-wide one).
 template <int M>
-struct SmemWarpLine : SmemLine<M> {
-    static_assert(M / 8 <= 32, "a warp-synchronised line has at most 32 threads");
-    __device__ __forceinline__ static void sync() { __syncwarp(); }
+struct SmemZLine : SmemLine<M> {
+    int group;
+    __device__ __forceinline__ void sync() const {
+        if constexpr (M / 8 <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;\n" ::"r"(1 + group), "n"(M / 8) : "memory");
+    }
 };
-template <int M>
-using SmemZLine = std::conditional_t<(M / 8 <= 32), SmemWarpLine<M>, SmemLine<M>>;
 template <int M>
 struct LinePad {
     static constexpr int value = M + (M >> line_shift(M)) + 1;
@@ -195,7 +198,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* 
 // In-register/shared FFT of length M (8 <= M <= TW).  Precondition: v[i] =
 // x[t + i*M/8].  Postcondition: v[i] = X[t + i*M/8], X_k = sum_n x_n
 // e^{-+2 pi i k n / M} (unnormalised).  All threads that share the layout's
-// synchronisation (the block, or the warp of a SmemWarpLine) must call it the
+// synchronisation (the block, or the thread group of a SmemZLine) must call it the
 // same number of times (it synchronises them when M > 8).
 template <int M, bool INV, class S>
 __device__ __forceinline__ void fft_line(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {

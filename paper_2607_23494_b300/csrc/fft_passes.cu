@@ -32,6 +32,7 @@ namespace hermes {
 template <int N>
 struct Cfg {
     static constexpr int H = N / 2;
+    static_assert(N / 16 <= 32 || 256 / (N / 16) <= 15, "z lines of a block beyond the named barriers");
     static constexpr int W = (N >= 512) ? 8 : (N / 2 < 16 ? N / 2 : 16);  // columns per strided tile
     static constexpr int TS = (N / 8) * W;                                  // threads per strided tile
     static constexpr int MZ = N / 2;                                        // half-length z transform
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_fwd_z_r2c(float* __restric
     extern __shared__ float2 smem[];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemZLine<M> sm{smem + li * LP};
+    const SmemZLine<M> sm{{smem + li * LP}, li};
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         grid += cat * N * N * N;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line0 = (size_t)blockIdx.x * LZ;
     const size_t line = line0 + li;
-    const SmemZLine<M> sm{lines + li * LP};
+    const SmemZLine<M> sm{{lines + li * LP}, li};
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         work += cat * S * N * N * H;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS) k_inv_z_c2r_store(const floa
     extern __shared__ float2 smem[];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const size_t line = (size_t)blockIdx.x * C::LZ + li;
-    const SmemZLine<M> sm{smem + li * LP};
+    const SmemZLine<M> sm{{smem + li * LP}, li};
     const float2* X = work + line * H;
     float2 v[8];
 #pragma unroll

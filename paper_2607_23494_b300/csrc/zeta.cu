@@ -40,6 +40,7 @@ struct ZCfg {
                                      (PREFETCH ? (size_t)16 * N * sizeof(float2) : 0);
 };
 static_assert(ZCfg<16>::ZPER >= 1 && ZCfg<1024>::NZS == 32, "z-pass layout");
+static_assert(ZCfg<512>::GB <= 15 && ZCfg<1024>::GB <= 15, "one named barrier per z line group");
 
 template <class K>
 static cudaError_t allow_smem_z(K kernel, size_t bytes) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
 #pragma unroll
                 for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
             }
-            const SmemZLine<N> sm{smem + b * LPZ};  // one warp per bin line when N <= 256
+            const SmemZLine<N> sm{{smem + b * LPZ}, bb};  // threads of group bb only
             fft_line<N, true>(v, t, tw, sm);
 #pragma unroll
             for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
