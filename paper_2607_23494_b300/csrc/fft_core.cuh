@@ -147,7 +147,9 @@ struct FirstRadix {
 };
 
 // One Stockham stage.  v[u + r*U] is input r of butterfly b = t + u*T.
-template <int M, int R, int NS, bool INV, class S>
+// TW7: load all seven radix-8 twiddles instead of three (for passes whose
+// loads are already hidden and that are short of issue slots).
+template <int M, int R, int NS, bool INV, bool TW7, class S>
 __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
     constexpr int T = M / 8;
     constexpr int U = 8 / R;
@@ -160,10 +162,23 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
         float2 x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
-        if constexpr (NS > 1) {
+        if constexpr (NS > 1 && TW7) {
             static_assert(R == 8, "only the leading stage may use radix 2 or 4");
 #pragma unroll
             for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], twiddle_stage8<INV>(tw, NS, r, k));
+        } else if constexpr (NS > 1) {
+            static_assert(R == 8, "only the leading stage may use radix 2 or 4");
+            // w^1, w^2, w^4 from the table; w^3, w^5, w^6, w^7 as products of at most two of
+            // them (three loads instead of seven; relative error a few float32 ulps)
+            const float2 w1 = twiddle_stage8<INV>(tw, NS, 1, k), w2 = twiddle_stage8<INV>(tw, NS, 2, k);
+            const float2 w4 = twiddle_stage8<INV>(tw, NS, 4, k), w3 = cmul(w1, w2);
+            x[1] = cmul(x[1], w1);
+            x[2] = cmul(x[2], w2);
+            x[3] = cmul(x[3], w3);
+            x[4] = cmul(x[4], w4);
+            x[5] = cmul(x[5], cmul(w1, w4));
+            x[6] = cmul(x[6], cmul(w2, w4));
+            x[7] = cmul(x[7], cmul(w3, w4));
         }
         dftR<R, INV>(x);
 #pragma unroll
@@ -188,11 +203,11 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
     }
 }
 
-template <int M, int NS, bool INV, class S>
+template <int M, int NS, bool INV, bool TW7, class S>
 __device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
     constexpr int R = (NS == 1) ? FirstRadix<M>::value : 8;
-    fft_stage<M, R, NS, INV, S>(v, t, tw, sm);
-    if constexpr (NS * R < M) fft_stages<M, NS * R, INV, S>(v, t, tw, sm);
+    fft_stage<M, R, NS, INV, TW7, S>(v, t, tw, sm);
+    if constexpr (NS * R < M) fft_stages<M, NS * R, INV, TW7, S>(v, t, tw, sm);
 }
 
 // In-register/shared FFT of length M (8 <= M <= TW).  Precondition: v[i] =
@@ -200,10 +215,10 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* 
 // e^{-+2 pi i k n / M} (unnormalised).  All threads that share the layout's
 // synchronisation (the block, or the thread group of a SmemZLine) must call it the
 // same number of times (it synchronises them when M > 8).
-template <int M, bool INV, class S>
+template <int M, bool INV, bool TW7 = false, class S>
 __device__ __forceinline__ void fft_line(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
     static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
-    fft_stages<M, 1, INV, S>(v, t, tw, sm);
+    fft_stages<M, 1, INV, TW7, S>(v, t, tw, sm);
 }
 
 }  // namespace hermes

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 2) k_strided_pf(float2* __restrict
 #pragma unroll
             for (int i = 0; i < 8; ++i) vn[i] = b[(t + i * T) * pos_stride];
         }
-        fft_line<N, INV>(v, t, tw, SmemStrided<W>{smem, col});
+        fft_line<N, INV, true>(v, t, tw, SmemStrided<W>{smem, col});
         float2* b = base_of(bx, by, bz);
 #pragma unroll
         for (int i = 0; i < 8; ++i) b[(t + i * T) * pos_stride] = v[i];
