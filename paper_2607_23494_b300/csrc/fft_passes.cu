@@ -354,9 +354,12 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
         ac::bulk_g2s(stage, work + line0 * H, STAGE, &full[0]);
     }
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
-    float2 d2[8];
+    float2 d2[8], wk[8];  // the thread's delta pairs and split twiddles e^{+2 pi i k / N}, k = t + iT
 #pragma unroll
-    for (int i = 0; i < 8; ++i) d2[i] = dl[t + i * T];
+    for (int i = 0; i < 8; ++i) {
+        d2[i] = dl[t + i * T];
+        wk[i] = cconj(__ldg(tw + N + t + i * T));
+    }
     bool late = false;
     for (int s = 0; s < S; ++s) {
         __syncthreads();  // every thread is done with the buffer that the next copy overwrites
@@ -391,12 +394,10 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int k = t + i * T;
             const float2 xk = v[i];
             const float2 xc = cconj(xm[i]);
             const float2 a = cadd(xk, xc);
-            const float2 w = cconj(__ldg(tw + N + k));  // e^{+2 pi i k / N}
-            const float2 c = cmul(w, csub(xk, xc));
+            const float2 c = cmul(wk[i], csub(xk, xc));
             v[i] = make_float2(a.x - c.y, a.y + c.x);
         }
         fft_line<M, true>(v, t, tw, sm);
