@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
     // Phi^, the Nyquist mask, scale and L_l(k_z/k) are folded into the input once,
     // so per window v = v0 * T_s(|n|^2)
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
-    int q[8];  // |n|^2, or the shared-table row offset (a*W + col)*RS under STAB
+    int q[8];  // |n|^2 (gather form only)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int kx = t + i * T;
@@ -279,10 +279,15 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         const float a = wb.cyl ? __ldg(wb.par + nz)
                                : wb.scale * legendre(wb.ell, qi > 0 ? (float)nz * rsqrtf((float)qi) : 0.0f);
         v0[i] = cscale(v0[i], ph * a);
-        const int qq = (wb.cyl && !nyq) ? nx * nx + ny * ny : qi;
-        const int ax = (kx < H) ? kx : (kx == H ? 0 : N - kx);  // |n_x|; the Nyquist lane reads row 0
-        q[i] = STAB ? (ax * W + col) * RS : qq;
+        q[i] = (wb.cyl && !nyq) ? nx * nx + ny * ny : qi;
     }
+    // Under STAB the row of element i is |n_x| = t + iT (i < 4) or N - t - iT (i >= 4; the
+    // Nyquist element t = 0, i = 4 reads row 0): two per-thread bases and constant steps,
+    // so the offsets need no registers of their own.
+    const int qlo = (t * W + col) * RS, qhi = ((N - t) * W + col) * RS;
+    auto trow = [&](int i) {
+        return i < 4 ? qlo + i * (T * W) * RS : ((t == 0 && i == 4) ? col * RS : qhi - i * (T * W) * RS);
+    };
     if constexpr (STAB) {
         ac::cp_async_wait_all();
         __syncthreads();
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         float4 tv[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + q[i] + g)
+            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + trow(i) + g)
                          : __ldg(reinterpret_cast<const float4*>(wb.tab + (size_t)q[i] * nbp + g));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
