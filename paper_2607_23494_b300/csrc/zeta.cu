@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     }
     const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
     float2 v0[8];
-    int q[8];
+    int q[8];  // table index (gather form only)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int kx = t + i * T;
@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
         }
         const bool nyq = (kx == H) || (ky == H) || (kz == H);
         const int qq = nx * nx + ny * ny + nz * nz;
-        const int ax = (kx < H) ? kx : (kx == H ? 0 : N - kx);  // |n_x|; the Nyquist lane reads row 0
-        q[i] = STAB ? (ax * W + col) * RS : (nyq ? 0 : qq);    // table index stays in range on Nyquist lanes
+        q[i] = nyq ? 0 : qq;  // table index stays in range on Nyquist lanes
         const float2 y = ylm_unnorm(hb.ell, hb.m, nx, ny, nz, qq);
         const float2 ang = mul_ipow(cscale(y, hb.ylm_norm * __ldg(tb.phi + kx) * phyz), hb.ell);
         v0[i] = nyq ? make_float2(0.f, 0.f) : cmul(d, ang);
@@ -144,12 +143,18 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
         ac::cp_async_wait_all();
         __syncthreads();
     }
+    // Under STAB the row of element i is |n_x| = t + iT (i < 4) or N - t - iT (i >= 4; the
+    // Nyquist element t = 0, i = 4 reads row 0): two per-thread bases and constant steps.
+    const int qlo = (t * W + col) * RS, qhi = ((N - t) * W + col) * RS;
+    auto trow = [&](int i) {
+        return i < 4 ? qlo + i * (T * W) * RS : ((t == 0 && i == 4) ? col * RS : qhi - i * (T * W) * RS);
+    };
     const int nbp = hb.nbp;
     for (int g = 0; g < hb.S; g += 4) {
         float4 tv[8];  // radial factors of bins g..g+3: one 16-byte load per element
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + q[i] + g)
+            tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + trow(i) + g)
                          : __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     }
 }
 
-// Z2 is k_strided<N, true> from fft_passes.cu instantiated here for full-length k_z.
+// Z2: inverse y FFT of every bin field in place (full-length k_z columns, strided tiles).
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_y(float2* __restrict__ fields, const float2* __restrict__ tw) {
     using C = ZCfg<N>;
