@@ -13,9 +13,9 @@
 //
 // Inverse per batch of S windows (Sec. 3.5, eps_W = iFT[FT(eps) K_W]):
 //   I1 along x: read delta^ once, multiply by K_s = W^_s Phi^ for every window
-//      s of the batch, accumulate the self-pair term sum_n K_s(n) S^(n), inverse
-//      FFT, store;
-//   I2 along y;
+//      s of the batch, inverse FFT, store (the self-pair term of each window is
+//      the radial contraction of the self-pair histogram, kspace.cu);
+//   I2 along y (persistent blocks, next tile's loads in flight);
 //   I3 complex-to-real along z fused with the cell contraction
 //      sum_x delta(x) delta~_s(x) (Eq. pair-counting / Eq. 2rdEs): the filtered
 //      fields never return to HBM.
@@ -211,8 +211,9 @@ __device__ __forceinline__ float cos_tab(const float2* __restrict__ tw, int j) {
 // windows fused in: K_s(n) = scale * T_s(|n|^2) * Phi^(n) * L_l(k_z/k), all
 // windows of the batch sharing the order l (Phi^, L_l and scale are applied to
 // the input once); for axisymmetric windows K_s(n) = T_perp_s(n_x^2 + n_y^2) *
-// T_par_j(|n_z|) * Phi^(n), the batch sharing the line-of-sight bin j.  The self-pair term of each window is not summed here: it
-// is the radial contraction of the self-pair histogram (kspace.cu).
+// T_par_j(|n_z|) * Phi^(n), the batch sharing the line-of-sight bin j.  The
+// self-pair term of each window is not summed here: it is the radial
+// contraction of the self-pair histogram (kspace.cu).
 //
 // STAB: the block first copies the radial factors it needs into shared memory
 // (its columns see |n|^2 = a^2 + n_y^2 + n_z^2 for a = |n_x| only, so H rows per
