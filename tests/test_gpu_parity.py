@@ -299,6 +299,26 @@ def test_kspace_route_matches_oracle_and_real_space_path(N, p, L, ells):
     _close(got, real)
 
 
+def test_inverse_passes_at_1024_match_kspace_route():
+    # 1024^3 has its own launch shapes: 1024-thread strided tiles (one per SM), the
+    # plain inverse y pass instead of the persistent one, and 512-point z lines that
+    # span two warps (one named barrier per line).  The real-space xi_l must equal the
+    # Parseval route, which reads only delta^ and the radial tables (that route is
+    # pinned to the oracle at small grids above).
+    H = _hermes()
+    N, p, L = 1024, 4, 2000.0
+    pos = S.lognormal_catalogue(200000, L, seed=1024, n_grid=64)
+    mass = S.lognormal_masses(pos.shape[0], seed=1025)
+    edges = np.linspace(L / 200, L / 20, 7)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(edges, l_max=2)
+        ctx.assign(pos, mass)
+        ks = ctx.xi_multipoles_kspace((0, 2))
+        real = ctx.xi_multipoles((0, 2))
+    assert np.all(np.isfinite(real)) and real.shape == (2, 6)
+    _close(real, ks)
+
+
 def test_kspace_route_planted_mode_and_errors():
     # delta = cos(2 pi n0.x / N): |delta^|^2 = (N^3/2)^2 at +-n0, so
     # xi_{b,l} = K_{b,l}(n0) / 2 with no self-pair term (the field has no catalogue)
