@@ -257,6 +257,30 @@ def test_fused_yz_pass_matches_three_pass_path(N, L, n, monkeypatch):
         _close(res["1"], O.xi_multipoles(pos, None, N, L, 4, edges, ells=(0, 2))["xi"])
 
 
+def test_zeta_two_warp_lines_at_512_match_block_synchronised_gram(monkeypatch):
+    # at 512^3 each 512-point z line of the SIMT Gram pass spans two warps that wait on
+    # a named barrier of their own; the opt-in tensor-core pass transforms the same lines
+    # with block-wide barriers, so the two agree only if the per-line barriers are right
+    H = _hermes()
+    N, p, L, l_max = 512, 4, 500.0, 2
+    pos = S.lognormal_catalogue(100000, L, seed=512, n_grid=64)
+    edges = np.linspace(10.0, 90.0, 9)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("HERMES_ZETA_TC", flag)
+        with H.Context(L, N, p) as ctx:
+            ctx.assign(pos)
+            ctx.window_shells(edges, l_max=l_max)
+            res[flag] = ctx.zeta_multipoles()
+    assert np.all(np.isfinite(res["0"]))
+    # the two Grams round differently (split TF32 in TMEM vs float32 partials flushed
+    # to float64 every 8 lines) and at 512^3 they differ by up to ~1.3e-4 relative; a
+    # barrier fault would corrupt whole lines, an error of the order of the values
+    _close(res["1"], res["0"], rel=1e-3, ab=1e-7)
+    for ell in range(l_max + 1):
+        np.testing.assert_array_equal(res["0"][ell], res["0"][ell].T)
+
+
 @pytest.mark.parametrize("N,nb", [(32, 16), (64, 7), (128, 16)])
 def test_zeta_tensor_core_gram_matches_simt_and_oracle(N, nb, monkeypatch):
     # the tcgen05 split-TF32 Gram (opt-in) against the float32 SIMT Gram (default),
