@@ -310,34 +310,38 @@ __global__ void __launch_bounds__(256) k_tile_deposit(const float* __restrict__ 
 }
 
 // grid[x,y,z] = sum over the regions covering the cell: per axis the cell's own tile
-// (local l = x % SB) and the previous tile (local l + SB, when l + SB < RB).
+// (local l = x % SB) and the previous tile (local l + SB, when l + SB < RB).  One block
+// per (x, y) row: the (x, y) part of the up to four covering region rows is set up
+// once, and each thread walks z with shifts only (same summation order as the
+// per-axis enumeration (x tile, y tile, z tile)).
 template <int P>
 __global__ void __launch_bounds__(256) k_tile_gather(const float* __restrict__ regions, int N, int NT,
                                                      float* __restrict__ grid) {
     constexpr int RB = SB + P - 1, R3 = RB * RB * RB;
-    const size_t n3 = (size_t)N * N * N;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += stride) {
-        const int z = (int)(c % N), y = (int)((c / N) % N), x = (int)(c / ((size_t)N * N));
-        const int X[2] = {x / SB, (x / SB + NT - 1) % NT}, LX[2] = {x % SB, x % SB + SB};
-        const int Y[2] = {y / SB, (y / SB + NT - 1) % NT}, LY[2] = {y % SB, y % SB + SB};
-        const int Z[2] = {z / SB, (z / SB + NT - 1) % NT}, LZ[2] = {z % SB, z % SB + SB};
+    const int y = blockIdx.x, x = blockIdx.y;
+    const float* row[4];
+    bool use[4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int lx = x % SB + a * SB, ly = y % SB + b * SB;
+            const int tx = a ? (x / SB + NT - 1) % NT : x / SB, ty = b ? (y / SB + NT - 1) % NT : y / SB;
+            use[2 * a + b] = lx < RB && ly < RB;
+            row[2 * a + b] = regions + (size_t)(tx * NT + ty) * NT * R3 + (size_t)(lx * RB + ly) * RB;
+        }
+    float* out = grid + ((size_t)x * N + y) * N;
+    for (int z = threadIdx.x; z < N; z += blockDim.x) {
+        const int tz = z / SB, lz = z % SB;
+        const int tzp = (tz == 0 ? NT : tz) - 1;  // previous z tile
         float acc = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            if (LX[a] >= RB) continue;
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                if (LY[b] >= RB) continue;
-#pragma unroll
-                for (int d = 0; d < 2; ++d) {
-                    if (LZ[d] >= RB) continue;
-                    const size_t t = ((size_t)X[a] * NT + Y[b]) * NT + Z[d];
-                    acc += __ldg(regions + t * R3 + ((size_t)LX[a] * RB + LY[b]) * RB + LZ[d]);
-                }
-            }
+        for (int k = 0; k < 4; ++k) {
+            if (!use[k]) continue;  // uniform across the block
+            acc += __ldg(row[k] + (size_t)tz * R3 + lz);
+            if (lz + SB < RB) acc += __ldg(row[k] + (size_t)tzp * R3 + lz + SB);
         }
-        grid[c] = acc;
+        out[z] = acc;
     }
 }
 
@@ -723,12 +727,13 @@ cudaError_t launch_scatter_tiled(int N, int p, const float* pos, const float* w,
     }
     k_tile_scan<<<1, 1024, 0, st>>>(counts, ntiles, offs, cursor);
     k_tile_fill<<<nb, 256, 0, st>>>(tile_of, n, cursor, perm);
-    const int ng = nblocks_for((int64_t)N * N * N, 256, 148 * 32);
+    const dim3 ng((unsigned)N, (unsigned)N);  // one block per (x, y) row
+    const int gt = N < 256 ? N : 256;
     switch (p) {
 #define HERMES_TD(P)                                                                                    \
     case P:                                                                                             \
         k_tile_deposit<P><<<ntiles, 256, 0, st>>>(pos, w, perm, offs, s, N, wrap, NT, regions);         \
-        k_tile_gather<P><<<ng, 256, 0, st>>>(regions, N, NT, grid);                                     \
+        k_tile_gather<P><<<ng, gt, 0, st>>>(regions, N, NT, grid);                                      \
         break;
         HERMES_TD(1) HERMES_TD(2) HERMES_TD(3) HERMES_TD(4) HERMES_TD(5) HERMES_TD(6) HERMES_TD(7) HERMES_TD(8)
 #undef HERMES_TD
