@@ -271,38 +271,61 @@ __global__ void __launch_bounds__(256) k_tile_fill(const int* __restrict__ tile_
     }
 }
 
+constexpr int kDepositBatch = 256;  // points staged per round (one per thread)
+constexpr size_t deposit_smem(int p) {
+    return ((size_t)(SB + p - 1) * (SB + p - 1) * (SB + p - 1) + (size_t)kDepositBatch * (3 * p + 1)) * sizeof(float);
+}
+
+// One block per tile: the tile's points deposit into a shared (SB+P-1)^3 region with
+// shared-memory atomics.  Points are taken in batches of 256: each thread evaluates
+// the node rule of one point into shared memory, then the P*P (a, b) columns of a
+// point go to consecutive threads, each adding its P values along z.  For P = 4 the
+// 16 columns of a point lie on 16 distinct banks (row stride RB = 19, plane stride
+// 361 = 9 mod 32), so a warp's atomics (two points) conflict at most two ways.
 template <int P>
 __global__ void __launch_bounds__(256) k_tile_deposit(const float* __restrict__ pos, const float* __restrict__ w,
                                                       const int* __restrict__ perm, const int* __restrict__ offs,
                                                       float s, int N, int wrap, int NT, float* __restrict__ regions) {
-    constexpr int RB = SB + P - 1, R3 = RB * RB * RB;
-    __shared__ float reg[R3];
+    constexpr int RB = SB + P - 1, R3 = RB * RB * RB, PP = P * P, BATCH = kDepositBatch;
+    // dynamic shared memory: the region, then the staged weights and offsets
+    extern __shared__ float dsm[];
+    float* reg = dsm;                                                   // [R3]
+    float(*sw)[3 * P] = reinterpret_cast<float(*)[3 * P]>(dsm + R3);   // [BATCH][3P]: w_i bx[a], by[b], bz[c]
+    int* soff = reinterpret_cast<int*>(dsm + R3 + BATCH * 3 * P);      // [BATCH]: region offset of the first node
     const int t = blockIdx.x;
     const int tx = t / (NT * NT), ty = (t / NT) % NT, tz = t % NT;
     const int msk = N - 1;
     for (int e = threadIdx.x; e < R3; e += blockDim.x) reg[e] = 0.0f;
-    __syncthreads();
     const int lo = offs[t], hi = offs[t + 1];
-    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-        const int i = perm[k];
-        float bx[P], by[P], bz[P];
-        int fx, fy, fz;
-        node_rule<P>(__ldg(pos + 3 * i), s, N, wrap, fx, bx);
-        node_rule<P>(__ldg(pos + 3 * i + 1), s, N, wrap, fy, by);
-        node_rule<P>(__ldg(pos + 3 * i + 2), s, N, wrap, fz, bz);
-        const float wi = w ? __ldg(w + i) : 1.0f;
-        const int lx = (fx & msk) - tx * SB, ly = (fy & msk) - ty * SB, lz = (fz & msk) - tz * SB;
+    for (int base = lo; base < hi; base += BATCH) {
+        const int nb = min(BATCH, hi - base);
+        if (threadIdx.x < nb) {
+            const int i = perm[base + threadIdx.x];
+            float bx[P], by[P], bz[P];
+            int fx, fy, fz;
+            node_rule<P>(__ldg(pos + 3 * i), s, N, wrap, fx, bx);
+            node_rule<P>(__ldg(pos + 3 * i + 1), s, N, wrap, fy, by);
+            node_rule<P>(__ldg(pos + 3 * i + 2), s, N, wrap, fz, bz);
+            const float wi = w ? __ldg(w + i) : 1.0f;
+            float* row = sw[threadIdx.x];
 #pragma unroll
-        for (int a = 0; a < P; ++a) {
-            const float wa = wi * bx[a];
-#pragma unroll
-            for (int b = 0; b < P; ++b) {
-                const float wab = wa * by[b];
-                float* row = reg + ((lx + a) * RB + (ly + b)) * RB + lz;
-#pragma unroll
-                for (int c = 0; c < P; ++c) atomicAdd(row + c, wab * bz[c]);
+            for (int o = 0; o < P; ++o) {
+                row[o] = wi * bx[o];
+                row[P + o] = by[o];
+                row[2 * P + o] = bz[o];
             }
+            soff[threadIdx.x] = (((fx & msk) - tx * SB) * RB + ((fy & msk) - ty * SB)) * RB + ((fz & msk) - tz * SB);
         }
+        __syncthreads();  // staged weights visible (and, the first time, the cleared region)
+        for (int e = threadIdx.x; e < nb * PP; e += blockDim.x) {
+            const int kp = e / PP, ab = e % PP, a = ab / P, b = ab % P;
+            const float* wt = sw[kp];
+            const float wab = wt[a] * wt[P + b];
+            float* row = reg + soff[kp] + (a * RB + b) * RB;
+#pragma unroll
+            for (int c = 0; c < P; ++c) atomicAdd(row + c, wab * wt[2 * P + c]);
+        }
+        __syncthreads();  // the staging slots are reused by the next batch
     }
     __syncthreads();
     float* out = regions + (size_t)t * R3;
@@ -732,7 +755,11 @@ cudaError_t launch_scatter_tiled(int N, int p, const float* pos, const float* w,
     switch (p) {
 #define HERMES_TD(P)                                                                                    \
     case P:                                                                                             \
-        k_tile_deposit<P><<<ntiles, 256, 0, st>>>(pos, w, perm, offs, s, N, wrap, NT, regions);         \
+        if (deposit_smem(P) > 48 * 1024 &&                                                              \
+            (e = cudaFuncSetAttribute(k_tile_deposit<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                      (int)deposit_smem(P))) != cudaSuccess)                             \
+            return e;                                                                                   \
+        k_tile_deposit<P><<<ntiles, 256, deposit_smem(P), st>>>(pos, w, perm, offs, s, N, wrap, NT, regions); \
         k_tile_gather<P><<<ng, gt, 0, st>>>(regions, N, NT, grid);                                      \
         break;
         HERMES_TD(1) HERMES_TD(2) HERMES_TD(3) HERMES_TD(4) HERMES_TD(5) HERMES_TD(6) HERMES_TD(7) HERMES_TD(8)
