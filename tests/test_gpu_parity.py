@@ -31,7 +31,7 @@ def _close(got, ref, rel=REL, ab=ABS):
                            f"got {got[bad][:5]} ref {ref[bad][:5]}")
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("p", range(1, 9))
 def test_scatter_and_delta_match_oracle(p):
     H = _hermes()
     N, L = 32, 100.0
