@@ -237,29 +237,59 @@ __global__ void __launch_bounds__(256) k_tile_count(const float* __restrict__ po
     }
 }
 
-// Exclusive scan of n counts by one block of 1024 threads; offs[n] = total.
+// Exclusive scan of n counts by one block of 1024 threads; offs[n] = total.  The
+// counts pass through shared memory in chunks of 8192 with coalesced loads and
+// stores; each thread scans 8 consecutive entries of a chunk (one padding word per
+// 32, so those reads fall on distinct banks) and a running carry links the chunks.
 __global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ counts, int n, int* __restrict__ offs,
                                                     int* __restrict__ cursor) {
+    constexpr int K = 8, CH = 1024 * K;
+    __shared__ int buf[CH + CH / 32];
     __shared__ int part[1024];
-    const int per = (n + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(n, lo + per);
-    int sum = 0;
-    for (int i = lo; i < hi; ++i) sum += counts[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
-        const int v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+    auto at = [](int i) { return i + (i >> 5); };
+    int carry = 0;  // identical in every thread
+    for (int base = 0; base < n; base += CH) {
+        const int m = min(CH, n - base);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = threadIdx.x + k * 1024;
+            buf[at(i)] = i < m ? counts[base + i] : 0;
+        }
         __syncthreads();
-        part[threadIdx.x] += v;
+        int v[K], sum = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            v[j] = buf[at(K * threadIdx.x + j)];
+            sum += v[j];
+        }
+        part[threadIdx.x] = sum;
         __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
+            const int u = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+            __syncthreads();
+            part[threadIdx.x] += u;
+            __syncthreads();
+        }
+        int run = carry + part[threadIdx.x] - sum;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            buf[at(K * threadIdx.x + j)] = run;
+            run += v[j];
+        }
+        carry += part[1023];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = threadIdx.x + k * 1024;
+            if (i < m) {
+                const int o = buf[at(i)];
+                offs[base + i] = o;
+                cursor[base + i] = o;
+            }
+        }
+        __syncthreads();  // buf and part are reused by the next chunk
     }
-    int run = part[threadIdx.x] - sum;
-    for (int i = lo; i < hi; ++i) {
-        offs[i] = run;
-        cursor[i] = run;
-        run += counts[i];
-    }
-    if (threadIdx.x == 1023) offs[n] = part[1023];
+    if (threadIdx.x == 0) offs[n] = carry;
 }
 
 __global__ void __launch_bounds__(256) k_tile_fill(const int* __restrict__ tile_of, int64_t n,
