@@ -149,8 +149,13 @@ struct FirstRadix {
 // One Stockham stage.  v[u + r*U] is input r of butterfly b = t + u*T.
 // TW7: load all seven radix-8 twiddles instead of three (for passes whose
 // loads are already hidden and that are short of issue slots).
-template <int M, int R, int NS, bool INV, bool TW7, class S>
-__device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
+// WC: the twiddles w^1, w^2, w^4 of the thread's butterfly in every twiddled stage
+// come preloaded in wc[3 (SI - 1) + {0, 1, 2}] (SI = index of the stage); with 8
+// values per thread and radix 8 a thread's butterfly index is t in every such
+// stage, so they are the same for every transform the thread runs.
+template <int M, int R, int NS, bool INV, bool TW7, bool WC, int SI, class S>
+__device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm,
+                                          const float2* wc) {
     constexpr int T = M / 8;
     constexpr int U = 8 / R;
     constexpr bool LAST = (NS * R == M);
@@ -162,7 +167,18 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
         float2 x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
-        if constexpr (NS > 1 && TW7) {
+        if constexpr (NS > 1 && WC) {
+            static_assert(R == 8 && U == 1, "preloaded twiddles serve radix-8 stages of one butterfly per thread");
+            const float2 w1 = wc[3 * (SI - 1)], w2 = wc[3 * (SI - 1) + 1], w4 = wc[3 * (SI - 1) + 2];
+            const float2 w3 = cmul(w1, w2);
+            x[1] = cmul(x[1], w1);
+            x[2] = cmul(x[2], w2);
+            x[3] = cmul(x[3], w3);
+            x[4] = cmul(x[4], w4);
+            x[5] = cmul(x[5], cmul(w1, w4));
+            x[6] = cmul(x[6], cmul(w2, w4));
+            x[7] = cmul(x[7], cmul(w3, w4));
+        } else if constexpr (NS > 1 && TW7) {
             static_assert(R == 8, "only the leading stage may use radix 2 or 4");
 #pragma unroll
             for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], twiddle_stage8<INV>(tw, NS, r, k));
@@ -203,11 +219,33 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
     }
 }
 
-template <int M, int NS, bool INV, bool TW7, class S>
-__device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
+template <int M, int NS, bool INV, bool TW7, bool WC, int SI, class S>
+__device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm,
+                                           const float2* wc) {
     constexpr int R = (NS == 1) ? FirstRadix<M>::value : 8;
-    fft_stage<M, R, NS, INV, TW7, S>(v, t, tw, sm);
-    if constexpr (NS * R < M) fft_stages<M, NS * R, INV, TW7, S>(v, t, tw, sm);
+    fft_stage<M, R, NS, INV, TW7, WC, SI, S>(v, t, tw, sm, wc);
+    if constexpr (NS * R < M) fft_stages<M, NS * R, INV, TW7, WC, SI + 1, S>(v, t, tw, sm, wc);
+}
+
+// Number of twiddled (NS > 1) stages of an M-point transform.
+template <int M>
+constexpr int twiddled_stages() {
+    int n = 0;
+    for (int ns = FirstRadix<M>::value; ns < M; ns *= 8) ++n;
+    return n;
+}
+// Loads the w^1, w^2, w^4 of thread t's butterfly for every twiddled stage of an
+// M-point transform (8 values per thread) into wc[3 * twiddled_stages<M>()].
+template <int M, bool INV>
+__device__ __forceinline__ void load_stage_twiddles(int t, const float2* __restrict__ tw, float2* wc) {
+    int ns = FirstRadix<M>::value;
+#pragma unroll
+    for (int si = 0; si < twiddled_stages<M>(); ++si, ns *= 8) {
+        const int k = t & (ns - 1);
+        wc[3 * si] = twiddle_stage8<INV>(tw, ns, 1, k);
+        wc[3 * si + 1] = twiddle_stage8<INV>(tw, ns, 2, k);
+        wc[3 * si + 2] = twiddle_stage8<INV>(tw, ns, 4, k);
+    }
 }
 
 // In-register/shared FFT of length M (8 <= M <= TW).  Precondition: v[i] =
@@ -218,7 +256,15 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[8], int t, const float2* 
 template <int M, bool INV, bool TW7 = false, class S>
 __device__ __forceinline__ void fft_line(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm) {
     static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
-    fft_stages<M, 1, INV, TW7, S>(v, t, tw, sm);
+    fft_stages<M, 1, INV, TW7, false, 0, S>(v, t, tw, sm, nullptr);
+}
+
+// The same with the stage twiddles preloaded by load_stage_twiddles<M, INV>.
+template <int M, bool INV, class S>
+__device__ __forceinline__ void fft_line_wc(float2 (&v)[8], int t, const float2* __restrict__ tw, const S& sm,
+                                            const float2* wc) {
+    static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
+    fft_stages<M, 1, INV, false, true, 0, S>(v, t, tw, sm, wc);
 }
 
 }  // namespace hermes

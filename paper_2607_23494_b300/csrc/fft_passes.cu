@@ -293,6 +293,8 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         ac::cp_async_wait_all();
         __syncthreads();
     }
+    float2 wc[3 * twiddled_stages<N>()];  // the thread's stage twiddles, the same for every window
+    load_stage_twiddles<N, true>(t, tb.tw, wc);
     const int nbp = wb.nbp;
     for (int g = 0; g < wb.S; g += 4) {
         // radial factors of windows g..g+3 at every element: one 16-byte load each
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 v[i] = cscale(v0[i], j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
-            fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
+            fft_line_wc<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col}, wc);
             float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
 #pragma unroll
             for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[i];
