@@ -362,6 +362,8 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
         ac::bulk_g2s(stage, work + line0 * H, STAGE, &full[0]);
     }
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
+    float2 wc[3 * twiddled_stages<M>() + 1];  // the thread's stage twiddles (+1: M = 8 has none)
+    load_stage_twiddles<M, true>(t, tw, wc);
     float2 d2[8], wk[8];  // the thread's delta pairs and split twiddles e^{+2 pi i k / N}, k = t + iT
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
             const float2 c = cmul(wk[i], csub(xk, xc));
             v[i] = make_float2(a.x - c.y, a.y + c.x);
         }
-        fft_line<M, true>(v, t, tw, sm);
+        fft_line_wc<M, true>(v, t, tw, sm, wc);
         float acc = 0.0f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc = fmaf(d2[i].x, v[i].x, fmaf(d2[i].y, v[i].y, acc));

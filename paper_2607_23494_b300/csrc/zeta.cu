@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     auto trow = [&](int i) {
         return i < 4 ? qlo + i * (T * W) * RS : ((t == 0 && i == 4) ? col * RS : qhi - i * (T * W) * RS);
     };
+    float2 wc[3 * twiddled_stages<N>()];  // the thread's stage twiddles, the same for every bin
+    load_stage_twiddles<N, true>(t, tb.tw, wc);
     const int nbp = hb.nbp;
     for (int g = 0; g < hb.S; g += 4) {
         float4 tv[8];  // radial factors of bins g..g+3: one 16-byte load per element
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 v[i] = cscale(v0[i], j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
-            fft_line<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col});
+            fft_line_wc<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col}, wc);
             float2* dst = fields + (size_t)b * n3 + (size_t)ky * N + kz;
 #pragma unroll
             for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N] = v[i];
