@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
         }
     const int rounds = (S + GB - 1) / GB;
     int since_flush = 0;
+    float2 wc[3 * twiddled_stages<N>()];  // the thread's stage twiddles, the same for every bin line
+    load_stage_twiddles<N, true>(t, tw, wc);
     // fetch the S bin lines and the delta line of `line` by bulk copies
     auto fetch = [&](size_t ln, int slot) {
         ac::mbar_expect_tx(&full, (uint32_t)(S * N * sizeof(float2) + N * sizeof(float)));
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
                 for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
             }
             const SmemZLine<N> sm{{smem + b * LPZ}, bb};  // threads of group bb only
-            fft_line<N, true>(v, t, tw, sm);
+            fft_line_wc<N, true>(v, t, tw, sm, wc);
 #pragma unroll
             for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
         }
