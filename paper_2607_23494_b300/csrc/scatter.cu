@@ -527,27 +527,41 @@ __global__ void __launch_bounds__(256) k_selfpair(const float* __restrict__ pos,
     for (int e = threadIdx.x; e < P3; e += blockDim.x) part[(size_t)e * gridDim.x + blockIdx.x] = tot[e];
 }
 
+// Sum of one row by a block of kReduceThreads threads in a fixed order: each thread
+// keeps 8 independent partial sums (8 loads in flight instead of one dependent
+// chain), combined pairwise, then a block reduction.  Result valid in thread 0.
+constexpr int kReduceThreads = 1024;
+__device__ __forceinline__ double row_sum(const double* __restrict__ row, int cols, double* red) {
+    constexpr int U = 8, B = kReduceThreads;
+    double a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) a[j] = 0.0;
+    int c = threadIdx.x;
+    for (; c + (U - 1) * B < cols; c += U * B) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) a[j] += row[c + j * B];
+    }
+    for (; c < cols; c += B) a[0] += row[c];
+    const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    return block_sum_double(s, red);
+}
+
 // out[r] = sum_c part[r*cols + c], one block per row (deterministic order).
-__global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ part, int cols,
-                                                     double* __restrict__ out) {
-    __shared__ double red[8];
-    const double* row = part + (size_t)blockIdx.x * cols;
-    double s = 0.0;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += row[c];
-    s = block_sum_double(s, red);
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_rows(const double* __restrict__ part, int cols,
+                                                                double* __restrict__ out) {
+    __shared__ double red[kReduceThreads / 32];
+    const double s = row_sum(part + (size_t)blockIdx.x * cols, cols, red);
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 // Row r of part (cols wide) summed into out[(r / S) * out_stride + r % S]: the
 // rows of a batched launch are [catalogue][window] and land in a [catalogue][...]
 // result array.
-__global__ void __launch_bounds__(256) k_reduce_rows_strided(const double* __restrict__ part, int cols, int S,
-                                                             double* __restrict__ out, int out_stride) {
-    __shared__ double red[8];
-    const double* row = part + (size_t)blockIdx.x * cols;
-    double s = 0.0;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) s += row[c];
-    s = block_sum_double(s, red);
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_rows_strided(const double* __restrict__ part, int cols,
+                                                                        int S, double* __restrict__ out,
+                                                                        int out_stride) {
+    __shared__ double red[kReduceThreads / 32];
+    const double s = row_sum(part + (size_t)blockIdx.x * cols, cols, red);
     if (threadIdx.x == 0) out[(size_t)(blockIdx.x / S) * out_stride + blockIdx.x % S] = s;
 }
 
@@ -674,7 +688,7 @@ cudaError_t launch_reduce_rows(const double* part, int rows, int cols, double* o
                                const Tracer& tr) {
     if (rows <= 0) return cudaSuccess;
     tr(K_REDUCE, 0, st);
-    k_reduce_rows<<<rows, 256, 0, st>>>(part, cols, out);
+    k_reduce_rows<<<rows, kReduceThreads, 0, st>>>(part, cols, out);
     tr(K_REDUCE, 1, st);
     return cudaGetLastError();
 }
@@ -718,7 +732,7 @@ cudaError_t launch_reduce_rows_strided(const double* part, int rows, int cols, i
                                        cudaStream_t st, const Tracer& tr) {
     if (rows <= 0) return cudaSuccess;
     tr(K_REDUCE, 0, st);
-    k_reduce_rows_strided<<<rows, 256, 0, st>>>(part, cols, S, out, out_stride);
+    k_reduce_rows_strided<<<rows, kReduceThreads, 0, st>>>(part, cols, S, out, out_stride);
     tr(K_REDUCE, 1, st);
     return cudaGetLastError();
 }
