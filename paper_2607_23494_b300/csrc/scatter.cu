@@ -447,6 +447,71 @@ __global__ void __launch_bounds__(256) k_weight_sums(const float* __restrict__ w
 // Self-pair overlap table.  Each warp stages 32 points' per-axis overlaps in
 // shared memory; every lane owns table entries e = lane + 32k and accumulates
 // them over the staged points (float32), then the block sums in float64.
+// p <= 4: every thread accumulates the whole table (P^3 <= 64 floats) over its own
+// points as the outer product w_i^2 s_x (x) s_y (x) s_z, with no shared staging;
+// the block then reduces entry by entry (warp shuffles, then the warps in a fixed
+// order).  Same output layout as k_selfpair.
+template <int P>
+__global__ void __launch_bounds__(256) k_selfpair_reg(const float* __restrict__ pos, const float* __restrict__ w,
+                                                      int64_t n, const int64_t* __restrict__ offs, float s, int N,
+                                                      double* __restrict__ part) {
+    constexpr int P3 = P * P * P;
+    if (offs) {  // batched: blockIdx.y = catalogue, as k_weight_sums
+        const int64_t lo = offs[blockIdx.y];
+        n = offs[blockIdx.y + 1] - lo;
+        pos += 3 * lo;
+        if (w) w += lo;
+        part += (size_t)blockIdx.y * P3 * gridDim.x;
+    }
+    __shared__ double tot[8][P3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float acc[P3];
+#pragma unroll
+    for (int e = 0; e < P3; ++e) acc[e] = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float b[3][P], sv[3][P];
+        int f;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ok &= node_rule<P>(__ldg(pos + 3 * i + d), s, N, 1, f, b[d]);
+        const float wi = w ? __ldg(w + i) : 1.0f;
+        const float w2 = ok ? wi * wi : 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                float sacc = 0.0f;
+#pragma unroll
+                for (int o = 0; o + a < P; ++o) sacc = fmaf(b[d][o], b[d][o + a], sacc);
+                sv[d][a] = sacc;
+            }
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const float xa = w2 * sv[0][a];
+#pragma unroll
+            for (int bb = 0; bb < P; ++bb) {
+                const float xab = xa * sv[1][bb];
+#pragma unroll
+                for (int c = 0; c < P; ++c) acc[(a * P + bb) * P + c] = fmaf(xab, sv[2][c], acc[(a * P + bb) * P + c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < P3; ++e) {
+        float v = acc[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[wid][e] = (double)v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P3; e += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += tot[q][e];
+        part[(size_t)e * gridDim.x + blockIdx.x] = t;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_selfpair(const float* __restrict__ pos, const float* __restrict__ w,
                                                   int64_t n, const int64_t* __restrict__ offs, float s, int N,
@@ -674,9 +739,12 @@ cudaError_t launch_selfpair(int N, int p, const float* pos, const float* w, int6
     tr(K_SELFPAIR, 0, st);
     const dim3 g(nblk, offs ? ncat : 1);
     switch (p) {
+#define HERMES_SPR(P) \
+    case P: k_selfpair_reg<P><<<g, 256, 0, st>>>(pos, w, n, offs, s, N, part); break;
 #define HERMES_SP(P) \
     case P: k_selfpair<P><<<g, 256, 0, st>>>(pos, w, n, offs, s, N, part); break;
-        HERMES_SP(1) HERMES_SP(2) HERMES_SP(3) HERMES_SP(4) HERMES_SP(5) HERMES_SP(6) HERMES_SP(7) HERMES_SP(8)
+        HERMES_SPR(1) HERMES_SPR(2) HERMES_SPR(3) HERMES_SPR(4) HERMES_SP(5) HERMES_SP(6) HERMES_SP(7) HERMES_SP(8)
+#undef HERMES_SPR
 #undef HERMES_SP
         default: return cudaErrorInvalidValue;
     }
