@@ -444,9 +444,6 @@ __global__ void __launch_bounds__(256) k_weight_sums(const float* __restrict__ w
     }
 }
 
-// Self-pair overlap table.  Each warp stages 32 points' per-axis overlaps in
-// shared memory; every lane owns table entries e = lane + 32k and accumulates
-// them over the staged points (float32), then the block sums in float64.
 // p <= 4: every thread accumulates the whole table (P^3 <= 64 floats) over its own
 // points as the outer product w_i^2 s_x (x) s_y (x) s_z, with no shared staging;
 // the block then reduces entry by entry (warp shuffles, then the warps in a fixed
@@ -512,6 +509,9 @@ __global__ void __launch_bounds__(256) k_selfpair_reg(const float* __restrict__ 
     }
 }
 
+// Self-pair overlap table (p > 4).  Each warp stages 32 points' per-axis overlaps in
+// shared memory; every lane owns table entries e = lane + 32k and accumulates
+// them over the staged points (float32), then the block sums in float64.
 template <int P>
 __global__ void __launch_bounds__(256) k_selfpair(const float* __restrict__ pos, const float* __restrict__ w,
                                                   int64_t n, const int64_t* __restrict__ offs, float s, int N,
