@@ -12,7 +12,6 @@
 // host in float64 and laid out so each load is coalesced; the inverse uses
 // conjugates.
 #pragma once
-#include <type_traits>
 #include "common.cuh"
 
 namespace hermes {
@@ -146,6 +145,19 @@ struct FirstRadix {
     static constexpr int value = (lg % 3 == 0) ? 8 : (lg % 3 == 1 ? 2 : 4);
 };
 
+// x[r] *= w^r for r = 1..7 from w^1, w^2, w^4 (w^3, w^5, w^6, w^7 as products of at
+// most two of them; relative error a few float32 ulps).
+__device__ __forceinline__ void twiddle_from3(float2 (&x)[8], float2 w1, float2 w2, float2 w4) {
+    const float2 w3 = cmul(w1, w2);
+    x[1] = cmul(x[1], w1);
+    x[2] = cmul(x[2], w2);
+    x[3] = cmul(x[3], w3);
+    x[4] = cmul(x[4], w4);
+    x[5] = cmul(x[5], cmul(w1, w4));
+    x[6] = cmul(x[6], cmul(w2, w4));
+    x[7] = cmul(x[7], cmul(w3, w4));
+}
+
 // One Stockham stage.  v[u + r*U] is input r of butterfly b = t + u*T.
 // TW7: load all seven radix-8 twiddles instead of three (for passes whose
 // loads are already hidden and that are short of issue slots).
@@ -169,32 +181,16 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[8], int t, const float2* _
         for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
         if constexpr (NS > 1 && WC) {
             static_assert(R == 8 && U == 1, "preloaded twiddles serve radix-8 stages of one butterfly per thread");
-            const float2 w1 = wc[3 * (SI - 1)], w2 = wc[3 * (SI - 1) + 1], w4 = wc[3 * (SI - 1) + 2];
-            const float2 w3 = cmul(w1, w2);
-            x[1] = cmul(x[1], w1);
-            x[2] = cmul(x[2], w2);
-            x[3] = cmul(x[3], w3);
-            x[4] = cmul(x[4], w4);
-            x[5] = cmul(x[5], cmul(w1, w4));
-            x[6] = cmul(x[6], cmul(w2, w4));
-            x[7] = cmul(x[7], cmul(w3, w4));
+            twiddle_from3(x, wc[3 * (SI - 1)], wc[3 * (SI - 1) + 1], wc[3 * (SI - 1) + 2]);
         } else if constexpr (NS > 1 && TW7) {
             static_assert(R == 8, "only the leading stage may use radix 2 or 4");
 #pragma unroll
             for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], twiddle_stage8<INV>(tw, NS, r, k));
         } else if constexpr (NS > 1) {
             static_assert(R == 8, "only the leading stage may use radix 2 or 4");
-            // w^1, w^2, w^4 from the table; w^3, w^5, w^6, w^7 as products of at most two of
-            // them (three loads instead of seven; relative error a few float32 ulps)
-            const float2 w1 = twiddle_stage8<INV>(tw, NS, 1, k), w2 = twiddle_stage8<INV>(tw, NS, 2, k);
-            const float2 w4 = twiddle_stage8<INV>(tw, NS, 4, k), w3 = cmul(w1, w2);
-            x[1] = cmul(x[1], w1);
-            x[2] = cmul(x[2], w2);
-            x[3] = cmul(x[3], w3);
-            x[4] = cmul(x[4], w4);
-            x[5] = cmul(x[5], cmul(w1, w4));
-            x[6] = cmul(x[6], cmul(w2, w4));
-            x[7] = cmul(x[7], cmul(w3, w4));
+            // three table loads instead of seven
+            twiddle_from3(x, twiddle_stage8<INV>(tw, NS, 1, k), twiddle_stage8<INV>(tw, NS, 2, k),
+                          twiddle_stage8<INV>(tw, NS, 4, k));
         }
         dftR<R, INV>(x);
 #pragma unroll
