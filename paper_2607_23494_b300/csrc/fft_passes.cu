@@ -384,23 +384,12 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
         float2 v[8], xm[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = X[t + i * T];
-        if constexpr (T == 32) {
-            // one line per warp: X_{M-k} of element k = t + iT sits in lane 32-t, slot 7-i
-            // (lane 0 holds its own partners in slot 8-i; X_M = 0)
+        // the partner X_{M-k} of element k = t + iT comes from the stage too (a warp's reads are
+        // one contiguous descending run; X_M = 0); this beats 16 warp shuffles
 #pragma unroll
-            for (int i = 0; i < 8; ++i) xm[i] = make_float2(__shfl_sync(0xffffffffu, v[7 - i].x, (32 - t) & 31),
-                                                          __shfl_sync(0xffffffffu, v[7 - i].y, (32 - t) & 31));
-            if (t == 0) {
-                xm[0] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = 1; i < 8; ++i) xm[i] = v[8 - i];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = t + i * T;
-                xm[i] = (k == 0) ? make_float2(0.f, 0.f) : X[M - k];
-            }
+        for (int i = 0; i < 8; ++i) {
+            const int k = t + i * T;
+            xm[i] = (k == 0) ? make_float2(0.f, 0.f) : X[M - k];
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
