@@ -97,14 +97,16 @@ __device__ __forceinline__ float2 twiddle_stage8(const float2* __restrict__ tw, 
 
 // Shared-memory line layouts -------------------------------------------------
 // Strided tile: W lines stored position-major, element (pos, col) at
-// pos*W + col, plus 4 padding slots after every 8 rows (bank skew for the
-// Stockham write patterns of 512-point tiles).
+// pos*W + col, plus 8 padding slots after every 8 rows.  With W = 8 the first
+// exchange of a 512-point transform stores rows 8t + r from the four t of a warp;
+// the 8-slot skew puts the two t of each half-warp on disjoint bank pairs (a
+// 4-slot skew overlapped half of them: twice the minimum wavefronts).
 template <int W>
 struct SmemStrided {
     float2* p;
     int col;
-    static constexpr int words(int n) { return n * W + (n / 8) * 4; }
-    __device__ __forceinline__ int at(int pos) const { return pos * W + col + (pos >> 3) * 4; }
+    static constexpr int words(int n) { return n * W + (n / 8) * 8; }
+    __device__ __forceinline__ int at(int pos) const { return pos * W + col + (pos >> 3) * 8; }
     __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
     __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
     __device__ __forceinline__ static void sync() { __syncthreads(); }  // a tile spans the block
