@@ -144,9 +144,9 @@ def gen_catalogue3(seed: int):
 # passes at 512^3 on a 5-window launch of the current kernels (summary and command in
 # profiles/xi_512_inverse_passes_ncu.md): bytes per launch (read once per launch) and per window.
 NCU_TRAFFIC_512 = {
-    "inv_x_window": {"per_launch": 0.561232e9, "per_window": 2.634594e9 / 5},
-    "inv_y": {"per_launch": 0.0, "per_window": (2.684522e9 + 2.630081e9) / 5},
-    "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221295e9 + 0.005049e9) / 5},
+    "inv_x_window": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
+    "inv_y": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
+    "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
 }
 
 
