@@ -58,6 +58,7 @@ __all__ = [
     "kappa_from_K", "shot_noise", "xi_multipoles", "zeta_multipoles", "lm_modes",
     "keff_pair_direct", "xi_brute_force", "direct_convolution", "annulus_avg_j0", "slab_avg_cos",
     "window_cyl", "xi_cylinders", "xi_randoms", "smoothing_window", "density_at", "density_marks",
+    "window_xi_at", "window_zeta_at", "planted_xi", "planted_zeta",
 ]
 
 
@@ -375,6 +376,92 @@ def window_zeta(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int, m:
     K = 4.0 * np.pi * (1j ** ell) * rad * Y * phi3
     K[nyq] = 0.0
     return K
+
+
+def _modes_at(N: int, L: float, p: int, modes):
+    """Signed integer modes n [m,3], |n|^2, |k|, Phi^(n) and the Nyquist mask of a mode list."""
+    n = np.asarray(modes, dtype=np.int64).reshape(-1, 3)
+    q = np.sum(n * n, axis=1)
+    k = (2.0 * np.pi / L) * np.sqrt(q.astype(np.float64))
+    ph = phi_hat_1d(N, p)
+    phi3 = ph[n[:, 0] % N] * ph[n[:, 1] % N] * ph[n[:, 2] % N]
+    nyq = np.any(np.abs(n) == N // 2, axis=1)
+    return n, q, k, phi3, nyq
+
+
+def window_xi_at(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int, modes) -> np.ndarray:
+    """window_xi evaluated only at the listed signed modes (for grids too large to tabulate).
+
+    Same definition: (2l+1) i^l <j_l>_b(k) L_l(n_z/|n|) Phi^(n), zero on Nyquist planes;
+    <j_l>_b by Eq. (Wshell_k) for l = 0 and by the Gauss-Legendre average otherwise.
+    """
+    if ell % 2:
+        raise ValueError("odd l gives an identically zero auto-multipole")
+    n, q, k, phi3, nyq = _modes_at(N, L, p, modes)
+    rad = shell_window_l0(k, r_lo, r_hi) if ell == 0 else shell_avg_jl(ell, k, r_lo, r_hi)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = np.where(q > 0, n[:, 2] / np.sqrt(q.astype(np.float64)), 0.0)
+    K = (2 * ell + 1) * np.real(1j ** ell) * rad * sps.eval_legendre(ell, mu) * phi3
+    return np.where(nyq, 0.0, K)
+
+
+def window_zeta_at(N: int, L: float, p: int, r_lo: float, r_hi: float, ell: int, m: int, modes) -> np.ndarray:
+    """window_zeta evaluated only at the listed signed modes: 4 pi i^l <j_l>_b Y_lm(k^) Phi^."""
+    n, q, k, phi3, nyq = _modes_at(N, L, p, modes)
+    rad = shell_window_l0(k, r_lo, r_hi) if ell == 0 else shell_avg_jl(ell, k, r_lo, r_hi)
+    r = np.sqrt(q.astype(np.float64))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ct = np.where(q > 0, n[:, 2] / r, 1.0)
+    theta = np.arccos(np.clip(ct, -1.0, 1.0))
+    phi = np.mod(np.arctan2(n[:, 1].astype(np.float64), n[:, 0].astype(np.float64)), 2 * np.pi)
+    K = 4.0 * np.pi * (1j ** ell) * rad * sps.sph_harm_y(ell, m, theta, phi) * phi3
+    return np.where(nyq, 0.0, K)
+
+
+def planted_xi(N: int, L: float, p: int, r_edges, ells, modes) -> np.ndarray:
+    """xi_l of the planted field delta_l = sum_j cos(2 pi n_j.l / N) with no catalogue.
+
+    delta^ is N^3/2 at +-n_j and zero elsewhere, so Eq. (pair-counting-kspace) gives
+    (1/N^3) sum_l delta delta~ = sum_j K(n_j) / 2 exactly (distinct n_j, none the
+    negative of another, none zero).  Returns [n_ells, n_bins].
+    """
+    nb = len(r_edges) - 1
+    out = np.zeros((len(ells), nb))
+    for a, ell in enumerate(ells):
+        for b in range(nb):
+            out[a, b] = 0.5 * float(np.sum(window_xi_at(N, L, p, r_edges[b], r_edges[b + 1], ell, modes)))
+    return out
+
+
+def planted_zeta(N: int, L: float, p: int, r_edges, l_max: int, modes) -> np.ndarray:
+    """zeta_l of delta_l = sum_{s in S} cos(2 pi s.l / N) as a finite sum over mode triples.
+
+    a_{b lm}(l) = (1/2) sum_{n in +-S} K_{b lm}(n) e^{2 pi i n.l/N}, and the cell sum of
+    Eq. (2-fold-translation) keeps the triples with n' + n'' = n:
+      zeta_l(b1, b2) = 1/(4 pi) (1/8) sum_m sum_{n, n', n'' in +-S, n' + n'' = n} conj(K_b1(n)) K_b2(n'),
+    all m in [-l, l] written out (no conjugation shortcut).  Returns [l_max+1, nb, nb].
+    """
+    S = [tuple(int(x) for x in s) for s in modes]
+    pm = S + [tuple(-x for x in s) for s in S]
+    members = {tuple(x % N for x in n) for n in pm}
+    if len(members) != len(pm):
+        raise ValueError("planted modes must be distinct and none the negative of another (mod N)")
+    # index pairs (n, n') of +-S whose difference n'' = n - n' is also in +-S (modes are
+    # periodic in N: the cell sum of e^{2 pi i (n' + n'' - n).l/N} is N^3 when n' + n'' = n mod N)
+    trip = [(a, c) for a, n in enumerate(pm) for c, n1 in enumerate(pm)
+            if tuple((x - y) % N for x, y in zip(n, n1)) in members]
+    nb = len(r_edges) - 1
+    out = np.zeros((l_max + 1, nb, nb))
+    for ell in range(l_max + 1):
+        for m in range(-ell, ell + 1):
+            Kb = [window_zeta_at(N, L, p, r_edges[b], r_edges[b + 1], ell, m, pm) for b in range(nb)]
+            for b1 in range(nb):
+                for b2 in range(nb):
+                    tot = 0.0
+                    for (a, c) in trip:
+                        tot += np.conj(Kb[b1][a]) * Kb[b2][c]
+                    out[ell, b1, b2] += (tot / 8.0 / (4.0 * np.pi)).real
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -13,9 +13,9 @@ import scipy.special as sps
 from oracle import hermes_oracle as O
 
 
-def test_forward_fft_matches_direct_dft():
-    N = 4
-    rng = np.random.default_rng(0)
+@pytest.mark.parametrize("N", [4, 8])
+def test_forward_fft_matches_direct_dft(N):
+    rng = np.random.default_rng(N)
     d = rng.standard_normal((N, N, N))
     got = O.forward(d)
     l = np.arange(N)

@@ -151,3 +151,47 @@ def test_zeta_symmetric_and_real():
     assert imag < 1e-10 * max(1.0, np.abs(z).max())
     for ell in range(3):
         np.testing.assert_allclose(z[ell], z[ell].T, rtol=1e-10, atol=1e-14)
+
+
+def test_windows_at_listed_modes_equal_the_full_grid():
+    # the mode-list forms (used where a grid is too large to tabulate) give the
+    # full-grid windows entry by entry, Nyquist zeros and n = 0 included
+    import itertools
+    N, L, p = 16, 80.0, 4
+    f = O.signed_freqs(N)
+    modes = np.array(list(itertools.product(f, f, f)))
+    idx = tuple((modes % N).T)
+    for ell in (0, 2, 4):
+        K = O.window_xi(N, L, p, 10.0, 16.0, ell)
+        np.testing.assert_allclose(O.window_xi_at(N, L, p, 10.0, 16.0, ell, modes), K[idx], rtol=1e-12, atol=1e-15)
+    for ell, m in ((0, 0), (1, -1), (3, 2), (6, -5)):
+        K = O.window_zeta(N, L, p, 6.0, 13.0, ell, m)
+        np.testing.assert_allclose(O.window_zeta_at(N, L, p, 6.0, 13.0, ell, m, modes), K[idx],
+                                   rtol=1e-12, atol=1e-15)
+
+
+def test_planted_xi_sum_of_modes_matches_cell_contraction():
+    # several planted modes: the cross terms vanish and each mode adds K(n_j)/2
+    N, L, p = 16, 80.0, 4
+    modes = [(1, 2, 3), (5, -2, 1), (-7, 3, 6), (2, 0, 0)]
+    d = sum(_mode(N, s) for s in modes)
+    dh = O.forward(d)
+    edges = [3.0, 8.0, 14.0, 25.0]
+    ref = O.planted_xi(N, L, p, edges, (0, 2, 4), modes)
+    for a, ell in enumerate((0, 2, 4)):
+        for b in range(3):
+            K = O.window_xi(N, L, p, edges[b], edges[b + 1], ell)
+            assert O.xi_cell_contraction(d, dh, K) == pytest.approx(ref[a, b], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("N,L,S,edges,l_max", [
+    (8, 40.0, [(1, 0, 2), (2, 1, -1), (-3, -1, -1)], [5.0, 10.0, 16.0], 3),
+    (16, 80.0, [(1, 2, -3), (3, -1, 2), (-4, -1, 1)], [4.0, 9.0, 15.0, 22.0], 4),
+])
+def test_planted_zeta_triples_match_explicit_harmonic_fields(N, L, S, edges, l_max):
+    # the finite triple sum against the oracle's explicit inverse transforms of every m
+    p = 4
+    d = sum(_mode(N, s) for s in S)
+    got, imag = O.zeta_multipoles(d, N, L, p, edges, l_max)
+    assert imag < 1e-10
+    np.testing.assert_allclose(O.planted_zeta(N, L, p, edges, l_max, S), got, rtol=1e-10, atol=1e-14)
