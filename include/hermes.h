@@ -93,13 +93,15 @@ int hermes_set_stream(hermes_ctx *ctx, void *cuda_stream);
 int hermes_assign(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
 
 /*
- * hermes_assign for callers that cannot allocate GPU memory at call time:
- * code running while a CUDA stream is being captured into a graph, serving
- * loops that must not stall on the allocator, or hosts whose device memory is
- * owned by another allocator (a framework's caching pool).  It does what
- * hermes_assign does, with the same arguments and errors, but calls no
- * cudaMalloc, cudaFree or other allocating routine.  (The paper has no
- * counterpart; this is an interface of this library only.)
+ * hermes_assign for callers that cannot allocate GPU memory at call time.  Some
+ * hosts own all device memory through an allocator of their own (a framework's
+ * caching pool that has reserved most of the GPU, an embedding application with a
+ * fixed memory budget): a cudaMalloc behind their back may fail or push them out
+ * of memory, and a cudaFree waits for the whole device, stalling every stream of
+ * the host.  Others run a serving loop whose latency must not include allocator
+ * calls.  This entry point does what hermes_assign does, with the same arguments
+ * and errors, but calls no cudaMalloc, cudaFree or other allocating routine.
+ * (The paper has no counterpart; this is an interface of this library only.)
  *   - pos / w must already be device memory of the context's device (no host
  *     staging copy); HERMES_DEVICE_PTR is implied, HERMES_WRAP is honoured.
  *   - The block partial sums of the weight and self-pair reductions use one
@@ -113,6 +115,8 @@ int hermes_assign(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, 
  *   - Every call on a device shares the array: calls whose work overlaps on the
  *     GPU (other contexts on other streams included) race on it; serialise them.
  *     Each call overwrites every entry it reads, so no state carries over.
+ *   - Like hermes_assign, the call waits for the context's stream twice (it reads
+ *     the range flag and the weight sums on the host before the transform).
  * The context must have been created (hermes_create allocates the field).
  */
 int hermes_assign_noalloc(hermes_ctx *ctx, const float *pos, const float *w, int64_t n, unsigned flags);
@@ -349,6 +353,25 @@ int hermes_debug_set_delta(hermes_ctx *ctx, const float *host_delta);
  * memory.  HERMES_WRAP in flags as for hermes_assign.
  */
 int hermes_debug_nodes(hermes_ctx *ctx, const float *pos, int64_t n, unsigned flags, int *first, float *wts);
+
+/*
+ * Failure-detection check of the bounded device waits (no counterpart in the
+ * paper).  Runs a one-thread kernel that waits, with the same bounded mbarrier
+ * wait that guards every bulk-copy pipeline, on a barrier phase that nothing
+ * completes and for which no copy is issued.  The wait gives up after one second
+ * of wall time, the kernel records it in the context's error word and exits, and
+ * the call returns HERMES_ERR_TIMEOUT.  The context stays usable afterwards.
+ */
+int hermes_debug_bounded_wait(hermes_ctx *ctx);
+
+/*
+ * Failure-detection hook for allocation errors (no counterpart in the paper):
+ * the next `count` device allocations made by the library, in any context of
+ * this process, report out of memory without allocating (count <= 0 disarms).
+ * The failing call returns HERMES_ERR_NOMEM and keeps what it held before.
+ * Returns the previous count.  No device is needed.
+ */
+int hermes_debug_fail_allocs(int count);
 
 /* sums[0] = sum w, sums[1] = sum w^2, and the p^3 self-pair table (float64). */
 int hermes_debug_get_sums(hermes_ctx *ctx, double *sums2, double *selfpair_p3);

@@ -1,8 +1,9 @@
 """hermes_assign_noalloc: the scatter entry point for callers that cannot allocate
-GPU memory while they run (a stream being captured into a CUDA graph, a serving
-loop that must not wait on the allocator, device memory owned by a framework's
-caching pool).  Its reduction scratch is a fixed static device array instead of
-context buffers that grow on demand.
+GPU memory while they run -- hosts whose device memory belongs to an allocator of
+their own (a framework's caching pool, a fixed budget), where a cudaMalloc behind
+their back may fail and a cudaFree stalls every stream, and serving loops that must
+not wait on the allocator.  Its reduction scratch is a fixed static device array
+instead of context buffers that grow on demand.
 
 Through the C ABI, two calls in a row must reproduce what hermes_assign gives for
 the same inputs (resident field, sums, self-pair table and the xi_l measured from
