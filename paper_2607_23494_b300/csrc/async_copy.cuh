@@ -1,5 +1,5 @@
 // mbarrier and bulk-copy (TMA, non-tensor) helpers for sm_100-family GPUs.
-// Every wait is bounded: it gives up after about a second and reports failure,
+// Every wait is bounded: it gives up after one second and reports failure,
 // so a kernel can flag HERMES_ERR_TIMEOUT instead of hanging the device.
 #pragma once
 #include <cuda_runtime.h>
@@ -25,11 +25,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Completion of phase `parity`; false if it did not complete within the bound.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Completion of phase `parity`; false if it did not complete within one second of
+// wall time (the global nanosecond timer), or after 2^24 tries, whichever comes first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (int i = 0; i < (1 << 20); ++i)
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (int i = 0; i < (1 << 24); ++i) {
         if (mbar_try(b, parity)) return true;
+        if (globaltimer_ns() - t0 > 1000000000ull) return false;
+    }
     return false;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* b) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
 }
 // One arrival that also announces `bytes` of transactions (the issuing thread).
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {

@@ -141,13 +141,29 @@ int cuda_fail(hermes_ctx* c, cudaError_t e, const char* what) {
         if (_e != cudaSuccess) return cuda_fail(c, _e, what);   \
     } while (0)
 
+// Every device allocation of the library goes through here.  The test hook
+// hermes_debug_fail_allocs makes the next few report out of memory without
+// allocating, so the error paths can be exercised without exhausting a GPU.
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 template <class T>
 cudaError_t grow(T*& ptr, size_t& cap_bytes, size_t need_bytes) {
     if (need_bytes <= cap_bytes && ptr) return cudaSuccess;
     if (ptr) cudaFree(ptr);
     ptr = nullptr;
     cap_bytes = 0;
-    cudaError_t e = cudaMalloc((void**)&ptr, need_bytes);
+    cudaError_t e = dev_malloc((void**)&ptr, need_bytes);
     if (e == cudaSuccess) cap_bytes = need_bytes;
     return e;
 }
@@ -389,20 +405,20 @@ cudaError_t tiled_scratch(hermes_ctx* c, int64_t n) {
         c->ts_tile_of = nullptr;
         c->ts_perm = nullptr;
         c->ts_pts_cap = 0;
-        if ((e = cudaMalloc((void**)&c->ts_tile_of, (size_t)n * sizeof(int))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&c->ts_perm, (size_t)n * sizeof(int))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&c->ts_tile_of, (size_t)n * sizeof(int))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&c->ts_perm, (size_t)n * sizeof(int))) != cudaSuccess) return e;
         c->ts_pts_cap = (size_t)n;
     }
     if (!c->ts_tiles) {
         const size_t nt = (size_t)scatter_tiled_tiles(c->N);
-        if ((e = cudaMalloc((void**)&c->ts_tiles, (3 * nt + 1) * sizeof(int))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&c->ts_tiles, (3 * nt + 1) * sizeof(int))) != cudaSuccess) return e;
     }
     const size_t rf = scatter_tiled_region_floats(c->N, c->p);
     if (rf > c->ts_regions_cap) {
         cudaFree(c->ts_regions);
         c->ts_regions = nullptr;
         c->ts_regions_cap = 0;
-        if ((e = cudaMalloc((void**)&c->ts_regions, rf * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&c->ts_regions, rf * sizeof(float))) != cudaSuccess) return e;
         c->ts_regions_cap = rf;
     }
     return cudaSuccess;
@@ -460,14 +476,14 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
     const size_t n3 = (size_t)N * N * N;
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     c->stream = c->own_stream;
-    if (cudaMalloc((void**)&c->grid, n3 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->spec, (size_t)N * N * c->H * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->scal, 8 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->stab_d, 512 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->stab_f, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->err, sizeof(unsigned)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->tw, TW_ENTRIES * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
-    if (cudaMalloc((void**)&c->phi, N * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->grid, n3 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->spec, (size_t)N * N * c->H * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->scal, 8 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->stab_d, 512 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->stab_f, 512 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->err, sizeof(unsigned)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->tw, TW_ENTRIES * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    if (dev_malloc((void**)&c->phi, N * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     // multi-level twiddles tw[L + j] = e^{-2 pi i j / L} (L = 2, 4, ..., TW) and
     // Phi^(n) = sinc^{2p}(pi n / N), in float64, stored as float32
     std::vector<float2> tw(TW_ENTRIES, make_float2(0.f, 0.f));
@@ -588,8 +604,8 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
-            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
-            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
+            CK(dev_malloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(dev_malloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
             c->stage_cap = (size_t)n;
         }
         CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
@@ -739,7 +755,7 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     cudaFree(c->rad);
     c->rad = nullptr;
     c->n_bins = 0;
-    CK(cudaMalloc((void**)&c->rad, count_dev * sizeof(float)), "window tables");
+    CK(dev_malloc((void**)&c->rad, count_dev * sizeof(float)), "window tables");
     // the orders 0..l_max are the leading blocks of a cached table built for a larger l_max
     CK(cudaMemcpy(c->rad, tab->data(), count_dev * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
     c->edges.assign(r_edges, r_edges + n_edges);
@@ -1029,9 +1045,9 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
     float* dw = nullptr;
     int rc = HERMES_OK;
     unsigned herr = 0;
-    cudaError_t e = cudaMalloc((void**)&dpos, (size_t)n * 3 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&dfirst, (size_t)n * 3 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&dw, (size_t)n * 3 * p * sizeof(float));
+    cudaError_t e = dev_malloc((void**)&dpos, (size_t)n * 3 * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc((void**)&dfirst, (size_t)n * 3 * sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc((void**)&dw, (size_t)n * 3 * p * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(dpos, host_pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
@@ -1052,7 +1068,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms", "inv_z_store", "gather_marks"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms", "inv_z_store", "gather_marks", "wait_check"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -1087,6 +1103,21 @@ const char* hermes_kernel_name(int id) {
 }
 
 int64_t hermes_launch_count(const hermes_ctx* c) { return c ? c->launches : -1; }
+
+int hermes_debug_bounded_wait(hermes_ctx* c) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    CK(launch_wait_unarrived(c->err, st, c->tracer), "bounded wait");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "bounded wait");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on an mbarrier gave up");
+    return HERMES_OK;
+}
+
+int hermes_debug_fail_allocs(int count) { return g_fail_allocs.exchange(count < 0 ? 0 : count); }
 
 int hermes_debug_get_sums(hermes_ctx* c, double* sums2, double* selfpair) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
@@ -1296,11 +1327,11 @@ cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
         b->pos = nullptr;
         b->w = nullptr;
         b->pts_cap = 0;
-        if ((e = cudaMalloc((void**)&b->pos, (size_t)j.n_total * 3 * sizeof(float))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->w, (size_t)j.n_total * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->pos, (size_t)j.n_total * 3 * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->w, (size_t)j.n_total * sizeof(float))) != cudaSuccess) return e;
         b->pts_cap = (size_t)j.n_total;
     }
-    if (!b->offs && (e = cudaMalloc((void**)&b->offs, (MAX_CATALOGUES + 1) * sizeof(int64_t))) != cudaSuccess) return e;
+    if (!b->offs && (e = dev_malloc((void**)&b->offs, (MAX_CATALOGUES + 1) * sizeof(int64_t))) != cudaSuccess) return e;
     if (j.ncat > b->cat_cap) {
         cudaFree(b->grid);
         cudaFree(b->spec);
@@ -1316,12 +1347,12 @@ cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
         b->sp = nullptr;
         b->cat_cap = 0;
         const size_t k = (size_t)j.ncat;
-        if ((e = cudaMalloc((void**)&b->grid, k * n3 * sizeof(float))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->spec, k * (size_t)N * N * (N / 2) * sizeof(float2))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->scal, k * SCAL_STRIDE * sizeof(double))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->stab_f, k * STAB_STRIDE * sizeof(float))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->sums, k * 2 * sizeof(double))) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void**)&b->sp, k * 512 * sizeof(double))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->grid, k * n3 * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->spec, k * (size_t)N * N * (N / 2) * sizeof(float2))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->scal, k * SCAL_STRIDE * sizeof(double))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->stab_f, k * STAB_STRIDE * sizeof(float))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->sums, k * 2 * sizeof(double))) != cudaSuccess) return e;
+        if ((e = dev_malloc((void**)&b->sp, k * 512 * sizeof(double))) != cudaSuccess) return e;
         b->cat_cap = j.ncat;
     }
     const int p3 = c->p * c->p * c->p;
@@ -1789,8 +1820,8 @@ extern "C" int hermes_window_cylinders(hermes_ctx* c, const double* perp_edges, 
     c->cyl_perp = nullptr;
     c->cyl_par = nullptr;
     c->cyl_nperp = c->cyl_npar = 0;
-    CK(cudaMalloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "transverse table");
-    CK(cudaMalloc((void**)&c->cyl_par, par.size() * sizeof(float)), "line-of-sight table");
+    CK(dev_malloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "transverse table");
+    CK(dev_malloc((void**)&c->cyl_par, par.size() * sizeof(float)), "line-of-sight table");
     CK(cudaMemcpy(c->cyl_perp, perp.data(), perp.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
     CK(cudaMemcpy(c->cyl_par, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
     c->cyl_nperp = np;
@@ -1910,8 +1941,8 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
-            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
-            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
+            CK(dev_malloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(dev_malloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging weights");
             c->stage_cap = (size_t)n;
         }
         CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
@@ -1919,12 +1950,12 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
         dpos = c->stage_pos;
         dw = w ? c->stage_w : nullptr;
     }
-    if (!c->rgrid) CK(cudaMalloc((void**)&c->rgrid, n3 * sizeof(float)), "random field");
-    if (!c->rspec) CK(cudaMalloc((void**)&c->rspec, (size_t)N * N * (N / 2) * sizeof(float2)), "random spectrum");
-    if (!c->rstab_d) CK(cudaMalloc((void**)&c->rstab_d, 512 * sizeof(double)), "random self-pair table");
-    if (!c->rstab_f) CK(cudaMalloc((void**)&c->rstab_f, 512 * sizeof(float)), "random self-pair table");
+    if (!c->rgrid) CK(dev_malloc((void**)&c->rgrid, n3 * sizeof(float)), "random field");
+    if (!c->rspec) CK(dev_malloc((void**)&c->rspec, (size_t)N * N * (N / 2) * sizeof(float2)), "random spectrum");
+    if (!c->rstab_d) CK(dev_malloc((void**)&c->rstab_d, 512 * sizeof(double)), "random self-pair table");
+    if (!c->rstab_f) CK(dev_malloc((void**)&c->rstab_f, 512 * sizeof(float)), "random self-pair table");
     if (!c->rscal) {
-        CK(cudaMalloc((void**)&c->rscal, 8 * sizeof(double)), "random scalars");
+        CK(dev_malloc((void**)&c->rscal, 8 * sizeof(double)), "random scalars");
         const double one[8] = {0, 0, 1, 0, 0, 0, 0, 0};
         CK(cudaMemcpy(c->rscal, one, sizeof(one), cudaMemcpyHostToDevice), "random scalars");
     }
@@ -1998,8 +2029,8 @@ extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kin
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
-            CK(cudaMalloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
-            CK(cudaMalloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging marks");
+            CK(dev_malloc((void**)&c->stage_pos, (size_t)n * 3 * sizeof(float)), "staging positions");
+            CK(dev_malloc((void**)&c->stage_w, (size_t)n * sizeof(float)), "staging marks");
             c->stage_cap = (size_t)n;
         }
         CK(cudaMemcpyAsync(c->stage_pos, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyDefault, st), "copy positions");
@@ -2021,7 +2052,7 @@ extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kin
     cudaStreamSynchronize(st);
     cudaFree(c->smooth_tab);
     c->smooth_tab = nullptr;
-    CK(cudaMalloc((void**)&c->smooth_tab, tab.size() * sizeof(float)), "smoothing table");
+    CK(dev_malloc((void**)&c->smooth_tab, tab.size() * sizeof(float)), "smoothing table");
     CK(cudaMemcpy(c->smooth_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice), "upload table");
     // work: one half spectrum, then the real smoothed field (N^3 floats) behind it
     const size_t spec_bytes = (size_t)N * N * H * sizeof(float2);

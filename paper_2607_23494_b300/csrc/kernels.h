@@ -16,7 +16,7 @@ constexpr int STAB_STRIDE = 512;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_INV_Z_STORE, K_GATHER, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_INV_Z_STORE, K_GATHER, K_WAIT_CHECK, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -152,6 +152,10 @@ cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int 
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
                                    int N, double* out, int nb, cudaStream_t st, const Tracer& tr,
                                    int trace_id = K_KSPACE_CONTRACT);
+
+// wait_check.cu: one thread waits, with the bounded mbarrier wait of the bulk-copy
+// pipelines, on a barrier phase that nothing completes; err bit 4 marks the expiry
+cudaError_t launch_wait_unarrived(unsigned* err, cudaStream_t st, const Tracer& tr);
 
 // zeta.cu
 int zeta_z_blocks(int N);

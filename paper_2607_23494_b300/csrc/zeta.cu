@@ -376,12 +376,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the completion of phase `parity` of barrier b; false after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (int i = 0; i < (1 << 20); ++i)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
+// Waits for the completion of phase `parity` of barrier b; false after one second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) { return ac::mbar_wait(b, parity); }
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));

@@ -89,6 +89,8 @@ def _load() -> C.CDLL:
         "hermes_debug_set_delta": (i32, [vp, fp]),
         "hermes_debug_get_sums": (i32, [vp, dp, dp]),
         "hermes_debug_nodes": (i32, [vp, fp, i64, u32, fp, fp]),
+        "hermes_debug_bounded_wait": (i32, [vp]),
+        "hermes_debug_fail_allocs": (i32, [i32]),
         "hermes_shell_table_host": (i32, [C.c_double, i32, dp, i32, i32, dp]),
         "hermes_shell_table_len": (i64, [i32]),
         "hermes_trace_enable": (i32, [vp, i32]),

@@ -113,3 +113,11 @@ def test_footprint_estimate_follows_the_allocation_rules():
         # more orders only enlarge the tables
         assert estimate_bytes(N, STAT_XI_MULTIPOLES, 40, 4, 10 ** 6, host_inputs=False) > xi
     assert estimate_bytes(512, STAT_XI, 40, 0, 0) > estimate_bytes(256, STAT_XI, 40, 0, 0)
+
+
+def test_allocation_failure_hook_counts_without_a_gpu():
+    from paper_2607_23494_b300 import hermes as H
+    lib = H.lib()
+    assert lib.hermes_debug_fail_allocs(3) == 0
+    assert lib.hermes_debug_fail_allocs(-5) == 3     # negative disarms
+    assert lib.hermes_debug_fail_allocs(0) == 0
