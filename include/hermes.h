@@ -291,6 +291,42 @@ int hermes_xi_cylinders(hermes_ctx *ctx, double *out);
 int hermes_xi_cylinders_kspace(hermes_ctx *ctx, double *out);
 
 /*
+ * Ring windows for the redshift-space 2PCF at a list of (r_perp, r_par) points, such
+ * as the (s, mu) samples r_perp = s sqrt(1 - mu^2), r_par = s mu of xi(s, mu)
+ * (Sec. 3.4.4, the circular-ring window; Table A1 row (i), "standard (s, mu)
+ * binning geometry"), line of sight z.  Window w is
+ *   K_w(n) = T_perp,w(k_perp) exp(-k_perp^2 sigma_perp^2 / 2) T_par,w(k_par) Phi^(n):
+ *   dR_w = 0:  T_perp = J_0(k_perp R_w)            (thin ring)
+ *   dR_w > 0:  T_perp = area average of J_0(k_perp rho) over max(0, R_w - dR_w/2) <= rho <= R_w + dR_w/2
+ *   dH_w = 0:  T_par  = cos(k_par H_w)             (the double ring at z = +-H_w)
+ *   dH_w > 0:  T_par  = average of cos(k_par z) over max(0, H_w - dH_w/2) <= |z| <= H_w + dH_w/2
+ *              (sin(k dH/2)/(k dH/2) cos(k H) when the bin stays above 0).
+ * Tables are built on the host in float64 (J_0, J_1 closed forms) and stored as
+ * float32, indexed exactly by q_perp = n_x^2 + n_y^2 and |n_z|.  Replaces earlier
+ * cylindrical bins (hermes_window_cylinders) and is replaced by them.
+ *   R, H:   n values each, >= 0.   dR, dH: n widths each (>= 0), or NULL for 0 (thin).
+ *   R + dR/2 <= L/2 and H + dH/2 <= L/2 for every window; n: 1..4096.
+ * Errors: HERMES_ERR_ARG, HERMES_ERR_RANGE, HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ */
+int hermes_window_rings(hermes_ctx *ctx, const double *R, const double *H, const double *dR, const double *dH,
+                        int n, double sigma_perp);
+
+/*
+ * xi of the resident field for every ring window: window multiply, inverse
+ * transforms and cell contraction (windows in batches, each with its own
+ * line-of-sight factor), minus the exact self-pair term, over RR (uniform: 1;
+ * explicit randoms: their ring-window RR).  out: n float64.
+ * Errors: HERMES_ERR_STATE (no field or no ring windows), HERMES_ERR_TIMEOUT,
+ * HERMES_ERR_CUDA, HERMES_ERR_NOMEM.
+ */
+int hermes_xi_rings(hermes_ctx *ctx, double *out);
+
+/* The same by Parseval's theorem (Eq. pair-counting-kspace): per window, a histogram
+ * over q_perp of (|delta^|^2 - S^/eps_bar^2) Phi^ T_par,w (eight windows per pass over
+ * delta^), contracted with the window's transverse column.  Errors: as hermes_xi_rings. */
+int hermes_xi_rings_kspace(hermes_ctx *ctx, double *out);
+
+/*
  * 3PCF Legendre multipoles zeta_l(r_b1, r_b2), 0 <= l <= l_max, from the
  * harmonic shell fields a_{b,lm} = iFFT[delta^ 4 pi i^l <j_l>_b Y_lm Phi^]
  * (Eq. multipole-window, Eq. iFFT-multipoleSFC):

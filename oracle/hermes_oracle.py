@@ -58,7 +58,7 @@ __all__ = [
     "kappa_from_K", "shot_noise", "xi_multipoles", "zeta_multipoles", "lm_modes",
     "keff_pair_direct", "xi_brute_force", "direct_convolution", "annulus_avg_j0", "slab_avg_cos",
     "window_cyl", "xi_cylinders", "xi_randoms", "smoothing_window", "density_at", "density_marks",
-    "window_xi_at", "window_zeta_at", "planted_xi", "planted_zeta",
+    "window_xi_at", "window_zeta_at", "planted_xi", "planted_zeta", "window_ring", "xi_rings",
 ]
 
 
@@ -353,6 +353,36 @@ def xi_cylinders(pos, w, N, L, p, rperp_edges, rpar_edges, sigma_perp=0.0):
             K = window_cyl(N, L, p, rperp_edges[i], rperp_edges[i + 1], rpar_edges[j], rpar_edges[j + 1],
                            sigma_perp)
             out[j, i] = xi_parseval(dh, K) - shot_noise(S, K, N, sw)
+    return out
+
+
+def window_ring(N: int, L: float, p: int, R: float, H: float, dR: float = 0.0, dH: float = 0.0,
+                sigma_perp: float = 0.0, half: bool = False) -> np.ndarray:
+    """Ring window at (r_perp, r_par) = (R, H), Sec. 3.4.4 and Table A1 row (i).
+
+    Thin (dR = dH = 0): J_0(k_perp R) cos(k_par H) Phi^.  Finite widths: the
+    axisymmetric window of the transverse bin R +- dR/2 and the line-of-sight bin
+    H +- dH/2, each clipped at 0 (the separations pairs can have), which is the
+    printed form sin(k dH/2)/(k dH/2) cos(k H) <J_0>_dR whenever the bins stay above 0.
+    """
+    return window_cyl(N, L, p, max(0.0, R - 0.5 * dR), R + 0.5 * dR, max(0.0, H - 0.5 * dH), H + 0.5 * dH,
+                      sigma_perp, half)
+
+
+def xi_rings(pos, w, N, L, p, R, H, dR=None, dH=None, sigma_perp=0.0):
+    """xi for every ring window (R_i, H_i, dR_i, dH_i): Parseval on the full spectrum minus the
+    exact self-pair term.  Widths None mean thin rings.  Returns [n]."""
+    eps, sw, _ = assign(pos, w, N, L, p)
+    delta = delta_from_eps(eps, sw)
+    dh = forward(delta)
+    S = self_pair_table(pos, w, N, L, p)
+    n = len(R)
+    dR = np.zeros(n) if dR is None else np.broadcast_to(np.asarray(dR, dtype=np.float64), (n,))
+    dH = np.zeros(n) if dH is None else np.broadcast_to(np.asarray(dH, dtype=np.float64), (n,))
+    out = np.zeros(n)
+    for i in range(n):
+        K = window_ring(N, L, p, R[i], H[i], dR[i], dH[i], sigma_perp)
+        out[i] = xi_parseval(dh, K) - shot_noise(S, K, N, sw)
     return out
 
 

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         const int qi = nyq ? 0 : nx * nx + ny * ny + nz * nz;  // table index stays in range on Nyquist lanes
         const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
         // the window's factor that does not depend on the bin: scale * L_l(k_z/k), or T_par_j(|n_z|)
-        const float a = wb.cyl ? __ldg(wb.par + nz)
+        // (ring windows apply their own line-of-sight factor per window below)
+        const float a = wb.cyl ? (wb.par_stride ? 1.0f : __ldg(wb.par + nz))
                                : wb.scale * legendre(wb.ell, qi > 0 ? (float)nz * rsqrtf((float)qi) : 0.0f);
         v0[i] = cscale(v0[i], ph * a);
         q[i] = (wb.cyl && !nyq) ? nx * nx + ny * ny : qi;
@@ -307,10 +308,12 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
         for (int j = 0; j < 4; ++j) {
             const int s = g + j;
             if (s >= wb.S) break;  // uniform across the block
+            // ring windows: this window's line-of-sight factor at the thread's |n_z|
+            const float pz = wb.par_stride ? __ldg(wb.par + (size_t)s * wb.par_stride + nz) : 1.0f;
             float2 v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                v[i] = cscale(v0[i], j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
+                v[i] = cscale(v0[i], pz * (j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w))));
             fft_line_wc<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col}, wc);
             float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
 #pragma unroll

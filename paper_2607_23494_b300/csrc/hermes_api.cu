@@ -65,6 +65,9 @@ struct hermes_ctx {
     float* cyl_par = nullptr;
     int cyl_nperp = 0, cyl_npar = 0, cyl_nbp = 0;
     int64_t cyl_Q = 0;
+    // ring windows (hermes_window_rings): window w pairs transverse column w with
+    // line-of-sight row w instead of spanning the product grid
+    bool cyl_ring = false;
     // explicit random catalogue (Landy-Szalay): raw field, its transform (k = 0 kept),
     // self-pair table; rscal[2] = 1 so the histogram kernel subtracts S^ unscaled
     float* rgrid = nullptr;
@@ -773,21 +776,24 @@ namespace {
 //                  tb.stab (divide by eps_bar^2 for SN_b);
 //   self_only = 0: H is the Parseval histogram (|delta^|^2 - S^/eps_bar^2), so out is xi.
 // cyl = 0: idx are even orders l over the isotropic tables; cyl = 1: idx are
-// line-of-sight bins j over the axisymmetric tables.  hist holds
-// min(n, 8) * Q doubles.
+// line-of-sight bins j over the axisymmetric tables, or, with ring windows, the
+// windows themselves (out[a] is then the single value of window idx[a]).  hist
+// holds min(n, 8) * Q doubles.
 cudaError_t enqueue_hist_terms(hermes_ctx* c, const Tables& tb, const double* scal, const int* idx, int n, int cyl,
                                int self_only, double* hist, double* out, cudaStream_t st, const Tracer& tr,
                                const float2* spec_override = nullptr) {
     const float* rad = cyl ? c->cyl_perp : c->rad;
     const int nbp = cyl ? c->cyl_nbp : c->nbp;
     const int64_t Q = cyl ? c->cyl_Q : c->Q;
-    const int nb = cyl ? c->cyl_nperp : c->n_bins;
+    const int diag = cyl && c->cyl_ring;  // ring windows: one value per entry
+    const int nb = diag ? 1 : (cyl ? c->cyl_nperp : c->n_bins);
     for (int a0 = 0; a0 < n; a0 += 8) {
         KsOrders ko;
         ko.n = std::min(8, n - a0);
         for (int k = 0; k < ko.n; ++k) ko.ell[k] = idx[a0 + k];
         ko.cyl = cyl;
         ko.par = c->cyl_par;
+        ko.diag = diag;
         cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)ko.n * Q * sizeof(double), st);
         if (e != cudaSuccess) return e;
         const float2* spec = self_only ? nullptr : (spec_override ? spec_override : c->spec);
@@ -1753,8 +1759,8 @@ namespace {
 // from int_0^r rho J_0(k rho) d rho = r J_1(k r) / k; 1 at k = 0.
 double annulus_j0(double k, double a, double b) {
     if (k == 0.0) return 1.0;
-    const double jb = b * std::cyl_bessel_j(1.0, k * b);
-    const double ja = a > 0.0 ? a * std::cyl_bessel_j(1.0, k * a) : 0.0;
+    const double jb = b * ::j1(k * b);
+    const double ja = a > 0.0 ? a * ::j1(k * a) : 0.0;
     return (jb - ja) / (k * 0.5 * (b * b - a * a));
 }
 
@@ -1828,14 +1834,90 @@ extern "C" int hermes_window_cylinders(hermes_ctx* c, const double* perp_edges, 
     c->cyl_npar = nz;
     c->cyl_nbp = nbp;
     c->cyl_Q = Qp;
+    c->cyl_ring = false;
+    return HERMES_OK;
+}
+
+extern "C" int hermes_window_rings(hermes_ctx* c, const double* R, const double* Hz, const double* dRs,
+                                   const double* dHs, int n, double sigma_perp) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!R || !Hz) return fail(c, HERMES_ERR_ARG, "R or H is NULL");
+    if (n < 1 || n > 4096) return fail(c, HERMES_ERR_ARG, "need 1..4096 ring windows (have %d)", n);
+    if (!std::isfinite(sigma_perp) || sigma_perp < 0.0)
+        return fail(c, HERMES_ERR_RANGE, "sigma_perp = %g must be finite and >= 0", sigma_perp);
+    for (int w = 0; w < n; ++w) {
+        const double dR = dRs ? dRs[w] : 0.0, dH = dHs ? dHs[w] : 0.0;
+        if (!std::isfinite(R[w]) || !std::isfinite(Hz[w]) || R[w] < 0.0 || Hz[w] < 0.0)
+            return fail(c, HERMES_ERR_RANGE, "ring %d: R = %g, H = %g must be finite and >= 0", w, R[w], Hz[w]);
+        if (!std::isfinite(dR) || !std::isfinite(dH) || dR < 0.0 || dH < 0.0)
+            return fail(c, HERMES_ERR_RANGE, "ring %d: widths dR = %g, dH = %g must be finite and >= 0", w, dR, dH);
+        if (R[w] + 0.5 * dR > 0.5 * c->L || Hz[w] + 0.5 * dH > 0.5 * c->L)
+            return fail(c, HERMES_ERR_RANGE, "ring %d reaches beyond L/2 = %g", w, 0.5 * c->L);
+    }
+    DeviceGuard g(c->device);
+    const int N = c->N, H = N / 2;
+    const int nbp = (n + 3) & ~3;
+    const int64_t Qp = 2 * (int64_t)(H - 1) * (H - 1) + 1;
+    const double kf = 2.0 * M_PI / c->L;
+    std::vector<float> perp, par;
+    try {
+        perp.assign((size_t)Qp * nbp, 0.0f);
+        par.assign((size_t)n * H, 0.0f);
+    } catch (...) {
+        return fail(c, HERMES_ERR_NOMEM, "host tables");
+    }
+    // Sec. 3.4.4: the thin double ring J_0(k_perp R) cos(k_par H); finite widths give the
+    // area average of J_0 over the transverse bin R +- dR/2 and the average of cos(k_par z)
+    // over the line-of-sight bin H +- dH/2 (sin(k dH/2)/(k dH/2) cos(k H)), each bin
+    // clipped at 0 where it would reach below (the separations the pairs actually cover)
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (int64_t q = t; q < Qp; q += nt) {
+                const double k = kf * std::sqrt((double)q);
+                const double gs = std::exp(-0.5 * k * k * sigma_perp * sigma_perp);
+                for (int w = 0; w < n; ++w) {
+                    const double dR = dRs ? dRs[w] : 0.0;
+                    const double v = dR > 0.0 ? annulus_j0(k, std::max(0.0, R[w] - 0.5 * dR), R[w] + 0.5 * dR)
+                                              : ::j0(k * R[w]);
+                    perp[(size_t)q * nbp + w] = (float)(v * gs);
+                }
+            }
+        });
+    for (auto& t : th) t.join();
+    for (int w = 0; w < n; ++w)
+        for (int a = 0; a < H; ++a) {
+            const double k = kf * a, dH = dHs ? dHs[w] : 0.0;
+            par[(size_t)w * H + a] =
+                (float)(dH > 0.0 ? slab_cos(k, std::max(0.0, Hz[w] - 0.5 * dH), Hz[w] + 0.5 * dH)
+                                 : std::cos(k * Hz[w]));
+        }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->cyl_perp);
+    cudaFree(c->cyl_par);
+    c->cyl_perp = nullptr;
+    c->cyl_par = nullptr;
+    c->cyl_nperp = c->cyl_npar = 0;
+    CK(dev_malloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "ring transverse table");
+    CK(dev_malloc((void**)&c->cyl_par, par.size() * sizeof(float)), "ring line-of-sight table");
+    CK(cudaMemcpy(c->cyl_perp, perp.data(), perp.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    CK(cudaMemcpy(c->cyl_par, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    c->cyl_nperp = n;
+    c->cyl_npar = n;
+    c->cyl_nbp = nbp;
+    c->cyl_Q = Qp;
+    c->cyl_ring = true;
     return HERMES_OK;
 }
 
 namespace {
-int check_cyl(hermes_ctx* c, double* out) {
+int check_cyl(hermes_ctx* c, double* out, bool ring = false) {
     if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
-    if (c->cyl_nperp < 1) return fail(c, HERMES_ERR_STATE, "no cylindrical bins: call hermes_window_cylinders first");
+    if (c->cyl_nperp < 1 || c->cyl_ring != ring)
+        return fail(c, HERMES_ERR_STATE, ring ? "no ring windows: call hermes_window_rings first"
+                                              : "no cylindrical bins: call hermes_window_cylinders first");
     return HERMES_OK;
 }
 }  // namespace
@@ -1910,6 +1992,80 @@ extern "C" int hermes_xi_cylinders_kspace(hermes_ctx* c, double* out) {
     CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
        "read xi");
     CK(cudaStreamSynchronize(st), "xi(r_perp, r_par) (k-space)");
+    const double n3 = (double)c->N * c->N * c->N;
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
+    for (int w = 0; w < nwin; ++w) out[w] = c->host_buf[w] / (nrr ? c->host_buf[nwin + w] * rr_scale : 1.0);
+    return HERMES_OK;
+}
+
+extern "C" int hermes_xi_rings(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (int r = check_cyl(c, out, true)) return r;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int N = c->N, H = N / 2, nwin = c->cyl_nperp;
+    const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
+    const int S = (int)xi_window_S(N, nwin);
+    CK(grow(c->work, c->work_bytes, (size_t)S * win_bytes), "window work buffer");
+    const int zb = inv_z_blocks(N);
+    CK(grow_doubles(c->part, c->part_cap, std::max((size_t)S * zb, (size_t)std::min(nwin, 8) * c->cyl_Q)),
+       "partials");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)3 * nwin), "reduction buffer");  // dd, sn, RR
+    const Tables tb = tables_of(c);
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
+    std::vector<int> ws(nwin);
+    for (int w = 0; w < nwin; ++w) ws[w] = w;
+    CK(enqueue_hist_terms(c, tb, nullptr, ws.data(), nwin, 1, 1, c->part, c->red + nwin, st, c->tracer),
+       "self-pair terms");
+    for (int w0 = 0; w0 < nwin; w0 += S) {
+        WinBatch wb;
+        wb.S = std::min(S, nwin - w0);
+        wb.tab = c->cyl_perp + w0;
+        wb.nbp = c->cyl_nbp;
+        wb.ell = 0;
+        wb.scale = 1.0f;
+        wb.cyl = 1;
+        wb.par = c->cyl_par + (size_t)w0 * H;
+        wb.par_stride = H;
+        CK(launch_inverse_xi(N, c->spec, c->work, c->grid, wb, tb, c->part, c->err, st, c->tracer), "inverse passes");
+        CK(launch_reduce_rows(c->part, wb.S, zb, c->red + w0, st, c->tracer), "reduce contractions");
+    }
+    const int nrr = c->have_randoms ? nwin : 0;
+    if (nrr) CK(enqueue_rr_terms(c, ws.data(), nwin, 1, c->part, c->red + 2 * nwin, st, c->tracer), "random pairs");
+    CK(ensure_host(c, (size_t)2 * nwin + nrr + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation,
+       "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(2 * nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)2 * nwin + nrr);
+    CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
+    CK(cudaStreamSynchronize(st), "xi over ring windows");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
+    const double n3 = (double)N * N * N, n6 = n3 * n3, eb = c->sum_w / n3;
+    const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
+    for (int w = 0; w < nwin; ++w)
+        out[w] = (c->host_buf[w] / n6 - c->host_buf[nwin + w] / (eb * eb)) /
+                 (nrr ? c->host_buf[2 * nwin + w] * rr_scale : 1.0);
+    return HERMES_OK;
+}
+
+extern "C" int hermes_xi_rings_kspace(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (int r = check_cyl(c, out, true)) return r;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int nwin = c->cyl_nperp;
+    CK(grow_doubles(c->part, c->part_cap, (size_t)std::min(nwin, 8) * c->cyl_Q), "histogram");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)2 * nwin), "reduction buffer");  // xi numerators, RR
+    std::vector<int> ws(nwin);
+    for (int w = 0; w < nwin; ++w) ws[w] = w;
+    CK(enqueue_hist_terms(c, tables_of(c), c->scal, ws.data(), nwin, 1, 0, c->part, c->red, st, c->tracer),
+       "k-space histogram");
+    const int nrr = c->have_randoms ? nwin : 0;
+    if (nrr) CK(enqueue_rr_terms(c, ws.data(), nwin, 1, c->part, c->red + nwin, st, c->tracer), "random pairs");
+    CK(ensure_host(c, (size_t)nwin + nrr) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)(nwin + nrr) * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "read xi");
+    CK(cudaStreamSynchronize(st), "xi over ring windows (k-space)");
     const double n3 = (double)c->N * c->N * c->N;
     const double rr_scale = nrr ? (n3 / c->sum_wr) * (n3 / c->sum_wr) : 0.0;
     for (int w = 0; w < nwin; ++w) out[w] = c->host_buf[w] / (nrr ? c->host_buf[nwin + w] * rr_scale : 1.0);

@@ -38,6 +38,9 @@ struct Tracer {
 // * T_par_j(|n_z|) * Phi^(n); tab is the transverse table indexed by q_perp =
 // n_x^2 + n_y^2 (bin fastest), par = T_par_j over |n_z| in [0, N/2) for the
 // batch's line-of-sight bin j; ell and scale are unused.
+// Ring windows (par_stride > 0): window s of the batch has its own line-of-sight
+// row, par + s * par_stride, paired with transverse column s (a list of (R, H)
+// rings instead of a product grid of bins).
 struct WinBatch {
     const float* tab;
     int nbp;
@@ -46,6 +49,7 @@ struct WinBatch {
     float scale;  // (2l+1) i^l, real for even l
     int cyl = 0;
     const float* par = nullptr;
+    int par_stride = 0;
 };
 
 // One batch of complex harmonic windows: all bins of a fixed (l, m).
@@ -62,11 +66,14 @@ struct HarmBatch {
 // are line-of-sight bins j of an axisymmetric window instead, each weighting a
 // mode by par[j*(N/2) + |n_z|], the histogram is indexed by q_perp = n_x^2 + n_y^2
 // and the contraction constant is 1.
+// diag = 1 (ring windows): entry o is window ell[o], whose line-of-sight row and
+// transverse column are both ell[o]; the contraction yields one value per entry.
 struct KsOrders {
     int n;
     int ell[8];
     int cyl = 0;
     const float* par = nullptr;
+    int diag = 0;
 };
 
 struct Tables {
@@ -148,7 +155,8 @@ cudaError_t launch_combine_randoms(float* grid, const float* rgrid, size_t n, fl
 cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int P, const double* scal,
                                const KsOrders& ko, double* hist, int64_t Q, cudaStream_t st, const Tracer& tr,
                                int self_only = 0);
-// out[o*nb + b] = c_l sum_q T_{b,l}(q) hist[o*Q + q] / N^6, c_l = (2l+1) i^l
+// out[o*nb + b] = c_l sum_q T_{b,l}(q) hist[o*Q + q] / N^6, c_l = (2l+1) i^l;
+// ko.diag: out[o] = sum_q T_{ell[o]}(q) hist[o*Q + q] / N^6 (one column per entry)
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
                                    int N, double* out, int nb, cudaStream_t st, const Tracer& tr,
                                    int trace_id = K_KSPACE_CONTRACT);

@@ -185,6 +185,37 @@ __global__ void __launch_bounds__(KC_THREADS) k_kspace_contract(const float* __r
     }
 }
 
+// Ring windows: out[o] = sum_q T[q*nbp + ell[o]] hist[o*Q + q] / N^6, one column per
+// entry.  Grid (q slices, entries); lane j of a warp takes q0 + j, products in float32
+// per group of 32 q, summed across the warp and added in float64.
+__global__ void __launch_bounds__(KC_THREADS) k_kspace_contract_diag(const float* __restrict__ rad, int nbp,
+                                                                     int64_t Q, KsOrders ko,
+                                                                     const double* __restrict__ hist, double n6,
+                                                                     double* __restrict__ out) {
+    __shared__ double part[KC_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int o = blockIdx.y;
+    const float* tab = rad + ko.ell[o];
+    const double* h = hist + (size_t)o * Q;
+    const int64_t ngroups = (Q + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * (KC_THREADS / 32);
+    double s = 0.0;
+    for (int64_t g = (int64_t)blockIdx.x * (KC_THREADS / 32) + wid; g < ngroups; g += nwarps) {
+        const int64_t q = g * 32 + lane;
+        float acc = q < Q ? __ldg(tab + (size_t)q * nbp) * (float)__ldg(h + q) : 0.0f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        s += (double)acc;
+    }
+    if (lane == 0) part[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < KC_THREADS / 32; ++w) t += part[w];
+        atomicAdd(out + o, t / n6);
+    }
+}
+
 template <int N>
 static cudaError_t kspace_impl(const float2* spec, const Tables& tb, int P, const double* scal, const KsOrders& ko,
                                double* hist, int64_t Q, cudaStream_t st, const Tracer& tr, int self_only) {
@@ -215,6 +246,18 @@ cudaError_t launch_kspace_hist(int N, const float2* spec, const Tables& tb, int 
 cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const KsOrders& ko, const double* hist,
                                    int N, double* out, int nb, cudaStream_t st, const Tracer& tr, int trace_id) {
     const double n3 = (double)N * N * N;
+    if (ko.diag) {
+        const int64_t groups = (Q + 31) / 32;
+        const int64_t most = (groups + KC_THREADS / 32 - 1) / (KC_THREADS / 32);
+        const int64_t want = (4 * 148 + ko.n - 1) / ko.n;
+        const int slices = (int)(want < most ? want : most);
+        tr(trace_id, 0, st);
+        cudaError_t e = cudaMemsetAsync(out, 0, (size_t)ko.n * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+        k_kspace_contract_diag<<<dim3(slices, ko.n), KC_THREADS, 0, st>>>(rad, nbp, Q, ko, hist, n3 * n3, out);
+        tr(trace_id, 1, st);
+        return cudaGetLastError();
+    }
     const int chunks = (nb + 31) / 32;
     // about four blocks per SM in total, but at least one group of 32 q per warp
     const int64_t groups = (Q + 31) / 32;

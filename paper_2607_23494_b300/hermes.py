@@ -83,6 +83,9 @@ def _load() -> C.CDLL:
         "hermes_window_cylinders": (i32, [vp, dp, i32, dp, i32, C.c_double]),
         "hermes_xi_cylinders": (i32, [vp, dp]),
         "hermes_xi_cylinders_kspace": (i32, [vp, dp]),
+        "hermes_window_rings": (i32, [vp, dp, dp, dp, dp, i32, C.c_double]),
+        "hermes_xi_rings": (i32, [vp, dp]),
+        "hermes_xi_rings_kspace": (i32, [vp, dp]),
         "hermes_last_error": (C.c_char_p, [vp]),
         "hermes_debug_get_delta": (i32, [vp, fp]),
         "hermes_debug_get_spectrum": (i32, [vp, fp]),
@@ -349,6 +352,47 @@ class Context:
         out = np.empty((self.n_par, self.n_perp), dtype=np.float64)
         f = _lib.hermes_xi_cylinders_kspace if kspace else _lib.hermes_xi_cylinders
         self._check(f(self._h, _dptr(out)), "hermes_xi_cylinders" + ("_kspace" if kspace else ""))
+        return out
+
+    def window_rings(self, R: Sequence[float], H: Sequence[float], dR=None, dH=None,
+                     sigma_perp: float = 0.0) -> None:
+        """Ring windows at the (R, H) = (r_perp, r_par) points (hermes_window_rings); dR, dH
+        are per-ring widths (scalars broadcast; None = thin)."""
+        r = np.ascontiguousarray(R, dtype=np.float64).ravel()
+        h = np.ascontiguousarray(H, dtype=np.float64).ravel()
+        if r.shape != h.shape:
+            raise HermesError(ERR_ARG, "R and H need the same length")
+
+        def widths(d):
+            if d is None:
+                return None
+            return np.ascontiguousarray(np.broadcast_to(np.asarray(d, dtype=np.float64), r.shape))
+
+        wr, wh = widths(dR), widths(dH)
+        self._check(_lib.hermes_window_rings(self._h, _dptr(r), _dptr(h), None if wr is None else _dptr(wr),
+                                             None if wh is None else _dptr(wh), len(r), float(sigma_perp)),
+                    "hermes_window_rings")
+        self.n_rings = len(r)
+
+    def window_s_mu(self, s: Sequence[float], mu: Sequence[float], ds: float = 0.0, dmu: float = 0.0,
+                    sigma_perp: float = 0.0) -> None:
+        """Ring windows on the s x mu sample grid of xi(s, mu) (ordered [s][mu]):
+        r_perp = s sqrt(1 - mu^2), r_par = s mu; thin when ds = dmu = 0, otherwise each ring
+        gets widths dR = ds and dH = s dmu."""
+        sv = np.asarray(s, dtype=np.float64)
+        mv = np.asarray(mu, dtype=np.float64)
+        R = (sv[:, None] * np.sqrt(np.clip(1.0 - mv[None, :] ** 2, 0.0, None))).ravel()
+        H = (sv[:, None] * mv[None, :]).ravel()
+        thin = ds == 0.0 and dmu == 0.0
+        dH = None if thin else np.repeat(sv * dmu, len(mv))
+        self.window_rings(R, H, dR=None if thin else ds, dH=dH, sigma_perp=sigma_perp)
+        self.s_mu_shape = (len(sv), len(mv))
+
+    def xi_rings(self, kspace: bool = False) -> np.ndarray:
+        """xi for every ring window (n,); kspace=True uses the Parseval route."""
+        out = np.empty(self.n_rings, dtype=np.float64)
+        f = _lib.hermes_xi_rings_kspace if kspace else _lib.hermes_xi_rings
+        self._check(f(self._h, _dptr(out)), "hermes_xi_rings" + ("_kspace" if kspace else ""))
         return out
 
     def zeta_multipoles(self) -> np.ndarray:

@@ -79,3 +79,56 @@ def test_xi_cylinders_equals_brute_force_pair_sums():
         Kc = O.window_cyl(N, L, p, rperp[i], rperp[i + 1], rpar[j], rpar[j + 1])
         ref = O.xi_brute_force(pos, w, N, L, p, Kc)
         assert got[j, i] == pytest.approx(ref, rel=1e-9, abs=1e-12)
+
+
+def _modes(N, L):
+    f = O.signed_freqs(N)
+    nx, ny, nz = np.meshgrid(f, f, f, indexing="ij")
+    kf = 2.0 * np.pi / L
+    nyq = (np.abs(nx) == N // 2) | (np.abs(ny) == N // 2) | (np.abs(nz) == N // 2)
+    return kf * np.sqrt(nx ** 2 + ny ** 2), kf * nz, nyq
+
+
+def test_thin_ring_is_table_a1_row_i():
+    # J_0(k_perp R) cos(k_par H) Phi^, written out here from the printed closed form
+    N, L, p = 16, 64.0, 4
+    kp, kz, nyq = _modes(N, L)
+    ph = O.phi_hat_1d(N, p)
+    phi3 = ph[:, None, None] * ph[None, :, None] * ph[None, None, :]
+    for R, H in ((7.0, 3.0), (0.0, 10.0), (12.5, 0.0)):
+        ref = np.where(nyq, 0.0, sps.j0(kp * R) * np.cos(kz * H) * phi3)
+        np.testing.assert_allclose(O.window_ring(N, L, p, R, H), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_finite_ring_is_the_printed_finite_bin_form():
+    # Sec. 3.4.4: sin(k_par D/2)/(k_par D/2) cos(k_par r_par) <J_0(k_perp r_perp)>_{Delta r_perp},
+    # <J_0> = 1/(r_perp Delta) int rho J_0 d rho = [rho J_1(k rho) / k] / (r_perp Delta)
+    N, L, p = 16, 64.0, 4
+    kp, kz, nyq = _modes(N, L)
+    ph = O.phi_hat_1d(N, p)
+    phi3 = ph[:, None, None] * ph[None, :, None] * ph[None, None, :]
+    R, dR, H, dH = 9.0, 3.0, 6.0, 2.0
+    a, b = R - dR / 2, R + dR / 2
+    with np.errstate(invalid="ignore", divide="ignore"):
+        j0avg = np.where(kp > 0, (b * sps.j1(kp * b) - a * sps.j1(kp * a)) / kp / (R * dR), 1.0)
+        los = np.where(kz != 0, np.sin(0.5 * kz * dH) / (0.5 * kz * dH), 1.0) * np.cos(kz * H)
+    ref = np.where(nyq, 0.0, j0avg * los * phi3)
+    np.testing.assert_allclose(O.window_ring(N, L, p, R, H, dR, dH), ref, rtol=1e-11, atol=1e-14)
+
+
+def test_ring_bins_clipped_at_zero_are_the_disk_and_filled_slab():
+    # a ring whose bins reach below zero covers [0, R + dR/2] and |z| in [0, H + dH/2]
+    N, L, p = 16, 64.0, 4
+    got = O.window_ring(N, L, p, 1.0, 0.5, 4.0, 3.0)
+    np.testing.assert_allclose(got, O.window_cyl(N, L, p, 0.0, 3.0, 0.0, 2.0), rtol=0, atol=1e-15)
+
+
+def test_xi_rings_equal_brute_force_pair_sums():
+    N, L, p = 16, 48.0, 3
+    pos = S.mixed_poisson_sp(60, L, seed=14)
+    w = S.lognormal_masses(pos.shape[0], seed=15)
+    R, H, dR, dH = [4.0, 7.0], [2.0, 5.0], [0.0, 2.0], [0.0, 3.0]
+    got = O.xi_rings(pos, w, N, L, p, R, H, dR, dH)
+    for i in range(2):
+        Kr = O.window_ring(N, L, p, R[i], H[i], dR[i], dH[i])
+        assert got[i] == pytest.approx(O.xi_brute_force(pos, w, N, L, p, Kr), rel=1e-9, abs=1e-12)
