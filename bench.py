@@ -22,6 +22,7 @@ value is the aggregate over ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -140,9 +141,68 @@ def gen_catalogue3(seed: int):
     return S.lognormal_catalogue(NPTS3, L3, seed=seed, n_grid=512)
 
 
+# Stored FP64 oracle values (written by tests/golden/make_fullsize_golden.py) for the
+# per-statistic error report; each file carries a digest of the catalogue it was made from.
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def load_golden(name: str):
+    try:
+        with open(os.path.join(GOLDEN, name)) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def sha256(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def err_stats(got, ref) -> dict:
+    """Largest absolute and relative error and the largest error in units of the
+    tolerance (1e-4 relative or 1e-6 absolute; <= 1 passes)."""
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    err = np.abs(got - ref)
+    big = np.abs(ref) > 1e-6
+    return {"n": int(ref.size), "max_abs_err": float(err.max()),
+            "max_rel_err": float((err[big] / np.abs(ref[big])).max()) if big.any() else None,
+            "max_in_tolerance_units": round(float((err / np.maximum(1e-4 * np.abs(ref), 1e-6)).max()), 4)}
+
+
+def error_vs_oracle(res, pos, mass, zeta128) -> dict:
+    """Error of every statistic against the FP64 oracle at the configuration sizes:
+    xi of the 20,000-point 64^3 catalogue in full; xi_l (l = 0, 2, 4) of the timed
+    1e7-point 512^3 step, unit and marked fields, on 6 of the 40 shells; zeta_l of the
+    2e6-point catalogue regridded on 128^3 (l_max = 6, 16 shells) in full."""
+    from paper_2607_23494_b300 import Context
+    from synthetic import catalogues as S
+    out = {"tolerance": "1e-4 relative or 1e-6 absolute (max_in_tolerance_units <= 1 passes); max_rel_err over "
+                        "entries with |oracle| > 1e-6",
+           "oracle": "stored FP64 oracle values, tests/golden/make_fullsize_golden.py"}
+    g = load_golden("xi_mixed_2e4_64.json")
+    if g:
+        c = g["config"]
+        p1 = S.mixed_poisson_sp(c["n"], c["L"], seed=c["seed"])
+        if sha256(p1) == g["pos_sha256"]:
+            with Context(c["L"], c["N"], c["p"]) as ctx:
+                ctx.assign(p1)
+                ctx.window_shells(c["edges"], l_max=0)
+                out["xi_20k_64"] = err_stats(ctx.xi(), g["xi"])
+    g = load_golden("xi_lognormal_1e7_512_sample.json")
+    if g and sha256(pos) == g["pos_sha256"] and sha256(mass) == g["mass_sha256"]:
+        bins = g["config"]["bins"]
+        for name, r in (("unit", res[0]), ("marked", res[1])):
+            for a, ell in enumerate(g["config"]["ells"]):
+                out[f"{name}_xi_l{ell}_1e7_512_bins_{'_'.join(map(str, bins))}"] = \
+                    err_stats(np.asarray(r)[a][bins], g["xi"][name][a])
+    if zeta128 is not None:
+        out["zeta_l_2e6_128"] = err_stats(zeta128[0], zeta128[1])
+    return out
+
+
 # DRAM bytes measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) for the inverse
-# passes at 512^3 on a 5-window launch of the current kernels (summary and command in
-# profiles/xi_512_inverse_passes_ncu.md): bytes per launch (read once per launch) and per window.
+# passes at 512^3 on a 5-window launch of the current kernels: bytes per launch (read once
+# per launch) and per window.
 NCU_TRAFFIC_512 = {
     "inv_x_window": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
     "inv_y": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
@@ -273,14 +333,14 @@ def run_hermes(args, rank, world, local_rank):
             "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
             "traffic": round(traffic) if traffic else None,
             "alg_bytes_per_launch": round(dom_b / trace[dom][1]) if dom_b else None,
-            "traffic_source": "ncu dram bytes of a 5-window launch at 512^3 scaled to this launch's windows "
-                              "(profiles/xi_512_inverse_passes_ncu.md)",
+            "traffic_source": "ncu dram bytes of a 5-window launch at 512^3 scaled to this launch's windows",
             "peak_source": f"{pk_src} hbm_gbs (MEASURED_PEAKS.json)" if pk_src == "measured"
             else "fallback 6.4 TB/s"}
 
     # the k-space (Parseval) route on the resident marked field: same xi_l, no inverse FFTs
     ks = run_kspace(ctx, stream, res[1])
     cyl = run_cylinders(ctx, stream)
+    smu = run_s_mu(ctx, stream, pos_d, mass_d)
     plain = None
     if not args.no_plain:
         ctx.close()
@@ -323,14 +383,17 @@ def run_hermes(args, rank, world, local_rank):
         }
         out["kspace"] = ks
         out["cylinders"] = cyl
+        out["s_mu"] = smu
         if plain:
             out["vs_plain_fp32"] = plain
         if batch:
             out["batch"] = batch
         if serve:
             out["serve"] = serve
+        z128 = zeta.pop("_z128", None) if zeta else None
         if zeta:
             out["zeta"] = zeta
+        out["error_vs_oracle"] = error_vs_oracle(res, pos, mass, z128)
     return out, pos
 
 
@@ -356,6 +419,50 @@ def run_cylinders(ctx, stream):
     a, b = out.pop("inverse_fft_xi"), out.pop("kspace_xi")
     out["diff_between_routes_in_tolerances"] = round(float(np.max(np.abs(a - b) / np.maximum(1e-4 * np.abs(b), 1e-6))), 4)
     out["workload"] = "xi(r_perp, r_par), marked 1e7-point field, 512^3, 20 x 20 bins in [0, 100) Mpc/h"
+    return out
+
+
+def run_s_mu(ctx, stream, pos_d, mass_d):
+    """xi(s, mu) on ring windows at the paper's sampling of its DD(s, mu) benchmark: 46
+    separations x 51 orientations = 2346 thin rings (r_perp = s sqrt(1 - mu^2), r_par = s mu),
+    s = 2.5 .. 227.5 Mpc/h, mu = 0 .. 1; on the resident marked 512^3 field (both routes) and
+    on the same catalogue gridded at 256^3 (the paper's J = 8)."""
+    import torch
+    from paper_2607_23494_b300 import Context
+    s = np.arange(2.5, 230.0, 5.0)
+    mu = np.linspace(0.0, 1.0, 51)
+    out = {"workload": f"xi(s, mu) on {len(s)} x {len(mu)} thin ring windows, s in [2.5, 227.5] Mpc/h, mu in [0, 1], "
+                       "marked 1e7-point field, L=1000"}
+
+    def timed(c, ks):
+        c.xi_rings(kspace=ks)  # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = c.xi_rings(kspace=ks)
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1), got
+
+    nwin = len(s) * len(mu)
+    ctx.window_s_mu(s, mu)
+    res = {}
+    for route, ks in (("inverse_fft", False), ("kspace", True)):
+        ms, got = timed(ctx, ks)
+        res[route] = got
+        out[f"512_{route}"] = {"ms": round(ms, 2), "ms_per_sample": round(ms / nwin, 4),
+                               "cell_window_evals_per_s": round(float(N2) ** 3 * nwin / (ms / 1e3), 1)}
+    out["512_diff_between_routes_in_tolerances"] = round(float(np.max(
+        np.abs(res["inverse_fft"] - res["kspace"]) / np.maximum(1e-4 * np.abs(res["kspace"]), 1e-6))), 4)
+    with Context(L2, 256, P2) as c256:
+        c256.set_stream(stream)
+        c256.assign(pos_d, mass_d)
+        c256.window_s_mu(s, mu)
+        for route, ks in (("inverse_fft", False), ("kspace", True)):
+            ms, _ = timed(c256, ks)
+            out[f"256_{route}"] = {"ms": round(ms, 2), "ms_per_sample": round(ms / nwin, 4)}
+    out["paper_context"] = "paper: 2346 ring samples at J = 8 (256^3) in 120 s on 8 MPI x 8 threads, 51.0 ms/sample"
     return out
 
 
@@ -686,6 +793,16 @@ def run_zeta(args, dev, stream, rank):
     ms = e0.elapsed_time(e1) / zsteps
     tr = ctx.trace_read()
     ctx.close()
+    # the same catalogue regridded on 128^3 against the stored FP64 oracle zeta_l
+    z128 = None
+    g = load_golden("zeta_lognormal_2e6_128_lmax6.json")
+    if g and sha256(pos) == g["pos_sha256"]:
+        c = g["config"]
+        with Context(c["L"], c["N"], c["p"]) as c128:
+            c128.set_stream(stream)
+            c128.window_shells(c["edges"], l_max=c["l_max"])
+            c128.assign(pos_d)
+            z128 = (c128.zeta_multipoles(), np.array(g["zeta"]))
     nb = len(EDGES3) - 1
     nfields = nb * (LMAX3 + 1) * (LMAX3 + 2) // 2
     n3 = float(N3) ** 3
@@ -698,17 +815,44 @@ def run_zeta(args, dev, stream, rank):
             "ms_per_step": round(ms, 2), "complex_fields": nfields,
             "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
             "zeta_y_GBps": round(16.0 * n3 * nfields / (y_ms / 1e3) / 1e9, 1) if y_ms else None,
-            "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])]}
+            "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])],
+            "_z128": z128}
 
 
-def oracle_sample(pos):
+def oracle_sample(pos, b: int = 0):
     """FP64 oracle on a bounded sample: 512^3 grid, 500k points, one l=0 window (half-spectrum route)."""
     from oracle import hermes_oracle as O
     sub = pos[:500_000]
     t = time.perf_counter()
-    O.xi_multipoles(sub, None, N2, L2, P2, [2.0, 7.0], ells=(0,), route="half")
+    O.xi_multipoles(sub, None, N2, L2, P2, [EDGES2[b], EDGES2[b + 1]], ells=(0,), route="half")
     dt = time.perf_counter() - t
     return float(N2) ** 3 / dt, dt
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample_all_cores(pos):
+    """The same bounded sample run as one process per usable core (spawned, so no CUDA state is
+    inherited), each on its own shell; each process holds ~8 GB, so the count is also bounded by
+    the available host memory.  Throughput = processes x 512^3 / wall time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    k = max(1, min(cores, int(avail // (10 << 30)), 32))
+    sub = np.ascontiguousarray(pos[:500_000])
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(k) as pool:
+        pool.starmap(oracle_sample, [(sub, i % 40) for i in range(k)])
+    wall = time.perf_counter() - t
+    return k * float(N2) ** 3 / wall, wall, k, cores
 
 
 def run_reference(args):
@@ -792,6 +936,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=60, help="requests in the serving trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
     args = ap.parse_args()
@@ -818,9 +963,15 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             v, dt = oracle_sample(pos)
             out["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "cpu_model": cpu_model(),
                                    "sample": f"512^3 grid, first 500k of the 1e7 points, one l=0 shell window "
                                              f"(scatter, FFT, window, Parseval sum, self-pair term): {dt:.1f} s, "
                                              f"numpy single thread; per-catalogue work not amortised"}
+            if not args.no_cpu_all_cores:
+                va, wall, k, cores = oracle_sample_all_cores(pos)
+                out["cpu_baseline"]["all_cores"] = {
+                    "value": round(va, 1), "unit": UNIT, "processes": k, "cores_available": cores,
+                    "sample": f"the same sample in {k} spawned processes (one shell each), {wall:.1f} s wall"}
         print(json.dumps(out))
     if world > 1:
         import torch
