@@ -422,6 +422,17 @@ int hermes_shell_table_host(double L, int N, const double *r_edges, int n_edges,
 /* Number of table entries Q for a grid of N cells per axis. */
 int64_t hermes_shell_table_len(int N);
 
+/*
+ * Frees the context's transient device buffers: the window work buffer, the
+ * harmonic fields of zeta_l, the staging buffers of host inputs and the scatter's
+ * per-point scratch.  The resident field, its spectrum, the window tables and
+ * explicit randoms stay, so every later statistic still runs (re-growing what it
+ * needs).  Waits for the context's stream.  (No counterpart in the paper: memory
+ * management for long-lived contexts, used by the request server when a context
+ * changes statistic.)  Errors: HERMES_ERR_ARG, HERMES_ERR_CUDA.
+ */
+int hermes_release_buffers(hermes_ctx *ctx);
+
 /* ------------------------------------------------------------------------
  * Device-memory accounting.
  *

@@ -54,10 +54,15 @@ static bool stab_x_enabled() {
     return !(env && env[0] == '1');
 }
 
+// Lets `kernel` take `bytes` of dynamic shared memory.  The attribute is a property
+// of the kernel shared by every host thread, so it is always set to the same value
+// (kMaxDynSmem), never to the size of one launch: concurrent callers whose launches
+// differ in size (the window pass stages S-dependent tables) then never undo each other.
 template <class K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes > kMaxDynSmem) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
 }
 
 // ---------------------------------------------------------------------------

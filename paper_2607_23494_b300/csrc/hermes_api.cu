@@ -562,6 +562,27 @@ int hermes_destroy(hermes_ctx* c) {
     return HERMES_OK;
 }
 
+int hermes_release_buffers(hermes_ctx* c) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->stream), "release buffers");
+    cudaFree(c->work);
+    cudaFree(c->zfields);
+    cudaFree(c->stage_pos);
+    cudaFree(c->stage_w);
+    cudaFree(c->ts_tile_of);
+    cudaFree(c->ts_perm);
+    cudaFree(c->ts_regions);
+    c->work = nullptr;
+    c->zfields = nullptr;
+    c->stage_pos = c->stage_w = nullptr;
+    c->ts_tile_of = c->ts_perm = nullptr;
+    c->ts_regions = nullptr;
+    c->work_bytes = c->zfields_bytes = 0;
+    c->stage_cap = c->ts_pts_cap = c->ts_regions_cap = 0;
+    return HERMES_OK;
+}
+
 int hermes_set_stream(hermes_ctx* c, void* s) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     c->stream = s ? (cudaStream_t)s : c->own_stream;

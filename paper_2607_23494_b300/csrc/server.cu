@@ -45,6 +45,7 @@ struct Slot {
     int64_t field_id = -1;       // resident catalogue, -1: none
     std::vector<double> edges;   // shells of the resident tables
     int l_max = -1;
+    int last_stat = -1;          // statistic of the last request (its buffers may still be held)
     bool busy = false;
     int64_t last_used = 0;
     int64_t bytes = 0;           // device footprint (measured after each use)
@@ -197,6 +198,16 @@ int execute(Slot* sl, Request* q, cudaStream_t st, bool reuse) {
     }
     hermes_ctx* c = sl->ctx;
     hermes_set_stream(c, st);
+    // a context changing statistic first drops the other statistic's buffers (the harmonic
+    // fields of zeta_l, the window batch of xi), so it never holds both: admission reserved
+    // only the larger of its previous footprint and this request's estimate
+    if (sl->last_stat >= 0 && (sl->last_stat == HERMES_STAT_ZETA) != (r.stat == HERMES_STAT_ZETA)) {
+        if ((rc = hermes_release_buffers(c)) != HERMES_OK) {
+            set_result(q, rc, hermes_last_error(c));
+            return rc;
+        }
+    }
+    sl->last_stat = r.stat;
     const int lmax = request_l_max(*q);
     if (sl->edges != q->edges || sl->l_max < lmax) {
         if ((rc = hermes_window_shells(c, q->edges.data(), (int)q->edges.size(), lmax)) != HERMES_OK) {

@@ -42,10 +42,15 @@ struct ZCfg {
 static_assert(ZCfg<16>::ZPER >= 1 && ZCfg<1024>::NZS == 32, "z-pass layout");
 static_assert(ZCfg<512>::GB <= 15 && ZCfg<1024>::GB <= 15, "one named barrier per z line group");
 
+// As allow_smem in the inverse passes: the attribute is shared by every host thread, so it
+// is always set to one value (220 KiB, next to at most 7 KiB of static arrays) rather than
+// to the size of one launch (the x pass stages S-dependent tables).
 template <class K>
 static cudaError_t allow_smem_z(K kernel, size_t bytes) {
+    constexpr size_t kMax = 220 * 1024;
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes > kMax) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax);
 }
 
 __device__ __forceinline__ float2 mul_ipow(float2 a, int ell) {

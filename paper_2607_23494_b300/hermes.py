@@ -65,6 +65,7 @@ def _load() -> C.CDLL:
         "hermes_create": (i32, [C.c_double, i32, i32, i32, C.POINTER(vp)]),
         "hermes_destroy": (i32, [vp]),
         "hermes_set_stream": (i32, [vp, vp]),
+        "hermes_release_buffers": (i32, [vp]),
         "hermes_assign": (i32, [vp, fp, fp, i64, u32]),
         "hermes_assign_noalloc": (i32, [vp, fp, fp, i64, u32]),
         "hermes_assign_randoms": (i32, [vp, fp, fp, i64, u32]),
@@ -174,6 +175,10 @@ class Context:
         if rc != OK:
             msg = _lib.hermes_last_error(self._h)
             raise HermesError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def release_buffers(self) -> None:
+        """hermes_release_buffers: free the transient device buffers; the field stays."""
+        self._check(_lib.hermes_release_buffers(self._h), "hermes_release_buffers")
 
     def set_stream(self, stream) -> None:
         """stream: a torch.cuda.Stream, an integer handle, or None for the context's own stream."""

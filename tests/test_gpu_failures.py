@@ -44,8 +44,9 @@ def test_bounded_wait_gives_up_and_the_context_survives():
         assert 0.5 < dt < 30.0, dt
         after = ctx.xi_multipoles([0, 2])       # same context, same stream, still usable
         np.testing.assert_array_equal(after, before)
-        ctx.assign(pos)
-        np.testing.assert_allclose(ctx.xi_multipoles([0, 2]), before, rtol=1e-6, atol=1e-9)
+        ctx.assign(pos)   # a new scatter: float atomics may add in another order
+        again = ctx.xi_multipoles([0, 2])
+        assert np.all(np.abs(again - before) <= np.maximum(1e-4 * np.abs(before), 1e-6))
 
 
 def test_allocation_failure_reports_nomem_keeps_state_and_recovers():

@@ -158,3 +158,61 @@ def test_server_errors_and_oversized_requests():
         assert res["status"] == H.ERR_ARG
         out, res = srv.wait(srv.submit(L, N, p, H.STAT_XI, [2.0, 10.0, 20.0], pos=pos, w=w, field_id=5))
         assert res["status"] == H.OK
+
+
+def test_contexts_on_concurrent_host_threads_with_different_window_batches():
+    # Two host threads drive their own 256^3 contexts at once: one measures 40 shells
+    # (window batches of 16, 16 and 8), the other 5 shells (one batch of 5), and the
+    # zeta_l pass runs beside them with its own bin count.  The batches stage radial
+    # tables of different sizes in shared memory; every launch must still run and
+    # every result equal the same call made alone.
+    import threading
+    torch, H = _hermes()
+    L, N, p = 400.0, 256, 4
+    pos = S.lognormal_catalogue(60000, L, seed=33, n_grid=64)
+    jobs = {"wide": (np.linspace(4.0, 84.0, 41), "xi"), "narrow": (np.linspace(6.0, 31.0, 6), "xi"),
+            "zeta": (np.linspace(8.0, 40.0, 7), "zeta")}
+
+    def run(edges, kind, reps, out, key):
+        try:
+            with H.Context(L, N, p) as ctx:
+                ctx.window_shells(edges, l_max=2)
+                ctx.assign(pos)
+                res = []
+                for _ in range(reps):
+                    res.append(ctx.xi_multipoles([0, 2]) if kind == "xi" else ctx.zeta_multipoles())
+                out[key] = res
+        except Exception as e:  # reported by the main thread
+            out[key] = e
+
+    alone = {}
+    for key, (edges, kind) in jobs.items():
+        run(edges, kind, 1, alone, key)
+        assert not isinstance(alone[key], Exception), alone[key]
+    mixed = {}
+    threads = [threading.Thread(target=run, args=(edges, kind, 6, mixed, key)) for key, (edges, kind) in jobs.items()]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for key in jobs:
+        assert not isinstance(mixed[key], Exception), (key, mixed[key])
+        for r in mixed[key]:
+            _close(r, alone[key][0])
+
+
+def test_release_buffers_keeps_the_field_and_frees_the_transients():
+    torch, H = _hermes()
+    L, N, p = 200.0, 64, 4
+    pos = S.lognormal_catalogue(20000, L, seed=44, n_grid=64)
+    with H.Context(L, N, p) as ctx:
+        ctx.window_shells(np.linspace(4.0, 60.0, 9), l_max=2)
+        ctx.assign(pos)
+        xi = ctx.xi_multipoles([0, 2])
+        z = ctx.zeta_multipoles()
+        full = H.lib().hermes_device_bytes(ctx._h)
+        ctx.release_buffers()
+        small = H.lib().hermes_device_bytes(ctx._h)
+        assert small < full - 8 * N ** 3 * 8      # at least the 8 harmonic fields are gone
+        np.testing.assert_allclose(ctx.xi_multipoles([0, 2]), xi, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(ctx.zeta_multipoles(), z, rtol=1e-9, atol=1e-12)
