@@ -338,9 +338,11 @@ def run_hermes(args, rank, world, local_rank):
             else "fallback 6.4 TB/s"}
 
     # the k-space (Parseval) route on the resident marked field: same xi_l, no inverse FFTs
-    ks = run_kspace(ctx, stream, res[1])
-    cyl = run_cylinders(ctx, stream)
-    smu = run_s_mu(ctx, stream, pos_d, mass_d)
+    ks = cyl = smu = None
+    if not args.minimal:
+        ks = run_kspace(ctx, stream, res[1])
+        cyl = run_cylinders(ctx, stream)
+        smu = run_s_mu(ctx, stream, pos_d, mass_d)
     plain = None
     if not args.no_plain:
         ctx.close()
@@ -381,9 +383,9 @@ def run_hermes(args, rank, world, local_rank):
             "kernels": kern,
             "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
         }
-        out["kspace"] = ks
-        out["cylinders"] = cyl
-        out["s_mu"] = smu
+        for key, val in (("kspace", ks), ("cylinders", cyl), ("s_mu", smu)):
+            if val is not None:
+                out[key] = val
         if plain:
             out["vs_plain_fp32"] = plain
         if batch:
@@ -393,7 +395,8 @@ def run_hermes(args, rank, world, local_rank):
         z128 = zeta.pop("_z128", None) if zeta else None
         if zeta:
             out["zeta"] = zeta
-        out["error_vs_oracle"] = error_vs_oracle(res, pos, mass, z128)
+        if not args.minimal:
+            out["error_vs_oracle"] = error_vs_oracle(res, pos, mass, z128)
     return out, pos
 
 
@@ -888,17 +891,25 @@ def run_zeta(args, dev, stream, rank):
             c128.assign(pos_d)
             z128 = (c128.zeta_multipoles(), np.array(g["zeta"]))
     nb = len(EDGES3) - 1
-    nfields = nb * (LMAX3 + 1) * (LMAX3 + 2) // 2
+    nlm = (LMAX3 + 1) * (LMAX3 + 2) // 2
+    nfields = nb * nlm
+    # complex transforms actually run: the m = 0 fields are real, two bins per transform
+    ntrans = nb * (nlm - (LMAX3 + 1)) + (LMAX3 + 1) * ((nb + 1) // 2)
     n3 = float(N3) ** 3
     tot = sum(v[0] for v in tr.values()) or 1.0
-    kern = {k: {"ms": round(v[0] / zsteps, 3), "launches": v[1] // zsteps, "share": round(v[0] / tot, 4)}
-            for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0])}
-    # algorithmic bytes of the y pass: read + write of every complex field (16 B / cell)
-    y_ms = tr.get("zeta_y", (0.0, 0))[0] / zsteps
+    # algorithmic bytes per pass over the step: Z1 reads delta^ (4 B / cell) once per (l, m) and
+    # writes every transform (8 B / cell); Z2 reads and writes them (16 B); Z3 reads them (8 B)
+    # and delta (4 B) once per (l, m)
+    zb = {"zeta_x": (4.0 * nlm + 8.0 * ntrans) * n3, "zeta_y": 16.0 * ntrans * n3,
+          "zeta_z_gram": (8.0 * ntrans + 4.0 * nlm) * n3}
+    kern = {}
+    for k, v in sorted(tr.items(), key=lambda kv: -kv[1][0]):
+        kern[k] = {"ms": round(v[0] / zsteps, 3), "launches": v[1] // zsteps, "share": round(v[0] / tot, 4)}
+        if k in zb and v[0] > 0:
+            kern[k]["alg_GBps"] = round(zb[k] / (v[0] / zsteps / 1e3) / 1e9, 1)
     return {"workload": "zeta_l, 2e6-point lognormal catalogue, L=500, 512^3, 16 shells [10,170), l_max=6",
-            "ms_per_step": round(ms, 2), "complex_fields": nfields,
+            "ms_per_step": round(ms, 2), "complex_fields": nfields, "complex_transforms": ntrans,
             "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
-            "zeta_y_GBps": round(16.0 * n3 * nfields / (y_ms / 1e3) / 1e9, 1) if y_ms else None,
             "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])],
             "_z128": z128}
 
@@ -1021,9 +1032,14 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=60, help="requests in the serving trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
+    ap.add_argument("--minimal", action="store_true",
+                    help="the timed step and its end-to-end form only (implies --no-plain --no-batch --no-serve "
+                         "--no-zeta --no-cpu-baseline); for launch-list captures")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
     args = ap.parse_args()
+    if args.minimal:
+        args.no_plain = args.no_batch = args.no_serve = args.no_zeta = args.no_cpu_baseline = True
     if args.profile_case:
         run_profile_case()
         return 0

@@ -54,12 +54,15 @@ struct WinBatch {
 
 // One batch of complex harmonic windows: all bins of a fixed (l, m).
 // tab = rad + l*Q*nbp; bin b uses tab[q*nbp + b].
+// pack = 1 (m = 0, whose fields are real): bins 2f and 2f+1 share complex field f as
+// its real and imaginary parts, so (S + 1) / 2 fields are transformed instead of S.
 struct HarmBatch {
     const float* tab;
     int nbp;
     int S;      // number of bins (<= 16)
     int ell, m;
     float ylm_norm;  // N_lm (-1)^m (2m-1)!!  times 4 pi
+    int pack = 0;
 };
 
 // Orders of one k-space evaluation (even l, at most 8).  cyl = 1: the entries

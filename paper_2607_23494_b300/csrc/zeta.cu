@@ -13,7 +13,9 @@
 // zeta_l = 1/(4 pi N^3) sum_x delta sum_{m=-l}^{l} conj(a_b1) a_b2 then equals
 // (G_{l0} + 2 sum_{m>0} G_{lm}) / (4 pi N^9) on the unnormalised transforms,
 // since a_{l,-m} = (-1)^m conj(a_{lm}) for a real field (Eq. 2-fold-translation,
-// negative m recovered by conjugation as in Sec. 4.4).
+// negative m recovered by conjugation as in Sec. 4.4).  For m = 0 the fields are real
+// (K_{b l0}(-k) = conj K_{b l0}(k)), so two bins share one complex transform,
+// a_{2f} + i a_{2f+1}, and the Gram takes their real and imaginary parts apart.
 #include "kernels.h"
 #include "fft_core.cuh"
 #include "async_copy.cuh"
@@ -157,12 +159,29 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     float2 wc[3 * twiddled_stages<N>()];  // the thread's stage twiddles, the same for every bin
     load_stage_twiddles<N, true>(t, tb.tw, wc);
     const int nbp = hb.nbp;
+    const int nf = (hb.S + 1) >> 1;  // packed fields (m = 0)
     for (int g = 0; g < hb.S; g += 4) {
         float4 tv[8];  // radial factors of bins g..g+3: one 16-byte load per element
 #pragma unroll
         for (int i = 0; i < 8; ++i)
             tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + trow(i) + g)
                          : __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
+        if (hb.pack) {  // field f = bins 2f (real part) and 2f + 1 (imaginary part; 0 past the last bin)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int f = (g >> 1) + j;
+                if (f >= nf) break;  // uniform across the block
+                float2 v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    v[i] = cmul(v0[i], j == 0 ? make_float2(tv[i].x, tv[i].y) : make_float2(tv[i].z, tv[i].w));
+                fft_line_wc<N, true>(v, t, tb.tw, SmemStrided<W>{smem, col}, wc);
+                float2* dst = fields + (size_t)f * n3 + (size_t)ky * N + kz;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N] = v[i];
+            }
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int b = g + j;
@@ -203,7 +222,9 @@ __constant__ int kGramTiles[10] = {0, 1, 2, 3, 5, 6, 7, 10, 11, 15};
 // transformed along z (T threads each) into shared memory; then the 10 upper
 // 4x4 bin tiles x 3 z-slices per warp accumulate the Gram, float32 per line, flushed to
 // float64 registers every 8 lines.  Partial Gram per block: part[(b1*16+b2)*nblk + blk].
-template <int N>
+// REAL: the S lines are packed real fields (m = 0): line f holds bins 2f and 2f + 1, and
+// the Gram runs over the 2S real components.
+template <int N, bool REAL>
 __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __restrict__ fields, int S,
                                                               const float* __restrict__ delta,
                                                               const float2* __restrict__ tw,
@@ -294,7 +315,21 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
                 fetch(line + gridDim.x, (it + 1) & 1);
             }
         }
-        if (active) {
+        if (REAL && active) {
+            for (int z = zs; z < N; z += NS) {
+                const float d = dsm[z];
+                const int zp = SmemLine<N>::at(z);
+                // rows 4 ti .. 4 ti + 3 are lines 2 ti, 2 ti + 1 (real, imaginary parts)
+                const float2 p0 = smem[(2 * ti) * LPZ + zp], p1 = smem[(2 * ti + 1) * LPZ + zp];
+                const float2 r0 = smem[(2 * tj) * LPZ + zp], r1 = smem[(2 * tj + 1) * LPZ + zp];
+                const float x[4] = {p0.x * d, p0.y * d, p1.x * d, p1.y * d};
+                const float y[4] = {r0.x, r0.y, r1.x, r1.y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) acc[k][k2] = fmaf(x[k], y[k2], acc[k][k2]);
+            }
+        } else if (active) {
             for (int z = zs; z < N; z += NS) {
                 const float d = dsm[z];
                 const int zp = SmemLine<N>::at(z);
@@ -621,12 +656,16 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     if ((e = allow_smem_z(k_zeta_x<N, false>, C::SMEM_X)) != cudaSuccess) return e;
     if (use_stab && (e = allow_smem_z(k_zeta_x<N, true>, stab_bytes)) != cudaSuccess) return e;
     if ((e = allow_smem_z(k_zeta_y<N>, C::SMEM_X)) != cudaSuccess) return e;
+    // m = 0: real fields, two bins per transform (the opt-in tensor-core Gram takes them unpacked)
+    HarmBatch hp = hb;
+    hp.pack = (hb.m == 0 && hb.S > 1 && !zeta_tc_enabled(N)) ? 1 : 0;
+    const int nf = hp.pack ? (hb.S + 1) / 2 : hb.S;  // complex fields transformed
     dim3 g1(N / C::W, N, 1);
     tr(K_ZETA_X, 0, st);
-    if (use_stab) k_zeta_x<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, fields, hb, tb);
-    else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hb, tb);
+    if (use_stab) k_zeta_x<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, fields, hp, tb);
+    else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hp, tb);
     tr(K_ZETA_X, 1, st);
-    dim3 g2(N / C::W, N, hb.S);
+    dim3 g2(N / C::W, N, nf);
     tr(K_ZETA_Y, 0, st);
     k_zeta_y<N><<<g2, C::TS, C::SMEM_X, st>>>(fields, tb.tw);
     tr(K_ZETA_Y, 1, st);
@@ -640,9 +679,16 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
             return cudaGetLastError();
         }
     }
-    if ((e = allow_smem_z(k_zeta_z_gram<N>, C::SMEM_Z)) != cudaSuccess) return e;
     tr(K_ZETA_Z_GRAM, 0, st);
-    k_zeta_z_gram<N><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw, gram_part, err);
+    if (hp.pack) {
+        if ((e = allow_smem_z(k_zeta_z_gram<N, true>, C::SMEM_Z)) != cudaSuccess) return e;
+        k_zeta_z_gram<N, true><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, nf, delta, tb.tw, gram_part,
+                                                                               err);
+    } else {
+        if ((e = allow_smem_z(k_zeta_z_gram<N, false>, C::SMEM_Z)) != cudaSuccess) return e;
+        k_zeta_z_gram<N, false><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw,
+                                                                                gram_part, err);
+    }
     tr(K_ZETA_Z_GRAM, 1, st);
     return cudaGetLastError();
 }
