@@ -285,6 +285,9 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
         }
         for (int r = 0; r < rounds; ++r) {
             const int b = r * GB + bb;
+            // lines past the last bin hold no data; where a line owns whole warps (N >= 256)
+            // they skip the transform (their Gram products are never read)
+            if (T >= 32 && b >= S) continue;
             float2 v[8];
             if (b < S) {
                 if constexpr (PREF) {

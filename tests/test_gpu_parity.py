@@ -281,9 +281,10 @@ def test_zeta_two_warp_lines_at_512_match_block_synchronised_gram(monkeypatch):
         np.testing.assert_array_equal(res["0"][ell], res["0"][ell].T)
 
 
-@pytest.mark.parametrize("N,nb", [(32, 16), (64, 7), (128, 16)])
+@pytest.mark.parametrize("N,nb", [(32, 16), (64, 7), (128, 16), (256, 5)])
 def test_zeta_tensor_core_gram_matches_simt_and_oracle(N, nb, monkeypatch):
-    # the tcgen05 split-TF32 Gram (opt-in) against the float32 SIMT Gram (default),
+    # the tcgen05 split-TF32 Gram (opt-in, unpacked fields) against the float32 SIMT Gram
+    # (default: m = 0 bins packed in pairs; at 256^3 an odd bin count leaves idle lines),
     # and both against the oracle at 32^3
     H = _hermes()
     L, p, l_max = 3.0 * N, 4, 3
