@@ -128,7 +128,7 @@ int hermes_assign_noalloc(hermes_ctx *ctx, const float *pos, const float *w, int
  * |k| of the grid (Eq. Wshell_k for l = 0; Sec. 3.4.3, "its average over the
  * corresponding radial window", for l > 0).  Tables are stored as float32.
  *   r_edges: strictly increasing, r_edges[0] >= 0, r_edges[n_edges-1] <= L/2.
- *   n_edges: 2 .. 4097.   l_max: 0 .. 12.
+ *   n_edges: 2 .. 4097.   l_max: 0 .. 24.
  * Errors: HERMES_ERR_ARG, HERMES_ERR_RANGE (edges out of range), HERMES_ERR_NOMEM.
  */
 int hermes_window_shells(hermes_ctx *ctx, const double *r_edges, int n_edges, int l_max);
@@ -335,9 +335,11 @@ int hermes_xi_rings_kspace(hermes_ctx *ctx, double *out);
  * (Eq. 2-fold-translation).  Only m >= 0 fields are built; m < 0 follows by
  * conjugation.  Returned raw: the diagonal b1 == b2 includes self triplets.
  *   out: [l_max+1][n_bins][n_bins] float64 (symmetric in b1, b2).
- *   Requires n_bins <= 16.
- * Errors: HERMES_ERR_STATE, HERMES_ERR_ARG (too many bins), HERMES_ERR_NOMEM,
- * HERMES_ERR_CUDA.
+ * Up to 16 bins are transformed and contracted together.  More bins are taken
+ * in blocks of 8, and every pair of blocks runs as one batch of at most 16 bins
+ * (B (B + 1) / 2 batches for B blocks, each Gram entry kept from its own pair).
+ * Errors: HERMES_ERR_STATE, HERMES_ERR_ARG, HERMES_ERR_NOMEM, HERMES_ERR_CUDA,
+ * HERMES_ERR_TIMEOUT (a bounded wait gave up).
  */
 int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
 

@@ -254,7 +254,7 @@ void bessel_moment_all(double x, int lmax, double* out) {
         }
     }
     if (first_rec > lmax) return;
-    // closed forms for l >= first_rec (all with x >= l + 4)
+    // closed forms for l >= first_rec (used for the orders with x >= l + 4)
     const double sn = std::sin(x), cs = std::cos(x), si = sine_integral(x);
     const int M = lmax + 1;
     std::vector<double> jl(M + 1), Hm(M + 1), Jm(M + 1), Il(M + 1);
@@ -270,7 +270,9 @@ void bessel_moment_all(double x, int lmax, double* out) {
     Il[0] = sn - x * cs;
     Il[1] = 2.0 - 2.0 * cs - x * sn;
     for (int l = 2; l <= lmax; ++l) Il[l] = (2.0 * l - 1.0) * Jm[l - 1] - Il[l - 2];
-    for (int l = first_rec; l <= lmax; ++l) out[l] = Il[l];
+    // only where x >= l + 4: below that the recurrence cancels and the series (above) holds
+    for (int l = first_rec; l <= lmax; ++l)
+        if (!(x < l + 4.0)) out[l] = Il[l];
 }
 
 // out[((b*(lmax+1)) + l)*Q + q] = <j_l>_b(k_q), k_q = 2 pi sqrt(q) / L.
@@ -682,7 +684,7 @@ int64_t hermes_shell_table_len(int N) {
 }
 
 int hermes_shell_table_host(double L, int N, const double* r_edges, int n_edges, int l_max, double* out) {
-    if (!valid_N(N) || !(L > 0) || !r_edges || !out || n_edges < 2 || l_max < 0 || l_max > 12) return HERMES_ERR_ARG;
+    if (!valid_N(N) || !(L > 0) || !r_edges || !out || n_edges < 2 || l_max < 0 || l_max > 24) return HERMES_ERR_ARG;
     for (int e = 0; e < n_edges; ++e)
         if (!std::isfinite(r_edges[e]) || (e > 0 && !(r_edges[e] > r_edges[e - 1])) || r_edges[e] < 0)
             return HERMES_ERR_RANGE;
@@ -739,7 +741,7 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!r_edges) return fail(c, HERMES_ERR_ARG, "r_edges is NULL");
     if (n_edges < 2 || n_edges > 4097) return fail(c, HERMES_ERR_ARG, "n_edges = %d (need 2..4097)", n_edges);
-    if (l_max < 0 || l_max > 12) return fail(c, HERMES_ERR_ARG, "l_max = %d (need 0..12)", l_max);
+    if (l_max < 0 || l_max > 24) return fail(c, HERMES_ERR_ARG, "l_max = %d (need 0..24)", l_max);
     for (int e = 0; e < n_edges; ++e) {
         if (!std::isfinite(r_edges[e]) || r_edges[e] < 0.0)
             return fail(c, HERMES_ERR_RANGE, "r_edges[%d] = %g is negative or not finite", e, r_edges[e]);
@@ -966,58 +968,88 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
                                          "hermes_assign first");
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
     if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
-    if (c->n_bins > 16) return fail(c, HERMES_ERR_ARG, "zeta_l supports at most 16 bins (have %d)", c->n_bins);
     DeviceGuard g(c->device);
     cudaStream_t st = c->stream;
     const int N = c->N, nb = c->n_bins, LM = c->l_max + 1;
     const size_t n3 = (size_t)N * N * N;
-    CK(grow(c->zfields, c->zfields_bytes, (size_t)nb * n3 * sizeof(float2)), "harmonic fields");
+    // Up to 16 bins go through the passes together.  More bins are taken in blocks of 8:
+    // every pair of blocks (I <= J) runs as one batch of at most 16 bins, and each Gram
+    // entry is kept from the run of its two bins' blocks.
+    struct Run {
+        int I, J, S;  // J = -1: block I alone (or all bins when nb <= 16)
+    };
+    std::vector<Run> runs;
+    const int nblk = (nb + 7) / 8;
+    auto bsize = [&](int I) { return std::min(8, nb - 8 * I); };
+    if (nb <= 16) {
+        runs.push_back({0, -1, nb});
+    } else {
+        for (int I = 0; I < nblk; ++I)
+            for (int J = I; J < nblk; ++J) runs.push_back({I, J == I ? -1 : J, bsize(I) + (J == I ? 0 : bsize(J))});
+    }
+    const int nruns = (int)runs.size();
+    const int smax = std::min(nb, 16);
+    CK(grow(c->zfields, c->zfields_bytes, (size_t)smax * n3 * sizeof(float2)), "harmonic fields");
     const int zb = zeta_z_blocks(N);
     CK(grow_doubles(c->part, c->part_cap, (size_t)256 * zb), "partials");
     const int nlm = LM * (LM + 1) / 2;
-    CK(grow_doubles(c->red, c->red_cap, (size_t)256 * nlm), "reduction buffer");
+    CK(grow_doubles(c->red, c->red_cap, (size_t)256 * nlm * nruns), "reduction buffer");
     const Tables tb = tables_of(c);
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     int lm = 0;
     for (int ell = 0; ell < LM; ++ell) {
         for (int m = 0; m <= ell; ++m, ++lm) {
-            HarmBatch hb;
-            hb.S = nb;
-            hb.ell = ell;
-            hb.m = m;
             double norm = std::sqrt((2.0 * ell + 1.0) / (4.0 * M_PI) * std::tgamma(ell - m + 1.0) /
                                     std::tgamma(ell + m + 1.0));
             norm *= ((m & 1) ? -1.0 : 1.0) * dfact2(2 * m - 1);
-            hb.ylm_norm = (float)(4.0 * M_PI * norm);
-            hb.tab = c->rad + (size_t)ell * c->Q * c->nbp;
-            hb.nbp = c->nbp;
-            CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, c->err, st, c->tracer),
-               "harmonic fields");
-            CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * lm, st, c->tracer), "reduce Gram");
+            const float* tab_l = c->rad + (size_t)ell * c->Q * c->nbp;
+            for (int r = 0; r < nruns; ++r) {
+                HarmBatch hb;
+                hb.S = runs[r].S;
+                hb.ell = ell;
+                hb.m = m;
+                hb.ylm_norm = (float)(4.0 * M_PI * norm);
+                hb.tab = tab_l + 8 * runs[r].I;
+                hb.tab2 = runs[r].J >= 0 ? tab_l + 8 * runs[r].J : nullptr;
+                hb.nbp = c->nbp;
+                CK(launch_zeta_lm(N, c->spec, c->zfields, c->grid, hb, tb, c->part, c->err, st, c->tracer),
+                   "harmonic fields");
+                CK(launch_reduce_rows(c->part, 256, zb, c->red + (size_t)256 * ((size_t)lm * nruns + r), st,
+                                      c->tracer),
+                   "reduce Gram");
+            }
         }
     }
-    CK(ensure_host(c, (size_t)256 * nlm) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(ensure_host(c, (size_t)256 * nlm + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
-    CK(cudaMemcpyAsync(c->host_buf, c->red, (size_t)256 * nlm * sizeof(double), cudaMemcpyDeviceToHost, st),
-       "read Gram");
-    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + (size_t)256 * nlm);
+    const size_t nred = (size_t)256 * nlm * nruns;
+    CK(ensure_host(c, nred + 1) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->red, nred * sizeof(double), cudaMemcpyDeviceToHost, st), "read Gram");
+    unsigned* hflag = reinterpret_cast<unsigned*>(c->host_buf + nred);
     CK(cudaMemcpyAsync(hflag, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "read flag");
     CK(cudaStreamSynchronize(st), "zeta");
     if (*hflag & 2u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on the tensor-core pipeline gave up");
+    if (*hflag & 4u) return fail(c, HERMES_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
     const double nn = (double)N;
     const double scale = 1.0 / (4.0 * M_PI * std::pow(nn, 9));
+    for (size_t e = 0; e < (size_t)LM * nb * nb; ++e) out[e] = 0.0;
     lm = 0;
     for (int ell = 0; ell < LM; ++ell) {
         double* o = out + (size_t)ell * nb * nb;
-        for (int i = 0; i < nb * nb; ++i) o[i] = 0.0;
         for (int m = 0; m <= ell; ++m, ++lm) {
-            const double* G = c->host_buf + (size_t)256 * lm;
             const double wm = (m == 0) ? 1.0 : 2.0;
-            for (int b1 = 0; b1 < nb; ++b1)
-                for (int b2 = 0; b2 < nb; ++b2) {
-                    const double gv = (b1 <= b2) ? G[b1 * 16 + b2] : G[b2 * 16 + b1];  // exact symmetry
-                    o[b1 * nb + b2] += wm * gv * scale;
-                }
+            for (int r = 0; r < nruns; ++r) {
+                const double* G = c->host_buf + (size_t)256 * ((size_t)lm * nruns + r);
+                const Run& ru = runs[r];
+                auto glob = [&](int i) { return (ru.J >= 0 && i >= 8) ? 8 * ru.J + (i - 8) : 8 * ru.I + i; };
+                for (int i1 = 0; i1 < ru.S; ++i1)
+                    for (int i2 = i1; i2 < ru.S; ++i2) {
+                        // a pair run keeps only its cross entries (block I x block J)
+                        if (ru.J >= 0 && !(i1 < 8 && i2 >= 8)) continue;
+                        const int b1 = glob(i1), b2 = glob(i2);
+                        const double v = wm * G[i1 * 16 + i2] * scale;  // upper triangle, exact symmetry
+                        o[(size_t)b1 * nb + b2] += v;
+                        if (b1 != b2) o[(size_t)b2 * nb + b1] += v;
+                    }
+            }
         }
     }
     return HERMES_OK;
@@ -1759,8 +1791,9 @@ extern "C" int64_t hermes_estimate_bytes(int N, int stat, int n_bins, int l_max,
          scatter_tiled_region_floats(N, 8) * sizeof(float);
     b += (size_t)std::max(2, 512) * 592 * sizeof(double) + 1024 * sizeof(double);  // assign partials
     if (stat == 2) {
-        b += (size_t)n_bins * n3 * sizeof(float2) + (size_t)256 * zeta_z_blocks(N) * sizeof(double);
-        b += (size_t)256 * (l_max + 1) * (l_max + 2) / 2 * sizeof(double);
+        const size_t nblk = (size_t)(n_bins + 7) / 8, nruns = n_bins <= 16 ? 1 : nblk * (nblk + 1) / 2;
+        b += (size_t)std::min(n_bins, 16) * n3 * sizeof(float2) + (size_t)256 * zeta_z_blocks(N) * sizeof(double);
+        b += (size_t)256 * (l_max + 1) * (l_max + 2) / 2 * nruns * sizeof(double);
     } else {
         const size_t S = xi_window_S(N, n_bins);
         b += S * n * n * (n / 2) * sizeof(float2);

@@ -56,8 +56,11 @@ struct WinBatch {
 // tab = rad + l*Q*nbp; bin b uses tab[q*nbp + b].
 // pack = 1 (m = 0, whose fields are real): bins 2f and 2f+1 share complex field f as
 // its real and imaginary parts, so (S + 1) / 2 fields are transformed instead of S.
+// tab2 != nullptr: bins 8..S-1 of the batch come from tab2 (bin b uses tab2[q*nbp + b - 8]),
+// so one launch can pair two blocks of 8 bins that are not adjacent in the table.
 struct HarmBatch {
     const float* tab;
+    const float* tab2 = nullptr;
     int nbp;
     int S;      // number of bins (<= 16)
     int ell, m;

@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
             const int kzc = blockIdx.x * W + c, nzc = signed_freq(kzc, N);
             // Nyquist rows and columns carry K = 0: read row 0, which is always in range
             const int qq = (ky == H || kzc == H) ? 0 : a * a + ny * ny + nzc * nzc;
-            ac::cp_async16(ttab + (a * W + c) * RS + 4 * s4,
-                           reinterpret_cast<const float4*>(hb.tab + (size_t)qq * hb.nbp) + s4);
+            const float* src = (hb.tab2 && s4 >= 2) ? hb.tab2 + (size_t)qq * hb.nbp + 4 * (s4 - 2)
+                                                     : hb.tab + (size_t)qq * hb.nbp + 4 * s4;
+            ac::cp_async16(ttab + (a * W + c) * RS + 4 * s4, src);
         }
         ac::cp_async_commit();
     }
@@ -165,7 +166,9 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
 #pragma unroll
         for (int i = 0; i < 8; ++i)
             tv[i] = STAB ? *reinterpret_cast<const float4*>(ttab + trow(i) + g)
-                         : __ldg(reinterpret_cast<const float4*>(hb.tab + (size_t)q[i] * nbp + g));
+                         : __ldg(reinterpret_cast<const float4*>(
+                               (hb.tab2 && g >= 8) ? hb.tab2 + (size_t)q[i] * nbp + (g - 8)
+                                                   : hb.tab + (size_t)q[i] * nbp + g));
         if (hb.pack) {  // field f = bins 2f (real part) and 2f + 1 (imaginary part; 0 past the last bin)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {

@@ -139,6 +139,24 @@ def test_xi_multipoles_and_marked_ragged_batches():
     _close(got_m, ref_m)
 
 
+def test_xi_multipoles_to_order_20_match_oracle():
+    # Legendre windows up to l = 20: the host tables switch between the power series and
+    # the closed-form recurrences of the Bessel moments at x = l + 4
+    H = _hermes()
+    N, L, p = 32, 120.0, 4
+    pos = S.mixed_poisson_sp(8000, L, seed=205)
+    edges = np.linspace(3.0, 45.0, 7)
+    ells = (0, 8, 14, 20)
+    with H.Context(L, N, p) as ctx:
+        ctx.assign(pos)
+        ctx.window_shells(edges, l_max=20)
+        got = ctx.xi_multipoles(ells)
+        gk = ctx.xi_multipoles_kspace(ells)
+    ref = O.xi_multipoles(pos, None, N, L, p, edges, ells=ells)["xi"]
+    _close(got, ref)
+    _close(gk, ref)
+
+
 def test_xi_other_orders_and_sizes():
     H = _hermes()
     for (N, p, L) in [(16, 2, 50.0), (32, 3, 120.0), (128, 6, 400.0)]:
@@ -211,7 +229,7 @@ def test_argument_errors():
             ctx.xi_multipoles([1])
         assert ei.value.code == H.ERR_ARG
         with pytest.raises(H.HermesError) as ei:
-            ctx.zeta_multipoles()                      # 17 bins > 16
+            ctx.window_shells(np.linspace(1, 40, 18), 25)  # l_max beyond 24
         assert ei.value.code == H.ERR_ARG
         bad = S.poisson_uniform(10, 100.0, 2)
         bad[3, 1] = np.nan
@@ -220,8 +238,10 @@ def test_argument_errors():
         assert ei.value.code == H.ERR_RANGE
 
 
-@pytest.mark.parametrize("N,nb,l_max", [(16, 3, 3), (32, 4, 4), (32, 16, 2)])
+@pytest.mark.parametrize("N,nb,l_max", [(16, 3, 3), (32, 4, 4), (32, 16, 2), (32, 20, 2), (32, 3, 14)])
 def test_zeta_multipoles_match_oracle(N, nb, l_max):
+    # 20 bins: blocks of 8, 8 and 4 run as the six pairs of blocks; l_max 14: the paper's
+    # DDD_l runs reach l_max 14 and 20
     H = _hermes()
     L, p = 4.0 * N, 4
     pos = S.mixed_poisson_sp(3000, L, seed=N + nb)

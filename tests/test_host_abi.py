@@ -55,8 +55,10 @@ def test_no_gpu_means_an_error_status_not_a_crash():
 @pytest.mark.parametrize("N,L", [(64, 250.0), (32, 1000.0)])
 def test_host_shell_tables_match_oracle_quadrature(N, L):
     from paper_2607_23494_b300 import shell_table_host
+    # orders up to 24 (the paper's 3PCF runs reach l_max 20): the series and the closed-form
+    # recurrences must each be used only where they are accurate
     edges = [0.0, 2.0, 5.0, 7.5, 30.0, 100.0, L / 2]
-    l_max = 6
+    l_max = 24
     tab = shell_table_host(L, N, edges, l_max)
     Q = tab.shape[-1]
     assert Q == 3 * (N // 2 - 1) ** 2 + 1
@@ -68,7 +70,7 @@ def test_host_shell_tables_match_oracle_quadrature(N, L):
         np.testing.assert_allclose(tab[b, 0], ref0, rtol=1e-10, atol=1e-13)
         for ell in range(1, l_max + 1):
             ref = O.shell_avg_jl(ell, k, lo, hi)
-            np.testing.assert_allclose(tab[b, ell], ref, rtol=1e-8, atol=1e-11,
+            np.testing.assert_allclose(tab[b, ell], ref, rtol=1e-8, atol=1e-11 + 1e-9 * np.abs(ref).max(),
                                        err_msg=f"bin {b} l {ell}")
 
 
