@@ -880,6 +880,27 @@ def run_zeta(args, dev, stream, rank):
     ms = e0.elapsed_time(e1) / zsteps
     tr = ctx.trace_read()
     ctx.close()
+    # the paper's DDD_l(20, 40) runs (its performance table: one (r12, r13) pair at l_max 7, 14
+    # and 20, J = 9 i.e. 512^3): two 2 Mpc/h shells at 20 and 40 Mpc/h on the same field
+    ddd = {}
+    c2 = Context(L3, N3, 4)
+    c2.set_stream(stream)
+    c2.assign(pos_d)
+    for lm_ in (7, 14, 20):
+        c2.window_shells([19.0, 21.0, 39.0, 41.0], l_max=lm_)
+        c2.zeta_multipoles()  # tables and buffers
+        torch.cuda.synchronize()
+        e0.record(stream)
+        zz = c2.zeta_multipoles()
+        e1.record(stream)
+        stream.synchronize()
+        nm = (lm_ + 1) * (lm_ + 2) // 2
+        ddd[f"l_max_{lm_}"] = {"ms": round(e0.elapsed_time(e1), 2), "m_modes": nm,
+                               "ms_per_m": round(e0.elapsed_time(e1) / nm, 3), "zeta0_12": float(zz[0, 0, 2])}
+    c2.close()
+    ddd["paper_context"] = ("paper, J = 9 (512^3): l_max 7 in 219 s (6.07 s/m), l_max 14 in 822 s (6.85 s/m) on "
+                            "12 MPI x 8 threads + an RTX 4090; shells here [19, 21) and [39, 41) Mpc/h (the paper's "
+                            "r12 = 20, r13 = 40; its bin widths are not given)")
     # the same catalogue regridded on 128^3 against the stored FP64 oracle zeta_l
     z128 = None
     g = load_golden("zeta_lognormal_2e6_128_lmax6.json")
@@ -911,7 +932,7 @@ def run_zeta(args, dev, stream, rank):
             "ms_per_step": round(ms, 2), "complex_fields": nfields, "complex_transforms": ntrans,
             "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
             "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])],
-            "_z128": z128}
+            "ddd_l_20_40": ddd, "_z128": z128}
 
 
 def oracle_sample(pos, b: int = 0):

@@ -11,6 +11,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -147,7 +148,38 @@ int cuda_fail(hermes_ctx* c, cudaError_t e, const char* what) {
 // Every device allocation of the library goes through here.  The test hook
 // hermes_debug_fail_allocs makes the next few report out of memory without
 // allocating, so the error paths can be exercised without exhausting a GPU.
+//
+// Context memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// context's stream, named by AllocStream for the duration of each entry point):
+// a context that grows or releases a buffer then never waits for the whole
+// device, so contexts on other streams (the request server's workers) keep
+// running.  Every entry point synchronises its stream before returning, so a
+// buffer is idle whenever it is freed or the context's stream is changed.
 std::atomic<int> g_fail_allocs{0};
+thread_local cudaStream_t t_alloc_stream = nullptr;
+
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+    ~AllocStream() { t_alloc_stream = prev; }
+};
+
+// The device's default pool keeps up to 8 GiB of freed memory between synchronisations
+// (released beyond that), so buffers that are freed and grown again are cheap.
+void pool_setup(int dev) {
+    static std::mutex mu;
+    static bool done[256] = {false};
+    if (dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = (uint64_t)8 << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
 
 cudaError_t dev_malloc(void** ptr, size_t bytes) {
     int n = g_fail_allocs.load();
@@ -157,13 +189,27 @@ cudaError_t dev_malloc(void** ptr, size_t bytes) {
             return cudaErrorMemoryAllocation;
         }
     }
+    if (t_alloc_stream) return cudaMallocAsync(ptr, bytes, t_alloc_stream);
     return cudaMalloc(ptr, bytes);
+}
+
+void dev_free(void* ptr) {
+    if (!ptr) return;
+    if (t_alloc_stream) cudaFreeAsync(ptr, t_alloc_stream);
+    else cudaFree(ptr);
+}
+
+// Host-to-device upload into a context buffer, ordered after its allocation on stream st;
+// returns once the host source may be reused.
+cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(st);
 }
 
 template <class T>
 cudaError_t grow(T*& ptr, size_t& cap_bytes, size_t need_bytes) {
     if (need_bytes <= cap_bytes && ptr) return cudaSuccess;
-    if (ptr) cudaFree(ptr);
+    if (ptr) dev_free(ptr);
     ptr = nullptr;
     cap_bytes = 0;
     cudaError_t e = dev_malloc((void**)&ptr, need_bytes);
@@ -405,8 +451,8 @@ int ensure_host(hermes_ctx* c, size_t n) {
 cudaError_t tiled_scratch(hermes_ctx* c, int64_t n) {
     cudaError_t e;
     if ((size_t)n > c->ts_pts_cap) {
-        cudaFree(c->ts_tile_of);
-        cudaFree(c->ts_perm);
+        dev_free(c->ts_tile_of);
+        dev_free(c->ts_perm);
         c->ts_tile_of = nullptr;
         c->ts_perm = nullptr;
         c->ts_pts_cap = 0;
@@ -420,7 +466,7 @@ cudaError_t tiled_scratch(hermes_ctx* c, int64_t n) {
     }
     const size_t rf = scatter_tiled_region_floats(c->N, c->p);
     if (rf > c->ts_regions_cap) {
-        cudaFree(c->ts_regions);
+        dev_free(c->ts_regions);
         c->ts_regions = nullptr;
         c->ts_regions_cap = 0;
         if ((e = dev_malloc((void**)&c->ts_regions, rf * sizeof(float))) != cudaSuccess) return e;
@@ -429,9 +475,30 @@ cudaError_t tiled_scratch(hermes_ctx* c, int64_t n) {
     return cudaSuccess;
 }
 
-// The shared-memory scatter of n points into dst (an N^3 grid; no clearing needed).
+// The tiled scatter has a fixed cost that grows with N^3 (it writes and re-reads one
+// (16+p-1)^3 region per 16^3 tile); per-point global atomics on a cleared grid cost more per
+// point but little per cell.  Measured on B300 (p = 4, whole hermes_assign): the atomics are
+// faster below about 1.2e6 points at 512^3 and 4e6 at 256^3, and at every size up to 1e7 at
+// 128^3; 1024^3 (eight times the fixed cost of 512^3) is extrapolated to 9e6.
+// HERMES_SCATTER=tiled or =atomic forces one form (tests run both on every order p).
+bool sparse_scatter(int N, int64_t n) {
+    const char* force = getenv("HERMES_SCATTER");
+    if (force && std::strcmp(force, "tiled") == 0) return false;
+    if (force && std::strcmp(force, "atomic") == 0) return true;
+    if (N <= 128) return true;
+    const double limit = N == 256 ? 4e6 : (N == 512 ? 1.2e6 : 9e6);
+    return (double)n < limit;
+}
+
+// Scatter of n points into dst (an N^3 grid): the shared-memory tiled form for dense
+// catalogues (no clearing needed), global atomics on a cleared grid for sparse ones.
 cudaError_t scatter_tiled(hermes_ctx* c, const float* pos, const float* w, int64_t n, float* dst, float s, int wrap,
                           cudaStream_t st) {
+    if (sparse_scatter(c->N, n)) {
+        cudaError_t e = cudaMemsetAsync(dst, 0, (size_t)c->N * c->N * c->N * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+        return launch_scatter(c->N, c->p, pos, w, n, dst, s, wrap, c->err, st, c->tracer);
+    }
     cudaError_t e = tiled_scratch(c, n);
     if (e != cudaSuccess) return e;
     const size_t nt = (size_t)scatter_tiled_tiles(c->N);
@@ -481,6 +548,8 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
     const size_t n3 = (size_t)N * N * N;
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     c->stream = c->own_stream;
+    pool_setup(c->device);
+    AllocStream as_(c->own_stream);  // every buffer of the context comes from the stream-ordered pool
     if (dev_malloc((void**)&c->grid, n3 * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (dev_malloc((void**)&c->spec, (size_t)N * N * c->H * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (dev_malloc((void**)&c->scal, 8 * sizeof(double)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
@@ -489,6 +558,9 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
     if (dev_malloc((void**)&c->err, sizeof(unsigned)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (dev_malloc((void**)&c->tw, TW_ENTRIES * sizeof(float2)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
     if (dev_malloc((void**)&c->phi, N * sizeof(float)) != cudaSuccess) return bail(HERMES_ERR_NOMEM);
+    // the allocations are ordered on the context's stream: complete them before the copies
+    // below (legacy stream) and before any other stream uses the buffers
+    if (cudaStreamSynchronize(c->own_stream) != cudaSuccess) return bail(HERMES_ERR_CUDA);
     // multi-level twiddles tw[L + j] = e^{-2 pi i j / L} (L = 2, 4, ..., TW) and
     // Phi^(n) = sinc^{2p}(pi n / N), in float64, stored as float32
     std::vector<float2> tw(TW_ENTRIES, make_float2(0.f, 0.f));
@@ -522,34 +594,35 @@ int hermes_create(double L, int N, int p, int j, hermes_ctx** out) {
 int hermes_destroy(hermes_ctx* c) {
     if (!c) return HERMES_OK;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    cudaFree(c->grid);
-    cudaFree(c->spec);
-    cudaFree(c->work);
-    cudaFree(c->zfields);
-    cudaFree(c->part);
-    cudaFree(c->red);
-    cudaFree(c->scal);
-    cudaFree(c->stab_d);
-    cudaFree(c->stab_f);
-    cudaFree(c->err);
-    cudaFree(c->tw);
-    cudaFree(c->phi);
-    cudaFree(c->stage_pos);
-    cudaFree(c->stage_w);
-    cudaFree(c->rad);
-    cudaFree(c->cyl_perp);
-    cudaFree(c->cyl_par);
-    cudaFree(c->rgrid);
-    cudaFree(c->rspec);
-    cudaFree(c->rstab_d);
-    cudaFree(c->rstab_f);
-    cudaFree(c->rscal);
-    cudaFree(c->smooth_tab);
-    cudaFree(c->ts_tile_of);
-    cudaFree(c->ts_perm);
-    cudaFree(c->ts_tiles);
-    cudaFree(c->ts_regions);
+    dev_free(c->grid);
+    dev_free(c->spec);
+    dev_free(c->work);
+    dev_free(c->zfields);
+    dev_free(c->part);
+    dev_free(c->red);
+    dev_free(c->scal);
+    dev_free(c->stab_d);
+    dev_free(c->stab_f);
+    dev_free(c->err);
+    dev_free(c->tw);
+    dev_free(c->phi);
+    dev_free(c->stage_pos);
+    dev_free(c->stage_w);
+    dev_free(c->rad);
+    dev_free(c->cyl_perp);
+    dev_free(c->cyl_par);
+    dev_free(c->rgrid);
+    dev_free(c->rspec);
+    dev_free(c->rstab_d);
+    dev_free(c->rstab_f);
+    dev_free(c->rscal);
+    dev_free(c->smooth_tab);
+    dev_free(c->ts_tile_of);
+    dev_free(c->ts_perm);
+    dev_free(c->ts_tiles);
+    dev_free(c->ts_regions);
     batch_free(c->batch);
     c->batch = nullptr;
     if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -567,14 +640,15 @@ int hermes_destroy(hermes_ctx* c) {
 int hermes_release_buffers(hermes_ctx* c) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     CK(cudaStreamSynchronize(c->stream), "release buffers");
-    cudaFree(c->work);
-    cudaFree(c->zfields);
-    cudaFree(c->stage_pos);
-    cudaFree(c->stage_w);
-    cudaFree(c->ts_tile_of);
-    cudaFree(c->ts_perm);
-    cudaFree(c->ts_regions);
+    dev_free(c->work);
+    dev_free(c->zfields);
+    dev_free(c->stage_pos);
+    dev_free(c->stage_w);
+    dev_free(c->ts_tile_of);
+    dev_free(c->ts_perm);
+    dev_free(c->ts_regions);
     c->work = nullptr;
     c->zfields = nullptr;
     c->stage_pos = c->stage_w = nullptr;
@@ -614,6 +688,7 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
                            (long long)n);
     if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     c->have_field = false;
     cudaStream_t st = c->stream;
     const int N = c->N, p = c->p;
@@ -625,8 +700,8 @@ int hermes_assign(hermes_ctx* c, const float* pos, const float* w, int64_t n, un
         if (w && (r = check_device_ptr(c, w, "w"))) return r;
     } else {
         if ((size_t)n > c->stage_cap) {
-            cudaFree(c->stage_pos);
-            cudaFree(c->stage_w);
+            dev_free(c->stage_pos);
+            dev_free(c->stage_w);
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
@@ -751,6 +826,7 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
     if (r_edges[n_edges - 1] > 0.5 * c->L)
         return fail(c, HERMES_ERR_RANGE, "largest edge %g exceeds L/2 = %g", r_edges[n_edges - 1], 0.5 * c->L);
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const int64_t Q = table_len(c->N);
     const int nb = n_edges - 1;
     const int nbp = (nb + 3) & ~3;
@@ -778,12 +854,12 @@ int hermes_window_shells(hermes_ctx* c, const double* r_edges, int n_edges, int 
         table_insert(c->L, c->N, r_edges, n_edges, l_max, host32);
     }
     cudaStreamSynchronize(c->stream);
-    cudaFree(c->rad);
+    dev_free(c->rad);
     c->rad = nullptr;
     c->n_bins = 0;
     CK(dev_malloc((void**)&c->rad, count_dev * sizeof(float)), "window tables");
     // the orders 0..l_max are the leading blocks of a cached table built for a larger l_max
-    CK(cudaMemcpy(c->rad, tab->data(), count_dev * sizeof(float), cudaMemcpyHostToDevice), "upload window tables");
+    CK(upload(c->rad, tab->data(), count_dev * sizeof(float), c->stream), "upload window tables");
     c->edges.assign(r_edges, r_edges + n_edges);
     c->n_bins = nb;
     c->l_max = l_max;
@@ -857,6 +933,7 @@ int hermes_xi_multipoles(hermes_ctx* c, const int* ells, int n_ells, double* out
         if (ells[a] & 1) return fail(c, HERMES_ERR_ARG, "odd l = %d vanishes for an auto-correlation", ells[a]);
     }
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, H = c->H, nb = c->n_bins;
     const int nwin = n_ells * nb;
@@ -928,6 +1005,7 @@ int hermes_xi_multipoles_kspace(hermes_ctx* c, const int* ells, int n_ells, doub
         ko.ell[a] = ells[a];
     }
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int nb = c->n_bins;
     const size_t nh = (size_t)n_ells * c->Q;
@@ -969,6 +1047,7 @@ int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
     if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, nb = c->n_bins, LM = c->l_max + 1;
     const size_t n3 = (size_t)N * N * N;
@@ -1059,6 +1138,7 @@ int hermes_debug_get_delta(hermes_ctx* c, float* host_out) {
     if (check_ctx(c) || !host_out) return HERMES_ERR_ARG;
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const size_t n3 = (size_t)c->N * c->N * c->N;
     CK(cudaMemcpyAsync(host_out, c->grid, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "read delta");
     CK(cudaStreamSynchronize(c->stream), "read delta");
@@ -1069,6 +1149,7 @@ int hermes_debug_get_spectrum(hermes_ctx* c, float* host_out) {
     if (check_ctx(c) || !host_out) return HERMES_ERR_ARG;
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const size_t cnt = (size_t)c->N * c->N * c->H;
     CK(cudaMemcpyAsync(host_out, c->spec, cnt * sizeof(float2), cudaMemcpyDeviceToHost, c->stream), "read spectrum");
     CK(cudaStreamSynchronize(c->stream), "read spectrum");
@@ -1078,6 +1159,7 @@ int hermes_debug_get_spectrum(hermes_ctx* c, float* host_out) {
 int hermes_debug_set_delta(hermes_ctx* c, const float* host_delta) {
     if (check_ctx(c) || !host_delta) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const size_t n3 = (size_t)c->N * c->N * c->N;
     c->have_field = false;
     CK(cudaMemcpyAsync(c->grid, host_delta, n3 * sizeof(float), cudaMemcpyDefault, c->stream), "write delta");
@@ -1097,6 +1179,7 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
                        float* host_wts) {
     if (check_ctx(c) || !host_pos || !host_first || !host_wts || n < 1) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int p = c->p;
     float* dpos = nullptr;
@@ -1118,9 +1201,9 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(c, e, "node rule");
     else if (herr) rc = fail(c, HERMES_ERR_RANGE, "a coordinate is outside the accepted range");
-    cudaFree(dpos);
-    cudaFree(dfirst);
-    cudaFree(dw);
+    dev_free(dpos);
+    dev_free(dfirst);
+    dev_free(dw);
     return rc;
 }
 
@@ -1132,6 +1215,7 @@ static const char* const kKernelNames[K_COUNT] = {
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     trace_collect(c);
     for (int i = 0; i < K_COUNT; ++i) {
         c->trace_ms[i] = 0.0;
@@ -1144,6 +1228,7 @@ int hermes_trace_enable(hermes_ctx* c, int on) {
 int hermes_trace_read(hermes_ctx* c, double* ms, int64_t* launches, int n) {
     if (check_ctx(c) || n < 0) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     trace_collect(c);
     for (int i = 0; i < n && i < K_COUNT; ++i) {
         if (ms) ms[i] = c->trace_ms[i];
@@ -1166,6 +1251,7 @@ int64_t hermes_launch_count(const hermes_ctx* c) { return c ? c->launches : -1; 
 int hermes_debug_bounded_wait(hermes_ctx* c) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), st), "clear flag");
     CK(launch_wait_unarrived(c->err, st, c->tracer), "bounded wait");
@@ -1182,6 +1268,7 @@ int hermes_debug_get_sums(hermes_ctx* c, double* sums2, double* selfpair) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field");
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     if (sums2) {
         sums2[0] = c->sum_w;
         sums2[1] = c->sum_w2;
@@ -1247,6 +1334,7 @@ extern "C" int hermes_assign_noalloc(hermes_ctx* c, const float* pos, const floa
                     "hermes_assign_noalloc: its fixed scratch holds %zu doubles, order p = %d needs %zu "
                     "(p <= 6 fits); use hermes_assign", kNoallocDoubles, p, need);
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     int r = check_device_ptr(c, pos, "pos");
     if (r) return r;
     if (w && (r = check_device_ptr(c, w, "w"))) return r;
@@ -1327,18 +1415,18 @@ struct BatchState {
 
 void batch_free(BatchState* b) {
     if (!b) return;
-    cudaFree(b->pos);
-    cudaFree(b->w);
-    cudaFree(b->offs);
-    cudaFree(b->grid);
-    cudaFree(b->spec);
-    cudaFree(b->scal);
-    cudaFree(b->stab_f);
-    cudaFree(b->sums);
-    cudaFree(b->sp);
-    cudaFree(b->part);
-    cudaFree(b->res);
-    cudaFree(b->work);
+    dev_free(b->pos);
+    dev_free(b->w);
+    dev_free(b->offs);
+    dev_free(b->grid);
+    dev_free(b->spec);
+    dev_free(b->scal);
+    dev_free(b->stab_f);
+    dev_free(b->sums);
+    dev_free(b->sp);
+    dev_free(b->part);
+    dev_free(b->res);
+    dev_free(b->work);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaGetLastError();
@@ -1381,8 +1469,8 @@ cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
     const size_t n3 = (size_t)N * N * N;
     cudaError_t e;
     if ((size_t)j.n_total > b->pts_cap) {
-        cudaFree(b->pos);
-        cudaFree(b->w);
+        dev_free(b->pos);
+        dev_free(b->w);
         b->pos = nullptr;
         b->w = nullptr;
         b->pts_cap = 0;
@@ -1392,12 +1480,12 @@ cudaError_t batch_grow(hermes_ctx* c, const BatchJob& j, int S_max, int C_max) {
     }
     if (!b->offs && (e = dev_malloc((void**)&b->offs, (MAX_CATALOGUES + 1) * sizeof(int64_t))) != cudaSuccess) return e;
     if (j.ncat > b->cat_cap) {
-        cudaFree(b->grid);
-        cudaFree(b->spec);
-        cudaFree(b->scal);
-        cudaFree(b->stab_f);
-        cudaFree(b->sums);
-        cudaFree(b->sp);
+        dev_free(b->grid);
+        dev_free(b->spec);
+        dev_free(b->scal);
+        dev_free(b->stab_f);
+        dev_free(b->sums);
+        dev_free(b->sp);
         b->grid = nullptr;
         b->spec = nullptr;
         b->scal = nullptr;
@@ -1657,6 +1745,7 @@ extern "C" int hermes_xi_multipoles_batch(hermes_ctx* c, const float* pos, const
         j.ells.push_back(ells[a]);
     }
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     if (flags & HERMES_DEVICE_PTR) {
         int r = check_device_ptr(c, pos, "pos");
         if (r) return r;
@@ -1846,6 +1935,7 @@ extern "C" int hermes_window_cylinders(hermes_ctx* c, const double* perp_edges, 
             return fail(c, HERMES_ERR_RANGE, "largest edge %g exceeds L/2 = %g", ax.first[ax.second - 1], 0.5 * c->L);
     }
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const int N = c->N, H = N / 2;
     const int np = n_perp_edges - 1, nz = n_par_edges - 1;
     const int nbp = (np + 3) & ~3;
@@ -1875,15 +1965,15 @@ extern "C" int hermes_window_cylinders(hermes_ctx* c, const double* perp_edges, 
     for (int j = 0; j < nz; ++j)
         for (int a = 0; a < H; ++a) par[(size_t)j * H + a] = (float)slab_cos(kf * a, par_edges[j], par_edges[j + 1]);
     cudaStreamSynchronize(c->stream);
-    cudaFree(c->cyl_perp);
-    cudaFree(c->cyl_par);
+    dev_free(c->cyl_perp);
+    dev_free(c->cyl_par);
     c->cyl_perp = nullptr;
     c->cyl_par = nullptr;
     c->cyl_nperp = c->cyl_npar = 0;
     CK(dev_malloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "transverse table");
     CK(dev_malloc((void**)&c->cyl_par, par.size() * sizeof(float)), "line-of-sight table");
-    CK(cudaMemcpy(c->cyl_perp, perp.data(), perp.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
-    CK(cudaMemcpy(c->cyl_par, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    CK(upload(c->cyl_perp, perp.data(), perp.size() * sizeof(float), c->stream), "upload tables");
+    CK(upload(c->cyl_par, par.data(), par.size() * sizeof(float), c->stream), "upload tables");
     c->cyl_nperp = np;
     c->cyl_npar = nz;
     c->cyl_nbp = nbp;
@@ -1909,6 +1999,7 @@ extern "C" int hermes_window_rings(hermes_ctx* c, const double* R, const double*
             return fail(c, HERMES_ERR_RANGE, "ring %d reaches beyond L/2 = %g", w, 0.5 * c->L);
     }
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     const int N = c->N, H = N / 2;
     const int nbp = (n + 3) & ~3;
     const int64_t Qp = 2 * (int64_t)(H - 1) * (H - 1) + 1;
@@ -1948,15 +2039,15 @@ extern "C" int hermes_window_rings(hermes_ctx* c, const double* R, const double*
                                  : std::cos(k * Hz[w]));
         }
     cudaStreamSynchronize(c->stream);
-    cudaFree(c->cyl_perp);
-    cudaFree(c->cyl_par);
+    dev_free(c->cyl_perp);
+    dev_free(c->cyl_par);
     c->cyl_perp = nullptr;
     c->cyl_par = nullptr;
     c->cyl_nperp = c->cyl_npar = 0;
     CK(dev_malloc((void**)&c->cyl_perp, perp.size() * sizeof(float)), "ring transverse table");
     CK(dev_malloc((void**)&c->cyl_par, par.size() * sizeof(float)), "ring line-of-sight table");
-    CK(cudaMemcpy(c->cyl_perp, perp.data(), perp.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
-    CK(cudaMemcpy(c->cyl_par, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice), "upload tables");
+    CK(upload(c->cyl_perp, perp.data(), perp.size() * sizeof(float), c->stream), "upload tables");
+    CK(upload(c->cyl_par, par.data(), par.size() * sizeof(float), c->stream), "upload tables");
     c->cyl_nperp = n;
     c->cyl_npar = n;
     c->cyl_nbp = nbp;
@@ -1980,6 +2071,7 @@ extern "C" int hermes_xi_cylinders(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (int r = check_cyl(c, out)) return r;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, H = N / 2, np = c->cyl_nperp, nz = c->cyl_npar;
     const int nwin = np * nz;
@@ -2032,6 +2124,7 @@ extern "C" int hermes_xi_cylinders_kspace(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (int r = check_cyl(c, out)) return r;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int np = c->cyl_nperp, nz = c->cyl_npar, nwin = np * nz;
     CK(grow_doubles(c->part, c->part_cap, (size_t)std::min(nz, 8) * c->cyl_Q), "histogram");
@@ -2056,6 +2149,7 @@ extern "C" int hermes_xi_rings(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (int r = check_cyl(c, out, true)) return r;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, H = N / 2, nwin = c->cyl_nperp;
     const size_t win_bytes = (size_t)N * N * H * sizeof(float2);
@@ -2106,6 +2200,7 @@ extern "C" int hermes_xi_rings_kspace(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (int r = check_cyl(c, out, true)) return r;
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int nwin = c->cyl_nperp;
     CK(grow_doubles(c->part, c->part_cap, (size_t)std::min(nwin, 8) * c->cyl_Q), "histogram");
@@ -2135,6 +2230,7 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
     if (n < 1) return fail(c, HERMES_ERR_ARG, "empty random catalogue");
     if (flags & ~(HERMES_DEVICE_PTR | HERMES_WRAP)) return fail(c, HERMES_ERR_ARG, "unknown flags 0x%x", flags);
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, p = c->p, p3 = p * p * p;
     const size_t n3 = (size_t)N * N * N;
@@ -2146,8 +2242,8 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
         if (w && (r = check_device_ptr(c, w, "w"))) return r;
     } else {
         if ((size_t)n > c->stage_cap) {
-            cudaFree(c->stage_pos);
-            cudaFree(c->stage_w);
+            dev_free(c->stage_pos);
+            dev_free(c->stage_w);
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
@@ -2167,7 +2263,7 @@ extern "C" int hermes_assign_randoms(hermes_ctx* c, const float* pos, const floa
     if (!c->rscal) {
         CK(dev_malloc((void**)&c->rscal, 8 * sizeof(double)), "random scalars");
         const double one[8] = {0, 0, 1, 0, 0, 0, 0, 0};
-        CK(cudaMemcpy(c->rscal, one, sizeof(one), cudaMemcpyHostToDevice), "random scalars");
+        CK(upload(c->rscal, one, sizeof(one), c->stream), "random scalars");
     }
     c->have_field = false;  // the data field must be rebuilt against the new randoms
     c->have_randoms = false;
@@ -2223,6 +2319,7 @@ extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kin
         return fail(c, HERMES_ERR_STATE, "the resident field is a difference field (explicit randoms); "
                                          "call hermes_clear_randoms and hermes_assign first");
     DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
     const int N = c->N, H = N / 2;
     const size_t n3 = (size_t)N * N * N;
@@ -2234,8 +2331,8 @@ extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kin
         if ((r = check_device_ptr(c, out, "out"))) return r;
     } else {
         if ((size_t)n > c->stage_cap) {
-            cudaFree(c->stage_pos);
-            cudaFree(c->stage_w);
+            dev_free(c->stage_pos);
+            dev_free(c->stage_w);
             c->stage_pos = nullptr;
             c->stage_w = nullptr;
             c->stage_cap = 0;
@@ -2260,10 +2357,10 @@ extern "C" int hermes_density_marks(hermes_ctx* c, int window, double R, int kin
         tab[(size_t)q * 4] = (float)wv;
     }
     cudaStreamSynchronize(st);
-    cudaFree(c->smooth_tab);
+    dev_free(c->smooth_tab);
     c->smooth_tab = nullptr;
     CK(dev_malloc((void**)&c->smooth_tab, tab.size() * sizeof(float)), "smoothing table");
-    CK(cudaMemcpy(c->smooth_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice), "upload table");
+    CK(upload(c->smooth_tab, tab.data(), tab.size() * sizeof(float), c->stream), "upload table");
     // work: one half spectrum, then the real smoothed field (N^3 floats) behind it
     const size_t spec_bytes = (size_t)N * N * H * sizeof(float2);
     CK(grow(c->work, c->work_bytes, spec_bytes + n3 * sizeof(float)), "work buffer");

@@ -31,8 +31,11 @@ def _close(got, ref, rel=REL, ab=ABS):
                            f"got {got[bad][:5]} ref {ref[bad][:5]}")
 
 
+@pytest.mark.parametrize("form", ["tiled", "atomic"])
 @pytest.mark.parametrize("p", range(1, 9))
-def test_scatter_and_delta_match_oracle(p):
+def test_scatter_and_delta_match_oracle(p, form, monkeypatch):
+    # both scatter forms (the library picks by catalogue density; forced here)
+    monkeypatch.setenv("HERMES_SCATTER", form)
     H = _hermes()
     N, L = 32, 100.0
     pos = S.mixed_poisson_sp(5000, L, seed=30 + p)
