@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_y(float2* __restrict__ fie
 }
 
 // Z3 ------------------------------------------------------------------------
-// The 10 tiles (ti, tj), ti <= tj, of a symmetric 16x16 Gram in 4x4 tiles (tile = 4 ti + tj).
-__constant__ int kGramTiles[10] = {0, 1, 2, 3, 5, 6, 7, 10, 11, 15};
+// The 10 tiles (ti, tj), ti <= tj, of a symmetric 16x16 Gram in 4x4 tiles (tile = 4 ti + tj),
+// ordered by max(ti, tj): the first 1, 3, 6 or 10 cover the Gram of up to 4, 8, 12 or 16 rows.
+__constant__ int kGramTiles[10] = {0, 1, 5, 2, 6, 10, 3, 7, 11, 15};
 // Persistent over (x, y) lines.  Per line: GB bin lines per round are inverse
 // transformed along z (T threads each) into shared memory; then the 10 upper
 // 4x4 bin tiles x 3 z-slices per warp accumulate the Gram, float32 per line, flushed to
@@ -245,15 +246,20 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     const size_t n3 = (size_t)N * N * N;
     const int tid = threadIdx.x;
     const int bb = tid / T, t = tid % T;
-    // Gram phase: lane l < 30 of warp w owns 4x4 tile kActive[l % 10] (one of the 10 tiles with
-    // ti <= tj of the symmetric 16x16 Gram) and z-slice s = 3w + l / 10, z = s, s + NS, ...
-    // (lanes 30, 31 idle).  The 12 addresses a warp reads per z fall on distinct bank pairs.
-    const int lane_g = tid & 31, sub = lane_g / 10;
+    // Gram phase: only the nt tiles that hold Gram rows are computed (nt = 1, 3, 6, 10 for up
+    // to 4, 8, 12, 16 rows: S bins, or 2S real parts when REAL).  Lane l < 30 of warp w owns
+    // tile kGramTiles[l % nt] and z-slice s = per w + l / nt (per = 30 / nt slices per warp),
+    // z = s, s + NS, ... (lanes 30, 31 idle).  With all 10 tiles the 12 addresses a warp reads
+    // per z fall on distinct bank pairs.
+    const int rows = REAL ? 2 * S : S;
+    const int nt = rows <= 4 ? 1 : (rows <= 8 ? 3 : (rows <= 12 ? 6 : 10));
+    const int per = 30 / nt;
+    const int lane_g = tid & 31, sub = lane_g / nt;
     const bool active = lane_g < 30;
-    const int tile = active ? kGramTiles[lane_g % 10] : 0;
+    const int tile = active ? kGramTiles[lane_g % nt] : 0;
     const int ti = tile >> 2, tj = tile & 3;
-    const int NS = (int)(blockDim.x >> 5) * 3;
-    const int zs = (tid >> 5) * 3 + sub;
+    const int NS = (int)(blockDim.x >> 5) * per;
+    const int zs = (tid >> 5) * per + sub;
     float acc[4][4];
     double acc64[4][4];
 #pragma unroll
@@ -369,20 +375,22 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc64[a][b] += (double)acc[a][b];
-    // lanes l, l + 10, l + 20 hold the same tile: merge onto lane l, then warps add in turn
+    // lanes l, l + nt, l + 2 nt, ... < 30 hold the same tile: merge onto lane l, then warps
+    // add in turn
+    for (int k = 1; k < per; ++k) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const double v10 = __shfl_down_sync(0xffffffffu, acc64[a][b], 10);
-            const double v20 = __shfl_down_sync(0xffffffffu, acc64[a][b], 20);
-            acc64[a][b] += v10 + v20;
-        }
+            for (int b = 0; b < 4; ++b) {
+                const double v = __shfl_down_sync(0xffffffffu, acc64[a][b], k * nt);
+                if (lane_g < nt) acc64[a][b] += v;
+            }
+    }
     for (int e = tid; e < 256; e += blockDim.x) tot[e] = 0.0;
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int w = 0; w < nw; ++w) {
-        if (wid == w && lane < 10) {
+        if (wid == w && lane < nt) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
