@@ -402,6 +402,144 @@ __global__ void __launch_bounds__(ZCfg<N>::ZT) k_zeta_z_gram(const float2* __res
     if (late && (tid & 31) == 0) atomicOr(err, 4u);
 }
 
+// Z3, two blocks per SM (N = 512): the same transforms and Gram as k_zeta_z_gram in half
+// the resources, so that two blocks share each SM and one block's transforms overlap the
+// other's Gram phase instead of every warp of the SM waiting on the same barriers.  Bin
+// lines are loaded straight into registers (no bulk-copy stage), the float32 Gram tile of
+// each lane is flushed every 8 lines into float64 tiles per warp in shared memory, and the
+// kernel is held to 64 registers.
+template <int N>
+struct Z2Cfg {
+    static constexpr int T = N / 8;          // threads per bin line
+    static constexpr int GB = 512 / T;       // bin lines per round
+    static constexpr int THREADS = GB * T;   // 512
+    static constexpr int NW = THREADS / 32;
+    static constexpr int LPZ = ZCfg<N>::LPZ;
+    static constexpr size_t SMEM = (size_t)16 * LPZ * sizeof(float2)    // transformed bin lines
+                                   + (size_t)N * sizeof(float)          // delta line
+                                   + (size_t)NW * 160 * sizeof(double);  // float64 tiles per warp
+};
+
+template <int N, bool REAL>
+__global__ void __launch_bounds__(Z2Cfg<N>::THREADS, 2) k_zeta_z_gram2(const float2* __restrict__ fields, int S,
+                                                                      const float* __restrict__ delta,
+                                                                      const float2* __restrict__ tw,
+                                                                      double* __restrict__ part) {
+    using C = Z2Cfg<N>;
+    constexpr int T = C::T, GB = C::GB, LPZ = C::LPZ, NW = C::NW;
+    extern __shared__ __align__(16) float2 smem[];
+    float* dsm = reinterpret_cast<float*>(smem + 16 * LPZ);          // [N]
+    double* wacc = reinterpret_cast<double*>(dsm + N);               // [NW][10][16]
+    const size_t n3 = (size_t)N * N * N;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int bb = tid / T, t = tid % T;
+    // Gram lanes as in k_zeta_z_gram: nt tiles that hold rows, 30 lanes per warp spread over them
+    const int rows = REAL ? 2 * S : S;
+    const int nt = rows <= 4 ? 1 : (rows <= 8 ? 3 : (rows <= 12 ? 6 : 10));
+    const int per = 30 / nt;
+    const int sub = lane / nt;
+    const bool active = lane < 30;
+    const int tile = active ? kGramTiles[lane % nt] : 0;
+    const int ti = tile >> 2, tj = tile & 3;
+    const int NS = NW * per;
+    const int zs = wid * per + sub;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+    for (int e = tid; e < NW * 160; e += C::THREADS) wacc[e] = 0.0;
+    // the sum of the lanes that hold the same tile goes into the warp's float64 tile
+    auto flush = [&]() {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float v = acc[a][c];
+                for (int k = 1; k < per; ++k) v += __shfl_down_sync(0xffffffffu, acc[a][c], k * nt);
+                if (lane < nt) wacc[(wid * 10 + lane) * 16 + a * 4 + c] += (double)v;
+                acc[a][c] = 0.0f;
+            }
+    };
+    const int rounds = (S + GB - 1) / GB;
+    int since_flush = 0;
+    __syncthreads();
+    for (size_t line = blockIdx.x; line < (size_t)N * N; line += gridDim.x) {
+        for (int r = 0; r < rounds; ++r) {
+            const int b = r * GB + bb;
+            if (T >= 32 && b >= S) continue;  // no data; the whole line group skips
+            float2 v[8];
+            if (b < S) {
+                const float2* src = fields + (size_t)b * n3 + line * N;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = src[t + i * T];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
+            }
+            const SmemZLine<N> sm{{smem + b * LPZ}, bb};
+            fft_line<N, true>(v, t, tw, sm);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sm.st(t + i * T, v[i]);
+        }
+        for (int z = tid; z < N; z += C::THREADS) dsm[z] = delta[line * N + z];
+        __syncthreads();
+        if (REAL && active) {
+            for (int z = zs; z < N; z += NS) {
+                const float d = dsm[z];
+                const int zp = SmemLine<N>::at(z);
+                const float2 p0 = smem[(2 * ti) * LPZ + zp], p1 = smem[(2 * ti + 1) * LPZ + zp];
+                const float2 r0 = smem[(2 * tj) * LPZ + zp], r1 = smem[(2 * tj + 1) * LPZ + zp];
+                const float x[4] = {p0.x * d, p0.y * d, p1.x * d, p1.y * d};
+                const float y[4] = {r0.x, r0.y, r1.x, r1.y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) acc[k][k2] = fmaf(x[k], y[k2], acc[k][k2]);
+            }
+        } else if (active) {
+            for (int z = zs; z < N; z += NS) {
+                const float d = dsm[z];
+                const int zp = SmemLine<N>::at(z);
+                float2 a1[4], a2[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    a1[k] = smem[(4 * ti + k) * LPZ + zp];
+                    a2[k] = smem[(4 * tj + k) * LPZ + zp];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 e = cscale(a1[k], d);
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) acc[k][k2] = fmaf(e.x, a2[k2].x, fmaf(e.y, a2[k2].y, acc[k][k2]));
+                }
+            }
+        }
+        if (++since_flush == 8) {
+            since_flush = 0;
+            flush();
+        }
+        __syncthreads();
+    }
+    flush();
+    __syncthreads();
+    // entry (b1, b2) of the upper triangle by tiles: the sum over warps of the float64 tiles
+    for (int e = tid; e < 256; e += C::THREADS) {
+        const int b1 = e >> 4, b2 = e & 15, gi = b1 >> 2, gj = b2 >> 2;
+        double s = 0.0;
+        if (gi <= gj) {
+            const int code = 4 * gi + gj;
+            int idx = 0;
+            while (idx < 10 && kGramTiles[idx] != code) ++idx;
+            if (idx < nt) {
+                const int slot = idx * 16 + (b1 & 3) * 4 + (b2 & 3);
+                for (int w = 0; w < NW; ++w) s += wacc[w * 160 + slot];
+            }
+        }
+        part[(size_t)e * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 // Z3 on the tensor cores ---------------------------------------------------
 // Same line loop and z transforms as k_zeta_z_gram; the Gram runs on tcgen05.
 // With K = (z, Re/Im) the Gram is a plain product G = A B:
@@ -694,14 +832,28 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
         }
     }
     tr(K_ZETA_Z_GRAM, 0, st);
-    if (hp.pack) {
-        if ((e = allow_smem_z(k_zeta_z_gram<N, true>, C::SMEM_Z)) != cudaSuccess) return e;
-        k_zeta_z_gram<N, true><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, nf, delta, tb.tw, gram_part,
-                                                                               err);
+    if constexpr (N == 512) {
+        // two blocks per SM (the bench's zeta step: 219 ms in this pass against 227 for one block)
+        const int nblk = zeta_blocks_impl<N>();
+        if (hp.pack) {
+            if ((e = allow_smem_z(k_zeta_z_gram2<N, true>, Z2Cfg<N>::SMEM)) != cudaSuccess) return e;
+            k_zeta_z_gram2<N, true><<<nblk, Z2Cfg<N>::THREADS, Z2Cfg<N>::SMEM, st>>>(fields, nf, delta, tb.tw,
+                                                                                  gram_part);
+        } else {
+            if ((e = allow_smem_z(k_zeta_z_gram2<N, false>, Z2Cfg<N>::SMEM)) != cudaSuccess) return e;
+            k_zeta_z_gram2<N, false><<<nblk, Z2Cfg<N>::THREADS, Z2Cfg<N>::SMEM, st>>>(fields, hb.S, delta, tb.tw,
+                                                                                   gram_part);
+        }
     } else {
-        if ((e = allow_smem_z(k_zeta_z_gram<N, false>, C::SMEM_Z)) != cudaSuccess) return e;
-        k_zeta_z_gram<N, false><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw,
-                                                                                gram_part, err);
+        if (hp.pack) {
+            if ((e = allow_smem_z(k_zeta_z_gram<N, true>, C::SMEM_Z)) != cudaSuccess) return e;
+            k_zeta_z_gram<N, true><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, nf, delta, tb.tw,
+                                                                                   gram_part, err);
+        } else {
+            if ((e = allow_smem_z(k_zeta_z_gram<N, false>, C::SMEM_Z)) != cudaSuccess) return e;
+            k_zeta_z_gram<N, false><<<zeta_blocks_impl<N>(), C::ZT, C::SMEM_Z, st>>>(fields, hb.S, delta, tb.tw,
+                                                                                    gram_part, err);
+        }
     }
     tr(K_ZETA_Z_GRAM, 1, st);
     return cudaGetLastError();
