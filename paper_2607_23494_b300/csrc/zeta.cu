@@ -832,7 +832,7 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
         }
     }
     tr(K_ZETA_Z_GRAM, 0, st);
-    if constexpr (N == 512) {
+    if constexpr (N == 256 || N == 512) {
         // two blocks per SM (the bench's zeta step: 219 ms in this pass against 227 for one block)
         const int nblk = zeta_blocks_impl<N>();
         if (hp.pack) {
