@@ -205,13 +205,21 @@ def error_vs_oracle(res, pos, mass, zeta128) -> dict:
 # per launch) and per window.
 NCU_TRAFFIC_512 = {
     "inv_x_window": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
-    "inv_y": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
+    "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
 }
 
 
-def ncu_traffic(name: str, windows_per_launch: float) -> float | None:
-    t = NCU_TRAFFIC_512.get(name)
+def y_variant_tag(H, N: int) -> str:
+    """The inverse y-pass variant in use for grid N as kind / values per thread / tile width."""
+    info = H.fft_variants(N)
+    v = info["forced"] if info["forced"] >= 0 else max(info["chosen"], 0)
+    kind, E, W, _ = info["variants"][v]
+    return f"k{kind}e{E}w{W}"
+
+
+def ncu_traffic(name: str, windows_per_launch: float, y_tag: str) -> float | None:
+    t = NCU_TRAFFIC_512.get(f"{name}/{y_tag}" if name == "inv_y" else name)
     return None if t is None else t["per_launch"] + t["per_window"] * windows_per_launch
 
 
@@ -327,7 +335,9 @@ def run_hermes(args, rank, world, local_rank):
     dom_b = alg_bytes(dom, trace[dom][1], windows_per_step * args.steps, batches_per_step * args.steps,
                       (12 * n + 16 * n) * args.steps)
     achieved = dom_b / (trace[dom][0] / 1e3) / 1e9 if dom_b else None
-    traffic = ncu_traffic(dom, windows_per_step / batches_per_step)  # per launch, scaled from ncu
+    from paper_2607_23494_b300 import hermes as Hm
+    y_tag = y_variant_tag(Hm, N2)
+    traffic = ncu_traffic(dom, windows_per_step / batches_per_step, y_tag)  # per launch, scaled from ncu
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
             "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
@@ -381,6 +391,7 @@ def run_hermes(args, rank, world, local_rank):
             "gpu_launches": launches,
             "roofline": roof,
             "kernels": kern,
+            "fft_variants": {"inv_y_512": {**Hm.fft_variants(N2), "in_use": y_tag}},
             "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
         }
         for key, val in (("kspace", ks), ("cylinders", cyl), ("s_mu", smu)):
@@ -623,7 +634,7 @@ def run_batch(args, dev, stream, rank):
     Three arms on the same catalogues: the batched call (graph replay, autotuned
     plan), the same library one catalogue at a time, and the plain FP32 pipeline."""
     import torch
-    from paper_2607_23494_b300 import Context
+    from paper_2607_23494_b300 import Context, fft_variants
     pos, offs = gen_batch(rank_seeds(rank)["batch"])
     pos_d = torch.from_numpy(pos).to(dev)
     ncat, nb = len(offs) - 1, len(EDGES4) - 1
@@ -686,6 +697,7 @@ def run_batch(args, dev, stream, rank):
                         "tuning": [[int(a), int(b), round(c, 4)] for a, b, c in info["tuning"]]},
             "one_at_a_time": {"value": round(cw / (s_ms / 1e3), 1), "ms_per_batch": round(s_ms, 2),
                               "diff_vs_batched_in_tolerances": round(diff, 4)},
+            "inv_y_variants_256": fft_variants(N4),
             "plain_fp32": {"value": round(cw / (p_ms / 1e3), 1), "ms_per_batch": round(p_ms, 2),
                            "diff_vs_batched_in_tolerances": round(pdiff, 4)},
             "speedup_vs_plain": round(p_ms / b_ms, 2), "speedup_vs_one_at_a_time": round(s_ms / b_ms, 2)}

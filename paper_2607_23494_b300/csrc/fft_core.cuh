@@ -111,6 +111,19 @@ struct SmemStrided {
     __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
     __device__ __forceinline__ static void sync() { __syncthreads(); }  // a tile spans the block
 };
+// Strided tile with a skew of P slots after every 2^SH rows, for the transforms
+// at 16 or 32 values per thread, whose exchanges write runs of 2^k rows per warp
+// (the skew that reaches the minimum wavefront count depends on M, E and W).
+template <int W, int SH, int P>
+struct SmemStridedSk {
+    float2* p;
+    int col;
+    static constexpr int words(int n) { return n * W + (n >> SH) * P; }
+    __device__ __forceinline__ int at(int pos) const { return pos * W + col + (pos >> SH) * P; }
+    __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
+    __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
 // Contiguous line of length M with one padding slot every 2^SH elements.
 constexpr int line_shift(int m) { return m >= 128 ? 4 : (m == 32 ? 2 : 3); }
 template <int M>
@@ -263,6 +276,212 @@ __device__ __forceinline__ void fft_line_wc(float2 (&v)[8], int t, const float2*
                                             const float2* wc) {
     static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
     fft_stages<M, 1, INV, false, true, 0, S>(v, t, tw, sm, wc);
+}
+
+
+// ---------------------------------------------------------------------------
+// The same Stockham scheme with E = 8, 16 or 32 values per thread (M/E threads
+// per line): radix-E stages, after a leading radix-2^r stage when log2(M) is not a
+// multiple of log2(E).  More values per thread means fewer shared-memory exchanges
+// (a 256-point line: one at E = 16, two at E = 8; 1024 points: one at E = 32)
+// for more registers per thread.  Before and after the transform thread t holds
+// elements t + i*M/E, as in fft_line.
+
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a, float c, float s) {  // a * e^{-+ i theta}, c = cos, s = sin
+    return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
+               : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+// 16-point DFT: two 8-point DFTs of the even and odd samples joined with
+// e^{-+2 pi i k / 16}, k = 0..7.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* a) {
+    float2 e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        e[j] = a[2 * j];
+        o[j] = a[2 * j + 1];
+    }
+    dft8<INV>(e);
+    dft8<INV>(o);
+    constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;  // cos, sin (pi / 8)
+    constexpr float r2 = 0.70710678118654752440f;
+    o[1] = rot<INV>(o[1], c1, s1);
+    o[2] = rot<INV>(o[2], r2, r2);
+    o[3] = rot<INV>(o[3], s1, c1);
+    o[4] = mul_mi<INV>(o[4]);
+    o[5] = rot<INV>(o[5], -s1, c1);
+    o[6] = rot<INV>(o[6], -r2, r2);
+    o[7] = rot<INV>(o[7], -c1, s1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        a[k] = cadd(e[k], o[k]);
+        a[k + 8] = csub(e[k], o[k]);
+    }
+}
+
+// 32-point DFT: two 16-point DFTs joined with e^{-+2 pi i k / 32}, k = 0..15.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* a) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        e[j] = a[2 * j];
+        o[j] = a[2 * j + 1];
+    }
+    dft16<INV>(e);
+    dft16<INV>(o);
+    // cos and sin of k pi / 16, k = 0..8
+    constexpr float C[9] = {1.0f,
+                            0.98078528040323044913f,
+                            0.92387953251128675613f,
+                            0.83146961230254523708f,
+                            0.70710678118654752440f,
+                            0.55557023301960222474f,
+                            0.38268343236508977173f,
+                            0.19509032201612826785f,
+                            0.0f};
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+        if (k == 8) {
+            o[8] = mul_mi<INV>(o[8]);
+        } else if (k < 8) {
+            o[k] = rot<INV>(o[k], C[k], C[8 - k]);
+        } else {  // theta = k pi / 16 > pi / 2: cos = -sin((k - 8) pi / 16), sin = cos((k - 8) pi / 16)
+            o[k] = rot<INV>(o[k], -C[16 - k], C[k - 8]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        a[k] = cadd(e[k], o[k]);
+        a[k + 16] = csub(e[k], o[k]);
+    }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftRE(float2* a) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) dft2<INV>(a);
+    else if constexpr (R == 4) dft4<INV>(a);
+    else if constexpr (R == 8) dft8<INV>(a);
+    else if constexpr (R == 16) dft16<INV>(a);
+    else dft32<INV>(a);
+}
+
+// Leading radix of an M-point transform at E values per thread (1: none).
+template <int M, int E>
+struct LeadRadix {
+    static constexpr int value = 1 << (ilog2c(M) % ilog2c(E));
+};
+
+// Stage twiddles of a radix-R stage of span NS: e^{-+2 pi i k r / (R NS)}, read from
+// the multi-level table (exact entries tw[L + k r], L = R NS).
+template <int R, int NS, bool INV>
+__device__ __forceinline__ void stage_twiddles(const float2* __restrict__ tw, int k, float2* w) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r - 1] = twiddle_l<INV>(tw, R * NS, k * r);
+}
+
+// Number of twiddled stages (NS > 1) and the twiddles a thread needs for all of them
+// when it runs one butterfly per stage (U = 1 in every twiddled stage).
+template <int M, int E>
+constexpr int twiddled_stages_e() {
+    int n = 0;
+    for (int ns = LeadRadix<M, E>::value == 1 ? E : LeadRadix<M, E>::value; ns < M; ns *= E) ++n;
+    return n;
+}
+template <int M, int E>
+constexpr int stage_twiddle_count() {
+    return twiddled_stages_e<M, E>() * (E - 1);
+}
+
+// PRE: the twiddles of the thread's butterfly come preloaded in wc (as written by
+// load_stage_twiddles_e); otherwise they are read from the table in every stage.
+template <int M, int E, int R, int NS, bool INV, bool PRE, int SI, class S>
+__device__ __forceinline__ void fft_stage_e(float2 (&v)[E], int t, const float2* __restrict__ tw, const S& sm,
+                                            const float2* wc) {
+    constexpr int T = M / E;
+    constexpr int U = E / R;
+    constexpr bool LAST = (NS * R == M);
+    float2 out[E];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int b = t + u * T;
+        const int k = b & (NS - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = v[u + r * U];
+        if constexpr (NS > 1) {
+            if constexpr (PRE) {
+                static_assert(U == 1, "preloaded twiddles serve stages of one butterfly per thread");
+#pragma unroll
+                for (int r = 1; r < R; ++r) x[r] = cmul(x[r], wc[(E - 1) * (SI - 1) + r - 1]);
+            } else {
+                float2 w[R - 1];
+                stage_twiddles<R, NS, INV>(tw, k, w);
+#pragma unroll
+                for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r - 1]);
+            }
+        }
+        dftRE<R, INV>(x);
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[u + r * U] = x[r];
+    }
+    if constexpr (LAST) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = out[i];
+    } else {
+        sm.sync();
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = t + u * T;
+            const int base = (b / NS) * NS * R + (b & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm.st(base + r * NS, out[u + r * U]);
+        }
+        sm.sync();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = sm.ld(t + i * T);
+    }
+}
+
+template <int M, int E, int NS, bool INV, bool PRE, int SI, class S>
+__device__ __forceinline__ void fft_stages_e(float2 (&v)[E], int t, const float2* __restrict__ tw, const S& sm,
+                                             const float2* wc) {
+    constexpr int L0 = LeadRadix<M, E>::value;
+    constexpr int R = (NS == 1 && L0 > 1) ? L0 : E;
+    fft_stage_e<M, E, R, NS, INV, PRE, SI, S>(v, t, tw, sm, wc);
+    if constexpr (NS * R < M) fft_stages_e<M, E, NS * R, INV, PRE, SI + 1, S>(v, t, tw, sm, wc);
+}
+
+// Loads the twiddles of thread t's butterfly for every twiddled stage of an M-point
+// transform at E values per thread into wc[stage_twiddle_count<M, E>()].
+template <int M, int E, bool INV>
+__device__ __forceinline__ void load_stage_twiddles_e(int t, const float2* __restrict__ tw, float2* wc) {
+    int ns = LeadRadix<M, E>::value == 1 ? E : LeadRadix<M, E>::value;
+#pragma unroll
+    for (int si = 0; si < twiddled_stages_e<M, E>(); ++si, ns *= E) {
+        const int k = t & (ns - 1);
+#pragma unroll
+        for (int r = 1; r < E; ++r) wc[(E - 1) * si + r - 1] = twiddle_l<INV>(tw, E * ns, k * r);
+    }
+}
+
+// In-register/shared FFT of length M at E values per thread.  Precondition: v[i] =
+// x[t + i*M/E].  Postcondition: v[i] = X[t + i*M/E] (unnormalised, sign as fft_line).
+template <int M, int E, bool INV, class S>
+__device__ __forceinline__ void fft_line_e(float2 (&v)[E], int t, const float2* __restrict__ tw, const S& sm) {
+    static_assert(E == 8 || E == 16 || E == 32, "8, 16 or 32 values per thread");
+    static_assert(M >= E && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
+    fft_stages_e<M, E, 1, INV, false, 0, S>(v, t, tw, sm, nullptr);
+}
+template <int M, int E, bool INV, class S>
+__device__ __forceinline__ void fft_line_e_wc(float2 (&v)[E], int t, const float2* __restrict__ tw, const S& sm,
+                                              const float2* wc) {
+    static_assert(E == 8 || E == 16 || E == 32, "8, 16 or 32 values per thread");
+    static_assert(M >= E && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
+    fft_stages_e<M, E, 1, INV, true, 0, S>(v, t, tw, sm, wc);
 }
 
 }  // namespace hermes

@@ -26,6 +26,9 @@
 #include <cooperative_groups.h>
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <initializer_list>
 
 namespace hermes {
 
@@ -187,6 +190,79 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 2) k_strided_pf(float2* __restrict
         for (int i = 0; i < 8; ++i) b[(t + i * T) * pos_stride] = v[i];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = vn[i];
+        bx = nx_;
+        by = ny_;
+        bz = nz_;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The inverse y pass at 16 or 32 values per thread: a 256-point line needs one
+// shared-memory exchange instead of two, a 1024-point line two instead of three,
+// for more registers per thread.  Two forms over the tiles of k_strided_pf:
+//   k_strided_e   : one tile per block, stage twiddles read from the table;
+//   k_strided_pf_e: persistent blocks, the next tile's loads in flight during the
+//                   transform, the thread's stage twiddles held in registers.
+// The tile layout skews P slots after every 2^SH rows (chosen per shape for the
+// fewest shared-memory wavefronts).
+template <int N, int E, int W, int SH, int P>
+__global__ void __launch_bounds__((N / E) * W) k_strided_e(float2* __restrict__ data, int pos_stride, int ystride,
+                                                           long long zstride, const float2* __restrict__ tw) {
+    constexpr int T = N / E;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    float2* b = data + (size_t)blockIdx.z * zstride + (size_t)blockIdx.y * ystride + blockIdx.x * W + col;
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = b[(t + i * T) * pos_stride];
+    fft_line_e<N, E, true>(v, t, tw, SmemStridedSk<W, SH, P>{smem, col});
+#pragma unroll
+    for (int i = 0; i < E; ++i) b[(t + i * T) * pos_stride] = v[i];
+}
+
+template <int N, int E, int W, int SH, int P, int MINB>
+__global__ void __launch_bounds__((N / E) * W, MINB) k_strided_pf_e(float2* __restrict__ data, int pos_stride,
+                                                                    int ystride, long long zstride, int nxt, int nyt,
+                                                                    int ntiles, const float2* __restrict__ tw) {
+    constexpr int T = N / E;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    float2 wc[stage_twiddle_count<N, E>() + 1];
+    load_stage_twiddles_e<N, E, true>(t, tw, wc);
+    int bx = tile % nxt, by = (tile / nxt) % nyt, bz = tile / nxt / nyt;
+    const int dx = gridDim.x % nxt, dy = (gridDim.x / nxt) % nyt, dz = gridDim.x / nxt / nyt;
+    auto base_of = [&](int x, int y, int z) {
+        return data + (size_t)z * zstride + (size_t)y * ystride + x * W + col;
+    };
+    float2 v[E], vn[E];
+    {
+        const float2* b = base_of(bx, by, bz);
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = b[(t + i * T) * pos_stride];
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        int nx_ = bx + dx, ny_ = by + dy, nz_ = bz + dz;
+        if (nx_ >= nxt) {
+            nx_ -= nxt;
+            ++ny_;
+        }
+        if (ny_ >= nyt) {
+            ny_ -= nyt;
+            ++nz_;
+        }
+        if (tile + (int)gridDim.x < ntiles) {
+            const float2* b = base_of(nx_, ny_, nz_);
+#pragma unroll
+            for (int i = 0; i < E; ++i) vn[i] = b[(t + i * T) * pos_stride];
+        }
+        fft_line_e_wc<N, E, true>(v, t, tw, SmemStridedSk<W, SH, P>{smem, col}, wc);
+        float2* b = base_of(bx, by, bz);
+#pragma unroll
+        for (int i = 0; i < E; ++i) b[(t + i * T) * pos_stride] = v[i];
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = vn[i];
         bx = nx_;
         by = ny_;
         bz = nz_;
@@ -684,6 +760,214 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Variants of the inverse y pass and the autotuner that picks one per grid size.
+// A variant fixes the values per thread E (the radix of the FFT stages: radix 8
+// throughout for E = 8, radix 16 or 32 for E = 16, 32), the tile width W, the form
+// (one tile per block or persistent) and the blocks per SM.  The first inverse call
+// of a grid size that is not being captured into a graph times every variant on its
+// own work buffer, before the window pass writes it, and keeps the fastest for the
+// process; hermes_fft_set_variant fixes one instead.
+
+static int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            return 148;
+        }
+        return v;
+    }();
+    return n;
+}
+
+// kind 0: the radix-8 pass (k_strided_pf up to 512^3, k_strided above);
+// kind 1: k_strided_e; kind 2: k_strided_pf_e.
+struct YVariant {
+    int kind, E, W, minb;
+};
+static int y_variants(int N, YVariant* out) {
+    auto put = [&](std::initializer_list<YVariant> l) {
+        int k = 0;
+        for (const YVariant& v : l) out[k++] = v;
+        return k;
+    };
+    switch (N) {
+        case 16: return put({{0, 8, Cfg<16>::W, 2}});
+        case 32: return put({{0, 8, Cfg<32>::W, 2}});
+        case 64: return put({{0, 8, Cfg<64>::W, 2}});
+        case 128: return put({{0, 8, Cfg<128>::W, 2}, {1, 16, 8, 0}});
+        case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
+        case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+        case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+    }
+    return 0;
+}
+constexpr int kMaxYVariants = 4;
+
+// Tiles (column chunk, x, window) of nwin consecutive windows of work.
+template <int N>
+static cudaError_t run_y_r8(float2* work, int nwin, const float2* tw, cudaStream_t st) {
+    using C = Cfg<N>;
+    constexpr long long H = N / 2;
+    cudaError_t e;
+    const int nxt = (int)(H / C::W);
+    const long long ntiles = (long long)nxt * N * nwin;
+    if constexpr (N <= 512) {  // two 512-thread blocks per SM at 64 registers
+        if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if ((e = allow_smem(k_strided_pf<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+        const int nblk = (int)std::min<long long>(ntiles, 2LL * sm_count());
+        k_strided_pf<N, true><<<nblk, C::TS, C::SMEM_STRIDED, st>>>(work, (int)H, (int)(N * H), (long long)N * N * H,
+                                                                    nxt, N, (int)ntiles, tw);
+    } else {
+        if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+        dim3 g2(nxt, N, nwin);
+        k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0, tw);
+    }
+    return cudaGetLastError();
+}
+template <int N, int E, int W, int SH, int P>
+static cudaError_t run_y_plain(float2* work, int nwin, const float2* tw, cudaStream_t st) {
+    constexpr int H = N / 2, TS = (N / E) * W;
+    constexpr size_t smem = (size_t)SmemStridedSk<W, SH, P>::words(N) * sizeof(float2);
+    cudaError_t e;
+    if ((e = allow_smem(k_strided_e<N, E, W, SH, P>, smem)) != cudaSuccess) return e;
+    k_strided_e<N, E, W, SH, P><<<dim3(H / W, N, nwin), TS, smem, st>>>(work, H, N * H, (long long)N * N * H, tw);
+    return cudaGetLastError();
+}
+template <int N, int E, int W, int SH, int P, int MINB>
+static cudaError_t run_y_pf(float2* work, int nwin, const float2* tw, cudaStream_t st) {
+    constexpr int H = N / 2, TS = (N / E) * W;
+    constexpr size_t smem = (size_t)SmemStridedSk<W, SH, P>::words(N) * sizeof(float2);
+    const int nxt = H / W;
+    const long long ntiles = (long long)nxt * N * nwin;
+    if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = allow_smem(k_strided_pf_e<N, E, W, SH, P, MINB>, smem)) != cudaSuccess) return e;
+    const int nblk = (int)std::min<long long>(ntiles, (long long)MINB * sm_count());
+    k_strided_pf_e<N, E, W, SH, P, MINB><<<nblk, TS, smem, st>>>(work, H, N * H, (long long)N * N * H, nxt, N,
+                                                                  (int)ntiles, tw);
+    return cudaGetLastError();
+}
+// The skews (SH, P) below give the fewest shared-memory wavefronts for each shape.
+template <int N>
+static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* tw, cudaStream_t st) {
+    if constexpr (N == 128) {
+        if (var == 1) return run_y_plain<128, 16, 8, 2, 4>(work, nwin, tw, st);
+    } else if constexpr (N == 256) {
+        if (var == 1) return run_y_plain<256, 16, 8, 2, 2>(work, nwin, tw, st);
+        if (var == 2) return run_y_pf<256, 16, 8, 2, 2, 3>(work, nwin, tw, st);
+        if (var == 3) return run_y_plain<256, 32, 8, 2, 4>(work, nwin, tw, st);
+    } else if constexpr (N == 512) {
+        if (var == 1) return run_y_pf<512, 32, 8, 2, 2, 2>(work, nwin, tw, st);
+        if (var == 2) return run_y_plain<512, 32, 8, 2, 2>(work, nwin, tw, st);
+        if (var == 3) return run_y_plain<512, 16, 8, 2, 1>(work, nwin, tw, st);
+    } else if constexpr (N == 1024) {
+        if (var == 1) return run_y_plain<1024, 32, 8, 2, 1>(work, nwin, tw, st);
+        if (var == 2) return run_y_plain<1024, 16, 8, 2, 8>(work, nwin, tw, st);
+    }
+    return run_y_r8<N>(work, nwin, tw, st);
+}
+
+struct YTune {
+    int forced = -1, chosen = -1;
+    double ms[kMaxYVariants] = {-1.0, -1.0, -1.0, -1.0};
+};
+static std::mutex g_ytune_mu;
+static std::map<std::pair<int, int>, YTune> g_ytune;  // (device, N)
+
+static std::pair<int, int> ytune_key(int N) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    return {dev, N};
+}
+
+// The variant of this call: the forced one, else the tuned one, else (tuning on the
+// first nwin_avail windows of work when st is not capturing) the fastest; variant 0
+// while capturing before any tuning.
+template <int N>
+static int inv_y_pick(float2* work, int nwin_avail, const float2* tw, cudaStream_t st) {
+    YVariant vs[kMaxYVariants];
+    const int nvar = y_variants(N, vs);
+    if (nvar <= 1 || nwin_avail < 1) return 0;
+    std::lock_guard<std::mutex> lk(g_ytune_mu);
+    YTune& en = g_ytune[ytune_key(N)];
+    if (en.forced >= 0) return en.forced;
+    if (en.chosen >= 0) return en.chosen;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
+    const int nwin = (int)std::max<size_t>(1, std::min<size_t>((size_t)nwin_avail, ((size_t)1 << 30) / win_bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    double best_ms = 1e300;
+    for (int v = 0; v < nvar; ++v) {
+        en.ms[v] = -1.0;
+        if (launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess) {  // warm-up
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess || launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess ||
+            launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        en.ms[v] = ms / 2.0;
+        if (en.ms[v] < best_ms) best_ms = en.ms[v], best = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    en.chosen = best;
+    return best;
+}
+
+int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced) {
+    if (pass != 0) return -1;
+    YVariant vs[kMaxYVariants];
+    const int n = y_variants(N, vs);
+    if (n == 0) return -1;
+    std::lock_guard<std::mutex> lk(g_ytune_mu);
+    const auto it = g_ytune.find(ytune_key(N));
+    for (int i = 0; i < std::min(n, cap); ++i) {
+        if (desc) {
+            desc[4 * i] = vs[i].kind;
+            desc[4 * i + 1] = vs[i].E;
+            desc[4 * i + 2] = vs[i].W;
+            desc[4 * i + 3] = vs[i].minb;
+        }
+        if (ms) ms[i] = it == g_ytune.end() ? -1.0 : it->second.ms[i];
+    }
+    if (chosen) *chosen = it == g_ytune.end() ? -1 : it->second.chosen;
+    if (forced) *forced = it == g_ytune.end() ? -1 : it->second.forced;
+    return n;
+}
+
+int fft_set_variant(int N, int pass, int variant) {
+    if (pass != 0) return -1;
+    YVariant vs[kMaxYVariants];
+    const int n = y_variants(N, vs);
+    if (n == 0 || variant < -1 || variant >= n) return -1;
+    std::lock_guard<std::mutex> lk(g_ytune_mu);
+    YTune& en = g_ytune[ytune_key(N)];
+    en.forced = variant;
+    if (variant < 0) {  // back to autotuning: the next uncaptured call times the variants again
+        en.chosen = -1;
+        for (double& m : en.ms) m = -1.0;
+    }
+    return 0;
+}
+
 template <int N>
 static cudaError_t inverse_impl(const float2* spec, float2* work, const float* delta, const WinBatch& wb,
                                 const Tables& tb, double* dd_part, unsigned* err, cudaStream_t st, const Tracer& tr,
@@ -698,6 +982,9 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z3)) != cudaSuccess) return e;
     const long long H = N / 2;
+    // the y-pass variant, tuned (on this call's work buffer, before the window pass
+    // writes it) on the first uncaptured call of this grid size
+    const int yvar = (ncat == 1 && yz_fused_ok<N>()) ? 0 : inv_y_pick<N>(work, wb.S * ncat, tb.tw, st);
     dim3 g1(H / C::W, N, ncat);
     tr(K_INV_X_WINDOW, 0, st);
     if (use_stab) k_inv_x_window<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, work, wb, tb);
@@ -712,20 +999,8 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
         }
     }
     // windows of all catalogues are consecutive in work: tiles (column chunk, x, window)
-    const int nxt = (int)(H / C::W);
-    const long long ntiles = (long long)nxt * N * wb.S * ncat;
     tr(K_INV_Y, 0, st);
-    if constexpr (N <= 512) {  // two 512-thread blocks per SM at 64 registers; 1024^3 keeps the plain pass
-        if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-        if ((e = allow_smem(k_strided_pf<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
-        const int nblk = (int)std::min<long long>(ntiles, 2LL * 148);
-        k_strided_pf<N, true><<<nblk, C::TS, C::SMEM_STRIDED, st>>>(work, (int)H, (int)(N * H), (long long)N * N * H,
-                                                                    nxt, N, (int)ntiles, tb.tw);
-    } else {
-        dim3 g2(nxt, N, wb.S * ncat);
-        k_strided<N, true><<<g2, C::TS, C::SMEM_STRIDED, st>>>(work, H, (long long)N * H, (long long)N * N * H, 0,
-                                                               tb.tw);
-    }
+    if ((e = launch_inv_y<N>(yvar, work, wb.S * ncat, tb.tw, st)) != cudaSuccess) return e;
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
     k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw,

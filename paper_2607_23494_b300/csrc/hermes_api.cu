@@ -637,6 +637,15 @@ int hermes_destroy(hermes_ctx* c) {
     return HERMES_OK;
 }
 
+int hermes_fft_set_variant(int N, int pass, int variant) {
+    return fft_set_variant(N, pass, variant) == 0 ? HERMES_OK : HERMES_ERR_ARG;
+}
+
+int hermes_fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced) {
+    const int n = fft_variants(N, pass, desc, ms, std::max(cap, 0), chosen, forced);
+    return n < 0 ? HERMES_ERR_ARG : n;
+}
+
 int hermes_release_buffers(hermes_ctx* c) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     DeviceGuard g(c->device);

@@ -128,6 +128,9 @@ cudaError_t launch_xi_batch_finish(const double* dd, const double* sn, const dou
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                            cudaStream_t st, const Tracer& tr, int ncat = 1);
 int inv_x_blocks(int N);
+// Variants of the inverse y pass and their autotuner (pass 0); -1 on a bad argument.
+int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced);
+int fft_set_variant(int N, int pass, int variant);
 int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
 int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)
 // window multiply + inverse transforms + cell contraction of one window batch;

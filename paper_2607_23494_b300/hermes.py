@@ -103,6 +103,8 @@ def _load() -> C.CDLL:
         "hermes_launch_count": (i64, [vp]),
         "hermes_device_bytes": (i64, [vp]),
         "hermes_estimate_bytes": (i64, [i32, i32, i32, i32, i64, i32]),
+        "hermes_fft_set_variant": (i32, [i32, i32, i32]),
+        "hermes_fft_variants": (i32, [i32, i32, C.POINTER(i32), dp, i32, C.POINTER(i32), C.POINTER(i32)]),
         "hermes_server_create": (i32, [i32, i64, i32, C.POINTER(vp)]),
         "hermes_server_submit": (i32, [vp, C.POINTER(Request), C.POINTER(i64)]),
         "hermes_server_wait": (i32, [vp, i64, C.POINTER(Result)]),
@@ -458,6 +460,30 @@ def estimate_bytes(N: int, stat: int, n_bins: int, l_max: int, n_points: int, ho
     """hermes_estimate_bytes: device footprint of one request of this kind (-1 on a bad argument)."""
     return int(_lib.hermes_estimate_bytes(int(N), int(stat), int(n_bins), int(l_max), int(n_points),
                                           1 if host_inputs else 0))
+
+
+PASS_INV_Y = 0
+
+
+def fft_variants(N: int, pass_: int = PASS_INV_Y) -> dict:
+    """hermes_fft_variants: the variants of an FFT pass for grid size N, as
+    {"variants": [(kind, E, W, minb), ...], "ms": [...], "chosen": i, "forced": j}."""
+    desc = np.zeros(4 * 8, dtype=np.int32)
+    ms = np.zeros(8, dtype=np.float64)
+    chosen, forced = C.c_int(-1), C.c_int(-1)
+    n = _lib.hermes_fft_variants(int(N), int(pass_), desc.ctypes.data_as(C.POINTER(C.c_int)), _dptr(ms), 8,
+                                 C.byref(chosen), C.byref(forced))
+    if n < 0:
+        raise HermesError(n, "hermes_fft_variants")
+    return {"variants": [tuple(int(x) for x in desc[4 * i:4 * i + 4]) for i in range(n)],
+            "ms": [float(x) for x in ms[:n]], "chosen": chosen.value, "forced": forced.value}
+
+
+def fft_set_variant(N: int, variant: int, pass_: int = PASS_INV_Y) -> None:
+    """hermes_fft_set_variant: fix a variant for grid size N (-1: autotune again)."""
+    rc = _lib.hermes_fft_set_variant(int(N), int(pass_), int(variant))
+    if rc != OK:
+        raise HermesError(rc, "hermes_fft_set_variant")
 
 
 class Server:

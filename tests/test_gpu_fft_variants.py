@@ -1,0 +1,81 @@
+"""The variants of the inverse y pass (values per thread, hence the radix of the
+FFT stages; tile width; one tile per block or persistent blocks) and the
+autotuner that picks one per grid size.
+
+Every variant must give the same statistics: against the FP64 oracle at 128^3,
+and against the Parseval route (which reads only delta^ and the radial tables and
+is pinned to the oracle at small grids) at 256^3 and 512^3, with a ragged window
+batch (18 shells x 2 orders = 36 windows)."""
+import numpy as np
+import pytest
+
+from oracle import hermes_oracle as O
+from synthetic import catalogues as S
+
+pytestmark = pytest.mark.gpu
+
+REL, ABS = 1e-4, 1e-6
+
+
+def _hermes():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_23494_b300 import hermes as H
+    return H
+
+
+def _close(got, ref, rel=REL, ab=ABS):
+    got, ref = np.asarray(got), np.asarray(ref)
+    err = np.abs(got - ref)
+    bad = err > np.maximum(rel * np.abs(ref), ab)
+    assert not bad.any(), (f"{bad.sum()} of {bad.size} outside tolerance; worst abs err {err.max():.3e}; "
+                           f"got {got[bad][:5]} ref {ref[bad][:5]}")
+
+
+@pytest.mark.parametrize("N,L", [(128, 400.0), (256, 800.0), (512, 1000.0)])
+def test_every_inverse_y_variant_matches(N, L):
+    H = _hermes()
+    nvar = len(H.fft_variants(N)["variants"])
+    assert nvar >= 2
+    pos = S.lognormal_catalogue(100000, L, seed=N + 7, n_grid=64)
+    edges = np.linspace(L / 100, L / 10, 19)
+    ells = (0, 2)
+    outs = []
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(edges, l_max=2)
+            ctx.assign(pos)
+            ks = ctx.xi_multipoles_kspace(ells)
+            for v in range(nvar):
+                H.fft_set_variant(N, v)
+                assert H.fft_variants(N)["forced"] == v
+                outs.append(ctx.xi_multipoles(ells))
+    finally:
+        H.fft_set_variant(N, -1)
+    ref = O.xi_multipoles(pos, None, N, L, 4, edges, ells=ells)["xi"] if N == 128 else ks
+    for got in outs:
+        assert got.shape == (2, 18) and np.all(np.isfinite(got))
+        _close(got, ref)
+        # the variants differ only in float32 rounding
+        _close(got, outs[0], rel=2e-5, ab=1e-7)
+
+
+def test_autotuner_times_every_variant_and_keeps_the_fastest():
+    H = _hermes()
+    N, L = 256, 800.0
+    H.fft_set_variant(N, -1)
+    pos = S.lognormal_catalogue(50000, L, seed=3, n_grid=64)
+    with H.Context(L, N, 4) as ctx:
+        ctx.window_shells(np.linspace(10.0, 80.0, 9), l_max=0)
+        ctx.assign(pos)
+        first = ctx.xi()
+        info = H.fft_variants(N)
+        assert info["forced"] == -1 and info["chosen"] >= 0
+        ms = info["ms"]
+        assert len(ms) == len(info["variants"]) and all(m > 0 for m in ms)
+        assert info["chosen"] == int(np.argmin(ms))
+        # later calls keep the choice without timing again
+        again = ctx.xi()
+        assert H.fft_variants(N)["ms"] == ms
+    np.testing.assert_allclose(again, first, rtol=1e-5, atol=1e-8)

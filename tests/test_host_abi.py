@@ -123,3 +123,29 @@ def test_allocation_failure_hook_counts_without_a_gpu():
     assert lib.hermes_debug_fail_allocs(3) == 0
     assert lib.hermes_debug_fail_allocs(-5) == 3     # negative disarms
     assert lib.hermes_debug_fail_allocs(0) == 0
+
+
+def test_fft_variant_table_and_arguments_without_a_gpu():
+    # the inverse y pass has a radix-8 variant everywhere and 16 / 32 values per
+    # thread (radix-16 / radix-32 stages) from 128^3 up; fixing one is recorded,
+    # -1 returns to autotuning, anything else is an argument error
+    from paper_2607_23494_b300 import hermes as H
+    for N, n_min in ((16, 1), (64, 1), (128, 2), (256, 3), (512, 3), (1024, 2)):
+        info = H.fft_variants(N)
+        assert len(info["variants"]) >= n_min
+        kind, E, W, _ = info["variants"][0]
+        assert (kind, E) == (0, 8)
+        for kind, E, W, minb in info["variants"]:
+            assert kind in (0, 1, 2) and E in (8, 16, 32) and W >= 1 and N % E == 0
+    n512 = len(H.fft_variants(512)["variants"])
+    H.fft_set_variant(512, 1)
+    assert H.fft_variants(512)["forced"] == 1
+    H.fft_set_variant(512, -1)
+    info = H.fft_variants(512)
+    assert info["forced"] == -1 and info["chosen"] == -1 and all(m == -1.0 for m in info["ms"])
+    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 1)):
+        with pytest.raises(H.HermesError) as ei:
+            H.fft_set_variant(bad[0], bad[1], pass_=bad[2])
+        assert ei.value.code == H.ERR_ARG
+    with pytest.raises(H.HermesError):
+        H.fft_variants(2048)
