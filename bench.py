@@ -204,22 +204,28 @@ def error_vs_oracle(res, pos, mass, zeta128) -> dict:
 # passes at 512^3 on a 5-window launch of the current kernels: bytes per launch (read once
 # per launch) and per window.
 NCU_TRAFFIC_512 = {
-    "inv_x_window": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
+    "inv_x_window/k0e8w8": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
+    "inv_x_window/k1e8w8": {"per_launch": 0.561371e9, "per_window": 2.634040e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
+    "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
     "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
 }
+TUNED_PASSES = {"inv_y": 0, "inv_x_window": 1}  # trace name -> hermes_fft_variants pass
 
 
-def y_variant_tag(H, N: int) -> str:
-    """The inverse y-pass variant in use for grid N as kind / values per thread / tile width."""
-    info = H.fft_variants(N)
+def variant_tag(H, N: int, pass_: int) -> str:
+    """The variant of a tuned pass in use for grid N as kind / values per thread / tile width."""
+    info = H.fft_variants(N, pass_)
     v = info["forced"] if info["forced"] >= 0 else max(info["chosen"], 0)
     kind, E, W, _ = info["variants"][v]
     return f"k{kind}e{E}w{W}"
 
 
-def ncu_traffic(name: str, windows_per_launch: float, y_tag: str) -> float | None:
-    t = NCU_TRAFFIC_512.get(f"{name}/{y_tag}" if name == "inv_y" else name)
+def ncu_traffic(H, name: str, windows_per_launch: float) -> float | None:
+    """DRAM bytes per launch from an ncu capture of the same kernel (None when the
+    variant in use was not captured)."""
+    key = f"{name}/{variant_tag(H, N2, TUNED_PASSES[name])}" if name in TUNED_PASSES else name
+    t = NCU_TRAFFIC_512.get(key)
     return None if t is None else t["per_launch"] + t["per_window"] * windows_per_launch
 
 
@@ -336,8 +342,7 @@ def run_hermes(args, rank, world, local_rank):
                       (12 * n + 16 * n) * args.steps)
     achieved = dom_b / (trace[dom][0] / 1e3) / 1e9 if dom_b else None
     from paper_2607_23494_b300 import hermes as Hm
-    y_tag = y_variant_tag(Hm, N2)
-    traffic = ncu_traffic(dom, windows_per_step / batches_per_step, y_tag)  # per launch, scaled from ncu
+    traffic = ncu_traffic(Hm, dom, windows_per_step / batches_per_step)  # per launch, scaled from ncu
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
             "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
@@ -391,7 +396,8 @@ def run_hermes(args, rank, world, local_rank):
             "gpu_launches": launches,
             "roofline": roof,
             "kernels": kern,
-            "fft_variants": {"inv_y_512": {**Hm.fft_variants(N2), "in_use": y_tag}},
+            "fft_variants": {f"{name}_{N2}": {**Hm.fft_variants(N2, p), "in_use": variant_tag(Hm, N2, p)}
+                             for name, p in TUNED_PASSES.items()},
             "xi_sample": {"l0_first3": [float(x) for x in res[0][0][:3]]},
         }
         for key, val in (("kspace", ks), ("cylinders", cyl), ("s_mu", smu)):
@@ -697,7 +703,7 @@ def run_batch(args, dev, stream, rank):
                         "tuning": [[int(a), int(b), round(c, 4)] for a, b, c in info["tuning"]]},
             "one_at_a_time": {"value": round(cw / (s_ms / 1e3), 1), "ms_per_batch": round(s_ms, 2),
                               "diff_vs_batched_in_tolerances": round(diff, 4)},
-            "inv_y_variants_256": fft_variants(N4),
+            "fft_variants_256": {"inv_y": fft_variants(N4, 0), "inv_x_window": fft_variants(N4, 1)},
             "plain_fp32": {"value": round(cw / (p_ms / 1e3), 1), "ms_per_batch": round(p_ms, 2),
                            "diff_vs_batched_in_tolerances": round(pdiff, 4)},
             "speedup_vs_plain": round(p_ms / b_ms, 2), "speedup_vs_one_at_a_time": round(s_ms / b_ms, 2)}
@@ -1021,11 +1027,14 @@ def run_reference(args):
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_profile_case():
-    """Small case for ncu captures: 512^3 field of 300k Poisson points, 5 l=0 windows (one batch)."""
+def run_profile_case(args):
+    """Small case for ncu captures: 512^3 field of 300k Poisson points, 5 l=0 windows (one batch).
+    --y-variant / --x-variant fix the tuned passes' variants, so no tuning trials run."""
     import torch
-    from paper_2607_23494_b300 import Context
+    from paper_2607_23494_b300 import Context, fft_set_variant
     from synthetic import catalogues as S
+    fft_set_variant(N2, args.y_variant, 0)
+    fft_set_variant(N2, args.x_variant, 1)
     pos = torch.from_numpy(S.poisson_uniform(300_000, L2, seed=7)).cuda()
     ctx = Context(L2, N2, P2)
     ctx.window_shells(np.linspace(2.0, 52.0, 6), l_max=0)
@@ -1070,11 +1079,13 @@ def main():
                          "--no-zeta --no-cpu-baseline); for launch-list captures")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
+    ap.add_argument("--y-variant", type=int, default=0, help="inverse y-pass variant of --profile-case")
+    ap.add_argument("--x-variant", type=int, default=0, help="window-pass variant of --profile-case")
     args = ap.parse_args()
     if args.minimal:
         args.no_plain = args.no_batch = args.no_serve = args.no_zeta = args.no_cpu_baseline = True
     if args.profile_case:
-        run_profile_case()
+        run_profile_case(args)
         return 0
     if args.profile_zeta:
         run_profile_zeta()

@@ -279,6 +279,68 @@ __device__ __forceinline__ void fft_line_wc(float2 (&v)[8], int t, const float2*
 }
 
 
+// K lines per thread at once (8 values each), all exchanging behind the same
+// barriers: one barrier pair per stage serves the K transforms, and the K
+// butterflies between barriers are independent.  sms[k] is line k's layout; the
+// stage twiddles come preloaded (load_stage_twiddles), so every twiddled stage
+// must run one butterfly per thread.
+template <int M, int R, int NS, bool INV, int SI, class S, int K>
+__device__ __forceinline__ void fft_stage_k(float2 (&v)[K][8], int t, const S* sms, const float2* wc) {
+    constexpr int T = M / 8;
+    constexpr int U = 8 / R;
+    constexpr bool LAST = (NS * R == M);
+    float2 out[K][8];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float2 x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = v[k][u + r * U];
+            if constexpr (NS > 1) {
+                static_assert(R == 8 && U == 1, "preloaded twiddles serve radix-8 stages of one butterfly per thread");
+                twiddle_from3(x, wc[3 * (SI - 1)], wc[3 * (SI - 1) + 1], wc[3 * (SI - 1) + 2]);
+            }
+            dftR<R, INV>(x);
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[k][u + r * U] = x[r];
+        }
+    }
+    if constexpr (LAST) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[k][i] = out[k][i];
+    } else {
+        sms[0].sync();
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int b = t + u * T;
+                const int base = (b / NS) * NS * R + (b & (NS - 1));
+#pragma unroll
+                for (int r = 0; r < R; ++r) sms[k].st(base + r * NS, out[k][u + r * U]);
+            }
+        sms[0].sync();
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[k][i] = sms[k].ld(t + i * T);
+    }
+}
+template <int M, int NS, bool INV, int SI, class S, int K>
+__device__ __forceinline__ void fft_stages_k(float2 (&v)[K][8], int t, const S* sms, const float2* wc) {
+    constexpr int R = (NS == 1) ? FirstRadix<M>::value : 8;
+    fft_stage_k<M, R, NS, INV, SI, S, K>(v, t, sms, wc);
+    if constexpr (NS * R < M) fft_stages_k<M, NS * R, INV, SI + 1, S, K>(v, t, sms, wc);
+}
+template <int M, bool INV, int K, class S>
+__device__ __forceinline__ void fft_lines_wc(float2 (&v)[K][8], int t, const S* sms, const float2* wc) {
+    static_assert(M >= 8 && (M & (M - 1)) == 0 && M <= TW, "unsupported FFT length");
+    fft_stages_k<M, 1, INV, 0, S, K>(v, t, sms, wc);
+}
+
 // ---------------------------------------------------------------------------
 // The same Stockham scheme with E = 8, 16 or 32 values per thread (M/E threads
 // per line): radix-E stages, after a leading radix-2^r stage when log2(M) is not a

@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <initializer_list>
 
 namespace hermes {
@@ -403,6 +404,112 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window(const float2* __
     }
 }
 
+// The window pass with two windows in flight per thread: windows s and s + 1 are
+// scaled, transformed and stored together, their transforms exchanging through two
+// tile buffers behind the same barriers (half the barriers per window and twice the
+// independent instructions between them).  The radial table is staged as in
+// k_inv_x_window but with rows of RS = 4, 8 or 16 floats and no padding: the
+// 16-byte chunk j of row r sits at chunk j ^ ((r >> rsh) & (RS / 4 - 1)), so the
+// 16-byte reads of a quarter warp (8 consecutive rows) meet 8 distinct bank groups.
+// Used when the table of the batch (S <= 16) and two tiles fit in shared memory.
+__host__ __device__ constexpr int pair_row_floats(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float2* __restrict__ spec,
+                                                                   float2* __restrict__ work, const WinBatch wb,
+                                                                   const Tables tb) {
+    using C = Cfg<N>;
+    constexpr int W = C::W, T = N / 8, H = N / 2;
+    constexpr int TILE = SmemStrided<W>::words(N);
+    extern __shared__ __align__(16) float2 smem[];
+    float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
+    const int RS = pair_row_floats(wb.S);
+    const int rsh = RS == 16 ? 1 : 2, cmask = RS / 4 - 1;
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    const int ky = blockIdx.y, kz = blockIdx.x * W + col;
+    const size_t xstride = (size_t)N * H;
+    {  // batched launch: blockIdx.z = catalogue
+        const size_t cat = blockIdx.z;
+        spec += cat * N * N * H;
+        work += cat * wb.S * N * N * H;
+    }
+    const int ny = signed_freq(ky, N), nz = kz;
+    const bool nyq_y = (ky == H);
+    {
+        const int S4 = (wb.S + 3) >> 2;
+        const int total = H * W * S4;
+        const int ny2 = nyq_y ? 0 : ny * ny;
+        for (int e = threadIdx.x; e < total; e += C::TS) {
+            const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
+            const int nzc = blockIdx.x * W + c;
+            const int qq = nyq_y ? 0 : a * a + ny2 + (wb.cyl ? 0 : nzc * nzc);
+            const int row = a * W + c;
+            ac::cp_async16(ttab + row * RS + 4 * (s4 ^ ((row >> rsh) & cmask)),
+                           reinterpret_cast<const float4*>(wb.tab + (size_t)qq * wb.nbp) + s4);
+        }
+        ac::cp_async_commit();
+    }
+    const float2* src = spec + (size_t)ky * H + kz;
+    float2 v0[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v0[i] = src[(size_t)(t + i * T) * xstride];
+    const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int kx = t + i * T;
+        const int nx = signed_freq(kx, N);
+        const bool nyq = nyq_y || (kx == H);
+        const int qi = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+        const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
+        const float a = wb.cyl ? (wb.par_stride ? 1.0f : __ldg(wb.par + nz))
+                               : wb.scale * legendre(wb.ell, qi > 0 ? (float)nz * rsqrtf((float)qi) : 0.0f);
+        v0[i] = cscale(v0[i], ph * a);
+    }
+    // table row of element i: |n_x| = t + iT (i < 4) or N - t - iT (i >= 4; the Nyquist
+    // element t = 0, i = 4 is zero and reads row 0)
+    auto trow = [&](int i) {
+        const int ax = i < 4 ? t + i * T : ((t == 0 && i == 4) ? 0 : N - t - i * T);
+        return ax * W + col;
+    };
+    ac::cp_async_wait_all();
+    __syncthreads();
+    float2 wc[3 * twiddled_stages<N>()];
+    load_stage_twiddles<N, true>(t, tb.tw, wc);
+    const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
+    for (int g = 0; g < wb.S; g += 4) {
+        float4 tv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = trow(i);
+            tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+        }
+#pragma unroll
+        for (int jp = 0; jp < 4; jp += 2) {
+            const int s = g + jp;
+            if (s >= wb.S) break;  // uniform across the block
+            const bool two = s + 1 < wb.S;
+            const float pz0 = wb.par_stride ? __ldg(wb.par + (size_t)s * wb.par_stride + nz) : 1.0f;
+            const float pz1 = (wb.par_stride && two) ? __ldg(wb.par + (size_t)(s + 1) * wb.par_stride + nz) : 1.0f;
+            float2 v[2][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float f0 = jp == 0 ? tv[i].x : tv[i].z, f1 = jp == 0 ? tv[i].y : tv[i].w;
+                v[0][i] = cscale(v0[i], pz0 * f0);
+                v[1][i] = cscale(v0[i], pz1 * f1);
+            }
+            fft_lines_wc<N, true, 2>(v, t, sms, wc);
+            float2* dst = work + (size_t)s * N * N * H + (size_t)ky * H + kz;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[0][i];
+            if (two) {
+                dst += (size_t)N * N * H;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride] = v[1][i];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // I3: complex-to-real along z fused with the cell contraction.
 // Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), X_M = 0;
@@ -761,13 +868,19 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 }
 
 // ---------------------------------------------------------------------------
-// Variants of the inverse y pass and the autotuner that picks one per grid size.
-// A variant fixes the values per thread E (the radix of the FFT stages: radix 8
-// throughout for E = 8, radix 16 or 32 for E = 16, 32), the tile width W, the form
-// (one tile per block or persistent) and the blocks per SM.  The first inverse call
-// of a grid size that is not being captured into a graph times every variant on its
-// own work buffer, before the window pass writes it, and keeps the fastest for the
-// process; hermes_fft_set_variant fixes one instead.
+// Variants of the window pass (pass 1, I1) and of the inverse y pass (pass 0, I2),
+// and the autotuner that picks one per pass and grid size.  A variant fixes the
+// values per thread E (the radix of the FFT stages: radix 8 throughout for E = 8,
+// radix 16 or 32 for E = 16, 32), the tile width W, the blocks per SM it is
+// compiled for (minb, 0: not fixed) and a kind:
+//   pass 0: 0 the radix-8 pass (k_strided_pf up to 512^3, k_strided above),
+//           1 k_strided_e (one tile per block), 2 k_strided_pf_e (persistent);
+//   pass 1: 0 the radix-8 window pass (k_inv_x_window, shared table when it fits),
+//           1 k_inv_x_window_pair (two windows in flight per thread).
+// The first inverse call of a grid size that is not being captured into a graph
+// times every variant on that call's own buffers (the y pass before the window pass
+// writes the work buffer, the window pass on the first catalogue) and keeps the
+// fastest for the process and device; hermes_fft_set_variant fixes one instead.
 
 static int sm_count() {
     static int n = [] {
@@ -782,29 +895,39 @@ static int sm_count() {
     return n;
 }
 
-// kind 0: the radix-8 pass (k_strided_pf up to 512^3, k_strided above);
-// kind 1: k_strided_e; kind 2: k_strided_pf_e.
-struct YVariant {
+struct PassVariant {
     int kind, E, W, minb;
 };
-static int y_variants(int N, YVariant* out) {
-    auto put = [&](std::initializer_list<YVariant> l) {
+constexpr int kMaxVariants = 8;
+static int pass_variants(int N, int pass, PassVariant* out) {
+    auto put = [&](std::initializer_list<PassVariant> l) {
         int k = 0;
-        for (const YVariant& v : l) out[k++] = v;
+        for (const PassVariant& v : l) out[k++] = v;
         return k;
     };
-    switch (N) {
-        case 16: return put({{0, 8, Cfg<16>::W, 2}});
-        case 32: return put({{0, 8, Cfg<32>::W, 2}});
-        case 64: return put({{0, 8, Cfg<64>::W, 2}});
-        case 128: return put({{0, 8, Cfg<128>::W, 2}, {1, 16, 8, 0}});
-        case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
-        case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0}});
-        case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+    if (pass == 0) {
+        switch (N) {
+            case 16: return put({{0, 8, Cfg<16>::W, 2}});
+            case 32: return put({{0, 8, Cfg<32>::W, 2}});
+            case 64: return put({{0, 8, Cfg<64>::W, 2}});
+            case 128: return put({{0, 8, Cfg<128>::W, 2}, {1, 16, 8, 0}});
+            case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
+            case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+            case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+        }
+    } else if (pass == 1) {
+        switch (N) {
+            case 16: return put({{0, 8, Cfg<16>::W, 1}});
+            case 32: return put({{0, 8, Cfg<32>::W, 1}});
+            case 64: return put({{0, 8, Cfg<64>::W, 1}});
+            case 128: return put({{0, 8, Cfg<128>::W, 1}});
+            case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}});
+            case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
+        }
     }
     return 0;
 }
-constexpr int kMaxYVariants = 4;
 
 // Tiles (column chunk, x, window) of nwin consecutive windows of work.
 template <int N>
@@ -870,29 +993,77 @@ static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* t
     return run_y_r8<N>(work, nwin, tw, st);
 }
 
-struct YTune {
-    int forced = -1, chosen = -1;
-    double ms[kMaxYVariants] = {-1.0, -1.0, -1.0, -1.0};
-};
-static std::mutex g_ytune_mu;
-static std::map<std::pair<int, int>, YTune> g_ytune;  // (device, N)
-
-static std::pair<int, int> ytune_key(int N) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
-    return {dev, N};
+// The window pass: tiles of W k_z columns at one k_y (grid (H / W, N, ncat)).
+template <int N>
+static cudaError_t run_x_r8(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
+                            cudaStream_t st) {
+    using C = Cfg<N>;
+    cudaError_t e;
+    // radial factors staged in shared memory when they fit next to the FFT tile
+    const size_t stab_bytes = C::SMEM_STRIDED + (size_t)(N / 2) * C::W * stab_row_stride(wb.S) * sizeof(float);
+    const bool use_stab = stab_bytes <= kMaxDynSmem && stab_x_enabled();
+    dim3 g1((N / 2) / C::W, N, ncat);
+    if (use_stab) {
+        if ((e = allow_smem(k_inv_x_window<N, true>, stab_bytes)) != cudaSuccess) return e;
+        k_inv_x_window<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, work, wb, tb);
+    } else {
+        if ((e = allow_smem(k_inv_x_window<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+        k_inv_x_window<N, false><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb);
+    }
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t run_x_pair(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
+                              cudaStream_t st) {
+    using C = Cfg<N>;
+    const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
+    if (wb.S > 16 || bytes > kMaxDynSmem) return run_x_r8<N>(spec, work, wb, tb, ncat, st);
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_x_window_pair<N>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_pair<N><<<dim3((N / 2) / C::W, N, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const WinBatch& wb, const Tables& tb,
+                                int ncat, cudaStream_t st) {
+    if constexpr (N == 256) {
+        switch (var) {
+            case 1: return run_x_pair<256>(spec, work, wb, tb, ncat, st);
+        }
+    } else if constexpr (N == 512) {
+        switch (var) {
+            case 1: return run_x_pair<512>(spec, work, wb, tb, ncat, st);
+        }
+    }
+    return run_x_r8<N>(spec, work, wb, tb, ncat, st);
 }
 
-// The variant of this call: the forced one, else the tuned one, else (tuning on the
-// first nwin_avail windows of work when st is not capturing) the fastest; variant 0
-// while capturing before any tuning.
-template <int N>
-static int inv_y_pick(float2* work, int nwin_avail, const float2* tw, cudaStream_t st) {
-    YVariant vs[kMaxYVariants];
-    const int nvar = y_variants(N, vs);
-    if (nvar <= 1 || nwin_avail < 1) return 0;
-    std::lock_guard<std::mutex> lk(g_ytune_mu);
-    YTune& en = g_ytune[ytune_key(N)];
+struct Tune {
+    int forced = -1, chosen = -1;
+    double ms[kMaxVariants];
+    Tune() {
+        for (double& m : ms) m = -1.0;
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, Tune> g_tune;  // (device, N, pass)
+
+static std::tuple<int, int, int> tune_key(int N, int pass) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+    return {dev, N, pass};
+}
+
+// The variant of this call for (N, pass): the forced one, else the tuned one, else
+// (timing trial(v), one launch of variant v on the call's buffers, when st is not
+// capturing) the fastest; variant 0 while capturing before any tuning.
+template <class F>
+static int pick_variant(int N, int pass, cudaStream_t st, F&& trial) {
+    PassVariant vs[kMaxVariants];
+    const int nvar = pass_variants(N, pass, vs);
+    if (nvar <= 1) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    Tune& en = g_tune[tune_key(N, pass)];
     if (en.forced >= 0) return en.forced;
     if (en.chosen >= 0) return en.chosen;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -900,8 +1071,6 @@ static int inv_y_pick(float2* work, int nwin_avail, const float2* tw, cudaStream
         cudaGetLastError();
         return 0;
     }
-    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
-    const int nwin = (int)std::max<size_t>(1, std::min<size_t>((size_t)nwin_avail, ((size_t)1 << 30) / win_bytes));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
@@ -912,14 +1081,14 @@ static int inv_y_pick(float2* work, int nwin_avail, const float2* tw, cudaStream
     double best_ms = 1e300;
     for (int v = 0; v < nvar; ++v) {
         en.ms[v] = -1.0;
-        if (launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess) {  // warm-up
+        if (trial(v) != cudaSuccess) {  // warm-up
             cudaGetLastError();
             continue;
         }
         float ms = 0.f;
-        if (cudaEventRecord(e0, st) != cudaSuccess || launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess ||
-            launch_inv_y<N>(v, work, nwin, tw, st) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
-            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (cudaEventRecord(e0, st) != cudaSuccess || trial(v) != cudaSuccess || trial(v) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -933,12 +1102,11 @@ static int inv_y_pick(float2* work, int nwin_avail, const float2* tw, cudaStream
 }
 
 int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced) {
-    if (pass != 0) return -1;
-    YVariant vs[kMaxYVariants];
-    const int n = y_variants(N, vs);
+    PassVariant vs[kMaxVariants];
+    const int n = pass_variants(N, pass, vs);
     if (n == 0) return -1;
-    std::lock_guard<std::mutex> lk(g_ytune_mu);
-    const auto it = g_ytune.find(ytune_key(N));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune.find(tune_key(N, pass));
     for (int i = 0; i < std::min(n, cap); ++i) {
         if (desc) {
             desc[4 * i] = vs[i].kind;
@@ -946,20 +1114,19 @@ int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, i
             desc[4 * i + 2] = vs[i].W;
             desc[4 * i + 3] = vs[i].minb;
         }
-        if (ms) ms[i] = it == g_ytune.end() ? -1.0 : it->second.ms[i];
+        if (ms) ms[i] = it == g_tune.end() ? -1.0 : it->second.ms[i];
     }
-    if (chosen) *chosen = it == g_ytune.end() ? -1 : it->second.chosen;
-    if (forced) *forced = it == g_ytune.end() ? -1 : it->second.forced;
+    if (chosen) *chosen = it == g_tune.end() ? -1 : it->second.chosen;
+    if (forced) *forced = it == g_tune.end() ? -1 : it->second.forced;
     return n;
 }
 
 int fft_set_variant(int N, int pass, int variant) {
-    if (pass != 0) return -1;
-    YVariant vs[kMaxYVariants];
-    const int n = y_variants(N, vs);
+    PassVariant vs[kMaxVariants];
+    const int n = pass_variants(N, pass, vs);
     if (n == 0 || variant < -1 || variant >= n) return -1;
-    std::lock_guard<std::mutex> lk(g_ytune_mu);
-    YTune& en = g_ytune[ytune_key(N)];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    Tune& en = g_tune[tune_key(N, pass)];
     en.forced = variant;
     if (variant < 0) {  // back to autotuning: the next uncaptured call times the variants again
         en.chosen = -1;
@@ -974,24 +1141,20 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
                                 int ncat) {
     using C = Cfg<N>;
     cudaError_t e;
-    // radial factors staged in shared memory when they fit next to the FFT tile
-    const size_t stab_bytes = C::SMEM_STRIDED + (size_t)(N / 2) * C::W * stab_row_stride(wb.S) * sizeof(float);
-    const bool use_stab = stab_bytes <= kMaxDynSmem && stab_x_enabled();
-    if ((e = allow_smem(k_inv_x_window<N, false>, C::SMEM_STRIDED)) != cudaSuccess) return e;
-    if (use_stab && (e = allow_smem(k_inv_x_window<N, true>, stab_bytes)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
     if ((e = allow_smem(k_inv_z_c2r_contract<N>, C::SMEM_Z3)) != cudaSuccess) return e;
-    const long long H = N / 2;
-    // the y-pass variant, tuned (on this call's work buffer, before the window pass
-    // writes it) on the first uncaptured call of this grid size
-    const int yvar = (ncat == 1 && yz_fused_ok<N>()) ? 0 : inv_y_pick<N>(work, wb.S * ncat, tb.tw, st);
-    dim3 g1(H / C::W, N, ncat);
+    // the pass variants, tuned on the first uncaptured call of this grid size: the y
+    // pass on this call's work buffer before the window pass writes it (about 1 GiB
+    // of it), the window pass on the first catalogue
+    const bool yz = ncat == 1 && yz_fused_ok<N>();
+    const size_t win_bytes = (size_t)N * N * (N / 2) * sizeof(float2);
+    const int nwin_trial = (int)std::max<size_t>(1, std::min<size_t>((size_t)wb.S * ncat, ((size_t)1 << 30) / win_bytes));
+    const int yvar = yz ? 0 : pick_variant(N, 0, st, [&](int v) { return launch_inv_y<N>(v, work, nwin_trial, tb.tw, st); });
+    const int xvar = pick_variant(N, 1, st, [&](int v) { return launch_inv_x<N>(v, spec, work, wb, tb, 1, st); });
     tr(K_INV_X_WINDOW, 0, st);
-    if (use_stab) k_inv_x_window<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, work, wb, tb);
-    else k_inv_x_window<N, false><<<g1, C::TS, C::SMEM_STRIDED, st>>>(spec, work, wb, tb);
+    if ((e = launch_inv_x<N>(xvar, spec, work, wb, tb, ncat, st)) != cudaSuccess) return e;
     tr(K_INV_X_WINDOW, 1, st);
     if constexpr (N <= 512) {
-        if (ncat == 1 && yz_fused_ok<N>()) {
+        if (yz) {
             tr(K_INV_YZ_CONTRACT, 0, st);
             e = launch_yz<N>(work, wb.S, delta, tb.tw, dd_part, st);
             tr(K_INV_YZ_CONTRACT, 1, st);

@@ -1,6 +1,7 @@
 """The variants of the inverse y pass (values per thread, hence the radix of the
-FFT stages; tile width; one tile per block or persistent blocks) and the
-autotuner that picks one per grid size.
+FFT stages; tile width; one tile per block or persistent blocks) and of the window
+pass (one or two windows in flight per thread), and the autotuner that picks one
+per pass and grid size.
 
 Every variant must give the same statistics: against the FP64 oracle at 128^3,
 and against the Parseval route (which reads only delta^ and the radial tables and
@@ -33,10 +34,11 @@ def _close(got, ref, rel=REL, ab=ABS):
                            f"got {got[bad][:5]} ref {ref[bad][:5]}")
 
 
-@pytest.mark.parametrize("N,L", [(128, 400.0), (256, 800.0), (512, 1000.0)])
-def test_every_inverse_y_variant_matches(N, L):
+@pytest.mark.parametrize("pass_,N,L", [(0, 128, 400.0), (0, 256, 800.0), (0, 512, 1000.0), (1, 256, 800.0),
+                                        (1, 512, 1000.0)])
+def test_every_pass_variant_matches(pass_, N, L):
     H = _hermes()
-    nvar = len(H.fft_variants(N)["variants"])
+    nvar = len(H.fft_variants(N, pass_)["variants"])
     assert nvar >= 2
     pos = S.lognormal_catalogue(100000, L, seed=N + 7, n_grid=64)
     edges = np.linspace(L / 100, L / 10, 19)
@@ -48,11 +50,11 @@ def test_every_inverse_y_variant_matches(N, L):
             ctx.assign(pos)
             ks = ctx.xi_multipoles_kspace(ells)
             for v in range(nvar):
-                H.fft_set_variant(N, v)
-                assert H.fft_variants(N)["forced"] == v
+                H.fft_set_variant(N, v, pass_)
+                assert H.fft_variants(N, pass_)["forced"] == v
                 outs.append(ctx.xi_multipoles(ells))
     finally:
-        H.fft_set_variant(N, -1)
+        H.fft_set_variant(N, -1, pass_)
     ref = O.xi_multipoles(pos, None, N, L, 4, edges, ells=ells)["xi"] if N == 128 else ks
     for got in outs:
         assert got.shape == (2, 18) and np.all(np.isfinite(got))
@@ -66,16 +68,19 @@ def test_autotuner_times_every_variant_and_keeps_the_fastest():
     N, L = 256, 800.0
     H.fft_set_variant(N, -1)
     pos = S.lognormal_catalogue(50000, L, seed=3, n_grid=64)
+    H.fft_set_variant(N, -1, H.PASS_WINDOW)
     with H.Context(L, N, 4) as ctx:
         ctx.window_shells(np.linspace(10.0, 80.0, 9), l_max=0)
         ctx.assign(pos)
         first = ctx.xi()
-        info = H.fft_variants(N)
-        assert info["forced"] == -1 and info["chosen"] >= 0
-        ms = info["ms"]
-        assert len(ms) == len(info["variants"]) and all(m > 0 for m in ms)
-        assert info["chosen"] == int(np.argmin(ms))
+        for pass_ in (H.PASS_INV_Y, H.PASS_WINDOW):
+            info = H.fft_variants(N, pass_)
+            assert info["forced"] == -1 and info["chosen"] >= 0
+            ms = info["ms"]
+            assert len(ms) == len(info["variants"]) and all(m > 0 for m in ms)
+            assert info["chosen"] == int(np.argmin(ms))
         # later calls keep the choice without timing again
+        ms = [H.fft_variants(N, p)["ms"] for p in (0, 1)]
         again = ctx.xi()
-        assert H.fft_variants(N)["ms"] == ms
+        assert [H.fft_variants(N, p)["ms"] for p in (0, 1)] == ms
     np.testing.assert_allclose(again, first, rtol=1e-5, atol=1e-8)
