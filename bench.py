@@ -208,9 +208,10 @@ NCU_TRAFFIC_512 = {
     "inv_x_window/k1e8w8": {"per_launch": 0.561371e9, "per_window": 2.634040e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
-    "inv_z_c2r_contract": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
+    "inv_z_c2r_contract/k0e8w1": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
+    "inv_z_c2r_contract/k1e16w1": {"per_launch": 0.0, "per_window": (3.221317e9 + 0.013573e9) / 5},
 }
-TUNED_PASSES = {"inv_y": 0, "inv_x_window": 1}  # trace name -> hermes_fft_variants pass
+TUNED_PASSES = {"inv_y": 0, "inv_x_window": 1, "inv_z_c2r_contract": 2}  # trace name -> hermes_fft_variants pass
 
 
 def variant_tag(H, N: int, pass_: int) -> str:
@@ -703,7 +704,8 @@ def run_batch(args, dev, stream, rank):
                         "tuning": [[int(a), int(b), round(c, 4)] for a, b, c in info["tuning"]]},
             "one_at_a_time": {"value": round(cw / (s_ms / 1e3), 1), "ms_per_batch": round(s_ms, 2),
                               "diff_vs_batched_in_tolerances": round(diff, 4)},
-            "fft_variants_256": {"inv_y": fft_variants(N4, 0), "inv_x_window": fft_variants(N4, 1)},
+            "fft_variants_256": {"inv_y": fft_variants(N4, 0), "inv_x_window": fft_variants(N4, 1),
+                                 "inv_z_c2r_contract": fft_variants(N4, 2)},
             "plain_fp32": {"value": round(cw / (p_ms / 1e3), 1), "ms_per_batch": round(p_ms, 2),
                            "diff_vs_batched_in_tolerances": round(pdiff, 4)},
             "speedup_vs_plain": round(p_ms / b_ms, 2), "speedup_vs_one_at_a_time": round(s_ms / b_ms, 2)}
@@ -1035,6 +1037,7 @@ def run_profile_case(args):
     from synthetic import catalogues as S
     fft_set_variant(N2, args.y_variant, 0)
     fft_set_variant(N2, args.x_variant, 1)
+    fft_set_variant(N2, args.z_variant, 2)
     pos = torch.from_numpy(S.poisson_uniform(300_000, L2, seed=7)).cuda()
     ctx = Context(L2, N2, P2)
     ctx.window_shells(np.linspace(2.0, 52.0, 6), l_max=0)
@@ -1081,6 +1084,7 @@ def main():
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
     ap.add_argument("--y-variant", type=int, default=0, help="inverse y-pass variant of --profile-case")
     ap.add_argument("--x-variant", type=int, default=0, help="window-pass variant of --profile-case")
+    ap.add_argument("--z-variant", type=int, default=0, help="contraction-pass variant of --profile-case")
     args = ap.parse_args()
     if args.minimal:
         args.no_plain = args.no_batch = args.no_serve = args.no_zeta = args.no_cpu_baseline = True

@@ -439,19 +439,22 @@ int hermes_release_buffers(hermes_ctx *ctx);
  * FFT pass variants and their autotuner.  (The transforms are those of Sec. 3.5;
  * how a pass is tiled on the GPU has no counterpart in the paper.)
  *
- * pass: HERMES_PASS_INV_Y, the inverse transform along y of every filtered
- * window (the middle one of the three inverse passes of the xi statistics), or
- * HERMES_PASS_WINDOW, the first inverse pass (along x, window multiply fused in).
+ * pass: the three inverse passes of the xi statistics: HERMES_PASS_WINDOW, the
+ * first (along x, window multiply fused in); HERMES_PASS_INV_Y, the inverse
+ * transform along y of every filtered window; HERMES_PASS_CONTRACT, the last
+ * (complex-to-real along z fused with the cell contraction).
  * A variant fixes
  *   kind: inverse y: 0 the radix-8 pass, 1 one tile per block, 2 persistent blocks;
  *         window:    0 one window at a time, 1 two windows in flight per thread;
+ *         contract:  0 the radix-8 pass, 1 16 values per thread;
  *   E:    values per thread (8: radix-8 stages; 16, 32: radix-16 or radix-32
  *         stages, fewer shared-memory exchanges per line for more registers);
- *   W:    tile width, the adjacent k_z columns one block transforms together;
+ *   W:    tile width, the adjacent k_z columns one block transforms together
+ *         (1 for the contraction pass, whose z lines are contiguous);
  *   minb: blocks per SM the kernel is compiled for (0: not fixed).
  * Unless a variant is fixed, the first inverse call for grid size N whose stream
  * is not being captured into a graph times every variant on its own work buffer
- * (the y pass before the window pass writes it, the window pass on the first
+ * (the y pass before the window pass writes it, the other two on the first
  * catalogue) and keeps the fastest for the process and device; a call captured
  * before that uses variant 0.  Every variant computes the same transform (to
  * float32 rounding).
@@ -466,6 +469,7 @@ int hermes_release_buffers(hermes_ctx *ctx);
  */
 #define HERMES_PASS_INV_Y 0
 #define HERMES_PASS_WINDOW 1
+#define HERMES_PASS_CONTRACT 2
 int hermes_fft_set_variant(int N, int pass, int variant);
 int hermes_fft_variants(int N, int pass, int *desc, double *ms, int cap, int *chosen, int *forced);
 

@@ -607,6 +607,110 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
     }
 }
 
+// I3 at 16 values per thread: a half-length line (N/2 points) is held by N/32
+// threads, so one shared-memory exchange replaces two at N = 512 (256 = 16 x 16);
+// two lines share a warp.  LZ = THREADS / (N/32) lines per block, their windows
+// staged by bulk copies as in k_inv_z_c2r_contract; a block covering SLOTS blocks
+// of that kernel writes its sum into the first of their partial slots and 0 into
+// the others, so the partials keep the layout of the radix-8 form.  The stage
+// twiddles and the c2r split twiddles are held in registers.
+template <int N, int THREADS>
+struct Z16Cfg {
+    static constexpr int M = N / 2, E = 16, T = M / E, LZ = THREADS / T;
+    static constexpr int SLOTS = LZ / Cfg<N>::LZ;  // partial slots of the radix-8 layout per block
+    static_assert(SLOTS >= 1 && SLOTS * Cfg<N>::LZ == LZ, "blocks cover whole radix-8 blocks");
+    static constexpr size_t SMEM = (size_t)2 * LZ * (N / 2) * sizeof(float2) +
+                                   (size_t)LZ * LinePad<M>::value * sizeof(float2);
+};
+
+template <int N, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const float2* __restrict__ work, int S,
+                                                                       const float* __restrict__ delta,
+                                                                       const float2* __restrict__ tw,
+                                                                       double* __restrict__ dd_part,
+                                                                       unsigned* __restrict__ err) {
+    using C = Z16Cfg<N, THREADS>;
+    constexpr int M = C::M, E = C::E, T = C::T, LZ = C::LZ, LP = LinePad<M>::value, H = N / 2;
+    constexpr int SLOTS = C::SLOTS;
+    static_assert(T <= 32 && 32 % T == 0, "lines within a warp");
+    constexpr int NW = THREADS / 32;
+    constexpr uint32_t STAGE = (uint32_t)(LZ * H * sizeof(float2));
+    extern __shared__ __align__(16) float2 smem[];
+    float2* stage = smem;
+    float2* lines = smem + 2 * LZ * H;
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ float wdd[NW][MAX_BATCH];
+    const int t = threadIdx.x % T, li = threadIdx.x / T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t line0 = (size_t)blockIdx.x * LZ;
+    const size_t line = line0 + li;
+    const SmemZLine<M> sm{{lines + li * LP}, li};  // T <= 32: __syncwarp
+    {  // batched launch: blockIdx.y = catalogue
+        const size_t cat = blockIdx.y;
+        work += cat * S * N * N * H;
+        delta += cat * N * N * N;
+        dd_part += cat * S * (SLOTS * gridDim.x);  // partial layout of the radix-8 form
+    }
+    if (threadIdx.x == 0) {
+        ac::mbar_init(&full[0], 1);
+        ac::mbar_init(&full[1], 1);
+        ac::mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && S > 0) {
+        ac::mbar_expect_tx(&full[0], STAGE);
+        ac::bulk_g2s(stage, work + line0 * H, STAGE, &full[0]);
+    }
+    const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
+    float2 d2[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) d2[i] = dl[t + i * T];
+    float2 wk[E];  // the c2r split twiddles e^{+2 pi i k / N}, k = t + iT
+#pragma unroll
+    for (int i = 0; i < E; ++i) wk[i] = cconj(__ldg(tw + N + t + i * T));
+    float2 wc[stage_twiddle_count<M, E>() + 1];
+    load_stage_twiddles_e<M, E, true>(t, tw, wc);
+    bool late = false;
+    for (int s = 0; s < S; ++s) {
+        __syncthreads();  // every thread is done with the buffer that the next copy overwrites
+        if (threadIdx.x == 0 && s + 1 < S) {
+            ac::fence_proxy_async();
+            ac::mbar_expect_tx(&full[(s + 1) & 1], STAGE);
+            ac::bulk_g2s(stage + ((s + 1) & 1) * LZ * H, work + (size_t)(s + 1) * N * N * H + line0 * H, STAGE,
+                         &full[(s + 1) & 1]);
+        }
+        if (!ac::mbar_wait(&full[s & 1], (s >> 1) & 1)) late = true;
+        const float2* X = stage + (s & 1) * LZ * H + li * H;
+        float2 v[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = t + i * T;
+            const float2 xk = X[k];
+            const float2 xc = cconj((k == 0) ? make_float2(0.f, 0.f) : X[M - k]);
+            const float2 a = cadd(xk, xc);
+            const float2 c = cmul(wk[i], csub(xk, xc));
+            v[i] = make_float2(a.x - c.y, a.y + c.x);
+        }
+        fft_line_e_wc<M, E, true>(v, t, tw, sm, wc);
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < E; ++i) acc = fmaf(d2[i].x, v[i].x, fmaf(d2[i].y, v[i].y, acc));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) wdd[wid][s] = acc;
+    }
+    if (late) atomicOr(err, 4u);
+    __syncthreads();
+    if (threadIdx.x < S) {
+        double tot = 0.0;
+        for (int w = 0; w < NW; ++w) tot += (double)wdd[w][threadIdx.x];
+        double* slot = dd_part + (size_t)threadIdx.x * (SLOTS * gridDim.x) + SLOTS * blockIdx.x;
+        slot[0] = tot;
+#pragma unroll
+        for (int k = 1; k < SLOTS; ++k) slot[k] = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // c2r along z of one filtered spectrum, written out as a real field (no
 // contraction): out[line*N + 2j] = scale * Re z_j, out[line*N + 2j+1] = scale * Im z_j,
@@ -868,19 +972,23 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 }
 
 // ---------------------------------------------------------------------------
-// Variants of the window pass (pass 1, I1) and of the inverse y pass (pass 0, I2),
-// and the autotuner that picks one per pass and grid size.  A variant fixes the
+// Variants of the inverse y pass (pass 0, I2), the window pass (pass 1, I1) and the
+// c2r + contraction pass (pass 2, I3), and the autotuner that picks one per pass
+// and grid size.  A variant fixes the
 // values per thread E (the radix of the FFT stages: radix 8 throughout for E = 8,
 // radix 16 or 32 for E = 16, 32), the tile width W, the blocks per SM it is
 // compiled for (minb, 0: not fixed) and a kind:
 //   pass 0: 0 the radix-8 pass (k_strided_pf up to 512^3, k_strided above),
 //           1 k_strided_e (one tile per block), 2 k_strided_pf_e (persistent);
 //   pass 1: 0 the radix-8 window pass (k_inv_x_window, shared table when it fits),
-//           1 k_inv_x_window_pair (two windows in flight per thread).
+//           1 k_inv_x_window_pair (two windows in flight per thread);
+//   pass 2: 0 the radix-8 c2r + contraction pass (k_inv_z_c2r_contract),
+//           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks).
 // The first inverse call of a grid size that is not being captured into a graph
 // times every variant on that call's own buffers (the y pass before the window pass
-// writes the work buffer, the window pass on the first catalogue) and keeps the
-// fastest for the process and device; hermes_fft_set_variant fixes one instead.
+// writes the work buffer, the window pass and the last pass on the first catalogue)
+// and keeps the fastest for the process and device; hermes_fft_set_variant fixes
+// one instead.
 
 static int sm_count() {
     static int n = [] {
@@ -914,6 +1022,12 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
             case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+        }
+    } else if (pass == 2) {
+        switch (N) {
+            case 256: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
+            case 512: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
+            case 16: case 32: case 64: case 128: case 1024: return put({{0, 8, 1, 3}});
         }
     } else if (pass == 1) {
         switch (N) {
@@ -1038,6 +1152,32 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
     return run_x_r8<N>(spec, work, wb, tb, ncat, st);
 }
 
+// The last inverse pass (c2r along z and the contraction): delta of the first catalogue
+// of the launch at delta, partials [ncat][S][z blocks of the radix-8 form].
+template <int N, int THREADS, int MINB>
+static cudaError_t run_z_e16(const float2* work, int S, const float* delta, const float2* tw, double* dd_part,
+                             unsigned* err, int ncat, cudaStream_t st) {
+    using C = Z16Cfg<N, THREADS>;
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_z_c2r_contract_e16<N, THREADS, MINB>, C::SMEM)) != cudaSuccess) return e;
+    k_inv_z_c2r_contract_e16<N, THREADS, MINB><<<dim3((N * N) / C::LZ, ncat), THREADS, C::SMEM, st>>>(
+        work, S, delta, tw, dd_part, err);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_inv_z(int var, const float2* work, int S, const float* delta, const float2* tw,
+                                double* dd_part, unsigned* err, int ncat, cudaStream_t st) {
+    if constexpr (N == 256 || N == 512) {
+        if (var == 1) return run_z_e16<N, 128, 4>(work, S, delta, tw, dd_part, err, ncat, st);
+        if (var == 2) return run_z_e16<N, 128, 3>(work, S, delta, tw, dd_part, err, ncat, st);
+        if (var == 3) return run_z_e16<N, 128, 2>(work, S, delta, tw, dd_part, err, ncat, st);
+    }
+    using C = Cfg<N>;
+    k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, S, delta, tw,
+                                                                                        dd_part, err);
+    return cudaGetLastError();
+}
+
 struct Tune {
     int forced = -1, chosen = -1;
     double ms[kMaxVariants];
@@ -1150,6 +1290,10 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     const int nwin_trial = (int)std::max<size_t>(1, std::min<size_t>((size_t)wb.S * ncat, ((size_t)1 << 30) / win_bytes));
     const int yvar = yz ? 0 : pick_variant(N, 0, st, [&](int v) { return launch_inv_y<N>(v, work, nwin_trial, tb.tw, st); });
     const int xvar = pick_variant(N, 1, st, [&](int v) { return launch_inv_x<N>(v, spec, work, wb, tb, 1, st); });
+    // (the trials of the last pass read the work buffer as it is and write partials the real launch overwrites)
+    const int zvar = yz ? 0 : pick_variant(N, 2, st, [&](int v) {
+        return launch_inv_z<N>(v, work, wb.S, delta, tb.tw, dd_part, err, 1, st);
+    });
     tr(K_INV_X_WINDOW, 0, st);
     if ((e = launch_inv_x<N>(xvar, spec, work, wb, tb, ncat, st)) != cudaSuccess) return e;
     tr(K_INV_X_WINDOW, 1, st);
@@ -1166,8 +1310,7 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     if ((e = launch_inv_y<N>(yvar, work, wb.S * ncat, tb.tw, st)) != cudaSuccess) return e;
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
-    k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, wb.S, delta, tb.tw,
-                                                                                        dd_part, err);
+    if ((e = launch_inv_z<N>(zvar, work, wb.S, delta, tb.tw, dd_part, err, ncat, st)) != cudaSuccess) return e;
     tr(K_INV_Z_C2R_CONTRACT, 1, st);
     return cudaGetLastError();
 }

@@ -1,7 +1,8 @@
 """The variants of the inverse y pass (values per thread, hence the radix of the
 FFT stages; tile width; one tile per block or persistent blocks) and of the window
-pass (one or two windows in flight per thread), and the autotuner that picks one
-per pass and grid size.
+pass (one or two windows in flight per thread) and of the c2r + contraction pass
+(8 or 16 values per thread), and the autotuner that picks one per pass and grid
+size.
 
 Every variant must give the same statistics: against the FP64 oracle at 128^3,
 and against the Parseval route (which reads only delta^ and the radial tables and
@@ -35,7 +36,7 @@ def _close(got, ref, rel=REL, ab=ABS):
 
 
 @pytest.mark.parametrize("pass_,N,L", [(0, 128, 400.0), (0, 256, 800.0), (0, 512, 1000.0), (1, 256, 800.0),
-                                        (1, 512, 1000.0)])
+                                        (1, 512, 1000.0), (2, 256, 800.0), (2, 512, 1000.0)])
 def test_every_pass_variant_matches(pass_, N, L):
     H = _hermes()
     nvar = len(H.fft_variants(N, pass_)["variants"])
@@ -69,18 +70,19 @@ def test_autotuner_times_every_variant_and_keeps_the_fastest():
     H.fft_set_variant(N, -1)
     pos = S.lognormal_catalogue(50000, L, seed=3, n_grid=64)
     H.fft_set_variant(N, -1, H.PASS_WINDOW)
+    H.fft_set_variant(N, -1, H.PASS_CONTRACT)
     with H.Context(L, N, 4) as ctx:
         ctx.window_shells(np.linspace(10.0, 80.0, 9), l_max=0)
         ctx.assign(pos)
         first = ctx.xi()
-        for pass_ in (H.PASS_INV_Y, H.PASS_WINDOW):
+        for pass_ in (H.PASS_INV_Y, H.PASS_WINDOW, H.PASS_CONTRACT):
             info = H.fft_variants(N, pass_)
             assert info["forced"] == -1 and info["chosen"] >= 0
             ms = info["ms"]
             assert len(ms) == len(info["variants"]) and all(m > 0 for m in ms)
             assert info["chosen"] == int(np.argmin(ms))
         # later calls keep the choice without timing again
-        ms = [H.fft_variants(N, p)["ms"] for p in (0, 1)]
+        ms = [H.fft_variants(N, p)["ms"] for p in (0, 1, 2)]
         again = ctx.xi()
-        assert [H.fft_variants(N, p)["ms"] for p in (0, 1)] == ms
+        assert [H.fft_variants(N, p)["ms"] for p in (0, 1, 2)] == ms
     np.testing.assert_allclose(again, first, rtol=1e-5, atol=1e-8)
