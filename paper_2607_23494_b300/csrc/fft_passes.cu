@@ -983,7 +983,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //   pass 1: 0 the radix-8 window pass (k_inv_x_window, shared table when it fits),
 //           1 k_inv_x_window_pair (two windows in flight per thread);
 //   pass 2: 0 the radix-8 c2r + contraction pass (k_inv_z_c2r_contract),
-//           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks).
+//           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
+//   pass 3: the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e.
 // The first inverse call of a grid size that is not being captured into a graph
 // times every variant on that call's own buffers (the y pass before the window pass
 // writes the work buffer, the window pass and the last pass on the first catalogue)
@@ -1028,6 +1029,16 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 256: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
             case 512: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
             case 16: case 32: case 64: case 128: case 1024: return put({{0, 8, 1, 3}});
+        }
+    } else if (pass == 3) {
+        switch (N) {
+            case 16: return put({{0, 8, Cfg<16>::W, 0}});
+            case 32: return put({{0, 8, Cfg<32>::W, 0}});
+            case 64: return put({{0, 8, Cfg<64>::W, 0}});
+            case 128: return put({{0, 8, Cfg<128>::W, 0}});
+            case 256: return put({{0, 8, Cfg<256>::W, 0}, {1, 16, 8, 0}, {1, 32, 8, 0}});
+            case 512: return put({{0, 8, Cfg<512>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+            case 1024: return put({{0, 8, Cfg<1024>::W, 0}});
         }
     } else if (pass == 1) {
         switch (N) {
@@ -1178,6 +1189,35 @@ static cudaError_t launch_inv_z(int var, const float2* work, int S, const float*
     return cudaGetLastError();
 }
 
+// The inverse y transform of the zeta_l harmonic fields (pass 3): nf fields of N^3
+// complex values, [f][x][y][z]; tiles of W adjacent z columns at one (x, f).  Variant
+// 0 is the radix-8 strided pass (the tile of the zeta y pass: Cfg<N>::W columns).
+template <int N, int E, int W, int SH, int P>
+static cudaError_t run_zeta_y_e(float2* fields, int nf, const float2* tw, cudaStream_t st) {
+    constexpr int TS = (N / E) * W;
+    constexpr size_t smem = (size_t)SmemStridedSk<W, SH, P>::words(N) * sizeof(float2);
+    cudaError_t e;
+    if ((e = allow_smem(k_strided_e<N, E, W, SH, P>, smem)) != cudaSuccess) return e;
+    k_strided_e<N, E, W, SH, P><<<dim3(N / W, N, nf), TS, smem, st>>>(fields, N, N * N, (long long)N * N * N, tw);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t launch_zeta_y_var(int var, float2* fields, int nf, const float2* tw, cudaStream_t st) {
+    if constexpr (N == 256) {
+        if (var == 1) return run_zeta_y_e<256, 16, 8, 2, 2>(fields, nf, tw, st);
+        if (var == 2) return run_zeta_y_e<256, 32, 8, 2, 4>(fields, nf, tw, st);
+    } else if constexpr (N == 512) {
+        if (var == 1) return run_zeta_y_e<512, 32, 8, 2, 2>(fields, nf, tw, st);
+        if (var == 2) return run_zeta_y_e<512, 16, 8, 2, 1>(fields, nf, tw, st);
+    }
+    using C = Cfg<N>;
+    cudaError_t e;
+    if ((e = allow_smem(k_strided<N, true>, C::SMEM_STRIDED)) != cudaSuccess) return e;
+    k_strided<N, true><<<dim3(N / C::W, N, nf), C::TS, C::SMEM_STRIDED, st>>>(fields, N, (long long)N * N,
+                                                                            (long long)N * N * N, 0, tw);
+    return cudaGetLastError();
+}
+
 struct Tune {
     int forced = -1, chosen = -1;
     double ms[kMaxVariants];
@@ -1239,6 +1279,39 @@ static int pick_variant(int N, int pass, cudaStream_t st, F&& trial) {
     cudaEventDestroy(e1);
     en.chosen = best;
     return best;
+}
+
+template <int N>
+static int zeta_y_pick(float2* fields, int nf, const float2* tw, cudaStream_t st) {
+    // trials transform one field in place; the x pass rewrites every field afterwards
+    return pick_variant(N, 3, st, [&](int v) { return launch_zeta_y_var<N>(v, fields, std::min(nf, 1), tw, st); });
+}
+int zeta_y_variant(int N, float2* fields, int nf, const float2* tw, cudaStream_t st) {
+    if (nf < 1) return 0;
+#define F(n) zeta_y_pick<n>(fields, nf, tw, st)
+    switch (N) {
+        case 16: return F(16);
+        case 32: return F(32);
+        case 64: return F(64);
+        case 128: return F(128);
+        case 256: return F(256);
+        case 512: return F(512);
+        case 1024: return F(1024);
+    }
+#undef F
+    return 0;
+}
+cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st) {
+    switch (N) {
+        case 16: return launch_zeta_y_var<16>(var, fields, nf, tw, st);
+        case 32: return launch_zeta_y_var<32>(var, fields, nf, tw, st);
+        case 64: return launch_zeta_y_var<64>(var, fields, nf, tw, st);
+        case 128: return launch_zeta_y_var<128>(var, fields, nf, tw, st);
+        case 256: return launch_zeta_y_var<256>(var, fields, nf, tw, st);
+        case 512: return launch_zeta_y_var<512>(var, fields, nf, tw, st);
+        case 1024: return launch_zeta_y_var<1024>(var, fields, nf, tw, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced) {

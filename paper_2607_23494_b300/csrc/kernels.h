@@ -128,9 +128,14 @@ cudaError_t launch_xi_batch_finish(const double* dd, const double* sn, const dou
 cudaError_t launch_forward(int N, float* grid, float2* spec, const double* scal, const Tables& tb,
                            cudaStream_t st, const Tracer& tr, int ncat = 1);
 int inv_x_blocks(int N);
-// Variants of the inverse y pass and their autotuner (pass 0); -1 on a bad argument.
+// Variants of the tuned FFT passes and their autotuner; -1 on a bad argument.
 int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced);
 int fft_set_variant(int N, int pass, int variant);
+// The zeta_l y pass (pass 3): the variant for nf fields of N^3 (tuned on the first of
+// them, in place, when untuned and not capturing: call before the x pass writes them),
+// and its launch.
+int zeta_y_variant(int N, float2* fields, int nf, const float2* tw, cudaStream_t st);
+cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st);
 int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
 int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)
 // window multiply + inverse transforms + cell contraction of one window batch;

@@ -201,22 +201,8 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     }
 }
 
-// Z2: inverse y FFT of every bin field in place (full-length k_z columns, strided tiles).
-template <int N>
-__global__ void __launch_bounds__(ZCfg<N>::TS) k_zeta_y(float2* __restrict__ fields, const float2* __restrict__ tw) {
-    using C = ZCfg<N>;
-    constexpr int W = C::W, T = N / 8;
-    extern __shared__ float2 smem[];
-    const int col = threadIdx.x % W, t = threadIdx.x / W;
-    // block (kz chunk, x, bin); element (y) at stride N
-    float2* base = fields + (size_t)blockIdx.z * N * N * N + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * W + col;
-    float2 v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = base[(size_t)(t + i * T) * N];
-    fft_line<N, true>(v, t, tw, SmemStrided<W>{smem, col});
-#pragma unroll
-    for (int i = 0; i < 8; ++i) base[(size_t)(t + i * T) * N] = v[i];
-}
+// Z2: inverse y FFT of every bin field in place (full-length k_z columns, strided tiles):
+// launch_zeta_y in fft_passes.cu, whose variants the FFT autotuner picks (pass 3).
 
 // Z3 ------------------------------------------------------------------------
 // The 10 tiles (ti, tj), ti <= tj, of a symmetric 16x16 Gram in 4x4 tiles (tile = 4 ti + tj),
@@ -807,19 +793,19 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     const bool use_stab = stab_bytes <= 220 * 1024;
     if ((e = allow_smem_z(k_zeta_x<N, false>, C::SMEM_X)) != cudaSuccess) return e;
     if (use_stab && (e = allow_smem_z(k_zeta_x<N, true>, stab_bytes)) != cudaSuccess) return e;
-    if ((e = allow_smem_z(k_zeta_y<N>, C::SMEM_X)) != cudaSuccess) return e;
     // m = 0: real fields, two bins per transform (the opt-in tensor-core Gram takes them unpacked)
     HarmBatch hp = hb;
     hp.pack = (hb.m == 0 && hb.S > 1 && !zeta_tc_enabled(N)) ? 1 : 0;
     const int nf = hp.pack ? (hb.S + 1) / 2 : hb.S;  // complex fields transformed
+    // the y-pass variant (tuned on the first field before the x pass writes the fields)
+    const int yvar = zeta_y_variant(N, fields, nf, tb.tw, st);
     dim3 g1(N / C::W, N, 1);
     tr(K_ZETA_X, 0, st);
     if (use_stab) k_zeta_x<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, fields, hp, tb);
     else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hp, tb);
     tr(K_ZETA_X, 1, st);
-    dim3 g2(N / C::W, N, nf);
     tr(K_ZETA_Y, 0, st);
-    k_zeta_y<N><<<g2, C::TS, C::SMEM_X, st>>>(fields, tb.tw);
+    if ((e = launch_zeta_y(N, yvar, fields, nf, tb.tw, st)) != cudaSuccess) return e;
     tr(K_ZETA_Y, 1, st);
     if constexpr (N >= 32) {
         if (zeta_tc_enabled(N)) {

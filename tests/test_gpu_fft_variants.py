@@ -86,3 +86,27 @@ def test_autotuner_times_every_variant_and_keeps_the_fastest():
         again = ctx.xi()
         assert [H.fft_variants(N, p)["ms"] for p in (0, 1, 2)] == ms
     np.testing.assert_allclose(again, first, rtol=1e-5, atol=1e-8)
+
+
+def test_every_zeta_y_variant_matches():
+    # the zeta_l y pass: every variant gives the same multipoles (each within the stated bar
+    # of the radix-8 pass, which the oracle pins at small grids; the tuned variant is also
+    # checked against closed forms at 512^3 in the full-size tests)
+    H = _hermes()
+    N, L = 256, 500.0
+    nvar = len(H.fft_variants(N, H.PASS_ZETA_Y)["variants"])
+    assert nvar >= 2
+    pos = S.lognormal_catalogue(100000, L, seed=11, n_grid=64)
+    outs = []
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(np.linspace(10.0, 90.0, 7), l_max=2)
+            ctx.assign(pos)
+            for v in range(nvar):
+                H.fft_set_variant(N, v, H.PASS_ZETA_Y)
+                outs.append(ctx.zeta_multipoles())
+    finally:
+        H.fft_set_variant(N, -1, H.PASS_ZETA_Y)
+    for got in outs:
+        assert np.all(np.isfinite(got))
+        _close(got, outs[0])
