@@ -1049,11 +1049,14 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": "xi 512^3, 5 windows", "xi": [float(v) for v in x]}))
 
 
-def run_profile_zeta():
-    """Small zeta case for ncu captures: 256^3 field, 200k points, 16 shells, l_max = 1."""
+def run_profile_zeta(args):
+    """Small zeta case for ncu captures: 256^3 field, 200k points, 16 shells, l_max = 1.
+    --zy-variant fixes the zeta y-pass variant (no tuning trials)."""
     import torch
-    from paper_2607_23494_b300 import Context
+    from paper_2607_23494_b300 import Context, fft_set_variant
     from synthetic import catalogues as S
+    if args.zy_variant >= 0:
+        fft_set_variant(256, args.zy_variant, 3)
     pos = torch.from_numpy(S.poisson_uniform(200_000, L3, seed=8)).cuda()
     ctx = Context(L3, 256, 4)
     ctx.window_shells(np.linspace(10.0, 170.0, 17), l_max=1)
@@ -1085,14 +1088,22 @@ def main():
     ap.add_argument("--y-variant", type=int, default=0, help="inverse y-pass variant of --profile-case")
     ap.add_argument("--x-variant", type=int, default=0, help="window-pass variant of --profile-case")
     ap.add_argument("--z-variant", type=int, default=0, help="contraction-pass variant of --profile-case")
+    ap.add_argument("--zy-variant", type=int, default=-1, help="zeta y-pass variant of --profile-zeta")
+    ap.add_argument("--fft-variants", default="",
+                    help="Y,X,Z: fix the 512^3 inverse y, window and contraction pass variants instead of tuning "
+                         "(ncu distorts the tuner's trial timings, so launch lists run with the plain run's choice)")
     args = ap.parse_args()
     if args.minimal:
         args.no_plain = args.no_batch = args.no_serve = args.no_zeta = args.no_cpu_baseline = True
+    if args.fft_variants:
+        from paper_2607_23494_b300 import fft_set_variant
+        for pass_, v in zip((0, 1, 2), (int(x) for x in args.fft_variants.split(","))):
+            fft_set_variant(N2, v, pass_)
     if args.profile_case:
         run_profile_case(args)
         return 0
     if args.profile_zeta:
-        run_profile_zeta()
+        run_profile_zeta(args)
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
