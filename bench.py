@@ -824,7 +824,7 @@ def run_serve(args, dev, rank):
     pool_d = [torch.from_numpy(c).to(dev) for c in pool]
     pool_h = [torch.from_numpy(c).pin_memory().numpy() for c in pool]
     budget = 200 << 30
-    n_open, n_sat = args.serve_requests, max(args.serve_requests, 80)
+    n_open, n_sat = args.serve_requests, max(args.serve_requests, args.serve_saturated)
     # capacity of the one-at-a-time server on a calibration trace (back to back)
     cal = serve_trace(12, 0.0, len(pool), seed=99)
     run_serve_trace(H, pool_d, pool_h, cal[:3], 1, budget)  # warm-up (tables, allocator)
@@ -1077,7 +1077,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain torch/cuFFT comparison arm")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-catalogue measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-requests", type=int, default=60, help="requests in the serving trace")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests in the open-loop serving trace")
+    ap.add_argument("--serve-saturated", type=int, default=80,
+                    help="requests in the saturated mixed serving trace (twice as many in the small-grid one)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--minimal", action="store_true",
