@@ -148,6 +148,12 @@ struct SmemZLine : SmemLine<M> {
         else asm volatile("bar.sync %0, %1;\n" ::"r"(1 + group), "n"(M / 8) : "memory");
     }
 };
+// The padded line of SmemLine for a line whose threads all belong to one warp (any
+// length; the caller guarantees it): its exchanges only synchronise the warp.
+template <int M>
+struct SmemWarpLine : SmemLine<M> {
+    __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
 template <int M>
 struct LinePad {
     static constexpr int value = M + (M >> line_shift(M)) + 1;

@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line0 = (size_t)blockIdx.x * LZ;
     const size_t line = line0 + li;
-    const SmemZLine<M> sm{{lines + li * LP}, li};  // T <= 32: __syncwarp
+    const SmemWarpLine<M> sm{{lines + li * LP}};  // the T <= 32 threads of a line share a warp
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         work += cat * S * N * N * H;
@@ -1178,7 +1178,7 @@ static cudaError_t run_z_e16(const float2* work, int S, const float* delta, cons
 template <int N>
 static cudaError_t launch_inv_z(int var, const float2* work, int S, const float* delta, const float2* tw,
                                 double* dd_part, unsigned* err, int ncat, cudaStream_t st) {
-    if constexpr (N == 256 || N == 512) {
+    if constexpr (N == 256 || N == 512) {  // at 1024^3 (512-point lines) radix 8 measured as fast
         if (var == 1) return run_z_e16<N, 128, 4>(work, S, delta, tw, dd_part, err, ncat, st);
         if (var == 2) return run_z_e16<N, 128, 3>(work, S, delta, tw, dd_part, err, ncat, st);
         if (var == 3) return run_z_e16<N, 128, 2>(work, S, delta, tw, dd_part, err, ncat, st);

@@ -353,18 +353,31 @@ def test_inverse_passes_at_1024_match_kspace_route():
     # span two warps (one named barrier per line).  The real-space xi_l must equal the
     # Parseval route, which reads only delta^ and the radial tables (that route is
     # pinned to the oracle at small grids above).
+    # Every variant of the inverse y pass (radix 8, 32 and 16 values per thread) and of the
+    # contraction pass (radix 8, 16 values per thread) at 1024^3.
     H = _hermes()
     N, p, L = 1024, 4, 2000.0
     pos = S.lognormal_catalogue(200000, L, seed=1024, n_grid=64)
     mass = S.lognormal_masses(pos.shape[0], seed=1025)
     edges = np.linspace(L / 200, L / 20, 7)
-    with H.Context(L, N, p) as ctx:
-        ctx.window_shells(edges, l_max=2)
-        ctx.assign(pos, mass)
-        ks = ctx.xi_multipoles_kspace((0, 2))
-        real = ctx.xi_multipoles((0, 2))
-    assert np.all(np.isfinite(real)) and real.shape == (2, 6)
-    _close(real, ks)
+    reals = []
+    try:
+        with H.Context(L, N, p) as ctx:
+            ctx.window_shells(edges, l_max=2)
+            ctx.assign(pos, mass)
+            ks = ctx.xi_multipoles_kspace((0, 2))
+            for pass_ in (H.PASS_INV_Y, H.PASS_CONTRACT):
+                for v in range(len(H.fft_variants(N, pass_)["variants"])):
+                    H.fft_set_variant(N, v, pass_)
+                    reals.append(ctx.xi_multipoles((0, 2)))
+                H.fft_set_variant(N, 0, pass_)
+    finally:
+        H.fft_set_variant(N, -1, H.PASS_INV_Y)
+        H.fft_set_variant(N, -1, H.PASS_CONTRACT)
+    assert len(reals) >= 2
+    for real in reals:
+        assert np.all(np.isfinite(real)) and real.shape == (2, 6)
+        _close(real, ks)
 
 
 def test_kspace_route_planted_mode_and_errors():

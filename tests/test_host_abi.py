@@ -141,7 +141,7 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
     # the contraction pass: radix 8 everywhere, 16 values per thread at 256^3 and 512^3;
     # the zeta_l y pass: radix 8 everywhere, 16 or 32 values per thread at 256^3 and 512^3
     for pass_, N, n in ((1, 64, 1), (1, 256, 2), (1, 512, 2), (2, 64, 1), (2, 256, 4), (2, 512, 4), (3, 64, 1),
-                        (3, 256, 3), (3, 512, 3)):
+                        (3, 256, 3), (3, 512, 3), (2, 1024, 1)):
         info = H.fft_variants(N, pass_)
         assert len(info["variants"]) == n
         assert [v[0] for v in info["variants"]] == [0] + [1] * (n - 1)
