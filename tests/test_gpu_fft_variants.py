@@ -110,3 +110,37 @@ def test_every_zeta_y_variant_matches():
     for got in outs:
         assert np.all(np.isfinite(got))
         _close(got, outs[0])
+
+
+def test_window_pass_variants_with_cylinder_and_ring_windows():
+    # the window pass's cylindrical mode (one line-of-sight bin per batch) and ring mode (a
+    # line-of-sight row per window) through every window-pass variant at 256^3, against the
+    # Parseval route (which reads only delta^ and the window tables)
+    H = _hermes()
+    N, L = 256, 600.0
+    pos = S.lognormal_catalogue(150000, L, seed=21, n_grid=64)
+    mass = S.lognormal_masses(pos.shape[0], seed=22)
+    s = np.linspace(8.0, 60.0, 6)
+    mu = np.linspace(0.05, 0.95, 7)
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.assign(pos, mass)
+            ctx.window_cylinders(np.linspace(0.0, 50.0, 6), np.linspace(0.0, 40.0, 5), sigma_perp=2.0)
+            cyl_ks = ctx.xi_cylinders(kspace=True)
+            cyls = []
+            for v in range(len(H.fft_variants(N, H.PASS_WINDOW)["variants"])):
+                H.fft_set_variant(N, v, H.PASS_WINDOW)
+                cyls.append(ctx.xi_cylinders())
+            ctx.window_s_mu(s, mu, ds=4.0, dmu=0.1)
+            ring_ks = ctx.xi_rings(kspace=True)
+            rings = []
+            for v in range(len(H.fft_variants(N, H.PASS_WINDOW)["variants"])):
+                H.fft_set_variant(N, v, H.PASS_WINDOW)
+                rings.append(ctx.xi_rings())
+    finally:
+        H.fft_set_variant(N, -1, H.PASS_WINDOW)
+    assert len(cyls) >= 2 and len(rings) >= 2
+    for got in cyls:
+        _close(got, cyl_ks)
+    for got in rings:
+        _close(got, ring_ks)
