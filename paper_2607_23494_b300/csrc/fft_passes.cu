@@ -614,13 +614,36 @@ __global__ void __launch_bounds__(Cfg<N>::ZTHREADS, 3) k_inv_z_c2r_contract(cons
 // of that kernel writes its sum into the first of their partial slots and 0 into
 // the others, so the partials keep the layout of the radix-8 form.  The stage
 // twiddles and the c2r split twiddles are held in registers.
+// Shared-memory pitches of the 16-value contraction pass: SP float2 per staged line (N/2:
+// dense, one bulk copy per window; more: one copy per line) and the exchange lines (one pad
+// slot every 2^SH elements, LP float2 per line).  At 256^3 four 128-point lines share a warp:
+// the dense stage and one pad per 16 put the two lines of a half warp on the same banks,
+// and these pitches reach the minimum wavefronts (bank simulation of every access).
+template <int N>
+struct Z16Pitch {
+    static constexpr int SP = N / 2, SH = line_shift(N / 2), LP = LinePad<N / 2>::value;
+};
+template <>
+struct Z16Pitch<256> {
+    static constexpr int SP = 136, SH = 3, LP = 152;
+};
+template <int SH>
+struct SmemWarpLineSh {  // a padded line whose threads all belong to one warp
+    float2* p;
+    __device__ __forceinline__ static int at(int pos) { return pos + (pos >> SH); }
+    __device__ __forceinline__ float2 ld(int pos) const { return p[at(pos)]; }
+    __device__ __forceinline__ void st(int pos, float2 v) const { p[at(pos)] = v; }
+    __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
+
 template <int N, int THREADS>
 struct Z16Cfg {
     static constexpr int M = N / 2, E = 16, T = M / E, LZ = THREADS / T;
+    static constexpr int SP = Z16Pitch<N>::SP, SH = Z16Pitch<N>::SH, LP = Z16Pitch<N>::LP;
+    static_assert(((M - 1) + ((M - 1) >> SH)) < LP && SP >= M && (SP * 8) % 16 == 0, "line pitches");
     static constexpr int SLOTS = LZ / Cfg<N>::LZ;  // partial slots of the radix-8 layout per block
     static_assert(SLOTS >= 1 && SLOTS * Cfg<N>::LZ == LZ, "blocks cover whole radix-8 blocks");
-    static constexpr size_t SMEM = (size_t)2 * LZ * (N / 2) * sizeof(float2) +
-                                   (size_t)LZ * LinePad<M>::value * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)2 * LZ * SP * sizeof(float2) + (size_t)LZ * LP * sizeof(float2);
 };
 
 template <int N, int THREADS, int MINB>
@@ -630,21 +653,34 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
                                                                        double* __restrict__ dd_part,
                                                                        unsigned* __restrict__ err) {
     using C = Z16Cfg<N, THREADS>;
-    constexpr int M = C::M, E = C::E, T = C::T, LZ = C::LZ, LP = LinePad<M>::value, H = N / 2;
+    constexpr int M = C::M, E = C::E, T = C::T, LZ = C::LZ, LP = C::LP, SP = C::SP, H = N / 2;
     constexpr int SLOTS = C::SLOTS;
     static_assert(T <= 32 && 32 % T == 0, "lines within a warp");
     constexpr int NW = THREADS / 32;
-    constexpr uint32_t STAGE = (uint32_t)(LZ * H * sizeof(float2));
+    constexpr uint32_t STAGE = (uint32_t)(LZ * H * sizeof(float2));  // bytes per window
     extern __shared__ __align__(16) float2 smem[];
     float2* stage = smem;
-    float2* lines = smem + 2 * LZ * H;
+    float2* lines = smem + 2 * LZ * SP;
     __shared__ __align__(8) uint64_t full[2];
     __shared__ float wdd[NW][MAX_BATCH];
     const int t = threadIdx.x % T, li = threadIdx.x / T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t line0 = (size_t)blockIdx.x * LZ;
     const size_t line = line0 + li;
-    const SmemWarpLine<M> sm{{lines + li * LP}};  // the T <= 32 threads of a line share a warp
+    const SmemWarpLineSh<C::SH> sm{lines + li * LP};  // the T <= 32 threads of a line share a warp
+    // window w's LZ lines into stage buffer b: one bulk copy (dense) or one per line (pitch SP)
+    auto fetch = [&](int w, int b) {
+        const float2* src = work + (size_t)w * N * N * H + line0 * H;
+        float2* dst = stage + b * LZ * SP;
+        ac::mbar_expect_tx(&full[b], STAGE);
+        if constexpr (SP == H) {
+            ac::bulk_g2s(dst, src, STAGE, &full[b]);
+        } else {
+#pragma unroll 1
+            for (int l = 0; l < LZ; ++l)
+                ac::bulk_g2s(dst + l * SP, src + (size_t)l * H, (uint32_t)(H * sizeof(float2)), &full[b]);
+        }
+    };
     {  // batched launch: blockIdx.y = catalogue
         const size_t cat = blockIdx.y;
         work += cat * S * N * N * H;
@@ -657,10 +693,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
         ac::mbar_init_fence();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && S > 0) {
-        ac::mbar_expect_tx(&full[0], STAGE);
-        ac::bulk_g2s(stage, work + line0 * H, STAGE, &full[0]);
-    }
+    if (threadIdx.x == 0 && S > 0) fetch(0, 0);
     const float2* dl = reinterpret_cast<const float2*>(delta + line * N);
     float2 d2[E];
 #pragma unroll
@@ -675,12 +708,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
         __syncthreads();  // every thread is done with the buffer that the next copy overwrites
         if (threadIdx.x == 0 && s + 1 < S) {
             ac::fence_proxy_async();
-            ac::mbar_expect_tx(&full[(s + 1) & 1], STAGE);
-            ac::bulk_g2s(stage + ((s + 1) & 1) * LZ * H, work + (size_t)(s + 1) * N * N * H + line0 * H, STAGE,
-                         &full[(s + 1) & 1]);
+            fetch(s + 1, (s + 1) & 1);
         }
         if (!ac::mbar_wait(&full[s & 1], (s >> 1) & 1)) late = true;
-        const float2* X = stage + (s & 1) * LZ * H + li * H;
+        const float2* X = stage + (s & 1) * LZ * SP + li * SP;
         float2 v[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
