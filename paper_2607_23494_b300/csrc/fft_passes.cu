@@ -510,6 +510,108 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float
     }
 }
 
+// The window pass on mirror lines: the x lines at k_y and N - k_y (same n_y^2, same
+// Phi^(k_y)) see the same radial factor at every element, so a block transforms both for
+// its W columns, their FFTs exchanging through two tiles behind the same barriers, and one
+// table read serves the two lines (the table as in k_inv_x_window_pair).  Blocks at
+// k_y = 0 and N/2 (their own mirrors) transform one line set.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const float2* __restrict__ spec,
+                                                                     float2* __restrict__ work, const WinBatch wb,
+                                                                     const Tables tb) {
+    using C = Cfg<N>;
+    constexpr int W = C::W, T = N / 8, H = N / 2;
+    constexpr int TILE = SmemStrided<W>::words(N);
+    extern __shared__ __align__(16) float2 smem[];
+    float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
+    const int RS = pair_row_floats(wb.S);
+    const int rsh = RS == 16 ? 1 : 2, cmask = RS / 4 - 1;
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    const int ky = blockIdx.y, kyb = (N - ky) & (N - 1), kz = blockIdx.x * W + col;  // blockIdx.y in [0, H]
+    const bool two = (ky != 0 && ky != H);
+    const size_t xstride = (size_t)N * H;
+    {  // batched launch: blockIdx.z = catalogue
+        const size_t cat = blockIdx.z;
+        spec += cat * N * N * H;
+        work += cat * wb.S * N * N * H;
+    }
+    const int ny = signed_freq(ky, N), nz = kz;
+    const bool nyq_y = (ky == H);
+    {
+        const int S4 = (wb.S + 3) >> 2;
+        const int total = H * W * S4;
+        const int ny2 = nyq_y ? 0 : ny * ny;
+        for (int e = threadIdx.x; e < total; e += C::TS) {
+            const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
+            const int nzc = blockIdx.x * W + c;
+            const int qq = nyq_y ? 0 : a * a + ny2 + (wb.cyl ? 0 : nzc * nzc);
+            const int row = a * W + c;
+            ac::cp_async16(ttab + row * RS + 4 * (s4 ^ ((row >> rsh) & cmask)),
+                           reinterpret_cast<const float4*>(wb.tab + (size_t)qq * wb.nbp) + s4);
+        }
+        ac::cp_async_commit();
+    }
+    const float2* srca = spec + (size_t)ky * H + kz;
+    const float2* srcb = spec + (size_t)kyb * H + kz;
+    float2 va0[8], vb0[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        va0[i] = srca[(size_t)(t + i * T) * xstride];
+        vb0[i] = two ? srcb[(size_t)(t + i * T) * xstride] : make_float2(0.f, 0.f);
+    }
+    const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);  // Phi^(N - k_y) = Phi^(k_y)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int kx = t + i * T;
+        const int nx = signed_freq(kx, N);
+        const bool nyq = nyq_y || (kx == H);
+        const int qi = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+        const float ph = nyq ? 0.0f : __ldg(tb.phi + kx) * phyz;
+        const float a = wb.cyl ? (wb.par_stride ? 1.0f : __ldg(wb.par + nz))
+                               : wb.scale * legendre(wb.ell, qi > 0 ? (float)nz * rsqrtf((float)qi) : 0.0f);
+        va0[i] = cscale(va0[i], ph * a);
+        vb0[i] = cscale(vb0[i], ph * a);
+    }
+    auto trow = [&](int i) {
+        const int ax = i < 4 ? t + i * T : ((t == 0 && i == 4) ? 0 : N - t - i * T);
+        return ax * W + col;
+    };
+    ac::cp_async_wait_all();
+    __syncthreads();
+    float2 wc[3 * twiddled_stages<N>()];
+    load_stage_twiddles<N, true>(t, tb.tw, wc);
+    const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
+    for (int g = 0; g < wb.S; g += 4) {
+        float4 tv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = trow(i);
+            tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int s = g + j;
+            if (s >= wb.S) break;  // uniform across the block
+            const float pz = wb.par_stride ? __ldg(wb.par + (size_t)s * wb.par_stride + nz) : 1.0f;
+            float2 v[2][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float f = pz * (j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
+                v[0][i] = cscale(va0[i], f);
+                v[1][i] = cscale(vb0[i], f);
+            }
+            fft_lines_wc<N, true, 2>(v, t, sms, wc);
+            float2* dst = work + (size_t)s * N * N * H + (size_t)kz;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)ky * H] = v[0][i];
+            if (two) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)kyb * H] = v[1][i];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // I3: complex-to-real along z fused with the cell contraction.
 // Z'_k = (X_k + conj X_{M-k}) + i e^{+2 pi i k/N} (X_k - conj X_{M-k}), X_M = 0;
@@ -1012,7 +1114,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //   pass 0: 0 the radix-8 pass (k_strided_pf up to 512^3, k_strided above),
 //           1 k_strided_e (one tile per block), 2 k_strided_pf_e (persistent);
 //   pass 1: 0 the radix-8 window pass (k_inv_x_window, shared table when it fits),
-//           1 k_inv_x_window_pair (two windows in flight per thread);
+//           1 k_inv_x_window_pair (two windows in flight per thread),
+//           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read each);
 //   pass 2: 0 the radix-8 c2r + contraction pass (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
 //   pass 3: the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e.
@@ -1077,8 +1180,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 32: return put({{0, 8, Cfg<32>::W, 1}});
             case 64: return put({{0, 8, Cfg<64>::W, 1}});
             case 128: return put({{0, 8, Cfg<128>::W, 1}});
-            case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}});
-            case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}});
+            case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     }
@@ -1180,15 +1283,23 @@ static cudaError_t run_x_pair(const float2* spec, float2* work, const WinBatch& 
     return cudaGetLastError();
 }
 template <int N>
+static cudaError_t run_x_mirror(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
+                                cudaStream_t st) {
+    using C = Cfg<N>;
+    const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
+    if (wb.S > 16 || bytes > kMaxDynSmem) return run_x_r8<N>(spec, work, wb, tb, ncat, st);
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_x_window_mirror<N>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_mirror<N><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
+    return cudaGetLastError();
+}
+template <int N>
 static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const WinBatch& wb, const Tables& tb,
                                 int ncat, cudaStream_t st) {
-    if constexpr (N == 256) {
+    if constexpr (N == 256 || N == 512) {
         switch (var) {
-            case 1: return run_x_pair<256>(spec, work, wb, tb, ncat, st);
-        }
-    } else if constexpr (N == 512) {
-        switch (var) {
-            case 1: return run_x_pair<512>(spec, work, wb, tb, ncat, st);
+            case 1: return run_x_pair<N>(spec, work, wb, tb, ncat, st);
+            case 2: return run_x_mirror<N>(spec, work, wb, tb, ncat, st);
         }
     }
     return run_x_r8<N>(spec, work, wb, tb, ncat, st);

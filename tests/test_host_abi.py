@@ -137,21 +137,22 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
         assert (kind, E) == (0, 8)
         for kind, E, W, minb in info["variants"]:
             assert kind in (0, 1, 2) and E in (8, 16, 32) and W >= 1 and N % E == 0
-    # the window pass: one window at a time everywhere, two in flight at 256^3 and 512^3;
+    # the window pass: one window at a time everywhere; two windows in flight, or the k_y and
+    # N - k_y lines together, at 256^3 and 512^3;
     # the contraction pass: radix 8 everywhere, 16 values per thread at 256^3 and 512^3;
     # the zeta_l y pass: radix 8 everywhere, 16 or 32 values per thread at 256^3 and 512^3
-    for pass_, N, n in ((1, 64, 1), (1, 256, 2), (1, 512, 2), (2, 64, 1), (2, 256, 4), (2, 512, 4), (3, 64, 1),
-                        (3, 256, 3), (3, 512, 3), (2, 1024, 1)):
+    for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2]), (1, 512, [0, 1, 2]), (2, 64, [0]),
+                            (2, 256, [0, 1, 1, 1]), (2, 512, [0, 1, 1, 1]), (2, 1024, [0]), (3, 64, [0]),
+                            (3, 256, [0, 1, 1]), (3, 512, [0, 1, 1])):
         info = H.fft_variants(N, pass_)
-        assert len(info["variants"]) == n
-        assert [v[0] for v in info["variants"]] == [0] + [1] * (n - 1)
+        assert [v[0] for v in info["variants"]] == kinds
     n512 = len(H.fft_variants(512)["variants"])
     H.fft_set_variant(512, 1)
     assert H.fft_variants(512)["forced"] == 1
     H.fft_set_variant(512, -1)
     info = H.fft_variants(512)
     assert info["forced"] == -1 and info["chosen"] == -1 and all(m == -1.0 for m in info["ms"])
-    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 4), (512, 2, 1), (512, 4, 2), (512, 3, 3)):
+    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 4), (512, 3, 1), (512, 4, 2), (512, 3, 3)):
         with pytest.raises(H.HermesError) as ei:
             H.fft_set_variant(bad[0], bad[1], pass_=bad[2])
         assert ei.value.code == H.ERR_ARG
