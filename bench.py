@@ -206,6 +206,7 @@ def error_vs_oracle(res, pos, mass, zeta128) -> dict:
 NCU_TRAFFIC_512 = {
     "inv_x_window/k0e8w8": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
     "inv_x_window/k1e8w8": {"per_launch": 0.561371e9, "per_window": 2.634040e9 / 5},
+    "inv_x_window/k2e8w8": {"per_launch": 0.576038e9, "per_window": 2.796381e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
     "inv_z_c2r_contract/k0e8w1": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
