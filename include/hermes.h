@@ -444,12 +444,16 @@ int hermes_release_buffers(hermes_ctx *ctx);
  * transform along y of every filtered window; HERMES_PASS_CONTRACT, the last
  * (complex-to-real along z fused with the cell contraction); and
  * HERMES_PASS_ZETA_Y, the inverse transform along y of the zeta_l harmonic fields
- * (tuned on the first field of the first zeta_l call, before the x pass writes it).
+ * (tuned on the first field of the first zeta_l call, before the x pass writes it);
+ * HERMES_PASS_ZETA_X / HERMES_PASS_ZETA_X_M0, the first zeta_l pass (along x, the Y_lm
+ * window multiply fused in) for complex fields / for the packed real m = 0 fields.
  * A variant fixes
  *   kind: inverse y: 0 the radix-8 pass, 1 one tile per block, 2 persistent blocks;
- *         window:    0 one window at a time, 1 two windows in flight per thread;
+ *         window:    0 one window at a time, 1 two windows in flight per thread, 2 the
+ *                    k_y and N - k_y lines together;
  *         contract:  0 the radix-8 pass, 1 16 values per thread;
  *         zeta y:    0 the radix-8 pass, 1 one tile per block;
+ *         zeta x:    0 one line set at a time, 2 the k_y and N - k_y lines together;
  *   E:    values per thread (8: radix-8 stages; 16, 32: radix-16 or radix-32
  *         stages, fewer shared-memory exchanges per line for more registers);
  *   W:    tile width, the adjacent k_z columns one block transforms together
@@ -474,6 +478,8 @@ int hermes_release_buffers(hermes_ctx *ctx);
 #define HERMES_PASS_WINDOW 1
 #define HERMES_PASS_CONTRACT 2
 #define HERMES_PASS_ZETA_Y 3
+#define HERMES_PASS_ZETA_X 4
+#define HERMES_PASS_ZETA_X_M0 5
 int hermes_fft_set_variant(int N, int pass, int variant);
 int hermes_fft_variants(int N, int pass, int *desc, double *ms, int cap, int *chosen, int *forced);
 

@@ -1118,7 +1118,9 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read each);
 //   pass 2: 0 the radix-8 c2r + contraction pass (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
-//   pass 3: the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e.
+//   pass 3: the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e;
+//   passes 4, 5: the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at a time
+//           (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror).
 // The first inverse call of a grid size that is not being captured into a graph
 // times every variant on that call's own buffers (the y pass before the window pass
 // writes the work buffer, the window pass and the last pass on the first catalogue)
@@ -1163,6 +1165,16 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 256: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
             case 512: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
             case 16: case 32: case 64: case 128: case 1024: return put({{0, 8, 1, 3}});
+        }
+    } else if (pass == 4 || pass == 5) {  // the zeta_l x pass: complex fields / packed m = 0 fields
+        switch (N) {
+            case 16: return put({{0, 8, Cfg<16>::W, 1}});
+            case 32: return put({{0, 8, Cfg<32>::W, 1}});
+            case 64: return put({{0, 8, Cfg<64>::W, 1}});
+            case 128: return put({{0, 8, Cfg<128>::W, 1}});
+            case 256: return put({{0, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}});
+            case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     } else if (pass == 3) {
         switch (N) {
@@ -1454,6 +1466,10 @@ cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* 
         case 1024: return launch_zeta_y_var<1024>(var, fields, nf, tw, st);
     }
     return cudaErrorInvalidValue;
+}
+
+int tuned_variant(int N, int pass, cudaStream_t st, cudaError_t (*trial)(int v, void* arg), void* arg) {
+    return pick_variant(N, pass, st, [&](int v) { return trial(v, arg); });
 }
 
 int fft_variants(int N, int pass, int* desc, double* ms, int cap, int* chosen, int* forced) {

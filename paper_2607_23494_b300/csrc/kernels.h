@@ -135,6 +135,10 @@ int fft_set_variant(int N, int pass, int variant);
 // them, in place, when untuned and not capturing: call before the x pass writes them),
 // and its launch.
 int zeta_y_variant(int N, float2* fields, int nf, const float2* tw, cudaStream_t st);
+// The tuned variant of (N, pass): the fixed or tuned one, else (timing trial(v, arg), one
+// launch of variant v, for every variant when st is not capturing) the fastest; 0 while
+// capturing before any tuning.
+int tuned_variant(int N, int pass, cudaStream_t st, cudaError_t (*trial)(int v, void* arg), void* arg);
 cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st);
 int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
 int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)

@@ -201,6 +201,116 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
     }
 }
 
+// Z1 on mirror lines: the x lines at k_y and N - k_y see the same radial factor at every
+// element (the same n_y^2), so a block transforms both for its W columns, their FFTs
+// exchanging through two tiles behind the same barriers, and one table read serves the two
+// lines.  Their angular factors are conjugate: Y_lm(n_x, -n_y, n_z) = conj Y_lm(n_x, n_y, n_z)
+// (only the azimuth changes sign), so Y_lm is evaluated once per element.  The radial table
+// is staged without padding: the 16-byte chunk j of row r sits at chunk
+// j ^ ((r >> rsh) & (RS / 4 - 1)), RS = 4, 8 or 16 floats, so a quarter warp's 16-byte reads
+// meet 8 distinct bank groups.  Blocks at k_y = 0 and N/2 (their own mirrors) transform one
+// line set.
+__host__ __device__ constexpr int zmirror_row_floats(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }
+
+template <int N>
+__global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* __restrict__ spec,
+                                                                float2* __restrict__ fields, const HarmBatch hb,
+                                                                const Tables tb) {
+    using C = ZCfg<N>;
+    constexpr int W = C::W, T = N / 8, H = N / 2;
+    constexpr int TILE = SmemStrided<W>::words(N);
+    extern __shared__ __align__(16) float2 smem[];
+    float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
+    const int RS = zmirror_row_floats(hb.S);
+    const int rsh = RS == 16 ? 1 : 2, cmask = RS / 4 - 1;
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    const int ky = blockIdx.y, kyb = (N - ky) & (N - 1), kz = blockIdx.x * W + col;  // blockIdx.y in [0, H]
+    const bool two = (ky != 0 && ky != H);
+    const int ny = signed_freq(ky, N), nz = signed_freq(kz, N);
+    const size_t xs = (size_t)N * H;
+    const size_t n3 = (size_t)N * N * N;
+    {
+        const int S4 = (hb.S + 3) >> 2;
+        const int total = H * W * S4;
+        for (int e = threadIdx.x; e < total; e += C::TS) {
+            const int s4 = e % S4, c = (e / S4) % W, a = e / (S4 * W);
+            const int kzc = blockIdx.x * W + c, nzc = signed_freq(kzc, N);
+            const int qq = (ky == H || kzc == H) ? 0 : a * a + ny * ny + nzc * nzc;
+            const float* src = (hb.tab2 && s4 >= 2) ? hb.tab2 + (size_t)qq * hb.nbp + 4 * (s4 - 2)
+                                                     : hb.tab + (size_t)qq * hb.nbp + 4 * s4;
+            const int row = a * W + c;
+            ac::cp_async16(ttab + row * RS + 4 * (s4 ^ ((row >> rsh) & cmask)), src);
+        }
+        ac::cp_async_commit();
+    }
+    const float phyz = __ldg(tb.phi + ky) * __ldg(tb.phi + kz);  // Phi^(N - k_y) = Phi^(k_y)
+    // delta^ along the x line at (k_y', k_z), with the Hermitian expansion for k_z > N/2
+    auto load = [&](int kyl, int kx) {
+        if (kz < H) return spec[(size_t)kx * xs + (size_t)kyl * H + kz];
+        if (kz > H)
+            return cconj(spec[(size_t)((N - kx) & (N - 1)) * xs + (size_t)((N - kyl) & (N - 1)) * H + (N - kz)]);
+        return make_float2(0.f, 0.f);
+    };
+    float2 va0[8], vb0[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int kx = t + i * T;
+        const int nx = signed_freq(kx, N);
+        const bool nyq = (kx == H) || (ky == H) || (kz == H);
+        const int qq = nx * nx + ny * ny + nz * nz;
+        const float w = hb.ylm_norm * __ldg(tb.phi + kx) * phyz;
+        const float2 y = cscale(ylm_unnorm(hb.ell, hb.m, nx, ny, nz, qq), w);
+        va0[i] = nyq ? make_float2(0.f, 0.f) : cmul(load(ky, kx), mul_ipow(y, hb.ell));
+        vb0[i] = (nyq || !two) ? make_float2(0.f, 0.f) : cmul(load(kyb, kx), mul_ipow(cconj(y), hb.ell));
+    }
+    auto trow = [&](int i) {  // |n_x| = t + iT (i < 4) or N - t - iT (the Nyquist element reads row 0)
+        const int ax = i < 4 ? t + i * T : ((t == 0 && i == 4) ? 0 : N - t - i * T);
+        return ax * W + col;
+    };
+    ac::cp_async_wait_all();
+    __syncthreads();
+    float2 wc[3 * twiddled_stages<N>()];
+    load_stage_twiddles<N, true>(t, tb.tw, wc);
+    const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
+    const int nf = (hb.S + 1) >> 1;  // packed fields (m = 0)
+    const int nout = hb.pack ? nf : hb.S;
+    for (int g = 0; g < hb.S; g += 4) {
+        float4 tv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = trow(i);
+            tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+        }
+        // packed: fields g/2 and g/2 + 1 (bins (2f, 2f + 1) as real and imaginary parts); else bins g..g+3
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = hb.pack ? (g >> 1) + j : g + j;
+            if ((hb.pack && j >= 2) || f >= nout) break;  // uniform across the block
+            float2 v[2][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (hb.pack) {
+                    const float2 k2 = j == 0 ? make_float2(tv[i].x, tv[i].y) : make_float2(tv[i].z, tv[i].w);
+                    v[0][i] = cmul(va0[i], k2);
+                    v[1][i] = cmul(vb0[i], k2);
+                } else {
+                    const float k1 = j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w));
+                    v[0][i] = cscale(va0[i], k1);
+                    v[1][i] = cscale(vb0[i], k1);
+                }
+            }
+            fft_lines_wc<N, true, 2>(v, t, sms, wc);
+            float2* dst = fields + (size_t)f * n3 + (size_t)kz;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)ky * N] = v[0][i];
+            if (two) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)kyb * N] = v[1][i];
+            }
+        }
+    }
+}
+
 // Z2: inverse y FFT of every bin field in place (full-length k_z columns, strided tiles):
 // launch_zeta_y in fft_passes.cu, whose variants the FFT autotuner picks (pass 3).
 
@@ -784,6 +894,40 @@ int zeta_z_blocks(int N) {
     return 0;
 }
 
+// The x pass of one (l, m) batch: variant 0 one line set at a time (shared table when it
+// fits, gathered factors otherwise), variant 1 the mirror lines together (256^3 and 512^3,
+// when the unpadded table and two tiles fit).
+struct ZetaXArgs {
+    const float2* spec;
+    float2* fields;
+    const HarmBatch* hb;
+    const Tables* tb;
+    bool use_stab;
+    size_t stab_bytes;
+    cudaStream_t st;
+};
+template <int N>
+static cudaError_t launch_zeta_x(int var, const ZetaXArgs& a) {
+    using C = ZCfg<N>;
+    cudaError_t e;
+    if constexpr (N == 256 || N == 512) {
+        const size_t bytes = 2 * C::SMEM_X + (size_t)(N / 2) * C::W * zmirror_row_floats(a.hb->S) * sizeof(float);
+        if (var == 1 && bytes <= 220 * 1024) {
+            if ((e = allow_smem_z(k_zeta_x_mirror<N>, bytes)) != cudaSuccess) return e;
+            k_zeta_x_mirror<N><<<dim3(N / C::W, N / 2 + 1, 1), C::TS, bytes, a.st>>>(a.spec, a.fields, *a.hb, *a.tb);
+            return cudaGetLastError();
+        }
+    }
+    const dim3 g1(N / C::W, N, 1);
+    if (a.use_stab) k_zeta_x<N, true><<<g1, C::TS, a.stab_bytes, a.st>>>(a.spec, a.fields, *a.hb, *a.tb);
+    else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, a.st>>>(a.spec, a.fields, *a.hb, *a.tb);
+    return cudaGetLastError();
+}
+template <int N>
+static cudaError_t zeta_x_trial(int v, void* arg) {
+    return launch_zeta_x<N>(v, *static_cast<const ZetaXArgs*>(arg));
+}
+
 template <int N>
 static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* delta, const HarmBatch& hb,
                              const Tables& tb, double* gram_part, unsigned* err, cudaStream_t st, const Tracer& tr) {
@@ -799,10 +943,12 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     const int nf = hp.pack ? (hb.S + 1) / 2 : hb.S;  // complex fields transformed
     // the y-pass variant (tuned on the first field before the x pass writes the fields)
     const int yvar = zeta_y_variant(N, fields, nf, tb.tw, st);
-    dim3 g1(N / C::W, N, 1);
+    // the x-pass variant, tuned per packing on the first zeta call that uses it (its trials
+    // write the fields, which the real launch overwrites)
+    const ZetaXArgs xa{spec, fields, &hp, &tb, use_stab, stab_bytes, st};
+    const int xv = tuned_variant(N, hp.pack ? 5 : 4, st, zeta_x_trial<N>, const_cast<ZetaXArgs*>(&xa));
     tr(K_ZETA_X, 0, st);
-    if (use_stab) k_zeta_x<N, true><<<g1, C::TS, stab_bytes, st>>>(spec, fields, hp, tb);
-    else k_zeta_x<N, false><<<g1, C::TS, C::SMEM_X, st>>>(spec, fields, hp, tb);
+    if ((e = launch_zeta_x<N>(xv, xa)) != cudaSuccess) return e;
     tr(K_ZETA_X, 1, st);
     tr(K_ZETA_Y, 0, st);
     if ((e = launch_zeta_y(N, yvar, fields, nf, tb.tw, st)) != cudaSuccess) return e;

@@ -462,7 +462,7 @@ def estimate_bytes(N: int, stat: int, n_bins: int, l_max: int, n_points: int, ho
                                           1 if host_inputs else 0))
 
 
-PASS_INV_Y, PASS_WINDOW, PASS_CONTRACT, PASS_ZETA_Y = 0, 1, 2, 3
+PASS_INV_Y, PASS_WINDOW, PASS_CONTRACT, PASS_ZETA_Y, PASS_ZETA_X, PASS_ZETA_X_M0 = 0, 1, 2, 3, 4, 5
 
 
 def fft_variants(N: int, pass_: int = PASS_INV_Y) -> dict:

@@ -144,3 +144,28 @@ def test_window_pass_variants_with_cylinder_and_ring_windows():
         _close(got, cyl_ks)
     for got in rings:
         _close(got, ring_ks)
+
+
+@pytest.mark.parametrize("N,L", [(256, 500.0), (512, 1000.0)])
+def test_every_zeta_x_variant_matches(N, L):
+    # the zeta_l x pass (Y_lm window multiply fused in), one line set at a time or the k_y
+    # and N - k_y lines together, for complex fields (pass 4) and packed m = 0 fields (pass 5);
+    # l_max 5 so that the conjugate angular factor of the mirror line is checked at odd m
+    H = _hermes()
+    pos = S.lognormal_catalogue(100000, L, seed=13, n_grid=64)
+    outs = []
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(np.linspace(L / 50, L / 8, 8), l_max=5)
+            ctx.assign(pos)
+            for v in range(len(H.fft_variants(N, 4)["variants"])):
+                H.fft_set_variant(N, v, 4)
+                H.fft_set_variant(N, v, 5)
+                outs.append(ctx.zeta_multipoles())
+    finally:
+        H.fft_set_variant(N, -1, 4)
+        H.fft_set_variant(N, -1, 5)
+    assert len(outs) >= 2
+    for got in outs:
+        assert np.all(np.isfinite(got))
+        _close(got, outs[0])
