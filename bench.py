@@ -1052,12 +1052,15 @@ def run_profile_case(args):
 
 def run_profile_zeta(args):
     """Small zeta case for ncu captures: 256^3 field, 200k points, 16 shells, l_max = 1.
-    --zy-variant fixes the zeta y-pass variant (no tuning trials)."""
+    --zy-variant / --zx-variant fix the zeta y / x pass variants (no tuning trials)."""
     import torch
     from paper_2607_23494_b300 import Context, fft_set_variant
     from synthetic import catalogues as S
     if args.zy_variant >= 0:
         fft_set_variant(256, args.zy_variant, 3)
+    if args.zx_variant >= 0:
+        fft_set_variant(256, args.zx_variant, 4)
+        fft_set_variant(256, args.zx_variant, 5)
     pos = torch.from_numpy(S.poisson_uniform(200_000, L3, seed=8)).cuda()
     ctx = Context(L3, 256, 4)
     ctx.window_shells(np.linspace(10.0, 170.0, 17), l_max=1)
@@ -1092,6 +1095,7 @@ def main():
     ap.add_argument("--x-variant", type=int, default=0, help="window-pass variant of --profile-case")
     ap.add_argument("--z-variant", type=int, default=0, help="contraction-pass variant of --profile-case")
     ap.add_argument("--zy-variant", type=int, default=-1, help="zeta y-pass variant of --profile-zeta")
+    ap.add_argument("--zx-variant", type=int, default=-1, help="zeta x-pass variant of --profile-zeta")
     ap.add_argument("--fft-variants", default="",
                     help="Y,X,Z: fix the 512^3 inverse y, window and contraction pass variants instead of tuning "
                          "(ncu distorts the tuner's trial timings, so launch lists run with the plain run's choice)")
