@@ -1105,27 +1105,28 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 }
 
 // ---------------------------------------------------------------------------
-// Variants of the inverse y pass (pass 0, I2), the window pass (pass 1, I1) and the
-// c2r + contraction pass (pass 2, I3), and the autotuner that picks one per pass
-// and grid size.  A variant fixes the
-// values per thread E (the radix of the FFT stages: radix 8 throughout for E = 8,
-// radix 16 or 32 for E = 16, 32), the tile width W, the blocks per SM it is
-// compiled for (minb, 0: not fixed) and a kind:
-//   pass 0: 0 the radix-8 pass (k_strided_pf up to 512^3, k_strided above),
-//           1 k_strided_e (one tile per block), 2 k_strided_pf_e (persistent);
-//   pass 1: 0 the radix-8 window pass (k_inv_x_window, shared table when it fits),
-//           1 k_inv_x_window_pair (two windows in flight per thread),
-//           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read each);
-//   pass 2: 0 the radix-8 c2r + contraction pass (k_inv_z_c2r_contract),
+// Variants of the tuned FFT passes and the autotuner that picks one per pass and grid
+// size.  A variant fixes the values per thread E (the radix of the FFT stages: radix 8
+// throughout for E = 8, radix 16 or 32 for E = 16, 32), the tile width W, the blocks per
+// SM it is compiled for (minb, 0: not fixed) and a kind:
+//   pass 0, the inverse y pass (I2): 0 the radix-8 pass (k_strided_pf up to 512^3,
+//           k_strided above), 1 k_strided_e (one tile per block), 2 k_strided_pf_e
+//           (persistent);
+//   pass 1, the window pass (I1): 0 one window at a time (k_inv_x_window, shared table
+//           when it fits), 1 k_inv_x_window_pair (two windows in flight per thread),
+//           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read
+//           for both);
+//   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
-//   pass 3: the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e;
-//   passes 4, 5: the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at a time
-//           (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror).
-// The first inverse call of a grid size that is not being captured into a graph
-// times every variant on that call's own buffers (the y pass before the window pass
-// writes the work buffer, the window pass and the last pass on the first catalogue)
-// and keeps the fastest for the process and device; hermes_fft_set_variant fixes
-// one instead.
+//   pass 3, the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e;
+//   passes 4, 5, the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at
+//           a time (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror).
+// The first call of a grid size that runs a pass on a stream that is not being captured
+// into a graph times every variant on that call's own buffers (the y passes before the
+// passes that write their buffers, the others on the first catalogue), one warm-up and two
+// timed launches each, and keeps the fastest for the process and device;
+// hermes_fft_set_variant fixes one instead.  The choice is made for the shape of that
+// first call (windows per launch, orders, bins) and kept for later calls of other shapes.
 
 static int sm_count() {
     static int n = [] {
