@@ -221,6 +221,26 @@ __global__ void __launch_bounds__((N / E) * W) k_strided_e(float2* __restrict__ 
     for (int i = 0; i < E; ++i) b[(t + i * T) * pos_stride] = v[i];
 }
 
+// The inverse y pass of fields [f][x][y][z] with Z values along z (the window work
+// buffer: Z = N/2; the zeta_l harmonic fields: Z = N) as k_strided_e with the strides
+// fixed at compile time: the E element offsets of a thread are immediates of one base
+// address instead of E computed addresses, which leaves the registers for the
+// transform (MINB blocks per SM).  Grid (Z / W, N, fields).
+template <int N, int Z, int E, int W, int SH, int P, int MINB>
+__global__ void __launch_bounds__((N / E) * W, MINB) k_inv_y_e(float2* __restrict__ data,
+                                                               const float2* __restrict__ tw) {
+    constexpr int T = N / E;
+    extern __shared__ float2 smem[];
+    const int col = threadIdx.x % W, t = threadIdx.x / W;
+    float2* b = data + (size_t)blockIdx.z * N * N * Z + (size_t)blockIdx.y * N * Z + blockIdx.x * W + col + t * Z;
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = b[i * T * Z];
+    fft_line_e<N, E, true>(v, t, tw, SmemStridedSk<W, SH, P>{smem, col});
+#pragma unroll
+    for (int i = 0; i < E; ++i) b[i * T * Z] = v[i];
+}
+
 template <int N, int E, int W, int SH, int P, int MINB>
 __global__ void __launch_bounds__((N / E) * W, MINB) k_strided_pf_e(float2* __restrict__ data, int pos_stride,
                                                                     int ystride, long long zstride, int nxt, int nyt,
@@ -1110,7 +1130,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 // throughout for E = 8, radix 16 or 32 for E = 16, 32), the tile width W, the blocks per
 // SM it is compiled for (minb, 0: not fixed) and a kind:
 //   pass 0, the inverse y pass (I2): 0 the radix-8 pass (k_strided_pf up to 512^3,
-//           k_strided above), 1 k_strided_e (one tile per block), 2 k_strided_pf_e
+//           k_strided above), 1 one tile per block (k_strided_e; k_inv_y_e, the strides
+//           fixed at compile time, for the 16-column tiles), 2 k_strided_pf_e
 //           (persistent);
 //   pass 1, the window pass (I1): 0 one window at a time (k_inv_x_window, shared table
 //           when it fits), 1 k_inv_x_window_pair (two windows in flight per thread),
@@ -1118,7 +1139,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           for both);
 //   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
-//   pass 3, the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e;
+//   pass 3, the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e (k_inv_y_e for the
+//           16-column tiles);
 //   passes 4, 5, the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at
 //           a time (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror).
 // The first call of a grid size that runs a pass on a stream that is not being captured
@@ -1158,7 +1180,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 64: return put({{0, 8, Cfg<64>::W, 2}});
             case 128: return put({{0, 8, Cfg<128>::W, 2}, {1, 16, 8, 0}});
             case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
-            case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+            case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0},
+                                  {1, 32, 16, 1}, {1, 32, 16, 2}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
         }
     } else if (pass == 2) {
@@ -1184,7 +1207,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 64: return put({{0, 8, Cfg<64>::W, 0}});
             case 128: return put({{0, 8, Cfg<128>::W, 0}});
             case 256: return put({{0, 8, Cfg<256>::W, 0}, {1, 16, 8, 0}, {1, 32, 8, 0}});
-            case 512: return put({{0, 8, Cfg<512>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
+            case 512: return put({{0, 8, Cfg<512>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}, {1, 32, 16, 1},
+                                  {1, 32, 16, 2}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 0}});
         }
     } else if (pass == 1) {
@@ -1231,6 +1255,15 @@ static cudaError_t run_y_plain(float2* work, int nwin, const float2* tw, cudaStr
     k_strided_e<N, E, W, SH, P><<<dim3(H / W, N, nwin), TS, smem, st>>>(work, H, N * H, (long long)N * N * H, tw);
     return cudaGetLastError();
 }
+template <int N, int Z, int E, int W, int SH, int P, int MINB>
+static cudaError_t run_y_ct(float2* data, int nf, const float2* tw, cudaStream_t st) {
+    constexpr int TS = (N / E) * W;
+    constexpr size_t smem = (size_t)SmemStridedSk<W, SH, P>::words(N) * sizeof(float2);
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_y_e<N, Z, E, W, SH, P, MINB>, smem)) != cudaSuccess) return e;
+    k_inv_y_e<N, Z, E, W, SH, P, MINB><<<dim3(Z / W, N, nf), TS, smem, st>>>(data, tw);
+    return cudaGetLastError();
+}
 template <int N, int E, int W, int SH, int P, int MINB>
 static cudaError_t run_y_pf(float2* work, int nwin, const float2* tw, cudaStream_t st) {
     constexpr int H = N / 2, TS = (N / E) * W;
@@ -1258,6 +1291,10 @@ static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* t
         if (var == 1) return run_y_pf<512, 32, 8, 2, 2, 2>(work, nwin, tw, st);
         if (var == 2) return run_y_plain<512, 32, 8, 2, 2>(work, nwin, tw, st);
         if (var == 3) return run_y_plain<512, 16, 8, 2, 1>(work, nwin, tw, st);
+        // strides fixed at compile time; 16-column tiles read and write whole 128-byte lines
+        // (no skew needed at that width)
+        if (var == 4) return run_y_ct<512, 256, 32, 16, 3, 0, 1>(work, nwin, tw, st);
+        if (var == 5) return run_y_ct<512, 256, 32, 16, 3, 0, 2>(work, nwin, tw, st);
     } else if constexpr (N == 1024) {
         if (var == 1) return run_y_plain<1024, 32, 8, 2, 1>(work, nwin, tw, st);
         if (var == 2) return run_y_plain<1024, 16, 8, 2, 8>(work, nwin, tw, st);
@@ -1364,6 +1401,8 @@ static cudaError_t launch_zeta_y_var(int var, float2* fields, int nf, const floa
     } else if constexpr (N == 512) {
         if (var == 1) return run_zeta_y_e<512, 32, 8, 2, 2>(fields, nf, tw, st);
         if (var == 2) return run_zeta_y_e<512, 16, 8, 2, 1>(fields, nf, tw, st);
+        if (var == 3) return run_y_ct<512, 512, 32, 16, 3, 0, 1>(fields, nf, tw, st);
+        if (var == 4) return run_y_ct<512, 512, 32, 16, 3, 0, 2>(fields, nf, tw, st);
     }
     using C = Cfg<N>;
     cudaError_t e;

@@ -1,8 +1,8 @@
 """The variants of the inverse y pass (values per thread, hence the radix of the
-FFT stages; tile width; one tile per block or persistent blocks) and of the window
-pass (one or two windows in flight per thread) and of the c2r + contraction pass
-(8 or 16 values per thread), and the autotuner that picks one per pass and grid
-size.
+FFT stages; tile width; one tile per block or persistent blocks; strides given at
+run time or fixed at compile time), of the window pass (one or two windows in
+flight per thread, mirror lines) and of the c2r + contraction pass (8 or 16 values
+per thread), and the autotuner that picks one per pass and grid size.
 
 Every variant must give the same statistics: against the FP64 oracle at 128^3,
 and against the Parseval route (which reads only delta^ and the radial tables and
@@ -112,26 +112,27 @@ def test_every_zeta_y_variant_matches():
         _close(got, outs[0])
 
 
-def test_window_pass_variants_with_cylinder_and_ring_windows():
+@pytest.mark.parametrize("N,L", [(256, 600.0), (512, 1000.0)])
+def test_window_pass_variants_with_cylinder_and_ring_windows(N, L):
     # the window pass's cylindrical mode (one line-of-sight bin per batch) and ring mode (a
-    # line-of-sight row per window) through every window-pass variant at 256^3, against the
-    # Parseval route (which reads only delta^ and the window tables)
+    # line-of-sight row per window) through every window-pass variant, against the Parseval
+    # route (which reads only delta^ and the window tables)
     H = _hermes()
-    N, L = 256, 600.0
     pos = S.lognormal_catalogue(150000, L, seed=21, n_grid=64)
     mass = S.lognormal_masses(pos.shape[0], seed=22)
-    s = np.linspace(8.0, 60.0, 6)
+    f = L / 600.0
+    s = np.linspace(8.0, 60.0, 6) * f
     mu = np.linspace(0.05, 0.95, 7)
     try:
         with H.Context(L, N, 4) as ctx:
             ctx.assign(pos, mass)
-            ctx.window_cylinders(np.linspace(0.0, 50.0, 6), np.linspace(0.0, 40.0, 5), sigma_perp=2.0)
+            ctx.window_cylinders(np.linspace(0.0, 50.0, 6) * f, np.linspace(0.0, 40.0, 5) * f, sigma_perp=2.0 * f)
             cyl_ks = ctx.xi_cylinders(kspace=True)
             cyls = []
             for v in range(len(H.fft_variants(N, H.PASS_WINDOW)["variants"])):
                 H.fft_set_variant(N, v, H.PASS_WINDOW)
                 cyls.append(ctx.xi_cylinders())
-            ctx.window_s_mu(s, mu, ds=4.0, dmu=0.1)
+            ctx.window_s_mu(s, mu, ds=4.0 * f, dmu=0.1)
             ring_ks = ctx.xi_rings(kspace=True)
             rings = []
             for v in range(len(H.fft_variants(N, H.PASS_WINDOW)["variants"])):
