@@ -209,6 +209,7 @@ NCU_TRAFFIC_512 = {
     "inv_x_window/k2e8w8": {"per_launch": 0.576038e9, "per_window": 2.796381e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
+    "inv_y/k1e32w16": {"per_launch": 0.0, "per_window": (2.684860e9 + 2.624219e9) / 5},
     "inv_z_c2r_contract/k0e8w1": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
     "inv_z_c2r_contract/k1e16w1": {"per_launch": 0.0, "per_window": (3.221317e9 + 0.013573e9) / 5},
 }

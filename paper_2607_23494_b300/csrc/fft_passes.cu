@@ -1179,7 +1179,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 32: return put({{0, 8, Cfg<32>::W, 2}});
             case 64: return put({{0, 8, Cfg<64>::W, 2}});
             case 128: return put({{0, 8, Cfg<128>::W, 2}, {1, 16, 8, 0}});
-            case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0}});
+            case 256: return put({{0, 8, Cfg<256>::W, 2}, {1, 16, 8, 0}, {2, 16, 8, 3}, {1, 32, 8, 0},
+                                  {1, 16, 16, 2}, {1, 32, 16, 4}});
             case 512: return put({{0, 8, Cfg<512>::W, 2}, {2, 32, 8, 2}, {1, 32, 8, 0}, {1, 16, 8, 0},
                                   {1, 32, 16, 1}, {1, 32, 16, 2}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}});
@@ -1206,7 +1207,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 32: return put({{0, 8, Cfg<32>::W, 0}});
             case 64: return put({{0, 8, Cfg<64>::W, 0}});
             case 128: return put({{0, 8, Cfg<128>::W, 0}});
-            case 256: return put({{0, 8, Cfg<256>::W, 0}, {1, 16, 8, 0}, {1, 32, 8, 0}});
+            case 256: return put({{0, 8, Cfg<256>::W, 0}, {1, 16, 8, 0}, {1, 32, 8, 0}, {1, 16, 16, 2},
+                                  {1, 32, 16, 4}});
             case 512: return put({{0, 8, Cfg<512>::W, 0}, {1, 32, 8, 0}, {1, 16, 8, 0}, {1, 32, 16, 1},
                                   {1, 32, 16, 2}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 0}});
@@ -1287,6 +1289,8 @@ static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* t
         if (var == 1) return run_y_plain<256, 16, 8, 2, 2>(work, nwin, tw, st);
         if (var == 2) return run_y_pf<256, 16, 8, 2, 2, 3>(work, nwin, tw, st);
         if (var == 3) return run_y_plain<256, 32, 8, 2, 4>(work, nwin, tw, st);
+        if (var == 4) return run_y_ct<256, 128, 16, 16, 3, 0, 2>(work, nwin, tw, st);
+        if (var == 5) return run_y_ct<256, 128, 32, 16, 3, 0, 4>(work, nwin, tw, st);
     } else if constexpr (N == 512) {
         if (var == 1) return run_y_pf<512, 32, 8, 2, 2, 2>(work, nwin, tw, st);
         if (var == 2) return run_y_plain<512, 32, 8, 2, 2>(work, nwin, tw, st);
@@ -1398,6 +1402,8 @@ static cudaError_t launch_zeta_y_var(int var, float2* fields, int nf, const floa
     if constexpr (N == 256) {
         if (var == 1) return run_zeta_y_e<256, 16, 8, 2, 2>(fields, nf, tw, st);
         if (var == 2) return run_zeta_y_e<256, 32, 8, 2, 4>(fields, nf, tw, st);
+        if (var == 3) return run_y_ct<256, 256, 16, 16, 3, 0, 2>(fields, nf, tw, st);
+        if (var == 4) return run_y_ct<256, 256, 32, 16, 3, 0, 4>(fields, nf, tw, st);
     } else if constexpr (N == 512) {
         if (var == 1) return run_zeta_y_e<512, 32, 8, 2, 2>(fields, nf, tw, st);
         if (var == 2) return run_zeta_y_e<512, 16, 8, 2, 1>(fields, nf, tw, st);

@@ -141,10 +141,10 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
     # N - k_y lines together, at 256^3 and 512^3;
     # the contraction pass: radix 8 everywhere, 16 values per thread at 256^3 and 512^3;
     # the zeta_l y pass: radix 8 everywhere, 16 or 32 values per thread at 256^3 and 512^3
-    # (and 16-column tiles at 512^3)
+    # (and 16-column tiles at 256^3 and 512^3)
     for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2]), (1, 512, [0, 1, 2]), (2, 64, [0]),
                             (2, 256, [0, 1, 1, 1]), (2, 512, [0, 1, 1, 1]), (2, 1024, [0]), (3, 64, [0]),
-                            (3, 256, [0, 1, 1]), (3, 512, [0, 1, 1, 1, 1]), (4, 512, [0, 2]), (5, 256, [0, 2]),
+                            (3, 256, [0, 1, 1, 1, 1]), (3, 512, [0, 1, 1, 1, 1]), (4, 512, [0, 2]), (5, 256, [0, 2]),
                             (4, 1024, [0])):
         info = H.fft_variants(N, pass_)
         assert [v[0] for v in info["variants"]] == kinds
