@@ -28,6 +28,9 @@ float64, by the plainest route that follows the paper:
                                 Eq. (xi-deltaDD-over-RR) with a random field
   anisotropic xi(r_perp, r_par) Sec. 3.4.4 ring window with finite bins; Table A1 rows
                                 (f)-(i): separable transverse x line-of-sight windows
+  3PCF monopole DDD             Eq. (3PCF-ddd-monopole) two-fold coefficients through the
+                                triple connection coefficients of Eq. (con-coeff), then
+                                Eq. (DDD-vector-product)
 
 Readings of silent or ambiguous points (all restated in the design notes):
   * basis: centred cardinal B-spline M_p on unit cell spacing, partition of unity;
@@ -59,6 +62,7 @@ __all__ = [
     "keff_pair_direct", "xi_brute_force", "direct_convolution", "annulus_avg_j0", "slab_avg_cos",
     "window_cyl", "xi_cylinders", "xi_randoms", "smoothing_window", "density_at", "density_marks",
     "window_xi_at", "window_zeta_at", "planted_xi", "planted_zeta", "window_ring", "xi_rings",
+    "triple_overlap_1d", "connection_coefficients", "ddd_from_fields", "ddd_monopole", "planted_ddd",
 ]
 
 
@@ -732,6 +736,129 @@ def zeta_multipoles(delta, N, L, p, r_edges, l_max):
         out[ell] = acc.real
         imag_max = max(imag_max, float(np.max(np.abs(acc.imag))))
     return out, imag_max
+
+
+# --------------------------------------------------------------------------
+# 3PCF monopole by triple connection coefficients: Eq. (3pcfddd), Eq. (2-fold-density),
+# Eq. (3PCF-ddd-monopole), Eq. (con-coeff), Eq. (DDD-vector-product)
+# --------------------------------------------------------------------------
+def triple_overlap_1d(p: int) -> np.ndarray:
+    """gamma[a + p - 1, b + p - 1] = int M_p(u) M_p(u - a) M_p(u - b) du for |a|, |b| <= p - 1.
+
+    The one-dimensional factor of the triple connection coefficients of Eq. (con-coeff) for
+    the centred order-p B-spline (unit integral, grid units).  The three splines share one
+    knot lattice (integers for even p, half-integers for odd p), so between two knots the
+    integrand is a polynomial of degree 3(p - 1); a 2p-point Gauss-Legendre rule (exact to
+    degree 4p - 1) on each of the p knot intervals of the support of M_p(u) integrates it
+    exactly up to float64 rounding.
+    """
+    x, wt = np.polynomial.legendre.leggauss(2 * p)
+    t, wt = 0.5 * (x + 1.0), 0.5 * wt
+    u = (-0.5 * p + np.arange(p)[:, None] + t[None, :]).ravel()   # the knot intervals of M_p(u)
+    w = np.tile(wt, p)
+    r = np.arange(-(p - 1), p)
+    m0 = bspline(p, u)
+    sh = bspline(p, u[None, :] - r[:, None])
+    return np.einsum("k,k,ak,bk->ab", w, m0, sh, sh)
+
+
+def connection_coefficients(p: int) -> np.ndarray:
+    """Gamma_{a,b} of Eq. (con-coeff) over the lags a, b in [-(p-1), p-1]^3, as a matrix
+    [(2p-1)^3, (2p-1)^3] in the lag order of _lag_stack: the basis is a product of one-
+    dimensional splines, so Gamma_{a,b} = prod_d gamma(a_d, b_d).  Normalised to the unit-
+    integral basis in grid units (sum_{a,b} Gamma_{a,b} = 1), the paper's 1/N_j being
+    the 1/N^3 of ddd_from_fields."""
+    g = triple_overlap_1d(p)
+    n = 2 * p - 1
+    return np.einsum("ad,be,cf->abcdef", g, g, g).reshape(n ** 3, n ** 3)
+
+
+def _lag_stack(f, p):
+    """Rows f(l + a) (periodic) for every lag a = (ax, ay, az) in [-(p-1), p-1]^3, az fastest."""
+    r = range(-(p - 1), p)
+    return np.stack([np.roll(f, shift=(-ax, -ay, -az), axis=(0, 1, 2)).ravel()
+                     for ax in r for ay in r for az in r])
+
+
+def ddd_from_fields(delta, fields, p: int) -> np.ndarray:
+    """(1/N^3) sum_l delta_l eps~_l(b1, b2) for coefficient fields f_b (Eq. DDD-vector-product),
+    with the two-fold coefficients of Eq. (3PCF-ddd-monopole)
+        eps~_l(b1, b2) = sum_a sum_b Gamma_{a,b} f_b1(l + a) f_b2(l + b),
+    the double sum over the lag cube taken as a matrix product.  Returns [nb, nb]."""
+    N = delta.shape[0]
+    G = connection_coefficients(p)
+    stacks = [_lag_stack(np.asarray(f, dtype=np.float64), p) for f in fields]
+    d = np.asarray(delta, dtype=np.float64).ravel()
+    nb = len(fields)
+    out = np.zeros((nb, nb))
+    for b2 in range(nb):
+        gb = G @ stacks[b2]                      # sum_b Gamma_{a,b} f_b2(l + b), every lag a
+        for b1 in range(nb):
+            two_fold = np.einsum("an,an->n", stacks[b1], gb)
+            out[b1, b2] = float(d @ two_fold) / N ** 3
+    return out
+
+
+def ddd_monopole(delta, N: int, L: float, p: int, r_edges) -> np.ndarray:
+    """3PCF monopole DDD(b1, b2) of delta by the triple connection coefficients: the shell-
+    filtered coefficients f_b = iFFT[delta^ K_b] with K_b the l = 0 shell window of
+    window_xi (<j_0>_b Phi^), then ddd_from_fields.  Replacing Gamma by the identity stencil
+    (a = b = 0) gives the cell sum (1/N^3) sum_l delta f_b1 f_b2, i.e. zeta_0 of
+    zeta_multipoles.  Returns [nb, nb] float64."""
+    dh = forward(delta)
+    nb = len(r_edges) - 1
+    fields = [np.fft.ifftn(dh * window_xi(N, L, p, r_edges[b], r_edges[b + 1], 0)).real for b in range(nb)]
+    return ddd_from_fields(delta, fields, p)
+
+
+def planted_ddd(N: int, L: float, p: int, r_edges, modes, amps, mmax: int = 40) -> np.ndarray:
+    """ddd_monopole of delta_l = sum_q amps_q cos(2 pi n_q.l / N) by Poisson summation.
+
+    With complex amplitudes c_s (amps_q / 2 at +-n_q), a coefficient field sum_s c_s e^{i k_s.l}
+    is the spline field sum_s c_s sum_{m in Z^3} M^(k_s + 2 pi m) e^{i (k_s + 2 pi m).u}, where
+    M^(w) = prod_d sinc^p(w_d / 2) is the transform of the unit-integral centred B-spline.  The
+    box integral of a product of three such fields keeps the alias triples whose wavevectors
+    sum to zero, so
+        DDD(b1, b2) = sum_{s0, s1, s2} c_s0 c_s1 c_s2 K_b1(n_s1) K_b2(n_s2) prod_d A_d,
+        A_d = sum_{m0, m1} s(k0 + 2 pi m0) s(k1 + 2 pi m1) s(k2 + 2 pi (M - m0 - m1)),
+    with s(w) = sinc^p(w / 2), k_i = 2 pi n_i / N along axis d and M = -(n0 + n1 + n2) / N,
+    which must be an integer (otherwise the triple contributes nothing).  The alias sums
+    are truncated at |m| <= mmax; their terms decay like |m|^(-2p).  Returns [nb, nb].
+    """
+    modes = [tuple(int(x) for x in n) for n in modes]
+    pm = modes + [tuple(-x for x in n) for n in modes]
+    c = np.concatenate([np.asarray(amps, dtype=np.float64) / 2.0] * 2)
+    nb = len(r_edges) - 1
+    K = np.array([window_xi_at(N, L, p, r_edges[b], r_edges[b + 1], 0, pm) for b in range(nb)])
+    m = np.arange(-mmax, mmax + 1)
+
+    def s(w):
+        return np.sinc(w / (2.0 * np.pi)) ** p
+
+    def alias(n0, n1, n2):
+        tot = n0 + n1 + n2
+        if tot % N:
+            return 0.0
+        M = -tot // N
+        k0, k1, k2 = (2.0 * np.pi * n / N for n in (n0, n1, n2))
+        a0 = s(k0 + 2.0 * np.pi * m)[:, None]
+        a1 = s(k1 + 2.0 * np.pi * m)[None, :]
+        a2 = s(k2 + 2.0 * np.pi * (M - m[:, None] - m[None, :]))
+        return float(np.sum(a0 * a1 * a2))
+
+    out = np.zeros((nb, nb))
+    ns = len(pm)
+    for i0 in range(ns):
+        for i1 in range(ns):
+            for i2 in range(ns):
+                A = 1.0
+                for d in range(3):
+                    A *= alias(pm[i0][d], pm[i1][d], pm[i2][d])
+                    if A == 0.0:
+                        break
+                if A != 0.0:
+                    out += c[i0] * c[i1] * c[i2] * A * np.outer(K[:, i1], K[:, i2])
+    return out
 
 
 # --------------------------------------------------------------------------
