@@ -343,6 +343,26 @@ int hermes_xi_rings_kspace(hermes_ctx *ctx, double *out);
  */
 int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
 
+/*
+ * 3PCF monopole by triple connection coefficients (Eq. 3pcfddd, Eq. 2-fold-density,
+ * Eq. 3PCF-ddd-monopole, Eq. con-coeff, Eq. DDD-vector-product) on the order-p
+ * B-spline basis of the context:
+ *   DDD(b1, b2) = (1/N^3) sum_l delta_l sum_{a,b} Gamma_{a,b} f_b1(l + a) f_b2(l + b),
+ *   Gamma_{a,b} = int phi(u) phi(u - a) phi(u - b) du   (grid units, unit-integral phi),
+ * with f_b = iFFT[delta^ <j_0>_b Phi^] the l = 0 shell-filtered coefficients of the
+ * bins set by hermes_window_shells.  This is (1/N^3) int D F_b1 F_b2 du, the box
+ * integral of the three spline fields, evaluated exactly by a Gauss-Legendre rule of
+ * (3p - 1) / 2 points per axis in every knot cell (the integrand is a polynomial of
+ * degree 3(p - 1) there).  With Gamma replaced by the identity stencil it is the cell
+ * sum zeta_0 of hermes_zeta_multipoles; the two differ by the basis smoothing.
+ * Returned raw (self triplets included), like zeta_l.
+ *   out: [n_bins][n_bins] float64, symmetric.  n_bins: 1 .. 16.
+ * Device memory: n_bins half spectra and 2 (n_bins + 1) real fields of N^3.
+ * Errors: HERMES_ERR_ARG (out NULL, more than 16 bins), HERMES_ERR_STATE (no field,
+ * no bins, explicit randoms set), HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ */
+int hermes_ddd_monopole(hermes_ctx *ctx, double *out);
+
 /* Text of the last error of this context (never NULL; empty after success). */
 const char *hermes_last_error(const hermes_ctx *ctx);
 

@@ -15,7 +15,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhermes.so")
-SOURCES = ["hermes_api.cu", "scatter.cu", "fft_passes.cu", "zeta.cu", "kspace.cu", "server.cu", "wait_check.cu"]
+SOURCES = ["hermes_api.cu", "scatter.cu", "fft_passes.cu", "zeta.cu", "kspace.cu", "server.cu", "wait_check.cu",
+           "ddd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

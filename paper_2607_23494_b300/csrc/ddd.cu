@@ -1,0 +1,255 @@
+// 3PCF monopole by triple connection coefficients: Eq. (3pcfddd), Eq. (2-fold-density),
+// Eq. (3PCF-ddd-monopole), Eq. (con-coeff), Eq. (DDD-vector-product), for the centred
+// order-p B-spline basis of the scatter.
+//
+//   DDD(b1, b2) = (1/N^3) sum_l delta_l sum_{a,b} Gamma_{a,b} f_b1(l + a) f_b2(l + b),
+//   Gamma_{a,b} = int phi(u) phi(u - a) phi(u - b) du,
+//
+// with f_b the l = 0 shell-filtered coefficients.  Summed over l this is the box integral
+// (1/N^3) int D F_b1 F_b2 du of the three spline fields D = sum_l delta_l phi(u - l) and
+// F_b = sum_l f_b(l) phi(u - l).  Between knots (integers for even p, half-integers for
+// odd p) the integrand is a polynomial of degree 3(p - 1) along each axis, so a Gauss-
+// Legendre rule of n_g = (3p - 1) / 2 points per axis and knot cell integrates it exactly:
+// at order 4 the 37^3-term stencil becomes 125 samples per cell, and a spline field at the
+// sample t_g of cell c is a p-tap filter along each axis, sum_j B_g[j] f(c + j0 + j).
+//
+// For every sample pair (g_z, g_y):
+//   k_ddd_filter_yz: Y_f = the y and z filters of every field (delta and the S shell fields),
+//                    separable through shared memory;
+//   k_ddd_gram     : down each (y, z) column, the x filters at every g_x (each field once per
+//                    cell, from a sliding window of p x-taps in registers, shared through
+//                    shared memory), then the weighted Gram sum_gx w_g D F_b1 F_b2 on 8 x 8 bin
+//                    tiles (one warp per tile), in float32 over one column (N cells x n_g
+//                    samples), then float64.
+#include "kernels.h"
+
+#include <algorithm>
+
+namespace hermes {
+
+namespace {
+
+// Tiles of 32 y x 32 z outputs of one (field, x) plane (16 x 16 at N = 16): the
+// (T + P - 1)^2 inputs (periodic) staged once in shared memory by unrolled loads (several in
+// flight per thread), filtered along z into a second stage, then along y.
+template <int P>
+__global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__ in, float* __restrict__ out,
+                                                       int lgN, int lgT, const __grid_constant__ DddYZ tp) {
+    constexpr int TM = 32, RM = TM + P - 1;
+    constexpr int LOADS = (RM * RM + 255) / 256;
+    __shared__ float s_in[RM][RM + 1];
+    __shared__ float s_z[RM][TM + 1];
+    const int N = 1 << lgN, msk = N - 1, T = 1 << lgT, R = T + P - 1;
+    const int nt = N >> lgT;
+    const size_t blk = blockIdx.x;
+    const int tz = (int)(blk % nt), ty = (int)((blk / nt) % nt);
+    const size_t plane = blk / ((size_t)nt * nt);  // field * N + x
+    const int y0 = ty * T, z0 = tz * T;
+    const float* src = in + (plane << (2 * lgN));
+    float v[LOADS];
+#pragma unroll
+    for (int k = 0; k < LOADS; ++k) {
+        const int e = threadIdx.x + k * 256;
+        const int r = e / R, c = e - r * R;
+        v[k] = (e < R * R) ? __ldg(src + ((size_t)((y0 + tp.j0 + r) & msk) << lgN) + ((z0 + tp.j0 + c) & msk)) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < LOADS; ++k) {
+        const int e = threadIdx.x + k * 256;
+        const int r = e / R, c = e - r * R;
+        if (e < R * R) s_in[r][c] = v[k];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * T; e += 256) {
+        const int r = e >> lgT, c = e & (T - 1);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) acc = fmaf(tp.bz[j], s_in[r][c + j], acc);
+        s_z[r][c] = acc;
+    }
+    __syncthreads();
+    float* dst = out + (plane << (2 * lgN));
+    for (int e = threadIdx.x; e < T * T; e += 256) {
+        const int r = e >> lgT, c = e & (T - 1);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) acc = fmaf(tp.by[j], s_z[r + j][c], acc);
+        dst[((size_t)(y0 + r) << lgN) + z0 + c] = acc;
+    }
+}
+
+// Down 32 (y, z) columns per task, for x = 0 .. N-1: warp w x-filters fields w, w + nw, ...
+// (delta and the S shell fields) at every sample g_x from its sliding windows of P taps and
+// stages the values in shared memory (double-buffered, one barrier per cell); then warp w
+// adds w_gx D F_b1 F_b2 into its tile of the Gram: {(0, 0), (0, 8), (8, 8)} for three warps
+// (S > 8), (0, 0) for one.  Rows of fields beyond S stay zero.
+template <int P, int NW>
+__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const float* __restrict__ Y, int S, int lgN,
+                                                                      const __grid_constant__ DddTaps tp,
+                                                                      double* __restrict__ part) {
+    constexpr int NG = ddd_samples(P), FPW = (17 + NW - 1) / NW;  // fields filtered per warp, at most
+    constexpr int nw = NW;
+    __shared__ float s_v[2][NG][17][32];
+    const int N = 1 << lgN, msk = N - 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t n3 = (size_t)1 << (3 * lgN);
+    const int nf = S + 1;
+    for (int e = threadIdx.x; e < 2 * NG * 17 * 32; e += blockDim.x) (&s_v[0][0][0][0])[e] = 0.0f;
+    const int tile = nw == 1 ? 0 : w;
+    const int r0 = tile == 2 ? 8 : 0, c0 = tile == 0 ? 0 : 8;
+    const bool diag = tile != 1;
+    double d0 = 0.0, d1 = 0.0;
+    int buf = 0;
+    const int ntask = (N * N) >> 5;
+    __syncthreads();
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const float* col = Y + ((size_t)task << 5) + lane;
+        float t[FPW][P];
+#pragma unroll
+        for (int k = 0; k < FPW; ++k) {
+            const int f = w + k * nw;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                t[k][j] = f < nf ? __ldg(col + (size_t)f * n3 + ((size_t)((tp.j0 + j) & msk) << (2 * lgN))) : 0.0f;
+        }
+        float acc[64];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) acc[k] = 0.0f;
+        for (int x = 0; x < N; ++x) {
+            float nxt[FPW];  // the tap entering each window at x + 1, in flight during this cell
+            const size_t xn = (size_t)((x + 1 + tp.j0 + P - 1) & msk) << (2 * lgN);
+#pragma unroll
+            for (int k = 0; k < FPW; ++k) {
+                const int f = w + k * nw;
+                nxt[k] = f < nf ? __ldg(col + (size_t)f * n3 + xn) : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < FPW; ++k) {
+                const int f = w + k * nw;
+                if (f < nf) {
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        float v = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < P; ++j) v = fmaf(tp.bx[g][j], t[k][j], v);
+                        s_v[buf][g][f][lane] = v;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int g = 0; g < NG; ++g) {
+                const float h = tp.wx[g] * s_v[buf][g][0][lane];
+                float vr[8];
+#pragma unroll
+                for (int a2 = 0; a2 < 8; ++a2) vr[a2] = h * s_v[buf][g][1 + r0 + a2][lane];
+                if (diag) {
+#pragma unroll
+                    for (int a2 = 0; a2 < 8; ++a2) {
+#pragma unroll
+                        for (int b2 = a2; b2 < 8; ++b2)
+                            acc[a2 * 8 + b2] = fmaf(vr[a2], s_v[buf][g][1 + r0 + b2][lane], acc[a2 * 8 + b2]);
+                    }
+                } else {
+                    float vc[8];
+#pragma unroll
+                    for (int b2 = 0; b2 < 8; ++b2) vc[b2] = s_v[buf][g][1 + c0 + b2][lane];
+#pragma unroll
+                    for (int a2 = 0; a2 < 8; ++a2) {
+#pragma unroll
+                        for (int b2 = 0; b2 < 8; ++b2) acc[a2 * 8 + b2] = fmaf(vr[a2], vc[b2], acc[a2 * 8 + b2]);
+                    }
+                }
+            }
+            buf ^= 1;
+#pragma unroll
+            for (int k = 0; k < FPW; ++k) {
+#pragma unroll
+                for (int j = 0; j + 1 < P; ++j) t[k][j] = t[k][j + 1];
+                t[k][P - 1] = nxt[k];
+            }
+        }
+        // the column's float32 sums, summed over the warp, into float64 (entry k on lane k % 32);
+        // diagonal tiles leave the lower triangle at zero
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            float sum = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == (k & 31)) {
+                if (k < 32) d0 += (double)sum;
+                else d1 += (double)sum;
+            }
+        }
+    }
+    // accumulate over the (g_z, g_y) launches: each (block, tile, entry) has one owner
+    double* row = part + ((size_t)blockIdx.x * 3 + tile) * 64;
+    row[lane] += d0 * tp.wyz;
+    row[32 + lane] += d1 * tp.wyz;
+}
+
+int ilog2i(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+int sm_count_ddd() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            return 148;
+        }
+        return v;
+    }();
+    return n;
+}
+
+}  // namespace
+
+int ddd_gram_blocks(int N, int S) {
+    // the blocks per SM the two forms are compiled for (3 warps: 4, one warp: 8); never more
+    // blocks than 32-column tasks
+    return std::max(1, std::min((S <= 8 ? 8 : 4) * sm_count_ddd(), (N * N) / 32));
+}
+
+cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
+                                 cudaStream_t st, const Tracer& tr) {
+    if (N < 16) return cudaErrorInvalidValue;
+    const int lgN = ilog2i(N), lgT = std::min(lgN, 5);
+    const size_t nt = (size_t)N >> lgT;
+    const size_t nblk = (size_t)nf * N * nt * nt;  // (field, x) planes x y tiles x z tiles
+    if (nblk > 0x7fffffffULL) return cudaErrorInvalidValue;
+    tr(K_DDD_FILTER, 0, st);
+    switch (p) {
+#define C(P) case P: k_ddd_filter_yz<P><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, lgT, tp); break;
+        C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
+#undef C
+        default: return cudaErrorInvalidValue;
+    }
+    tr(K_DDD_FILTER, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ddd_gram(int N, int p, const float* Y, int S, const DddTaps& tp, double* part, cudaStream_t st,
+                            const Tracer& tr) {
+    if (S < 1 || S > 16 || N < 16) return cudaErrorInvalidValue;
+    const int lgN = ilog2i(N);
+    const int nblk = ddd_gram_blocks(N, S);
+    tr(K_DDD_GRAM, 0, st);
+    switch (p) {
+#define C(P)                                                                         \
+    case P:                                                                          \
+        if (S <= 8) k_ddd_gram<P, 1><<<nblk, 32, 0, st>>>(Y, S, lgN, tp, part);      \
+        else k_ddd_gram<P, 3><<<nblk, 96, 0, st>>>(Y, S, lgN, tp, part);             \
+        break;
+        C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
+#undef C
+        default: return cudaErrorInvalidValue;
+    }
+    tr(K_DDD_GRAM, 1, st);
+    return cudaGetLastError();
+}
+
+}  // namespace hermes

@@ -1604,6 +1604,38 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
         default: return cudaErrorInvalidValue; \
     }
 
+// The real filtered fields of a window batch (the 3PCF monopole's shell fields): the window
+// pass, the inverse y pass (radix-8 forms) and the c2r z pass of every window, stored.
+template <int N>
+static cudaError_t filtered_impl(const float2* spec, float2* work, float* out, const WinBatch& wb, const Tables& tb,
+                                 cudaStream_t st, const Tracer& tr) {
+    using C = Cfg<N>;
+    cudaError_t e;
+    if ((e = allow_smem(k_inv_z_c2r_store<N>, C::SMEM_Z)) != cudaSuccess) return e;
+    tr(K_INV_X_WINDOW, 0, st);
+    if ((e = launch_inv_x<N>(0, spec, work, wb, tb, 1, st)) != cudaSuccess) return e;
+    tr(K_INV_X_WINDOW, 1, st);
+    tr(K_INV_Y, 0, st);
+    if ((e = launch_inv_y<N>(0, work, wb.S, tb.tw, st)) != cudaSuccess) return e;
+    tr(K_INV_Y, 1, st);
+    const float scale = 1.0f / ((float)N * (float)N * (float)N);
+    for (int s = 0; s < wb.S; ++s) {
+        tr(K_INV_Z_STORE, 0, st);
+        k_inv_z_c2r_store<N><<<(N * N) / C::LZ, C::ZTHREADS, C::SMEM_Z, st>>>(
+            work + (size_t)s * N * N * (N / 2), out + (size_t)s * N * N * N, scale, tb.tw);
+        tr(K_INV_Z_STORE, 1, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filtered_fields(int N, const float2* spec, float2* work, float* out, const WinBatch& wb,
+                                   const Tables& tb, cudaStream_t st, const Tracer& tr) {
+    if (wb.S < 1 || wb.S > 16 || (reinterpret_cast<uintptr_t>(wb.tab) & 15)) return cudaErrorInvalidValue;
+#define F(n) filtered_impl<n>(spec, work, out, wb, tb, st, tr)
+    HERMES_DISPATCH_N(N, F)
+#undef F
+}
+
 cudaError_t launch_smooth_field(int N, const float2* spec, float2* work, float* out, const WinBatch& wb,
                                 const Tables& tb, cudaStream_t st, const Tracer& tr) {
     if (wb.S != 1) return cudaErrorInvalidValue;

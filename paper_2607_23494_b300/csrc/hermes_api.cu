@@ -1047,6 +1047,120 @@ int hermes_xi(hermes_ctx* c, double* out) {
     return hermes_xi_multipoles(c, &zero, 1, out);
 }
 
+namespace {
+// Centred cardinal B-spline M_p(x) (unit integral, support |x| < p/2) by the recursion of the
+// uniform B-spline, M_1 = the box [-1/2, 1/2) and
+// M_p(x) = ((x + p/2) M_{p-1}(x + 1/2) + (p/2 - x) M_{p-1}(x - 1/2)) / (p - 1).
+double bspline_host(int p, double x) {
+    if (p == 1) return (x >= -0.5 && x < 0.5) ? 1.0 : 0.0;
+    if (std::fabs(x) >= 0.5 * p) return 0.0;
+    return ((x + 0.5 * p) * bspline_host(p - 1, x + 0.5) + (0.5 * p - x) * bspline_host(p - 1, x - 0.5)) / (p - 1);
+}
+
+// n-point Gauss-Legendre nodes and weights on [0, 1]: the roots of P_n by Newton's method
+// from the estimates cos(pi (i + 3/4) / (n + 1/2)), P_n and P_n' by the three-term recurrence,
+// weights 2 / ((1 - z^2) P_n'(z)^2), mapped from [-1, 1].
+void gauss_legendre01(int n, double* t, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            dp = n * (z * p1 - p2) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-15) break;
+        }
+        t[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+}  // namespace
+
+int hermes_ddd_monopole(hermes_ctx* c, double* out) {
+    if (check_ctx(c)) return HERMES_ERR_ARG;
+    if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
+    if (c->have_randoms)
+        return fail(c, HERMES_ERR_STATE, "the monopole uses analytic uniform randoms: call hermes_clear_randoms and "
+                                         "hermes_assign first");
+    if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
+    if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
+    if (c->n_bins > 16) return fail(c, HERMES_ERR_ARG, "the monopole takes at most 16 bins (%d set)", c->n_bins);
+    DeviceGuard g(c->device);
+    AllocStream as_(c->stream);
+    cudaStream_t st = c->stream;
+    const int N = c->N, H = c->H, S = c->n_bins, p = c->p, nf = S + 1;
+    const size_t n3 = (size_t)N * N * N;
+    // work: S half spectra; F = [delta, f_0 .. f_{S-1}] and its filtered copy Y, N^3 floats each
+    CK(grow(c->work, c->work_bytes, (size_t)S * N * N * H * sizeof(float2)), "window work buffer");
+    CK(grow(c->zfields, c->zfields_bytes, (size_t)2 * nf * n3 * sizeof(float)), "monopole fields");
+    float* F = reinterpret_cast<float*>(c->zfields);
+    float* Y = F + (size_t)nf * n3;
+    const int gb = ddd_gram_blocks(N, S);
+    const size_t npart = (size_t)gb * 3 * 64;
+    CK(grow_doubles(c->part, c->part_cap, npart), "partials");
+    const Tables tb = tables_of(c);
+    CK(cudaMemcpyAsync(F, c->grid, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy delta");
+    // f_b = iFT[delta^ <j_0>_b Phi^] / N^3: the l = 0 shell windows of the xi tables, bins 0 .. S-1
+    WinBatch wb;
+    wb.S = S;
+    wb.tab = c->rad;
+    wb.nbp = c->nbp;
+    wb.ell = 0;
+    wb.scale = 1.0f;
+    CK(launch_filtered_fields(N, c->spec, c->work, F + n3, wb, tb, st, c->tracer), "shell fields");
+    // knot cells [c + o, c + o + 1) (o = 0 for even p, -1/2 for odd p); a spline field at
+    // u = c + o + t reads the coefficients c + j0 + j, j < p, with weights M_p(t + o - j0 - j)
+    const int ng = ddd_samples(p);
+    double t[DDD_MAX_SAMPLES], w[DDD_MAX_SAMPLES], B[DDD_MAX_SAMPLES][8] = {};
+    gauss_legendre01(ng, t, w);
+    const double o = (p & 1) ? -0.5 : 0.0;
+    const int j0 = (p & 1) ? -(p - 1) / 2 : 1 - p / 2;
+    DddTaps tx{};
+    for (int a = 0; a < ng; ++a) {
+        for (int j = 0; j < p; ++j) {
+            B[a][j] = bspline_host(p, t[a] + o - j0 - j);
+            tx.bx[a][j] = (float)B[a][j];
+        }
+        tx.wx[a] = (float)w[a];
+    }
+    tx.j0 = j0;
+    CK(cudaMemsetAsync(c->part, 0, npart * sizeof(double), st), "clear partials");
+    for (int gz = 0; gz < ng; ++gz) {
+        for (int gy = 0; gy < ng; ++gy) {
+            DddYZ yz{};
+            for (int j = 0; j < p; ++j) {
+                yz.by[j] = (float)B[gy][j];
+                yz.bz[j] = (float)B[gz][j];
+            }
+            yz.j0 = j0;
+            CK(launch_ddd_filter_yz(N, p, F, Y, nf, yz, st, c->tracer), "sample filters");
+            tx.wyz = w[gy] * w[gz];
+            CK(launch_ddd_gram(N, p, Y, S, tx, c->part, st, c->tracer), "monopole Gram");
+        }
+    }
+    CK(ensure_host(c, npart) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
+    CK(cudaMemcpyAsync(c->host_buf, c->part, npart * sizeof(double), cudaMemcpyDeviceToHost, st), "read Gram");
+    CK(cudaStreamSynchronize(st), "monopole");
+    // tile t of {(0, 0), (0, 8), (8, 8)}, entry 8 a + b = bins (r0 + a, c0 + b)
+    static const int r0s[3] = {0, 0, 8}, c0s[3] = {0, 8, 8};
+    for (int i = 0; i < S * S; ++i) out[i] = 0.0;
+    for (int tl = 0; tl < 3; ++tl) {
+        for (int k = 0; k < 64; ++k) {
+            const int b1 = r0s[tl] + k / 8, b2 = c0s[tl] + k % 8;
+            if (b1 >= S || b2 >= S || (tl != 1 && b2 < b1)) continue;
+            double sum = 0.0;
+            for (int blk = 0; blk < gb; ++blk) sum += c->host_buf[((size_t)blk * 3 + tl) * 64 + k];
+            out[b1 * S + b2] = out[b2 * S + b1] = sum / (double)n3;
+        }
+    }
+    return HERMES_OK;
+}
+
 int hermes_zeta_multipoles(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
@@ -1219,7 +1333,8 @@ int hermes_debug_nodes(hermes_ctx* c, const float* host_pos, int64_t n, unsigned
 static const char* const kKernelNames[K_COUNT] = {
     "scatter", "weight_sums", "selfpair", "reduce", "finish_field", "fwd_z_r2c", "fwd_y", "fwd_x",
     "inv_x_window", "inv_y", "inv_z_c2r_contract", "zeta_x", "zeta_y", "zeta_z_gram", "nodes",
-    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms", "inv_z_store", "gather_marks", "wait_check"};
+    "inv_yz_contract", "zeta_z_gram_tc", "kspace_hist", "kspace_contract", "batch_graph", "selfpair_hist", "selfpair_contract", "combine_randoms", "inv_z_store", "gather_marks", "wait_check",
+    "ddd_filter", "ddd_gram"};
 
 int hermes_trace_enable(hermes_ctx* c, int on) {
     if (check_ctx(c)) return HERMES_ERR_ARG;

@@ -16,7 +16,7 @@ constexpr int STAB_STRIDE = 512;
 // Kernel classes reported by the tracer.
 enum KernelId {
     K_SCATTER = 0, K_WEIGHT_SUMS, K_SELFPAIR, K_REDUCE, K_FINISH, K_FWD_Z_R2C, K_FWD_Y, K_FWD_X,
-    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_INV_Z_STORE, K_GATHER, K_WAIT_CHECK, K_COUNT
+    K_INV_X_WINDOW, K_INV_Y, K_INV_Z_C2R_CONTRACT, K_ZETA_X, K_ZETA_Y, K_ZETA_Z_GRAM, K_NODES, K_INV_YZ_CONTRACT, K_ZETA_Z_GRAM_TC, K_KSPACE_HIST, K_KSPACE_CONTRACT, K_BATCH_GRAPH, K_SN_HIST, K_SN_CONTRACT, K_COMBINE, K_INV_Z_STORE, K_GATHER, K_WAIT_CHECK, K_DDD_FILTER, K_DDD_GRAM, K_COUNT
 };
 
 // Called around every kernel launch (phase 0 before, 1 after) on the launching stream.
@@ -182,6 +182,36 @@ cudaError_t launch_kspace_contract(const float* rad, int nbp, int64_t Q, const K
 // wait_check.cu: one thread waits, with the bounded mbarrier wait of the bulk-copy
 // pipelines, on a barrier phase that nothing completes; err bit 4 marks the expiry
 cudaError_t launch_wait_unarrived(unsigned* err, cudaStream_t st, const Tracer& tr);
+
+// fft_passes.cu: the real filtered fields iFT(spec * K_s) / N^3 of a window batch
+// (wb.S <= 16 windows, tab 16-byte aligned) into out + s * N^3; work holds S half spectra
+cudaError_t launch_filtered_fields(int N, const float2* spec, float2* work, float* out, const WinBatch& wb,
+                                   const Tables& tb, cudaStream_t st, const Tracer& tr);
+
+// ddd.cu: the 3PCF monopole by triple connection coefficients, as an exact Gauss-Legendre
+// quadrature of the triple product of spline fields (n_g = ddd_samples(p) samples per axis
+// and knot cell; the sample t_g of cell c reads taps c + j0 + j, j < p, with weights b[g][j]).
+__host__ __device__ constexpr int ddd_samples(int p) { return (3 * p - 1) / 2; }
+constexpr int DDD_MAX_SAMPLES = 11;  // p = 8
+struct DddYZ {
+    float by[8], bz[8];  // the y and z taps of one (g_y, g_z) sample pair
+    int j0;
+};
+struct DddTaps {
+    float bx[DDD_MAX_SAMPLES][8];  // the x taps of every g_x
+    float wx[DDD_MAX_SAMPLES];     // the x Gauss weights
+    double wyz;                    // w_gy * w_gz
+    int j0;
+};
+// Y_f = the y and z filters of nf fields of N^3 (in and out [nf][N][N][N])
+cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
+                                 cudaStream_t st, const Tracer& tr);
+// the x filters and the weighted Gram of Y = [delta, f_0 .. f_{S-1}] (S <= 16, N >= 16),
+// added into part [ddd_gram_blocks(N, S)][3][64]: tile t of {(0, 0), (0, 8), (8, 8)}, entry
+// 8 a + b = bins (r0 + a, c0 + b) (upper triangle on the diagonal tiles), times wyz
+int ddd_gram_blocks(int N, int S);
+cudaError_t launch_ddd_gram(int N, int p, const float* Y, int S, const DddTaps& tp, double* part, cudaStream_t st,
+                            const Tracer& tr);
 
 // zeta.cu
 int zeta_z_blocks(int N);

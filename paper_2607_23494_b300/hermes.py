@@ -81,6 +81,7 @@ def _load() -> C.CDLL:
         "hermes_batch_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64), dp, i32, C.POINTER(i32)]),
         "hermes_zeta_multipoles": (i32, [vp, dp]),
+        "hermes_ddd_monopole": (i32, [vp, dp]),
         "hermes_window_cylinders": (i32, [vp, dp, i32, dp, i32, C.c_double]),
         "hermes_xi_cylinders": (i32, [vp, dp]),
         "hermes_xi_cylinders_kspace": (i32, [vp, dp]),
@@ -405,6 +406,13 @@ class Context:
     def zeta_multipoles(self) -> np.ndarray:
         out = np.empty((self.l_max + 1, self.n_bins, self.n_bins), dtype=np.float64)
         self._check(_lib.hermes_zeta_multipoles(self._h, _dptr(out)), "hermes_zeta_multipoles")
+        return out
+
+    def ddd_monopole(self) -> np.ndarray:
+        """hermes_ddd_monopole: the 3PCF monopole DDD(b1, b2) by triple connection
+        coefficients, [n_bins, n_bins] (at most 16 bins)."""
+        out = np.empty((self.n_bins, self.n_bins), dtype=np.float64)
+        self._check(_lib.hermes_ddd_monopole(self._h, _dptr(out)), "hermes_ddd_monopole")
         return out
 
     # tracing
