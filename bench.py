@@ -901,6 +901,22 @@ def run_zeta(args, dev, stream, rank):
     stream.synchronize()
     ms = e0.elapsed_time(e1) / zsteps
     tr = ctx.trace_read()
+    # the 3PCF monopole by triple connection coefficients (hermes_ddd_monopole) on the same field
+    # and shells, against the cell-sum zeta_0 of the step (they differ by the basis smoothing)
+    ctx.window_shells(EDGES3, l_max=0)
+    ctx.ddd_monopole()  # buffers
+    torch.cuda.synchronize()
+    ctx.trace(True)
+    e0.record(stream)
+    dm = ctx.ddd_monopole()
+    e1.record(stream)
+    stream.synchronize()
+    trd = ctx.trace_read()
+    ddd_cc = {"workload": "DDD(b1, b2) monopole by triple connection coefficients, the zeta_l field, 512^3, p=4, "
+                          "16 shells [10,170): 125 Gauss samples per cell",
+              "ms": round(e0.elapsed_time(e1), 2),
+              "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in trd.items()},
+              "diag_ratio_to_zeta0": [round(float(dm[b, b] / z[0, b, b]), 4) for b in range(dm.shape[0])]}
     ctx.close()
     # the paper's DDD_l(20, 40) runs (its performance table: one (r12, r13) pair at l_max 7, 14
     # and 20, J = 9 i.e. 512^3): two 2 Mpc/h shells at 20 and 40 Mpc/h on the same field
@@ -954,7 +970,7 @@ def run_zeta(args, dev, stream, rank):
             "ms_per_step": round(ms, 2), "complex_fields": nfields, "complex_transforms": ntrans,
             "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
             "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])],
-            "ddd_l_20_40": ddd, "_z128": z128}
+            "ddd_l_20_40": ddd, "ddd_monopole_cc": ddd_cc, "_z128": z128}
 
 
 def oracle_sample(pos, b: int = 0):
