@@ -29,17 +29,18 @@ namespace hermes {
 
 namespace {
 
-// Tiles of 32 y x 32 z outputs of one (field, x) plane (16 x 16 at N = 16): the
+// Tiles of T y x T z outputs of one (field, x) plane (T = 64, or N below 64): the
 // (T + P - 1)^2 inputs (periodic) staged once in shared memory by unrolled loads (several in
 // flight per thread), filtered along z into a second stage, then along y.
-template <int P>
+template <int P, int T>
 __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__ in, float* __restrict__ out,
-                                                       int lgN, int lgT, const __grid_constant__ DddYZ tp) {
-    constexpr int TM = 32, RM = TM + P - 1;
-    constexpr int LOADS = (RM * RM + 255) / 256;
+                                                       int lgN, const __grid_constant__ DddYZ tp) {
+    constexpr int R = T + P - 1, RM = R, TM = T;
+    constexpr int LOADS = (R * R + 255) / 256;
+    constexpr int lgT = T == 64 ? 6 : (T == 32 ? 5 : 4);
     __shared__ float s_in[RM][RM + 1];
     __shared__ float s_z[RM][TM + 1];
-    const int N = 1 << lgN, msk = N - 1, T = 1 << lgT, R = T + P - 1;
+    const int N = 1 << lgN, msk = N - 1;
     const int nt = N >> lgT;
     const size_t blk = blockIdx.x;
     const int tz = (int)(blk % nt), ty = (int)((blk / nt) % nt);
@@ -217,13 +218,18 @@ int ddd_gram_blocks(int N, int S) {
 cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
                                  cudaStream_t st, const Tracer& tr) {
     if (N < 16) return cudaErrorInvalidValue;
-    const int lgN = ilog2i(N), lgT = std::min(lgN, 5);
+    const int lgN = ilog2i(N), lgT = std::min(lgN, 6);
     const size_t nt = (size_t)N >> lgT;
     const size_t nblk = (size_t)nf * N * nt * nt;  // (field, x) planes x y tiles x z tiles
     if (nblk > 0x7fffffffULL) return cudaErrorInvalidValue;
     tr(K_DDD_FILTER, 0, st);
     switch (p) {
-#define C(P) case P: k_ddd_filter_yz<P><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, lgT, tp); break;
+#define C(P)                                                                                    \
+    case P:                                                                                     \
+        if (lgT == 6) k_ddd_filter_yz<P, 64><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, tp);   \
+        else if (lgT == 5) k_ddd_filter_yz<P, 32><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, tp); \
+        else k_ddd_filter_yz<P, 16><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, tp);            \
+        break;
         C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
 #undef C
         default: return cudaErrorInvalidValue;
