@@ -1088,6 +1088,23 @@ def run_profile_zeta(args):
     print(json.dumps({"profile_case": "zeta 256^3, 16 shells, l_max 1", "zeta00": float(z[0, 0, 0])}))
 
 
+def run_profile_ddd(args):
+    """Small case for ncu captures of the connection-coefficient monopole: 256^3 field of 200k
+    Poisson points, p = 4, 16 shells (about 3 GB on the device), two calls."""
+    import torch
+    from paper_2607_23494_b300 import Context
+    from synthetic import catalogues as S
+    pos = torch.from_numpy(S.poisson_uniform(200_000, L3, seed=9)).cuda()
+    ctx = Context(L3, 256, 4)
+    ctx.window_shells(np.linspace(10.0, 170.0, 17), l_max=0)
+    ctx.assign(pos)
+    for _ in range(2):
+        d = ctx.ddd_monopole()
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_case": "ddd monopole 256^3, 16 shells, p 4", "ddd00": float(d[0, 0])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1108,6 +1125,7 @@ def main():
                          "--no-zeta --no-cpu-baseline); for launch-list captures")
     ap.add_argument("--profile-case", action="store_true", help="small workload for ncu captures")
     ap.add_argument("--profile-zeta", action="store_true", help="small zeta workload for ncu captures")
+    ap.add_argument("--profile-ddd", action="store_true", help="small monopole workload for ncu captures")
     ap.add_argument("--y-variant", type=int, default=0, help="inverse y-pass variant of --profile-case")
     ap.add_argument("--x-variant", type=int, default=0, help="window-pass variant of --profile-case")
     ap.add_argument("--z-variant", type=int, default=0, help="contraction-pass variant of --profile-case")
@@ -1128,6 +1146,9 @@ def main():
         return 0
     if args.profile_zeta:
         run_profile_zeta(args)
+        return 0
+    if args.profile_ddd:
+        run_profile_ddd(args)
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
