@@ -356,10 +356,11 @@ int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
  * degree 3(p - 1) there).  With Gamma replaced by the identity stencil it is the cell
  * sum zeta_0 of hermes_zeta_multipoles; the two differ by the basis smoothing.
  * Returned raw (self triplets included), like zeta_l.
- *   out: [n_bins][n_bins] float64, symmetric.  n_bins: 1 .. 16.
- * Device memory: n_bins half spectra and 2 (n_bins + 1) real fields of N^3.
- * Errors: HERMES_ERR_ARG (out NULL, more than 16 bins), HERMES_ERR_STATE (no field,
- * no bins, explicit randoms set), HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ *   out: [n_bins][n_bins] float64, symmetric.  Up to 16 bins form one Gram; more run
+ *   every pair of 8-bin blocks (B (B + 1) / 2 runs for B blocks).
+ * Device memory: min(n_bins, 16) half spectra and 2 (n_bins + 1) real fields of N^3.
+ * Errors: HERMES_ERR_ARG (out NULL), HERMES_ERR_STATE (no field, no bins, explicit
+ * randoms set), HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
  */
 int hermes_ddd_monopole(hermes_ctx *ctx, double *out);
 

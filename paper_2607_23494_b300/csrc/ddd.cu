@@ -79,25 +79,33 @@ __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__
     }
 }
 
-// Down 32 (y, z) columns per task, for x = 0 .. N-1: warp w x-filters fields w, w + nw, ...
-// (delta and the S shell fields) at every sample g_x from its sliding windows of P taps and
-// stages the values in shared memory (double-buffered, one barrier per cell); then warp w
-// adds w_gx D F_b1 F_b2 into its tile of the Gram: {(0, 0), (0, 8), (8, 8)} for three warps
-// (S > 8), (0, 0) for one.  Rows of fields beyond S stay zero.
+// Down 32 (y, z) columns per task, for x = 0 .. N-1: warp w x-filters field slots w, w + nw,
+// ... (delta, the row block's bins, the column block's) at every sample g_x from its sliding
+// windows of P taps and stages the values in shared memory (double-buffered, one barrier per
+// cell); then warp w adds w_gx D F_b1 F_b2 into its tile of the Gram.  Empty slots stay zero.
 template <int P, int NW>
-__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const float* __restrict__ Y, int S, int lgN,
+__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const float* __restrict__ Y, int lgN,
                                                                       const __grid_constant__ DddTaps tp,
                                                                       double* __restrict__ part) {
-    constexpr int NG = ddd_samples(P), FPW = (17 + NW - 1) / NW;  // fields filtered per warp, at most
+    constexpr int NG = ddd_samples(P), FPW = (17 + NW - 1) / NW;  // slots filtered per warp, at most
     constexpr int nw = NW;
     __shared__ float s_v[2][NG][17][32];
     const int N = 1 << lgN, msk = N - 1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const size_t n3 = (size_t)1 << (3 * lgN);
-    const int nf = S + 1;
+    constexpr int nf = 17;
     for (int e = threadIdx.x; e < 2 * NG * 17 * 32; e += blockDim.x) (&s_v[0][0][0][0])[e] = 0.0f;
-    const int tile = nw == 1 ? 0 : w;
+    const int tile = nw == 1 ? tp.tile0 : w;      // 0 (rows, rows), 1 (rows, columns), 2 (columns, columns)
+    const int slot_out = nw == 1 ? 0 : w;         // where the tile's entries are written
     const int r0 = tile == 2 ? 8 : 0, c0 = tile == 0 ? 0 : 8;
     const bool diag = tile != 1;
+    // the Y offsets of the slots this warp filters (-1: empty), fixed for the kernel
+    long long foff[FPW];
+#pragma unroll
+    for (int k = 0; k < FPW; ++k) {
+        const int f = w + k * nw;
+        const int fi = f < nf ? tp.fld[f] : -1;
+        foff[k] = fi >= 0 ? (long long)fi * (long long)n3 : -1;
+    }
     double d0 = 0.0, d1 = 0.0;
     int buf = 0;
     const int ntask = (N * N) >> 5;
@@ -107,10 +115,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
         float t[FPW][P];
 #pragma unroll
         for (int k = 0; k < FPW; ++k) {
-            const int f = w + k * nw;
 #pragma unroll
             for (int j = 0; j < P; ++j)
-                t[k][j] = f < nf ? __ldg(col + (size_t)f * n3 + ((size_t)((tp.j0 + j) & msk) << (2 * lgN))) : 0.0f;
+                t[k][j] = foff[k] >= 0 ? __ldg(col + foff[k] + ((size_t)((tp.j0 + j) & msk) << (2 * lgN))) : 0.0f;
         }
         float acc[64];
 #pragma unroll
@@ -119,14 +126,11 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
             float nxt[FPW];  // the tap entering each window at x + 1, in flight during this cell
             const size_t xn = (size_t)((x + 1 + tp.j0 + P - 1) & msk) << (2 * lgN);
 #pragma unroll
-            for (int k = 0; k < FPW; ++k) {
-                const int f = w + k * nw;
-                nxt[k] = f < nf ? __ldg(col + (size_t)f * n3 + xn) : 0.0f;
-            }
+            for (int k = 0; k < FPW; ++k) nxt[k] = foff[k] >= 0 ? __ldg(col + foff[k] + xn) : 0.0f;
 #pragma unroll
             for (int k = 0; k < FPW; ++k) {
                 const int f = w + k * nw;
-                if (f < nf) {
+                if (foff[k] >= 0) {
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
                         float v = 0.0f;
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
         }
     }
     // accumulate over the (g_z, g_y) launches: each (block, tile, entry) has one owner
-    double* row = part + ((size_t)blockIdx.x * 3 + tile) * 64;
+    double* row = part + ((size_t)blockIdx.x * 3 + slot_out) * 64;
     row[lane] += d0 * tp.wyz;
     row[32 + lane] += d1 * tp.wyz;
 }
@@ -209,10 +213,10 @@ int sm_count_ddd() {
 
 }  // namespace
 
-int ddd_gram_blocks(int N, int S) {
+int ddd_gram_blocks(int N, int nw) {
     // the blocks per SM the two forms are compiled for (3 warps: 4, one warp: 8); never more
     // blocks than 32-column tasks
-    return std::max(1, std::min((S <= 8 ? 8 : 4) * sm_count_ddd(), (N * N) / 32));
+    return std::max(1, std::min((nw == 1 ? 8 : 4) * sm_count_ddd(), (N * N) / 32));
 }
 
 cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
@@ -238,17 +242,17 @@ cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ddd_gram(int N, int p, const float* Y, int S, const DddTaps& tp, double* part, cudaStream_t st,
+cudaError_t launch_ddd_gram(int N, int p, const float* Y, int nw, const DddTaps& tp, double* part, cudaStream_t st,
                             const Tracer& tr) {
-    if (S < 1 || S > 16 || N < 16) return cudaErrorInvalidValue;
+    if ((nw != 1 && nw != 3) || N < 16 || tp.fld[0] < 0) return cudaErrorInvalidValue;
     const int lgN = ilog2i(N);
-    const int nblk = ddd_gram_blocks(N, S);
+    const int nblk = ddd_gram_blocks(N, nw);
     tr(K_DDD_GRAM, 0, st);
     switch (p) {
-#define C(P)                                                                         \
-    case P:                                                                          \
-        if (S <= 8) k_ddd_gram<P, 1><<<nblk, 32, 0, st>>>(Y, S, lgN, tp, part);      \
-        else k_ddd_gram<P, 3><<<nblk, 96, 0, st>>>(Y, S, lgN, tp, part);             \
+#define C(P)                                                                      \
+    case P:                                                                       \
+        if (nw == 1) k_ddd_gram<P, 1><<<nblk, 32, 0, st>>>(Y, lgN, tp, part);      \
+        else k_ddd_gram<P, 3><<<nblk, 96, 0, st>>>(Y, lgN, tp, part);             \
         break;
         C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
 #undef C

@@ -1089,30 +1089,49 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
                                          "hermes_assign first");
     if (!c->have_field) return fail(c, HERMES_ERR_STATE, "no field: call hermes_assign first");
     if (c->n_bins < 1) return fail(c, HERMES_ERR_STATE, "no bins: call hermes_window_shells first");
-    if (c->n_bins > 16) return fail(c, HERMES_ERR_ARG, "the monopole takes at most 16 bins (%d set)", c->n_bins);
     DeviceGuard g(c->device);
     AllocStream as_(c->stream);
     cudaStream_t st = c->stream;
-    const int N = c->N, H = c->H, S = c->n_bins, p = c->p, nf = S + 1;
+    const int N = c->N, H = c->H, nb = c->n_bins, p = c->p, nf = nb + 1;
     const size_t n3 = (size_t)N * N * N;
-    // work: S half spectra; F = [delta, f_0 .. f_{S-1}] and its filtered copy Y, N^3 floats each
-    CK(grow(c->work, c->work_bytes, (size_t)S * N * N * H * sizeof(float2)), "window work buffer");
+    // The Gram runs over field-slot sets of delta and up to 16 bins: all bins at once (three
+    // warps, tiles (0-7, 0-7), (0-7, 8-15), (8-15, 8-15)) up to 16 bins; beyond, one run per
+    // pair of 8-bin blocks I <= J (one warp: the upper triangle of block I, or the block (I, J)).
+    struct Run {
+        int nw, I, J, tile0;
+    };
+    std::vector<Run> runs;
+    if (nb <= 16) {
+        runs.push_back({nb <= 8 ? 1 : 3, 0, 1, 0});
+    } else {
+        const int B = (nb + 7) / 8;
+        for (int I = 0; I < B; ++I)
+            for (int J = I; J < B; ++J) runs.push_back({1, I, J, I == J ? 0 : 1});
+    }
+    std::vector<size_t> part_off(runs.size() + 1, 0);
+    for (size_t r = 0; r < runs.size(); ++r)
+        part_off[r + 1] = part_off[r] + (size_t)ddd_gram_blocks(N, runs[r].nw) * 3 * 64;
+    const size_t npart = part_off.back();
+    // work: up to 16 half spectra; F = [delta, f_0 .. f_{nb-1}] and its filtered copy Y, N^3 floats each
+    const int wmax = std::min(nb, 16);
+    CK(grow(c->work, c->work_bytes, (size_t)wmax * N * N * H * sizeof(float2)), "window work buffer");
     CK(grow(c->zfields, c->zfields_bytes, (size_t)2 * nf * n3 * sizeof(float)), "monopole fields");
     float* F = reinterpret_cast<float*>(c->zfields);
     float* Y = F + (size_t)nf * n3;
-    const int gb = ddd_gram_blocks(N, S);
-    const size_t npart = (size_t)gb * 3 * 64;
     CK(grow_doubles(c->part, c->part_cap, npart), "partials");
     const Tables tb = tables_of(c);
     CK(cudaMemcpyAsync(F, c->grid, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy delta");
-    // f_b = iFT[delta^ <j_0>_b Phi^] / N^3: the l = 0 shell windows of the xi tables, bins 0 .. S-1
-    WinBatch wb;
-    wb.S = S;
-    wb.tab = c->rad;
-    wb.nbp = c->nbp;
-    wb.ell = 0;
-    wb.scale = 1.0f;
-    CK(launch_filtered_fields(N, c->spec, c->work, F + n3, wb, tb, st, c->tracer), "shell fields");
+    // f_b = iFT[delta^ <j_0>_b Phi^] / N^3: the l = 0 shell windows of the xi tables, 16 bins a batch
+    for (int b0 = 0; b0 < nb; b0 += 16) {
+        WinBatch wb;
+        wb.S = std::min(16, nb - b0);
+        wb.tab = c->rad + b0;
+        wb.nbp = c->nbp;
+        wb.ell = 0;
+        wb.scale = 1.0f;
+        CK(launch_filtered_fields(N, c->spec, c->work, F + (size_t)(1 + b0) * n3, wb, tb, st, c->tracer),
+           "shell fields");
+    }
     // knot cells [c + o, c + o + 1) (o = 0 for even p, -1/2 for odd p); a spline field at
     // u = c + o + t reads the coefficients c + j0 + j, j < p, with weights M_p(t + o - j0 - j)
     const int ng = ddd_samples(p);
@@ -1120,15 +1139,26 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     gauss_legendre01(ng, t, w);
     const double o = (p & 1) ? -0.5 : 0.0;
     const int j0 = (p & 1) ? -(p - 1) / 2 : 1 - p / 2;
-    DddTaps tx{};
-    for (int a = 0; a < ng; ++a) {
-        for (int j = 0; j < p; ++j) {
-            B[a][j] = bspline_host(p, t[a] + o - j0 - j);
-            tx.bx[a][j] = (float)B[a][j];
+    std::vector<DddTaps> tx(runs.size());
+    for (size_t r = 0; r < runs.size(); ++r) {
+        DddTaps& d = tx[r];
+        d = DddTaps{};
+        for (int a = 0; a < ng; ++a) {
+            for (int j = 0; j < p; ++j) {
+                B[a][j] = bspline_host(p, t[a] + o - j0 - j);
+                d.bx[a][j] = (float)B[a][j];
+            }
+            d.wx[a] = (float)w[a];
         }
-        tx.wx[a] = (float)w[a];
+        d.j0 = j0;
+        d.tile0 = runs[r].tile0;
+        d.fld[0] = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int br = 8 * runs[r].I + k, bc = 8 * runs[r].J + k;
+            d.fld[1 + k] = br < nb ? 1 + br : -1;
+            d.fld[9 + k] = (bc < nb && (runs[r].nw == 3 || runs[r].tile0 == 1)) ? 1 + bc : -1;
+        }
     }
-    tx.j0 = j0;
     CK(cudaMemsetAsync(c->part, 0, npart * sizeof(double), st), "clear partials");
     for (int gz = 0; gz < ng; ++gz) {
         for (int gy = 0; gy < ng; ++gy) {
@@ -1139,23 +1169,33 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
             }
             yz.j0 = j0;
             CK(launch_ddd_filter_yz(N, p, F, Y, nf, yz, st, c->tracer), "sample filters");
-            tx.wyz = w[gy] * w[gz];
-            CK(launch_ddd_gram(N, p, Y, S, tx, c->part, st, c->tracer), "monopole Gram");
+            for (size_t r = 0; r < runs.size(); ++r) {
+                tx[r].wyz = w[gy] * w[gz];
+                CK(launch_ddd_gram(N, p, Y, runs[r].nw, tx[r], c->part + part_off[r], st, c->tracer),
+                   "monopole Gram");
+            }
         }
     }
     CK(ensure_host(c, npart) == HERMES_OK ? cudaSuccess : cudaErrorMemoryAllocation, "host buffer");
     CK(cudaMemcpyAsync(c->host_buf, c->part, npart * sizeof(double), cudaMemcpyDeviceToHost, st), "read Gram");
     CK(cudaStreamSynchronize(st), "monopole");
-    // tile t of {(0, 0), (0, 8), (8, 8)}, entry 8 a + b = bins (r0 + a, c0 + b)
-    static const int r0s[3] = {0, 0, 8}, c0s[3] = {0, 8, 8};
-    for (int i = 0; i < S * S; ++i) out[i] = 0.0;
-    for (int tl = 0; tl < 3; ++tl) {
-        for (int k = 0; k < 64; ++k) {
-            const int b1 = r0s[tl] + k / 8, b2 = c0s[tl] + k % 8;
-            if (b1 >= S || b2 >= S || (tl != 1 && b2 < b1)) continue;
-            double sum = 0.0;
-            for (int blk = 0; blk < gb; ++blk) sum += c->host_buf[((size_t)blk * 3 + tl) * 64 + k];
-            out[b1 * S + b2] = out[b2 * S + b1] = sum / (double)n3;
+    for (int i = 0; i < nb * nb; ++i) out[i] = 0.0;
+    for (size_t r = 0; r < runs.size(); ++r) {
+        const int gb = ddd_gram_blocks(N, runs[r].nw);
+        const int ntile = runs[r].nw == 3 ? 3 : 1;
+        for (int ts = 0; ts < ntile; ++ts) {
+            // tile (row block, column block) of entries 8 a + b
+            const int tile = runs[r].nw == 3 ? ts : runs[r].tile0;
+            const int rb = runs[r].nw == 3 ? (tile == 2 ? 1 : 0) : runs[r].I;
+            const int cbk = runs[r].nw == 3 ? (tile == 0 ? 0 : 1) : (tile == 0 ? runs[r].I : runs[r].J);
+            const bool diag = tile != 1;
+            for (int k = 0; k < 64; ++k) {
+                const int b1 = 8 * rb + k / 8, b2 = 8 * cbk + k % 8;
+                if (b1 >= nb || b2 >= nb || (diag && k % 8 < k / 8)) continue;
+                double sum = 0.0;
+                for (int blk = 0; blk < gb; ++blk) sum += c->host_buf[part_off[r] + ((size_t)blk * 3 + ts) * 64 + k];
+                out[b1 * nb + b2] = out[b2 * nb + b1] = sum / (double)n3;
+            }
         }
     }
     return HERMES_OK;

@@ -202,15 +202,20 @@ struct DddTaps {
     float wx[DDD_MAX_SAMPLES];     // the x Gauss weights
     double wyz;                    // w_gy * w_gz
     int j0;
+    // the Gram's 17 field slots: slot 0 delta, slots 1..8 the row block's bins, 9..16 the
+    // column block's; fld[slot] = the field's index in Y, -1 for an empty slot
+    int fld[17];
+    int tile0;  // one warp per block: its tile, 0 = (rows, rows) upper triangle, 1 = (rows, columns)
 };
 // Y_f = the y and z filters of nf fields of N^3 (in and out [nf][N][N][N])
 cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
                                  cudaStream_t st, const Tracer& tr);
-// the x filters and the weighted Gram of Y = [delta, f_0 .. f_{S-1}] (S <= 16, N >= 16),
-// added into part [ddd_gram_blocks(N, S)][3][64]: tile t of {(0, 0), (0, 8), (8, 8)}, entry
-// 8 a + b = bins (r0 + a, c0 + b) (upper triangle on the diagonal tiles), times wyz
-int ddd_gram_blocks(int N, int S);
-cudaError_t launch_ddd_gram(int N, int p, const float* Y, int S, const DddTaps& tp, double* part, cudaStream_t st,
+// the x filters and the weighted Gram of the fields tp.fld of Y (N >= 16), added into part
+// [ddd_gram_blocks(N, nw)][3][64], times wyz.  nw = 3: tiles {(rows, rows), (rows, columns),
+// (columns, columns)} in tiles 0, 1, 2; nw = 1: tile tp.tile0 alone, in tile 0.  Entry 8 a + b
+// of a tile = slots (row a, column b); the diagonal tiles keep the upper triangle.
+int ddd_gram_blocks(int N, int nw);
+cudaError_t launch_ddd_gram(int N, int p, const float* Y, int nw, const DddTaps& tp, double* part, cudaStream_t st,
                             const Tracer& tr);
 
 // zeta.cu

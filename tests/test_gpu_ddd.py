@@ -31,9 +31,10 @@ def _close(got, ref, rel=REL, ab=ABS):
 
 
 @pytest.mark.parametrize("N,p,L,nb", [(16, 2, 120.0, 4), (16, 3, 120.0, 10), (16, 4, 120.0, 16), (32, 4, 200.0, 5),
-                                      (32, 1, 200.0, 3)])
+                                      (32, 1, 200.0, 3), (16, 4, 120.0, 17), (16, 3, 120.0, 27)])
 def test_monopole_matches_the_oracle_stencil(N, p, L, nb):
-    # nb > 8 runs the off-diagonal bin tile; 10 and 5 leave ragged tiles
+    # nb > 8 runs the off-diagonal bin tile; 10 and 5 leave ragged tiles; more than 16 bins run
+    # every pair of 8-bin blocks (17: a one-bin block; 27: four blocks, the last of three bins)
     H = _hermes()
     pos = S.lognormal_catalogue(6000 if N == 16 else 20000, L, seed=N + p, n_grid=16)
     w = S.lognormal_masses(pos.shape[0], seed=7 * p)
@@ -99,7 +100,7 @@ def test_monopole_errors():
             ctx.ddd_monopole()
         assert ei.value.code == H.ERR_STATE                       # no field yet
         ctx.assign(S.poisson_uniform(2000, L, seed=1))
-        ctx.window_shells(np.linspace(5.0, 45.0, 18), l_max=0)     # 17 bins
+        ctx.assign_randoms(S.poisson_uniform(4000, L, seed=2))
         with pytest.raises(H.HermesError) as ei:
             ctx.ddd_monopole()
-        assert ei.value.code == H.ERR_ARG
+        assert ei.value.code == H.ERR_STATE                       # explicit randoms set
