@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__
 // windows of P taps and stages the values in shared memory (double-buffered, one barrier per
 // cell); then warp w adds w_gx D F_b1 F_b2 into its tile of the Gram.  Empty slots stay zero.
 template <int P, int NW>
-__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const float* __restrict__ Y, int lgN,
+__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : (NW == 2 ? 6 : 8)) k_ddd_gram(const float* __restrict__ Y,
+                                                                                     int lgN,
                                                                       const __grid_constant__ DddTaps tp,
                                                                       double* __restrict__ part) {
     constexpr int NG = ddd_samples(P), FPW = (17 + NW - 1) / NW;  // slots filtered per warp, at most
@@ -94,8 +95,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
     const size_t n3 = (size_t)1 << (3 * lgN);
     constexpr int nf = 17;
     for (int e = threadIdx.x; e < 2 * NG * 17 * 32; e += blockDim.x) (&s_v[0][0][0][0])[e] = 0.0f;
-    const int tile = nw == 1 ? tp.tile0 : w;      // 0 (rows, rows), 1 (rows, columns), 2 (columns, columns)
-    const int slot_out = nw == 1 ? 0 : w;         // where the tile's entries are written
+    // 0 (rows, rows), 1 (rows, columns), 2 (columns, columns).  Two warps: warp w takes the
+    // diagonal tile 2w and the columns 4w .. 4w + 3 of tile 1 (equal work per warp).
+    const int tile = nw == 1 ? tp.tile0 : (nw == 2 ? 2 * w : w);
+    const int slot_out = nw == 1 ? 0 : tile;      // where the tile's entries are written
     const int r0 = tile == 2 ? 8 : 0, c0 = tile == 0 ? 0 : 8;
     const bool diag = tile != 1;
     // the Y offsets of the slots this warp filters (-1: empty), fixed for the kernel
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
         const int fi = f < nf ? tp.fld[f] : -1;
         foff[k] = fi >= 0 ? (long long)fi * (long long)n3 : -1;
     }
-    double d0 = 0.0, d1 = 0.0;
+    double d0 = 0.0, d1 = 0.0, e0 = 0.0, e1 = 0.0;  // e: the half of tile 1 (two warps)
     int buf = 0;
     const int ntask = (N * N) >> 5;
     __syncthreads();
@@ -122,6 +125,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
         float acc[64];
 #pragma unroll
         for (int k = 0; k < 64; ++k) acc[k] = 0.0f;
+        float acc2[NW == 2 ? 32 : 1];
+#pragma unroll
+        for (int k = 0; k < (NW == 2 ? 32 : 1); ++k) acc2[k] = 0.0f;
         for (int x = 0; x < N; ++x) {
             float nxt[FPW];  // the tap entering each window at x + 1, in flight during this cell
             const size_t xn = (size_t)((x + 1 + tp.j0 + P - 1) & msk) << (2 * lgN);
@@ -154,6 +160,17 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
                         for (int b2 = a2; b2 < 8; ++b2)
                             acc[a2 * 8 + b2] = fmaf(vr[a2], s_v[buf][g][1 + r0 + b2][lane], acc[a2 * 8 + b2]);
                     }
+                    if constexpr (NW == 2) {  // rows 1..8 x columns 9 + 4w .. 12 + 4w
+                        float vcb[4];
+#pragma unroll
+                        for (int b2 = 0; b2 < 4; ++b2) vcb[b2] = s_v[buf][g][9 + 4 * w + b2][lane];
+#pragma unroll
+                        for (int a2 = 0; a2 < 8; ++a2) {
+                            const float hr = w == 0 ? vr[a2] : h * s_v[buf][g][1 + a2][lane];
+#pragma unroll
+                            for (int b2 = 0; b2 < 4; ++b2) acc2[a2 * 4 + b2] = fmaf(hr, vcb[b2], acc2[a2 * 4 + b2]);
+                        }
+                    }
                 } else {
                     float vc[8];
 #pragma unroll
@@ -185,11 +202,29 @@ __global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : 8) k_ddd_gram(const flo
                 else d1 += (double)sum;
             }
         }
+        if constexpr (NW == 2) {  // entry 8 a + 4 w + b of tile 1
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) {
+                float sum = acc2[k2];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                const int k = 8 * (k2 / 4) + 4 * w + (k2 % 4);
+                if (lane == (k & 31)) {
+                    if (k < 32) e0 += (double)sum;
+                    else e1 += (double)sum;
+                }
+            }
+        }
     }
     // accumulate over the (g_z, g_y) launches: each (block, tile, entry) has one owner
     double* row = part + ((size_t)blockIdx.x * 3 + slot_out) * 64;
     row[lane] += d0 * tp.wyz;
     row[32 + lane] += d1 * tp.wyz;
+    if (NW == 2 && ((lane & 7) >> 2) == w) {  // entries lane and lane + 32 of tile 1 are this warp's
+        double* r1 = part + ((size_t)blockIdx.x * 3 + 1) * 64;
+        r1[lane] += e0 * tp.wyz;
+        r1[32 + lane] += e1 * tp.wyz;
+    }
 }
 
 int ilog2i(int n) {
@@ -216,7 +251,7 @@ int sm_count_ddd() {
 int ddd_gram_blocks(int N, int nw) {
     // the blocks per SM the two forms are compiled for (3 warps: 4, one warp: 8); never more
     // blocks than 32-column tasks
-    return std::max(1, std::min((nw == 1 ? 8 : 4) * sm_count_ddd(), (N * N) / 32));
+    return std::max(1, std::min((nw == 1 ? 8 : (nw == 2 ? 6 : 4)) * sm_count_ddd(), (N * N) / 32));
 }
 
 cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int nf, const DddYZ& tp,
@@ -244,7 +279,7 @@ cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int 
 
 cudaError_t launch_ddd_gram(int N, int p, const float* Y, int nw, const DddTaps& tp, double* part, cudaStream_t st,
                             const Tracer& tr) {
-    if ((nw != 1 && nw != 3) || N < 16 || tp.fld[0] < 0) return cudaErrorInvalidValue;
+    if (nw < 1 || nw > 3 || N < 16 || tp.fld[0] < 0) return cudaErrorInvalidValue;
     const int lgN = ilog2i(N);
     const int nblk = ddd_gram_blocks(N, nw);
     tr(K_DDD_GRAM, 0, st);
@@ -252,6 +287,7 @@ cudaError_t launch_ddd_gram(int N, int p, const float* Y, int nw, const DddTaps&
 #define C(P)                                                                      \
     case P:                                                                       \
         if (nw == 1) k_ddd_gram<P, 1><<<nblk, 32, 0, st>>>(Y, lgN, tp, part);      \
+        else if (nw == 2) k_ddd_gram<P, 2><<<nblk, 64, 0, st>>>(Y, lgN, tp, part); \
         else k_ddd_gram<P, 3><<<nblk, 96, 0, st>>>(Y, lgN, tp, part);             \
         break;
         C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)

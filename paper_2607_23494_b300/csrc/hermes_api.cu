@@ -1081,6 +1081,13 @@ void gauss_legendre01(int n, double* t, double* w) {
 }
 }  // namespace
 
+// Warps per block of the monopole Gram for 9 to 16 bins: 2 (each a diagonal tile and half of
+// the off-diagonal one) unless HERMES_DDD_WARPS=3 (one tile per warp; kept for comparison).
+static int ddd_gram_warps() {
+    const char* e = getenv("HERMES_DDD_WARPS");
+    return (e && e[0] == '3') ? 3 : 2;
+}
+
 int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
@@ -1102,7 +1109,7 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     };
     std::vector<Run> runs;
     if (nb <= 16) {
-        runs.push_back({nb <= 8 ? 1 : 3, 0, 1, 0});
+        runs.push_back({nb <= 8 ? 1 : ddd_gram_warps(), 0, 1, 0});
     } else {
         const int B = (nb + 7) / 8;
         for (int I = 0; I < B; ++I)
@@ -1156,7 +1163,7 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
         for (int k = 0; k < 8; ++k) {
             const int br = 8 * runs[r].I + k, bc = 8 * runs[r].J + k;
             d.fld[1 + k] = br < nb ? 1 + br : -1;
-            d.fld[9 + k] = (bc < nb && (runs[r].nw == 3 || runs[r].tile0 == 1)) ? 1 + bc : -1;
+            d.fld[9 + k] = (bc < nb && (runs[r].nw > 1 || runs[r].tile0 == 1)) ? 1 + bc : -1;
         }
     }
     CK(cudaMemsetAsync(c->part, 0, npart * sizeof(double), st), "clear partials");
@@ -1182,12 +1189,13 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     for (int i = 0; i < nb * nb; ++i) out[i] = 0.0;
     for (size_t r = 0; r < runs.size(); ++r) {
         const int gb = ddd_gram_blocks(N, runs[r].nw);
-        const int ntile = runs[r].nw == 3 ? 3 : 1;
+        const bool all3 = runs[r].nw > 1;  // tiles 0, 1, 2 in slots 0, 1, 2
+        const int ntile = all3 ? 3 : 1;
         for (int ts = 0; ts < ntile; ++ts) {
             // tile (row block, column block) of entries 8 a + b
-            const int tile = runs[r].nw == 3 ? ts : runs[r].tile0;
-            const int rb = runs[r].nw == 3 ? (tile == 2 ? 1 : 0) : runs[r].I;
-            const int cbk = runs[r].nw == 3 ? (tile == 0 ? 0 : 1) : (tile == 0 ? runs[r].I : runs[r].J);
+            const int tile = all3 ? ts : runs[r].tile0;
+            const int rb = all3 ? (tile == 2 ? 1 : 0) : runs[r].I;
+            const int cbk = all3 ? (tile == 0 ? 0 : 1) : (tile == 0 ? runs[r].I : runs[r].J);
             const bool diag = tile != 1;
             for (int k = 0; k < 64; ++k) {
                 const int b1 = 8 * rb + k / 8, b2 = 8 * cbk + k % 8;
