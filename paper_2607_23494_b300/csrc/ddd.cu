@@ -31,15 +31,20 @@ namespace {
 
 // Tiles of T y x T z outputs of one (field, x) plane (T = 64, or N below 64): the
 // (T + P - 1)^2 inputs (periodic) staged once in shared memory by unrolled loads (several in
-// flight per thread), filtered along z into a second stage, then along y.
+// flight per thread), filtered along z into a second stage, then along y.  Each filter step
+// gives a thread a run of C outputs (C = T / 4) along its axis from a register window of
+// C + P - 1 stage values, about 1.2 shared loads per output; the odd row pitches put the 32
+// rows (z step) or columns (y step) of a warp on distinct banks.
 template <int P, int T>
 __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__ in, float* __restrict__ out,
                                                        int lgN, const __grid_constant__ DddYZ tp) {
-    constexpr int R = T + P - 1, RM = R, TM = T;
+    constexpr int R = T + P - 1;
+    constexpr int PIN = R | 1, PZ = T | 1;  // odd pitches
+    constexpr int C = T / 4, NCH = 4;       // run length and runs per row / column
     constexpr int LOADS = (R * R + 255) / 256;
     constexpr int lgT = T == 64 ? 6 : (T == 32 ? 5 : 4);
-    __shared__ float s_in[RM][RM + 1];
-    __shared__ float s_z[RM][TM + 1];
+    __shared__ float s_in[R][PIN];
+    __shared__ float s_z[R][PZ];
     const int N = 1 << lgN, msk = N - 1;
     const int nt = N >> lgT;
     const size_t blk = blockIdx.x;
@@ -61,21 +66,35 @@ __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__
         if (e < R * R) s_in[r][c] = v[k];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < R * T; e += 256) {
-        const int r = e >> lgT, c = e & (T - 1);
-        float acc = 0.0f;
+    // along z: run (r, ch) = outputs ch*C .. ch*C + C - 1 of stage row r; consecutive threads, consecutive rows
+    for (int e = threadIdx.x; e < R * NCH; e += 256) {
+        const int r = e % R, ch = e / R;
+        float w[C + P - 1];
 #pragma unroll
-        for (int j = 0; j < P; ++j) acc = fmaf(tp.bz[j], s_in[r][c + j], acc);
-        s_z[r][c] = acc;
+        for (int q = 0; q < C + P - 1; ++q) w[q] = s_in[r][ch * C + q];
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) acc = fmaf(tp.bz[j], w[q + j], acc);
+            s_z[r][ch * C + q] = acc;
+        }
     }
     __syncthreads();
+    // along y: run (c, ch) = output rows ch*C .. ch*C + C - 1 of column c; consecutive threads, consecutive columns
     float* dst = out + (plane << (2 * lgN));
-    for (int e = threadIdx.x; e < T * T; e += 256) {
-        const int r = e >> lgT, c = e & (T - 1);
-        float acc = 0.0f;
+    for (int e = threadIdx.x; e < T * NCH; e += 256) {
+        const int c = e % T, ch = e / T;
+        float w[C + P - 1];
 #pragma unroll
-        for (int j = 0; j < P; ++j) acc = fmaf(tp.by[j], s_z[r + j][c], acc);
-        dst[((size_t)(y0 + r) << lgN) + z0 + c] = acc;
+        for (int q = 0; q < C + P - 1; ++q) w[q] = s_z[ch * C + q][c];
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) acc = fmaf(tp.by[j], w[q + j], acc);
+            dst[((size_t)(y0 + ch * C + q) << lgN) + z0 + c] = acc;
+        }
     }
 }
 
