@@ -14,13 +14,15 @@
 // sample t_g of cell c is a p-tap filter along each axis, sum_j B_g[j] f(c + j0 + j).
 //
 // For every sample pair (g_z, g_y):
-//   k_ddd_filter_yz: Y_f = the y and z filters of every field (delta and the S shell fields),
+//   k_ddd_filter_yz: Y_f = the y and z filters of every field (delta and the shell fields),
 //                    separable through shared memory;
 //   k_ddd_gram     : down each (y, z) column, the x filters at every g_x (each field once per
 //                    cell, from a sliding window of p x-taps in registers, shared through
 //                    shared memory), then the weighted Gram sum_gx w_g D F_b1 F_b2 on 8 x 8 bin
-//                    tiles (one warp per tile), in float32 over one column (N cells x n_g
-//                    samples), then float64.
+//                    tiles, in float32 over one column (N cells x n_g samples), then float64.
+//                    Up to 16 bins: two warps, each a diagonal tile and half of the off-
+//                    diagonal one (three warps of one tile each, or one warp for up to 8 bins);
+//                    more bins: one warp per pair of 8-bin blocks, the fields named by slot.
 #include "kernels.h"
 
 #include <algorithm>
@@ -103,10 +105,8 @@ __global__ void __launch_bounds__(256) k_ddd_filter_yz(const float* __restrict__
 // windows of P taps and stages the values in shared memory (double-buffered, one barrier per
 // cell); then warp w adds w_gx D F_b1 F_b2 into its tile of the Gram.  Empty slots stay zero.
 template <int P, int NW>
-__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : (NW == 2 ? 6 : 8)) k_ddd_gram(const float* __restrict__ Y,
-                                                                                     int lgN,
-                                                                      const __grid_constant__ DddTaps tp,
-                                                                      double* __restrict__ part) {
+__global__ void __launch_bounds__(32 * NW, NW == 3 ? 4 : (NW == 2 ? 6 : 8))
+    k_ddd_gram(const float* __restrict__ Y, int lgN, const __grid_constant__ DddTaps tp, double* __restrict__ part) {
     constexpr int NG = ddd_samples(P), FPW = (17 + NW - 1) / NW;  // slots filtered per warp, at most
     constexpr int nw = NW;
     __shared__ float s_v[2][NG][17][32];
