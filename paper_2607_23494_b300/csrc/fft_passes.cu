@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float
 // its W columns, their FFTs exchanging through two tiles behind the same barriers, and one
 // table read serves the two lines (the table as in k_inv_x_window_pair).  Blocks at
 // k_y = 0 and N/2 (their own mirrors) transform one line set.
-template <int N>
+template <int N, bool TWT = false>
 __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const float2* __restrict__ spec,
                                                                      float2* __restrict__ work, const WinBatch wb,
                                                                      const Tables tb) {
@@ -602,11 +602,13 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
     load_stage_twiddles<N, true>(t, tb.tw, wc);
     const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
     for (int g = 0; g < wb.S; g += 4) {
-        float4 tv[8];
+        float4 tv[TWT ? 1 : 8];  // TWT: one factor per element and window, read when used
+        if constexpr (!TWT) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = trow(i);
-            tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+            for (int i = 0; i < 8; ++i) {
+                const int r = trow(i);
+                tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+            }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -616,7 +618,13 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
             float2 v[2][8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const float f = pz * (j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
+                float f;
+                if constexpr (TWT) {
+                    const int r = trow(i);
+                    f = pz * ttab[r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)) + j];
+                } else {
+                    f = pz * (j == 0 ? tv[i].x : (j == 1 ? tv[i].y : (j == 2 ? tv[i].z : tv[i].w)));
+                }
                 v[0][i] = cscale(va0[i], f);
                 v[1][i] = cscale(vb0[i], f);
             }
@@ -1136,13 +1144,15 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //   pass 1, the window pass (I1): 0 one window at a time (k_inv_x_window, shared table
 //           when it fits), 1 k_inv_x_window_pair (two windows in flight per thread),
 //           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read
-//           for both);
+//           for both), 3 the same reading one radial factor per element and window
+//           instead of four windows' factors at once (24 registers fewer);
 //   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
 //   pass 3, the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e (k_inv_y_e for the
 //           16-column tiles);
 //   passes 4, 5, the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at
-//           a time (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror).
+//           a time (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror), 3 the
+//           same reading each field's radial factors when used (no spills).
 // The first call of a grid size that runs a pass on a stream that is not being captured
 // into a graph times every variant on that call's own buffers (the y passes before the
 // passes that write their buffers, the others on the first catalogue), one warm-up and two
@@ -1197,8 +1207,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 32: return put({{0, 8, Cfg<32>::W, 1}});
             case 64: return put({{0, 8, Cfg<64>::W, 1}});
             case 128: return put({{0, 8, Cfg<128>::W, 1}});
-            case 256: return put({{0, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}});
-            case 512: return put({{0, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}});
+            case 256: return put({{0, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}, {3, 8, Cfg<256>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}, {3, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     } else if (pass == 3) {
@@ -1219,8 +1229,10 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 32: return put({{0, 8, Cfg<32>::W, 1}});
             case 64: return put({{0, 8, Cfg<64>::W, 1}});
             case 128: return put({{0, 8, Cfg<128>::W, 1}});
-            case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}});
-            case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}});
+            case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1},
+                                  {3, 8, Cfg<256>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1},
+                                  {3, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     }
@@ -1336,15 +1348,15 @@ static cudaError_t run_x_pair(const float2* spec, float2* work, const WinBatch& 
     k_inv_x_window_pair<N><<<dim3((N / 2) / C::W, N, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
-template <int N>
+template <int N, bool TWT>
 static cudaError_t run_x_mirror(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
                                 cudaStream_t st) {
     using C = Cfg<N>;
     const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
     if (wb.S > 16 || bytes > kMaxDynSmem) return run_x_r8<N>(spec, work, wb, tb, ncat, st);
     cudaError_t e;
-    if ((e = allow_smem(k_inv_x_window_mirror<N>, bytes)) != cudaSuccess) return e;
-    k_inv_x_window_mirror<N><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
+    if ((e = allow_smem(k_inv_x_window_mirror<N, TWT>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_mirror<N, TWT><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
 template <int N>
@@ -1353,7 +1365,8 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
     if constexpr (N == 256 || N == 512) {
         switch (var) {
             case 1: return run_x_pair<N>(spec, work, wb, tb, ncat, st);
-            case 2: return run_x_mirror<N>(spec, work, wb, tb, ncat, st);
+            case 2: return run_x_mirror<N, false>(spec, work, wb, tb, ncat, st);
+            case 3: return run_x_mirror<N, true>(spec, work, wb, tb, ncat, st);
         }
     }
     return run_x_r8<N>(spec, work, wb, tb, ncat, st);

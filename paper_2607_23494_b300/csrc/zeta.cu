@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
 // line set.
 __host__ __device__ constexpr int zmirror_row_floats(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }
 
-template <int N>
+template <int N, bool ONE = false>
 __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* __restrict__ spec,
                                                                 float2* __restrict__ fields, const HarmBatch hb,
                                                                 const Tables tb) {
@@ -275,11 +275,15 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* 
     const int nf = (hb.S + 1) >> 1;  // packed fields (m = 0)
     const int nout = hb.pack ? nf : hb.S;
     for (int g = 0; g < hb.S; g += 4) {
-        float4 tv[8];
+        // ONE: each field's factors are read when used instead of four bins' at once
+        // (24 registers fewer, so the kernel does not spill)
+        float4 tv[ONE ? 1 : 8];
+        if constexpr (!ONE) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = trow(i);
-            tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+            for (int i = 0; i < 8; ++i) {
+                const int r = trow(i);
+                tv[i] = *reinterpret_cast<const float4*>(ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)));
+            }
         }
         // packed: fields g/2 and g/2 + 1 (bins (2f, 2f + 1) as real and imaginary parts); else bins g..g+3
 #pragma unroll
@@ -289,7 +293,19 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* 
             float2 v[2][8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                if (hb.pack) {
+                if constexpr (ONE) {
+                    const int r = trow(i);
+                    const float* cp = ttab + r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask));
+                    if (hb.pack) {
+                        const float2 k2 = *reinterpret_cast<const float2*>(cp + 2 * j);
+                        v[0][i] = cmul(va0[i], k2);
+                        v[1][i] = cmul(vb0[i], k2);
+                    } else {
+                        const float k1 = cp[j];
+                        v[0][i] = cscale(va0[i], k1);
+                        v[1][i] = cscale(vb0[i], k1);
+                    }
+                } else if (hb.pack) {
                     const float2 k2 = j == 0 ? make_float2(tv[i].x, tv[i].y) : make_float2(tv[i].z, tv[i].w);
                     v[0][i] = cmul(va0[i], k2);
                     v[1][i] = cmul(vb0[i], k2);
@@ -913,8 +929,15 @@ static cudaError_t launch_zeta_x(int var, const ZetaXArgs& a) {
     if constexpr (N == 256 || N == 512) {
         const size_t bytes = 2 * C::SMEM_X + (size_t)(N / 2) * C::W * zmirror_row_floats(a.hb->S) * sizeof(float);
         if (var == 1 && bytes <= 220 * 1024) {
-            if ((e = allow_smem_z(k_zeta_x_mirror<N>, bytes)) != cudaSuccess) return e;
-            k_zeta_x_mirror<N><<<dim3(N / C::W, N / 2 + 1, 1), C::TS, bytes, a.st>>>(a.spec, a.fields, *a.hb, *a.tb);
+            if ((e = allow_smem_z(k_zeta_x_mirror<N, false>, bytes)) != cudaSuccess) return e;
+            k_zeta_x_mirror<N, false><<<dim3(N / C::W, N / 2 + 1, 1), C::TS, bytes, a.st>>>(a.spec, a.fields, *a.hb,
+                                                                                           *a.tb);
+            return cudaGetLastError();
+        }
+        if (var == 2 && bytes <= 220 * 1024) {
+            if ((e = allow_smem_z(k_zeta_x_mirror<N, true>, bytes)) != cudaSuccess) return e;
+            k_zeta_x_mirror<N, true><<<dim3(N / C::W, N / 2 + 1, 1), C::TS, bytes, a.st>>>(a.spec, a.fields, *a.hb,
+                                                                                          *a.tb);
             return cudaGetLastError();
         }
     }

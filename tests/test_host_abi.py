@@ -142,9 +142,9 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
     # the contraction pass: radix 8 everywhere, 16 values per thread at 256^3 and 512^3;
     # the zeta_l y pass: radix 8 everywhere, 16 or 32 values per thread at 256^3 and 512^3
     # (and 16-column tiles at 256^3 and 512^3)
-    for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2]), (1, 512, [0, 1, 2]), (2, 64, [0]),
+    for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2, 3]), (1, 512, [0, 1, 2, 3]), (2, 64, [0]),
                             (2, 256, [0, 1, 1, 1]), (2, 512, [0, 1, 1, 1]), (2, 1024, [0]), (3, 64, [0]),
-                            (3, 256, [0, 1, 1, 1, 1]), (3, 512, [0, 1, 1, 1, 1]), (4, 512, [0, 2]), (5, 256, [0, 2]),
+                            (3, 256, [0, 1, 1, 1, 1]), (3, 512, [0, 1, 1, 1, 1]), (4, 512, [0, 2, 3]), (5, 256, [0, 2, 3]),
                             (4, 1024, [0])):
         info = H.fft_variants(N, pass_)
         assert [v[0] for v in info["variants"]] == kinds
@@ -154,7 +154,7 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
     H.fft_set_variant(512, -1)
     info = H.fft_variants(512)
     assert info["forced"] == -1 and info["chosen"] == -1 and all(m == -1.0 for m in info["ms"])
-    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 6), (512, 3, 1), (512, 4, 2), (512, 5, 3), (512, 2, 4)):
+    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 6), (512, 4, 1), (512, 4, 2), (512, 5, 3), (512, 3, 4)):
         with pytest.raises(H.HermesError) as ei:
             H.fft_set_variant(bad[0], bad[1], pass_=bad[2])
         assert ei.value.code == H.ERR_ARG
