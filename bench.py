@@ -207,6 +207,7 @@ NCU_TRAFFIC_512 = {
     "inv_x_window/k0e8w8": {"per_launch": 0.560689e9, "per_window": 2.634067e9 / 5},
     "inv_x_window/k1e8w8": {"per_launch": 0.561371e9, "per_window": 2.634040e9 / 5},
     "inv_x_window/k2e8w8": {"per_launch": 0.576038e9, "per_window": 2.796381e9 / 5},
+    "inv_x_window/k3e8w8": {"per_launch": 0.571600e9, "per_window": 2.632482e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
     "inv_y/k1e32w16": {"per_launch": 0.0, "per_window": (2.684860e9 + 2.624219e9) / 5},
