@@ -535,7 +535,11 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float
 // its W columns, their FFTs exchanging through two tiles behind the same barriers, and one
 // table read serves the two lines (the table as in k_inv_x_window_pair).  Blocks at
 // k_y = 0 and N/2 (their own mirrors) transform one line set.
-template <int N, bool TWT = false>
+// ONE: each window's factors are read from the table when that window is scaled (8 scalar
+// loads, 4-way bank conflicts) instead of four windows' factors held in 32 registers; at 128
+// registers a thread that frees them stops spilling, and the spill reloads were a large part
+// of the pass's long-scoreboard stalls.
+template <int N, bool ONE = false>
 __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const float2* __restrict__ spec,
                                                                      float2* __restrict__ work, const WinBatch wb,
                                                                      const Tables tb) {
@@ -602,8 +606,8 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
     load_stage_twiddles<N, true>(t, tb.tw, wc);
     const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
     for (int g = 0; g < wb.S; g += 4) {
-        float4 tv[TWT ? 1 : 8];  // TWT: one factor per element and window, read when used
-        if constexpr (!TWT) {
+        float4 tv[ONE ? 1 : 8];
+        if constexpr (!ONE) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = trow(i);
@@ -619,7 +623,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 float f;
-                if constexpr (TWT) {
+                if constexpr (ONE) {
                     const int r = trow(i);
                     f = pz * ttab[r * RS + 4 * ((g >> 2) ^ ((r >> rsh) & cmask)) + j];
                 } else {
@@ -1348,15 +1352,15 @@ static cudaError_t run_x_pair(const float2* spec, float2* work, const WinBatch& 
     k_inv_x_window_pair<N><<<dim3((N / 2) / C::W, N, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
-template <int N, bool TWT>
+template <int N, bool ONE>
 static cudaError_t run_x_mirror(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
                                 cudaStream_t st) {
     using C = Cfg<N>;
     const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
     if (wb.S > 16 || bytes > kMaxDynSmem) return run_x_r8<N>(spec, work, wb, tb, ncat, st);
     cudaError_t e;
-    if ((e = allow_smem(k_inv_x_window_mirror<N, TWT>, bytes)) != cudaSuccess) return e;
-    k_inv_x_window_mirror<N, TWT><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
+    if ((e = allow_smem(k_inv_x_window_mirror<N, ONE>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_mirror<N, ONE><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
 template <int N>
