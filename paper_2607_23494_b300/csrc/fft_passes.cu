@@ -780,7 +780,7 @@ struct Z16Cfg {
     static constexpr size_t SMEM = (size_t)2 * LZ * SP * sizeof(float2) + (size_t)LZ * LP * sizeof(float2);
 };
 
-template <int N, int THREADS, int MINB>
+template <int N, int THREADS, int MINB, bool WKS = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const float2* __restrict__ work, int S,
                                                                        const float* __restrict__ delta,
                                                                        const float2* __restrict__ tw,
@@ -832,9 +832,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
     float2 d2[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) d2[i] = dl[t + i * T];
-    float2 wk[E];  // the c2r split twiddles e^{+2 pi i k / N}, k = t + iT
+    // the c2r split twiddles e^{+2 pi i k / N}, k = t + iT: in registers, or (WKS) in a table
+    // shared by the block and read per window (32 registers fewer)
+    __shared__ float2 swk[WKS ? M : 1];
+    float2 wk[WKS ? 1 : E];
+    if constexpr (WKS) {
+        for (int k = threadIdx.x; k < M; k += THREADS) swk[k] = cconj(__ldg(tw + N + k));
+    } else {
 #pragma unroll
-    for (int i = 0; i < E; ++i) wk[i] = cconj(__ldg(tw + N + t + i * T));
+        for (int i = 0; i < E; ++i) wk[i] = cconj(__ldg(tw + N + t + i * T));
+    }
     float2 wc[stage_twiddle_count<M, E>() + 1];
     load_stage_twiddles_e<M, E, true>(t, tw, wc);
     bool late = false;
@@ -853,7 +860,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_inv_z_c2r_contract_e16(const 
             const float2 xk = X[k];
             const float2 xc = cconj((k == 0) ? make_float2(0.f, 0.f) : X[M - k]);
             const float2 a = cadd(xk, xc);
-            const float2 c = cmul(wk[i], csub(xk, xc));
+            const float2 c = cmul(WKS ? swk[k] : wk[i], csub(xk, xc));
             v[i] = make_float2(a.x - c.y, a.y + c.x);
         }
         fft_line_e_wc<M, E, true>(v, t, tw, sm, wc);
@@ -1151,7 +1158,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           for both), 3 the same reading one radial factor per element and window
 //           instead of four windows' factors at once (24 registers fewer);
 //   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
-//           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks);
+//           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks), 2 the same
+//           with its split twiddles in a table shared by the block (no spills);
 //   pass 3, the zeta_l y pass: 0 radix 8 (k_strided), 1 k_strided_e (k_inv_y_e for the
 //           16-column tiles);
 //   passes 4, 5, the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at
@@ -1201,8 +1209,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
         }
     } else if (pass == 2) {
         switch (N) {
-            case 256: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
-            case 512: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}});
+            case 256: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}, {2, 16, 1, 4}});
+            case 512: return put({{0, 8, 1, 3}, {1, 16, 1, 4}, {1, 16, 1, 3}, {1, 16, 1, 2}, {2, 16, 1, 4}});
             case 16: case 32: case 64: case 128: case 1024: return put({{0, 8, 1, 3}});
         }
     } else if (pass == 4 || pass == 5) {  // the zeta_l x pass: complex fields / packed m = 0 fields
@@ -1378,13 +1386,13 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
 
 // The last inverse pass (c2r along z and the contraction): delta of the first catalogue
 // of the launch at delta, partials [ncat][S][z blocks of the radix-8 form].
-template <int N, int THREADS, int MINB>
+template <int N, int THREADS, int MINB, bool WKS = false>
 static cudaError_t run_z_e16(const float2* work, int S, const float* delta, const float2* tw, double* dd_part,
                              unsigned* err, int ncat, cudaStream_t st) {
     using C = Z16Cfg<N, THREADS>;
     cudaError_t e;
-    if ((e = allow_smem(k_inv_z_c2r_contract_e16<N, THREADS, MINB>, C::SMEM)) != cudaSuccess) return e;
-    k_inv_z_c2r_contract_e16<N, THREADS, MINB><<<dim3((N * N) / C::LZ, ncat), THREADS, C::SMEM, st>>>(
+    if ((e = allow_smem(k_inv_z_c2r_contract_e16<N, THREADS, MINB, WKS>, C::SMEM)) != cudaSuccess) return e;
+    k_inv_z_c2r_contract_e16<N, THREADS, MINB, WKS><<<dim3((N * N) / C::LZ, ncat), THREADS, C::SMEM, st>>>(
         work, S, delta, tw, dd_part, err);
     return cudaGetLastError();
 }
@@ -1395,6 +1403,7 @@ static cudaError_t launch_inv_z(int var, const float2* work, int S, const float*
         if (var == 1) return run_z_e16<N, 128, 4>(work, S, delta, tw, dd_part, err, ncat, st);
         if (var == 2) return run_z_e16<N, 128, 3>(work, S, delta, tw, dd_part, err, ncat, st);
         if (var == 3) return run_z_e16<N, 128, 2>(work, S, delta, tw, dd_part, err, ncat, st);
+        if (var == 4) return run_z_e16<N, 128, 4, true>(work, S, delta, tw, dd_part, err, ncat, st);
     }
     using C = Cfg<N>;
     k_inv_z_c2r_contract<N><<<dim3((N * N) / C::LZ, ncat), C::ZTHREADS, C::SMEM_Z3, st>>>(work, S, delta, tw,
