@@ -879,6 +879,7 @@ def run_serve(args, dev, rank):
 def run_zeta(args, dev, stream, rank):
     import torch
     from paper_2607_23494_b300 import Context
+    from paper_2607_23494_b300 import hermes as Hz
     pos = gen_catalogue3(rank_seeds(rank)["zeta"])
     pos_d = torch.from_numpy(pos).to(dev)
     ctx = Context(L3, N3, 4)
@@ -971,7 +972,9 @@ def run_zeta(args, dev, stream, rank):
             "ms_per_step": round(ms, 2), "complex_fields": nfields, "complex_transforms": ntrans,
             "cell_field_evals_per_s": round(n3 * nfields / (ms / 1e3), 1),
             "kernels": kern, "zeta0_diag_first2": [float(z[0, 0, 0]), float(z[0, 1, 1])],
-            "ddd_l_20_40": ddd, "ddd_monopole_cc": ddd_cc, "_z128": z128}
+            "ddd_l_20_40": ddd, "ddd_monopole_cc": ddd_cc, "_z128": z128,
+            "fft_variants": {name: {**Hz.fft_variants(N3, p_), "in_use": variant_tag(Hz, N3, p_)}
+                             for name, p_ in (("zeta_y", 3), ("zeta_x", 4), ("zeta_x_m0", 5))}}
 
 
 def oracle_sample(pos, b: int = 0):
