@@ -226,16 +226,36 @@ __global__ void __launch_bounds__((N / E) * W) k_strided_e(float2* __restrict__ 
 // fixed at compile time: the E element offsets of a thread are immediates of one base
 // address instead of E computed addresses, which leaves the registers for the
 // transform (MINB blocks per SM).  Grid (Z / W, N, fields).
-template <int N, int Z, int E, int W, int SH, int P, int MINB>
+// PAIRED: the input is in the paired order the mirror-line window passes write (16-column
+// groups; in group g, line 2p + h holds columns 16g + 8h .. 16g + 8h + 7 of rows p and
+// N - p interleaved, (row p, row N - p) per column, and line h of pair 0 rows 0 and N/2),
+// so that those passes store whole 128-byte lines; the tile of a block covers the same
+// addresses in both orders, so it is read in the paired order and written in the plain one
+// in place.  Rows t + iT with iT < N/2 sit in the first slot of pair t + iT, the others in
+// the second slot of pair N - t - iT (pair 0 for the row N/2).
+template <int N, int Z, int E, int W, int SH, int P, int MINB, bool PAIRED = false>
 __global__ void __launch_bounds__((N / E) * W, MINB) k_inv_y_e(float2* __restrict__ data,
                                                                const float2* __restrict__ tw) {
     constexpr int T = N / E;
+    static_assert(!PAIRED || W == 16, "the paired order is laid out in 16-column groups");
     extern __shared__ float2 smem[];
     const int col = threadIdx.x % W, t = threadIdx.x / W;
     float2* b = data + (size_t)blockIdx.z * N * N * Z + (size_t)blockIdx.y * N * Z + blockIdx.x * W + col + t * Z;
     float2 v[E];
+    if constexpr (PAIRED) {
+        const float2* plane = data + (size_t)blockIdx.z * N * N * Z + (size_t)blockIdx.y * N * Z + blockIdx.x * W;
+        const int h = col >> 3, c2 = 2 * (col & 7);
+        const float2* pa = plane + (size_t)(2 * t + h) * Z + c2;              // row t + iT: line 2(t + iT) + h
+        const float2* pb = plane + (size_t)(2 * N - 2 * t + h) * Z + c2 + 1;  // line 2(N - t - iT) + h
+        const size_t nyq = t == 0 ? (size_t)N * Z : 0;                        // row N/2: line h of pair 0
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = b[i * T * Z];
+        for (int i = 0; i < E / 2; ++i) v[i] = pa[(size_t)i * 2 * T * Z];
+#pragma unroll
+        for (int i = E / 2; i < E; ++i) v[i] = *(pb - (size_t)i * 2 * T * Z - (i == E / 2 ? nyq : 0));
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = b[i * T * Z];
+    }
     fft_line_e<N, E, true>(v, t, tw, SmemStridedSk<W, SH, P>{smem, col});
 #pragma unroll
     for (int i = 0; i < E; ++i) b[i * T * Z] = v[i];
@@ -539,12 +559,18 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float
 // loads, 4-way bank conflicts) instead of four windows' factors held in 32 registers; at 128
 // registers a thread that frees them stops spilling, and the spill reloads were a large part
 // of the pass's long-scoreboard stalls.
-template <int N, bool ONE = false>
+// PAIRED (8-column tiles): the two lines' values of a column are stored side by side, one
+// 16-byte store per element, in the paired order that k_inv_y_e<..., PAIRED> reads, so
+// that every store instruction writes whole 128-byte lines (8-column tiles of the plain
+// order write half lines); grid (N / 2 / W, N / 2): the block at k_y = 0 also writes the
+// k_y = N/2 line, which is zero.
+template <int N, bool ONE = false, bool PAIRED = false>
 __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const float2* __restrict__ spec,
                                                                      float2* __restrict__ work, const WinBatch wb,
                                                                      const Tables tb) {
     using C = Cfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
+    static_assert(!PAIRED || W == 8, "the paired order pairs two 8-column tiles in a 16-column group");
     constexpr int TILE = SmemStrided<W>::words(N);
     extern __shared__ __align__(16) float2 smem[];
     float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
@@ -633,12 +659,22 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
                 v[1][i] = cscale(vb0[i], f);
             }
             fft_lines_wc<N, true, 2>(v, t, sms, wc);
-            float2* dst = work + (size_t)s * N * N * H + (size_t)kz;
+            if constexpr (PAIRED) {
+                // line 2 k_y + (tile & 1) of 16-column group tile / 2, slots (k_y, N - k_y) of column col
+                const int off = t * (N * H) + (2 * ky + (int)(blockIdx.x & 1)) * H + (int)(blockIdx.x >> 1) * 16 + 2 * col;
+                float2* dst = work + (size_t)s * N * N * H + off;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)ky * H] = v[0][i];
-            if (two) {
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<float4*>(dst + (size_t)i * T * N * H) =
+                        make_float4(v[0][i].x, v[0][i].y, v[1][i].x, v[1][i].y);
+            } else {
+                float2* dst = work + (size_t)s * N * N * H + (size_t)kz;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)kyb * H] = v[1][i];
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)ky * H] = v[0][i];
+                if (two) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * xstride + (size_t)kyb * H] = v[1][i];
+                }
             }
         }
     }
@@ -1156,7 +1192,10 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           when it fits), 1 k_inv_x_window_pair (two windows in flight per thread),
 //           2 k_inv_x_window_mirror (the k_y and N - k_y lines together, one table read
 //           for both), 3 the same reading one radial factor per element and window
-//           instead of four windows' factors at once (24 registers fewer);
+//           instead of four windows' factors at once (24 registers fewer), 4 (512^3) the
+//           same storing both lines of a column in one 16-byte store, in the paired order
+//           (whole 128-byte lines); the y pass then reads that order (its variants 4 and
+//           5 have a form for it; with another y variant, variant 3 runs in its place);
 //   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks), 2 the same
 //           with its split twiddles in a table shared by the block (no spills);
@@ -1164,7 +1203,9 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           16-column tiles);
 //   passes 4, 5, the zeta_l x pass for complex / packed m = 0 fields: 0 one line set at
 //           a time (k_zeta_x), 2 the k_y and N - k_y lines together (k_zeta_x_mirror), 3 the
-//           same reading each field's radial factors when used (no spills).
+//           same reading each field's radial factors when used (no spills), 4 (512^3) the
+//           same in the paired order, read by the zeta_l y pass's variants 3 and 4 (with
+//           another y variant, kind 3 runs in its place).
 // The first call of a grid size that runs a pass on a stream that is not being captured
 // into a graph times every variant on that call's own buffers (the y passes before the
 // passes that write their buffers, the others on the first catalogue), one warm-up and two
@@ -1220,7 +1261,8 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 64: return put({{0, 8, Cfg<64>::W, 1}});
             case 128: return put({{0, 8, Cfg<128>::W, 1}});
             case 256: return put({{0, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1}, {3, 8, Cfg<256>::W, 1}});
-            case 512: return put({{0, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}, {3, 8, Cfg<512>::W, 1}});
+            case 512: return put({{0, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1}, {3, 8, Cfg<512>::W, 1},
+                                  {4, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     } else if (pass == 3) {
@@ -1244,7 +1286,7 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1},
                                   {3, 8, Cfg<256>::W, 1}});
             case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1},
-                                  {3, 8, Cfg<512>::W, 1}});
+                                  {3, 8, Cfg<512>::W, 1}, {4, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     }
@@ -1281,13 +1323,13 @@ static cudaError_t run_y_plain(float2* work, int nwin, const float2* tw, cudaStr
     k_strided_e<N, E, W, SH, P><<<dim3(H / W, N, nwin), TS, smem, st>>>(work, H, N * H, (long long)N * N * H, tw);
     return cudaGetLastError();
 }
-template <int N, int Z, int E, int W, int SH, int P, int MINB>
+template <int N, int Z, int E, int W, int SH, int P, int MINB, bool PAIRED = false>
 static cudaError_t run_y_ct(float2* data, int nf, const float2* tw, cudaStream_t st) {
     constexpr int TS = (N / E) * W;
     constexpr size_t smem = (size_t)SmemStridedSk<W, SH, P>::words(N) * sizeof(float2);
     cudaError_t e;
-    if ((e = allow_smem(k_inv_y_e<N, Z, E, W, SH, P, MINB>, smem)) != cudaSuccess) return e;
-    k_inv_y_e<N, Z, E, W, SH, P, MINB><<<dim3(Z / W, N, nf), TS, smem, st>>>(data, tw);
+    if ((e = allow_smem(k_inv_y_e<N, Z, E, W, SH, P, MINB, PAIRED>, smem)) != cudaSuccess) return e;
+    k_inv_y_e<N, Z, E, W, SH, P, MINB, PAIRED><<<dim3(Z / W, N, nf), TS, smem, st>>>(data, tw);
     return cudaGetLastError();
 }
 template <int N, int E, int W, int SH, int P, int MINB>
@@ -1305,8 +1347,18 @@ static cudaError_t run_y_pf(float2* work, int nwin, const float2* tw, cudaStream
     return cudaGetLastError();
 }
 // The skews (SH, P) below give the fewest shared-memory wavefronts for each shape.
+// paired: the input is in the paired order of the window pass (variants 4 and 5 at 512^3).
 template <int N>
-static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* tw, cudaStream_t st) {
+static cudaError_t launch_inv_y(int var, float2* work, int nwin, const float2* tw, cudaStream_t st,
+                                bool paired = false) {
+    if constexpr (N == 512) {
+        if (paired) {
+            if (var == 4) return run_y_ct<512, 256, 32, 16, 3, 0, 1, true>(work, nwin, tw, st);
+            if (var == 5) return run_y_ct<512, 256, 32, 16, 3, 0, 2, true>(work, nwin, tw, st);
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (paired) return cudaErrorInvalidValue;
     if constexpr (N == 128) {
         if (var == 1) return run_y_plain<128, 16, 8, 2, 4>(work, nwin, tw, st);
     } else if constexpr (N == 256) {
@@ -1360,15 +1412,23 @@ static cudaError_t run_x_pair(const float2* spec, float2* work, const WinBatch& 
     k_inv_x_window_pair<N><<<dim3((N / 2) / C::W, N, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
-template <int N, bool ONE>
+template <int N>
+static bool mirror_fits(const WinBatch& wb) {
+    using C = Cfg<N>;
+    const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
+    return wb.S <= 16 && bytes <= kMaxDynSmem;
+}
+// The paired order never falls back to another form: the y pass that follows reads it.
+template <int N, bool ONE, bool PAIRED = false>
 static cudaError_t run_x_mirror(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
                                 cudaStream_t st) {
     using C = Cfg<N>;
     const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
-    if (wb.S > 16 || bytes > kMaxDynSmem) return run_x_r8<N>(spec, work, wb, tb, ncat, st);
+    if (!mirror_fits<N>(wb)) return PAIRED ? cudaErrorInvalidValue : run_x_r8<N>(spec, work, wb, tb, ncat, st);
     cudaError_t e;
-    if ((e = allow_smem(k_inv_x_window_mirror<N, ONE>, bytes)) != cudaSuccess) return e;
-    k_inv_x_window_mirror<N, ONE><<<dim3((N / 2) / C::W, N / 2 + 1, ncat), C::TS, bytes, st>>>(spec, work, wb, tb);
+    if ((e = allow_smem(k_inv_x_window_mirror<N, ONE, PAIRED>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_mirror<N, ONE, PAIRED><<<dim3((N / 2) / C::W, PAIRED ? N / 2 : N / 2 + 1, ncat), C::TS, bytes,
+                                            st>>>(spec, work, wb, tb);
     return cudaGetLastError();
 }
 template <int N>
@@ -1381,7 +1441,20 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
             case 3: return run_x_mirror<N, true>(spec, work, wb, tb, ncat, st);
         }
     }
+    if constexpr (N == 512) {
+        if (var == 4) return run_x_mirror<N, true, true>(spec, work, wb, tb, ncat, st);
+    }
     return run_x_r8<N>(spec, work, wb, tb, ncat, st);
+}
+// Whether the window pass variant writes the paired order, and whether the y pass
+// variant has a form that reads it.
+template <int N>
+static bool x_writes_paired(int xvar) {
+    return N == 512 && xvar == 4;
+}
+template <int N>
+static bool y_reads_paired(int yvar) {
+    return N == 512 && (yvar == 4 || yvar == 5);
 }
 
 // The last inverse pass (c2r along z and the contraction): delta of the first catalogue
@@ -1424,7 +1497,16 @@ static cudaError_t run_zeta_y_e(float2* fields, int nf, const float2* tw, cudaSt
     return cudaGetLastError();
 }
 template <int N>
-static cudaError_t launch_zeta_y_var(int var, float2* fields, int nf, const float2* tw, cudaStream_t st) {
+static cudaError_t launch_zeta_y_var(int var, float2* fields, int nf, const float2* tw, cudaStream_t st,
+                                     bool paired = false) {
+    if constexpr (N == 512) {
+        if (paired) {  // the fields in the paired order of the x pass (its variant 3)
+            if (var == 3) return run_y_ct<512, 512, 32, 16, 3, 0, 1, true>(fields, nf, tw, st);
+            if (var == 4) return run_y_ct<512, 512, 32, 16, 3, 0, 2, true>(fields, nf, tw, st);
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (paired) return cudaErrorInvalidValue;
     if constexpr (N == 256) {
         if (var == 1) return run_zeta_y_e<256, 16, 8, 2, 2>(fields, nf, tw, st);
         if (var == 2) return run_zeta_y_e<256, 32, 8, 2, 4>(fields, nf, tw, st);
@@ -1527,15 +1609,16 @@ int zeta_y_variant(int N, float2* fields, int nf, const float2* tw, cudaStream_t
 #undef F
     return 0;
 }
-cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st) {
+bool zeta_y_reads_paired(int N, int var) { return N == 512 && (var == 3 || var == 4); }
+cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st, bool paired) {
     switch (N) {
-        case 16: return launch_zeta_y_var<16>(var, fields, nf, tw, st);
-        case 32: return launch_zeta_y_var<32>(var, fields, nf, tw, st);
-        case 64: return launch_zeta_y_var<64>(var, fields, nf, tw, st);
-        case 128: return launch_zeta_y_var<128>(var, fields, nf, tw, st);
-        case 256: return launch_zeta_y_var<256>(var, fields, nf, tw, st);
-        case 512: return launch_zeta_y_var<512>(var, fields, nf, tw, st);
-        case 1024: return launch_zeta_y_var<1024>(var, fields, nf, tw, st);
+        case 16: return launch_zeta_y_var<16>(var, fields, nf, tw, st, paired);
+        case 32: return launch_zeta_y_var<32>(var, fields, nf, tw, st, paired);
+        case 64: return launch_zeta_y_var<64>(var, fields, nf, tw, st, paired);
+        case 128: return launch_zeta_y_var<128>(var, fields, nf, tw, st, paired);
+        case 256: return launch_zeta_y_var<256>(var, fields, nf, tw, st, paired);
+        case 512: return launch_zeta_y_var<512>(var, fields, nf, tw, st, paired);
+        case 1024: return launch_zeta_y_var<1024>(var, fields, nf, tw, st, paired);
     }
     return cudaErrorInvalidValue;
 }
@@ -1597,8 +1680,12 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     const int zvar = yz ? 0 : pick_variant(N, 2, st, [&](int v) {
         return launch_inv_z<N>(v, work, wb.S, delta, tb.tw, dd_part, err, 1, st);
     });
+    // the paired order of the window pass needs a y pass that reads it; otherwise the same
+    // window pass runs with plain stores
+    const bool paired = x_writes_paired<N>(xvar) && !yz && y_reads_paired<N>(yvar) && mirror_fits<N>(wb);
+    const int xrun = x_writes_paired<N>(xvar) && !paired ? 3 : xvar;
     tr(K_INV_X_WINDOW, 0, st);
-    if ((e = launch_inv_x<N>(xvar, spec, work, wb, tb, ncat, st)) != cudaSuccess) return e;
+    if ((e = launch_inv_x<N>(xrun, spec, work, wb, tb, ncat, st)) != cudaSuccess) return e;
     tr(K_INV_X_WINDOW, 1, st);
     if constexpr (N <= 512) {
         if (yz) {
@@ -1610,7 +1697,7 @@ static cudaError_t inverse_impl(const float2* spec, float2* work, const float* d
     }
     // windows of all catalogues are consecutive in work: tiles (column chunk, x, window)
     tr(K_INV_Y, 0, st);
-    if ((e = launch_inv_y<N>(yvar, work, wb.S * ncat, tb.tw, st)) != cudaSuccess) return e;
+    if ((e = launch_inv_y<N>(yvar, work, wb.S * ncat, tb.tw, st, paired)) != cudaSuccess) return e;
     tr(K_INV_Y, 1, st);
     tr(K_INV_Z_C2R_CONTRACT, 0, st);
     if ((e = launch_inv_z<N>(zvar, work, wb.S, delta, tb.tw, dd_part, err, ncat, st)) != cudaSuccess) return e;

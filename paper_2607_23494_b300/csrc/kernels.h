@@ -139,7 +139,11 @@ int zeta_y_variant(int N, float2* fields, int nf, const float2* tw, cudaStream_t
 // launch of variant v, for every variant when st is not capturing) the fastest; 0 while
 // capturing before any tuning.
 int tuned_variant(int N, int pass, cudaStream_t st, cudaError_t (*trial)(int v, void* arg), void* arg);
-cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st);
+// paired: the fields are in the paired order of the zeta_l x pass's paired variant, which
+// only the variants for which zeta_y_reads_paired holds can read.
+cudaError_t launch_zeta_y(int N, int var, float2* fields, int nf, const float2* tw, cudaStream_t st,
+                          bool paired = false);
+bool zeta_y_reads_paired(int N, int var);
 int inv_z_blocks(int N);        // blocks of the last inverse pass for one catalogue (fused y-z if enabled)
 int inv_z_blocks_plain(int N);  // the same for the three-pass form (always used when ncat > 1)
 // window multiply + inverse transforms + cell contraction of one window batch;

@@ -210,14 +210,20 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x(const float2* __restr
 // j ^ ((r >> rsh) & (RS / 4 - 1)), RS = 4, 8 or 16 floats, so a quarter warp's 16-byte reads
 // meet 8 distinct bank groups.  Blocks at k_y = 0 and N/2 (their own mirrors) transform one
 // line set.
+// PAIRED (8-column tiles): both lines' values of a column go out in one 16-byte store, in
+// the paired order of the window pass (16-column groups, line 2 k_y + h of group g holding
+// rows k_y and N - k_y of its columns side by side), which the y pass reads
+// (k_inv_y_e<..., PAIRED>); grid (N / W, N / 2): the block at k_y = 0 also writes the zero
+// k_y = N/2 line.
 __host__ __device__ constexpr int zmirror_row_floats(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }
 
-template <int N, bool ONE = false>
+template <int N, bool ONE = false, bool PAIRED = false>
 __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* __restrict__ spec,
                                                                 float2* __restrict__ fields, const HarmBatch hb,
                                                                 const Tables tb) {
     using C = ZCfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
+    static_assert(!PAIRED || W == 8, "the paired order pairs two 8-column tiles in a 16-column group");
     constexpr int TILE = SmemStrided<W>::words(N);
     extern __shared__ __align__(16) float2 smem[];
     float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
@@ -316,12 +322,21 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* 
                 }
             }
             fft_lines_wc<N, true, 2>(v, t, sms, wc);
-            float2* dst = fields + (size_t)f * n3 + (size_t)kz;
+            if constexpr (PAIRED) {
+                const int off = t * (N * N) + (2 * ky + (int)(blockIdx.x & 1)) * N + (int)(blockIdx.x >> 1) * 16 + 2 * col;
+                float2* dst = fields + (size_t)f * n3 + off;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)ky * N] = v[0][i];
-            if (two) {
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<float4*>(dst + (size_t)i * T * N * N) =
+                        make_float4(v[0][i].x, v[0][i].y, v[1][i].x, v[1][i].y);
+            } else {
+                float2* dst = fields + (size_t)f * n3 + (size_t)kz;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)kyb * N] = v[1][i];
+                for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)ky * N] = v[0][i];
+                if (two) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) dst[(size_t)(t + i * T) * N * N + (size_t)kyb * N] = v[1][i];
+                }
             }
         }
     }
@@ -912,7 +927,9 @@ int zeta_z_blocks(int N) {
 
 // The x pass of one (l, m) batch: variant 0 one line set at a time (shared table when it
 // fits, gathered factors otherwise), variant 1 the mirror lines together (256^3 and 512^3,
-// when the unpadded table and two tiles fit).
+// when the unpadded table and two tiles fit), 2 the same reading each field's factors when
+// used, 3 (512^3) the same in the paired order (it never falls back to another form: the
+// y pass that follows reads that order).
 struct ZetaXArgs {
     const float2* spec;
     float2* fields;
@@ -939,6 +956,15 @@ static cudaError_t launch_zeta_x(int var, const ZetaXArgs& a) {
             k_zeta_x_mirror<N, true><<<dim3(N / C::W, N / 2 + 1, 1), C::TS, bytes, a.st>>>(a.spec, a.fields, *a.hb,
                                                                                           *a.tb);
             return cudaGetLastError();
+        }
+        if constexpr (N == 512) {
+            if (var == 3) {
+                if (bytes > 220 * 1024) return cudaErrorInvalidValue;
+                if ((e = allow_smem_z(k_zeta_x_mirror<N, true, true>, bytes)) != cudaSuccess) return e;
+                k_zeta_x_mirror<N, true, true><<<dim3(N / C::W, N / 2, 1), C::TS, bytes, a.st>>>(a.spec, a.fields,
+                                                                                               *a.hb, *a.tb);
+                return cudaGetLastError();
+            }
         }
     }
     const dim3 g1(N / C::W, N, 1);
@@ -970,11 +996,16 @@ static cudaError_t zeta_impl(const float2* spec, float2* fields, const float* de
     // write the fields, which the real launch overwrites)
     const ZetaXArgs xa{spec, fields, &hp, &tb, use_stab, stab_bytes, st};
     const int xv = tuned_variant(N, hp.pack ? 5 : 4, st, zeta_x_trial<N>, const_cast<ZetaXArgs*>(&xa));
+    // the paired order of the x pass needs a y pass that reads it; otherwise the same x
+    // pass runs with plain stores
+    const size_t mbytes = 2 * C::SMEM_X + (size_t)(N / 2) * C::W * zmirror_row_floats(hp.S) * sizeof(float);
+    const bool paired = N == 512 && xv == 3 && mbytes <= 220 * 1024 && zeta_y_reads_paired(N, yvar);
+    const int xrun = (N == 512 && xv == 3 && !paired) ? 2 : xv;
     tr(K_ZETA_X, 0, st);
-    if ((e = launch_zeta_x<N>(xv, xa)) != cudaSuccess) return e;
+    if ((e = launch_zeta_x<N>(xrun, xa)) != cudaSuccess) return e;
     tr(K_ZETA_X, 1, st);
     tr(K_ZETA_Y, 0, st);
-    if ((e = launch_zeta_y(N, yvar, fields, nf, tb.tw, st)) != cudaSuccess) return e;
+    if ((e = launch_zeta_y(N, yvar, fields, nf, tb.tw, st, paired)) != cudaSuccess) return e;
     tr(K_ZETA_Y, 1, st);
     if constexpr (N >= 32) {
         if (zeta_tc_enabled(N)) {

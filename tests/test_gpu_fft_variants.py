@@ -170,3 +170,64 @@ def test_every_zeta_x_variant_matches(N, L):
     for got in outs:
         assert np.all(np.isfinite(got))
         _close(got, outs[0])
+
+
+def test_paired_order_with_every_kind_of_y_variant():
+    # the window pass in the paired order (variant 4 at 512^3: the k_y and N - k_y values of a
+    # column side by side) with the y variants that read that order (4, 5) and one that does
+    # not (2: the window pass then stores the plain order): one catalogue against the Parseval
+    # route, and a two-catalogue batch (both catalogues' windows in one launch) against the
+    # same path one catalogue at a time
+    H = _hermes()
+    N, L = 512, 1000.0
+    pos = S.lognormal_catalogue(100000, L, seed=31, n_grid=64)
+    pos2 = S.mixed_poisson_sp(80000, L, seed=32)
+    edges = np.linspace(L / 100, L / 10, 19)
+    ells = (0, 2)
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(edges, l_max=2)
+            ctx.assign(pos2)
+            ks2 = ctx.xi_multipoles_kspace(ells)
+            ctx.assign(pos)
+            ks = ctx.xi_multipoles_kspace(ells)
+            H.fft_set_variant(N, 4, H.PASS_WINDOW)
+            for yv in (4, 5, 2):
+                H.fft_set_variant(N, yv, H.PASS_INV_Y)
+                _close(ctx.xi_multipoles(ells), ks)
+            H.fft_set_variant(N, 4, H.PASS_INV_Y)
+            both = np.concatenate([pos, pos2]).astype(np.float32)
+            offs = np.array([0, pos.shape[0], both.shape[0]], dtype=np.int64)
+            ctx.batch_set_plan(4, 2)
+            got = ctx.xi_multipoles_batch(both, None, offs, ells)
+    finally:
+        H.fft_set_variant(N, -1, H.PASS_WINDOW)
+        H.fft_set_variant(N, -1, H.PASS_INV_Y)
+    _close(got[0], ks)
+    _close(got[1], ks2)
+
+
+def test_zeta_paired_order_with_every_kind_of_y_variant():
+    # the zeta_l x pass in the paired order (variant 3 at 512^3) with the zeta y variants that
+    # read it (3, 4) and one that does not (1), complex and packed m = 0 fields (l_max 3: odd
+    # m too), against the plain order's result
+    H = _hermes()
+    N, L = 512, 1000.0
+    pos = S.lognormal_catalogue(100000, L, seed=33, n_grid=64)
+    outs = []
+    try:
+        with H.Context(L, N, 4) as ctx:
+            ctx.window_shells(np.linspace(L / 50, L / 8, 6), l_max=3)
+            ctx.assign(pos)
+            for xv, yv in ((2, 4), (3, 4), (3, 3), (3, 1)):
+                for p_ in (H.PASS_ZETA_X, H.PASS_ZETA_X_M0):
+                    H.fft_set_variant(N, xv, p_)
+                H.fft_set_variant(N, yv, H.PASS_ZETA_Y)
+                outs.append(ctx.zeta_multipoles())
+    finally:
+        for p_ in (H.PASS_ZETA_X, H.PASS_ZETA_X_M0, H.PASS_ZETA_Y):
+            H.fft_set_variant(N, -1, p_)
+    assert np.abs(outs[0]).max() > 0
+    for got in outs[1:]:
+        assert np.all(np.isfinite(got))
+        _close(got, outs[0])
