@@ -208,9 +208,11 @@ NCU_TRAFFIC_512 = {
     "inv_x_window/k1e8w8": {"per_launch": 0.561371e9, "per_window": 2.634040e9 / 5},
     "inv_x_window/k2e8w8": {"per_launch": 0.576038e9, "per_window": 2.796381e9 / 5},
     "inv_x_window/k3e8w8": {"per_launch": 0.571600e9, "per_window": 2.632482e9 / 5},
+    "inv_x_window/k4e8w8": {"per_launch": 0.583437e9, "per_window": 2.626260e9 / 5},
     "inv_y/k0e8w8": {"per_launch": 0.0, "per_window": (2.684387e9 + 2.630191e9) / 5},
     "inv_y/k1e32w8": {"per_launch": 0.0, "per_window": (2.684618e9 + 2.630152e9) / 5},
     "inv_y/k1e32w16": {"per_launch": 0.0, "per_window": (2.684860e9 + 2.624219e9) / 5},
+    "inv_y/k1e32w16p": {"per_launch": 0.0, "per_window": (2.684456e9 + 2.624291e9) / 5},
     "inv_z_c2r_contract/k0e8w1": {"per_launch": 0.0, "per_window": (3.221783e9 + 0.005084e9) / 5},
     "inv_z_c2r_contract/k1e16w1": {"per_launch": 0.0, "per_window": (3.221317e9 + 0.013573e9) / 5},
 }
@@ -218,11 +220,15 @@ TUNED_PASSES = {"inv_y": 0, "inv_x_window": 1, "inv_z_c2r_contract": 2}  # trace
 
 
 def variant_tag(H, N: int, pass_: int) -> str:
-    """The variant of a tuned pass in use for grid N as kind / values per thread / tile width."""
-    info = H.fft_variants(N, pass_)
-    v = info["forced"] if info["forced"] >= 0 else max(info["chosen"], 0)
-    kind, E, W, _ = info["variants"][v]
-    return f"k{kind}e{E}w{W}"
+    """The variant of a tuned pass in use for grid N as kind / values per thread / tile width
+    (a trailing p: the inverse y pass reading the paired order of the window pass)."""
+    def tag(p_):
+        info = H.fft_variants(N, p_)
+        v = info["forced"] if info["forced"] >= 0 else max(info["chosen"], 0)
+        return info["variants"][v]
+    kind, E, W, _ = tag(pass_)
+    paired = pass_ == 0 and N == 512 and (kind, E, W) == (1, 32, 16) and tag(1)[0] == 4
+    return f"k{kind}e{E}w{W}" + ("p" if paired else "")
 
 
 def ncu_traffic(H, name: str, windows_per_launch: float) -> float | None:
