@@ -59,6 +59,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// Tiled bulk store (TMA) of one 3-D box from this CTA's shared memory to global memory,
+// described by a tensor map that is a __grid_constant__ kernel parameter; coordinates in
+// elements, the innermost one times the element size a multiple of 16 bytes; the shared
+// source 16-byte aligned, its generic-proxy writes ordered before by fence_proxy_async.
+// The store joins the calling thread's current bulk group; commit closes the group.
+__device__ __forceinline__ void tma_store_3d(const void* tmap, const void* src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(tmap),
+                 "r"(su32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Until every committed bulk group of this thread has read its shared source (the copies
+// always complete: no bound needed), so the source may be overwritten.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Until every committed bulk group of this thread has completed its global writes.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // 16-byte asynchronous copy global -> shared (both 16-byte aligned), in the
 // calling thread's current group; commit closes the group, wait_all waits for
 // every group of this thread (the copies always complete: no bound needed).

@@ -23,6 +23,8 @@
 #include "fft_core.cuh"
 #include "async_copy.cuh"
 
+#include <cuda.h>          // CUtensorMap (the encoder is reached through the runtime's driver entry point)
+#include <cudaTypedefs.h>  // its function type
 #include <cooperative_groups.h>
 #include <algorithm>
 #include <cstdlib>
@@ -564,13 +566,22 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_pair(const float
 // that every store instruction writes whole 128-byte lines (8-column tiles of the plain
 // order write half lines); grid (N / 2 / W, N / 2): the block at k_y = 0 also writes the
 // k_y = N/2 line, which is zero.
-template <int N, bool ONE = false, bool PAIRED = false>
+// TMA (paired order only): each window's tile goes out as two tiled bulk stores through the
+// tensor map tmap (a 3-D view of the work buffer: float32 along k_z, the N lines of an x
+// plane, x planes of every window), staged densely ([x][8 columns][two lines]) over the
+// FFT's two exchange tiles once the last exchange has been read; the next window's first
+// exchange waits until the stores have read the stage.  The threads' stores become shared
+// stores; the DRAM writes leave the SM as 32 KB boxes.
+template <int N, bool ONE = false, bool PAIRED = false, bool TMA = false>
 __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const float2* __restrict__ spec,
                                                                      float2* __restrict__ work, const WinBatch wb,
-                                                                     const Tables tb) {
+                                                                     const Tables tb,
+                                                                     const __grid_constant__ CUtensorMap tmap) {
     using C = Cfg<N>;
     constexpr int W = C::W, T = N / 8, H = N / 2;
     static_assert(!PAIRED || W == 8, "the paired order pairs two 8-column tiles in a 16-column group");
+    static_assert(!TMA || (PAIRED && N == 512), "tiled bulk stores of the paired order at 512^3");
+    static_assert(!TMA || 2 * SmemStrided<W>::words(N) >= N * 2 * W, "the stage fits in the two exchange tiles");
     constexpr int TILE = SmemStrided<W>::words(N);
     extern __shared__ __align__(16) float2 smem[];
     float* ttab = reinterpret_cast<float*>(smem + 2 * TILE);  // [a][col][RS], chunks swizzled
@@ -631,6 +642,7 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
     float2 wc[3 * twiddled_stages<N>()];
     load_stage_twiddles<N, true>(t, tb.tw, wc);
     const SmemStrided<W> sms[2] = {{smem, col}, {smem + TILE, col}};
+    const int cat = blockIdx.z;
     for (int g = 0; g < wb.S; g += 4) {
         float4 tv[ONE ? 1 : 8];
         if constexpr (!ONE) {
@@ -658,8 +670,26 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
                 v[0][i] = cscale(va0[i], f);
                 v[1][i] = cscale(vb0[i], f);
             }
+            if constexpr (TMA) {  // the previous window's stores have read the stage before its first exchange
+                if (threadIdx.x == 0) ac::bulk_wait_read_all();
+            }
             fft_lines_wc<N, true, 2>(v, t, sms, wc);
-            if constexpr (PAIRED) {
+            if constexpr (TMA) {
+                __syncthreads();  // every thread has read the last exchange
+                float4* stg = reinterpret_cast<float4*>(smem);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    stg[(t + i * T) * W + col] = make_float4(v[0][i].x, v[0][i].y, v[1][i].x, v[1][i].y);
+                ac::fence_proxy_async();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const int c0 = 32 * (int)(blockIdx.x >> 1), c1 = 2 * ky + (int)(blockIdx.x & 1);
+                    const int c2 = (cat * wb.S + s) * N;
+                    ac::tma_store_3d(&tmap, smem, c0, c1, c2);
+                    ac::tma_store_3d(&tmap, smem + (N / 2) * 2 * W, c0, c1, c2 + N / 2);
+                    ac::bulk_commit();
+                }
+            } else if constexpr (PAIRED) {
                 // line 2 k_y + (tile & 1) of 16-column group tile / 2, slots (k_y, N - k_y) of column col
                 const int off = t * (N * H) + (2 * ky + (int)(blockIdx.x & 1)) * H + (int)(blockIdx.x >> 1) * 16 + 2 * col;
                 float2* dst = work + (size_t)s * N * N * H + off;
@@ -677,6 +707,9 @@ __global__ void __launch_bounds__(Cfg<N>::TS, 1) k_inv_x_window_mirror(const flo
                 }
             }
         }
+    }
+    if constexpr (TMA) {  // the stage stays valid until the last stores have completed
+        if (threadIdx.x == 0) ac::bulk_wait_all();
     }
 }
 
@@ -1195,7 +1228,8 @@ static cudaError_t forward_impl(float* grid, float2* spec, const double* scal, i
 //           instead of four windows' factors at once (24 registers fewer), 4 (512^3) the
 //           same storing both lines of a column in one 16-byte store, in the paired order
 //           (whole 128-byte lines); the y pass then reads that order (its variants 4 and
-//           5 have a form for it; with another y variant, variant 3 runs in its place);
+//           5 have a form for it; with another y variant, variant 3 runs in its place),
+//           5 (512^3) the paired order written by tiled bulk stores (TMA) of a shared stage;
 //   pass 2, the c2r + contraction pass (I3): 0 radix 8 (k_inv_z_c2r_contract),
 //           1 k_inv_z_c2r_contract_e16 (16 values per thread, 128-thread blocks), 2 the same
 //           with its split twiddles in a table shared by the block (no spills);
@@ -1286,7 +1320,7 @@ static int pass_variants(int N, int pass, PassVariant* out) {
             case 256: return put({{0, 8, Cfg<256>::W, 1}, {1, 8, Cfg<256>::W, 1}, {2, 8, Cfg<256>::W, 1},
                                   {3, 8, Cfg<256>::W, 1}});
             case 512: return put({{0, 8, Cfg<512>::W, 1}, {1, 8, Cfg<512>::W, 1}, {2, 8, Cfg<512>::W, 1},
-                                  {3, 8, Cfg<512>::W, 1}, {4, 8, Cfg<512>::W, 1}});
+                                  {3, 8, Cfg<512>::W, 1}, {4, 8, Cfg<512>::W, 1}, {5, 8, Cfg<512>::W, 1}});
             case 1024: return put({{0, 8, Cfg<1024>::W, 1}});
         }
     }
@@ -1418,17 +1452,50 @@ static bool mirror_fits(const WinBatch& wb) {
     const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
     return wb.S <= 16 && bytes <= kMaxDynSmem;
 }
-// The paired order never falls back to another form: the y pass that follows reads it.
-template <int N, bool ONE, bool PAIRED = false>
+// The tensor map of the paired-order stores of k_inv_x_window_mirror<512, ..., TMA>: the
+// work buffer of nwin windows as float32 [nwin * N][N][N] (k_z fastest, as real and
+// imaginary parts), boxes of 32 floats (one 16-column group) x 1 line x N/2 x planes.
+// false when the driver's encoder is unavailable or refuses the map.
+static bool encode_paired_store_map(CUtensorMap* map, float2* work, int N, long long nwin) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || (reinterpret_cast<uintptr_t>(work) & 15) != 0 || nwin * N > 0x7fffffffLL) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(nwin * N)};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * sizeof(float), (cuuint64_t)N * N * sizeof(float)};
+    const cuuint32_t box[3] = {32, 1, (cuuint32_t)(N / 2)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, work, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The paired order never falls back to the plain one: the y pass that follows reads it.
+// TMA: the paired order by tiled bulk stores (512^3); the threads' own stores when the
+// tensor map cannot be made.
+template <int N, bool ONE, bool PAIRED = false, bool TMA = false>
 static cudaError_t run_x_mirror(const float2* spec, float2* work, const WinBatch& wb, const Tables& tb, int ncat,
                                 cudaStream_t st) {
     using C = Cfg<N>;
     const size_t bytes = 2 * C::SMEM_STRIDED + (size_t)(N / 2) * C::W * pair_row_floats(wb.S) * sizeof(float);
     if (!mirror_fits<N>(wb)) return PAIRED ? cudaErrorInvalidValue : run_x_r8<N>(spec, work, wb, tb, ncat, st);
+    alignas(64) CUtensorMap map{};
+    if constexpr (TMA) {
+        if (!encode_paired_store_map(&map, work, N, (long long)wb.S * ncat))
+            return run_x_mirror<N, ONE, true, false>(spec, work, wb, tb, ncat, st);
+    }
     cudaError_t e;
-    if ((e = allow_smem(k_inv_x_window_mirror<N, ONE, PAIRED>, bytes)) != cudaSuccess) return e;
-    k_inv_x_window_mirror<N, ONE, PAIRED><<<dim3((N / 2) / C::W, PAIRED ? N / 2 : N / 2 + 1, ncat), C::TS, bytes,
-                                            st>>>(spec, work, wb, tb);
+    if ((e = allow_smem(k_inv_x_window_mirror<N, ONE, PAIRED, TMA>, bytes)) != cudaSuccess) return e;
+    k_inv_x_window_mirror<N, ONE, PAIRED, TMA><<<dim3((N / 2) / C::W, PAIRED ? N / 2 : N / 2 + 1, ncat), C::TS,
+                                                 bytes, st>>>(spec, work, wb, tb, map);
     return cudaGetLastError();
 }
 template <int N>
@@ -1443,6 +1510,7 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
     }
     if constexpr (N == 512) {
         if (var == 4) return run_x_mirror<N, true, true>(spec, work, wb, tb, ncat, st);
+        if (var == 5) return run_x_mirror<N, true, true, true>(spec, work, wb, tb, ncat, st);
     }
     return run_x_r8<N>(spec, work, wb, tb, ncat, st);
 }
@@ -1450,7 +1518,7 @@ static cudaError_t launch_inv_x(int var, const float2* spec, float2* work, const
 // variant has a form that reads it.
 template <int N>
 static bool x_writes_paired(int xvar) {
-    return N == 512 && xvar == 4;
+    return N == 512 && (xvar == 4 || xvar == 5);
 }
 template <int N>
 static bool y_reads_paired(int yvar) {

@@ -172,12 +172,14 @@ def test_every_zeta_x_variant_matches(N, L):
         _close(got, outs[0])
 
 
-def test_paired_order_with_every_kind_of_y_variant():
-    # the window pass in the paired order (variant 4 at 512^3: the k_y and N - k_y values of a
-    # column side by side) with the y variants that read that order (4, 5) and one that does
-    # not (2: the window pass then stores the plain order): one catalogue against the Parseval
-    # route, and a two-catalogue batch (both catalogues' windows in one launch) against the
-    # same path one catalogue at a time
+@pytest.mark.parametrize("xv", [4, 5])
+def test_paired_order_with_every_kind_of_y_variant(xv):
+    # the window pass in the paired order (variants 4 and 5 at 512^3: the k_y and N - k_y
+    # values of a column side by side, by the threads' stores or by tiled bulk stores) with the
+    # y variants that read that order (4, 5) and one that does not (2: the window pass then
+    # stores the plain order): one catalogue against the Parseval route, and a two-catalogue
+    # batch (both catalogues' windows in one launch, the bulk stores' coordinates spanning
+    # both) against the Parseval route of each catalogue
     H = _hermes()
     N, L = 512, 1000.0
     pos = S.lognormal_catalogue(100000, L, seed=31, n_grid=64)
@@ -191,7 +193,7 @@ def test_paired_order_with_every_kind_of_y_variant():
             ks2 = ctx.xi_multipoles_kspace(ells)
             ctx.assign(pos)
             ks = ctx.xi_multipoles_kspace(ells)
-            H.fft_set_variant(N, 4, H.PASS_WINDOW)
+            H.fft_set_variant(N, xv, H.PASS_WINDOW)
             for yv in (4, 5, 2):
                 H.fft_set_variant(N, yv, H.PASS_INV_Y)
                 _close(ctx.xi_multipoles(ells), ks)

@@ -139,12 +139,12 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
             assert kind in (0, 1, 2) and E in (8, 16, 32) and W >= 1 and N % E == 0
     # the window pass: one window at a time everywhere; two windows in flight, or the k_y and
     # N - k_y lines together, at 256^3 and 512^3, and at 512^3 (8-column tiles) the same in the
-    # paired order (kind 4; the zeta_l x pass likewise);
+    # paired order (kind 4, and kind 5 by tiled bulk stores; the zeta_l x pass has kind 4);
     # the contraction pass: radix 8 everywhere, 16 values per thread at 256^3 and 512^3 (kind 2:
     # its split twiddles in a shared table);
     # the zeta_l y pass: radix 8 everywhere, 16 or 32 values per thread at 256^3 and 512^3
     # (and 16-column tiles at 256^3 and 512^3)
-    for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2, 3]), (1, 512, [0, 1, 2, 3, 4]), (2, 64, [0]),
+    for pass_, N, kinds in ((1, 64, [0]), (1, 256, [0, 1, 2, 3]), (1, 512, [0, 1, 2, 3, 4, 5]), (2, 64, [0]),
                             (2, 256, [0, 1, 1, 1, 2]), (2, 512, [0, 1, 1, 1, 2]), (2, 1024, [0]), (3, 64, [0]),
                             (3, 256, [0, 1, 1, 1, 1]), (3, 512, [0, 1, 1, 1, 1]), (4, 512, [0, 2, 3, 4]),
                             (5, 512, [0, 2, 3, 4]), (5, 256, [0, 2, 3]), (4, 1024, [0])):
@@ -156,7 +156,7 @@ def test_fft_variant_table_and_arguments_without_a_gpu():
     H.fft_set_variant(512, -1)
     info = H.fft_variants(512)
     assert info["forced"] == -1 and info["chosen"] == -1 and all(m == -1.0 for m in info["ms"])
-    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 6), (512, 5, 1), (256, 4, 1), (512, 5, 2), (512, 5, 3),
+    for bad in ((48, 0, 0), (512, n512, 0), (512, -2, 0), (512, 0, 6), (512, 6, 1), (256, 4, 1), (512, 5, 2), (512, 5, 3),
                 (512, 4, 4), (256, 3, 5)):
         with pytest.raises(H.HermesError) as ei:
             H.fft_set_variant(bad[0], bad[1], pass_=bad[2])
