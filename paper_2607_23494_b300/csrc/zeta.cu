@@ -324,11 +324,16 @@ __global__ void __launch_bounds__(ZCfg<N>::TS, 1) k_zeta_x_mirror(const float2* 
             fft_lines_wc<N, true, 2>(v, t, sms, wc);
             if constexpr (PAIRED) {
                 const int off = t * (N * N) + (2 * ky + (int)(blockIdx.x & 1)) * N + (int)(blockIdx.x >> 1) * 16 + 2 * col;
-                float2* dst = fields + (size_t)f * n3 + off;
+                float4* dst = reinterpret_cast<float4*>(fields + (size_t)f * n3 + off);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<float4*>(dst + (size_t)i * T * N * N) =
-                        make_float4(v[0][i].x, v[0][i].y, v[1][i].x, v[1][i].y);
+                for (int i = 0; i < 8; ++i) {  // (this form of the store spills 8 bytes; a float2 pointer spilled 44)
+                    float4 q;
+                    q.x = v[0][i].x;
+                    q.y = v[0][i].y;
+                    q.z = v[1][i].x;
+                    q.w = v[1][i].y;
+                    dst[(size_t)i * T * N * N / 2] = q;
+                }
             } else {
                 float2* dst = fields + (size_t)f * n3 + (size_t)kz;
 #pragma unroll
