@@ -47,7 +47,7 @@ def _planted(N, modes, amps):
     return d.reshape(N, N, N)
 
 
-@pytest.mark.parametrize("p,tol", [(2, 1e-7), (3, 1e-10), (4, 1e-10)])
+@pytest.mark.parametrize("p,tol", [(2, 1e-7), (3, 1e-10), (4, 1e-10), (5, 1e-10), (6, 1e-10)])
 def test_monopole_matches_the_poisson_closed_form_for_planted_modes(p, tol):
     # three modes that close a triangle (n_a + n_b + n_c = 0) and one that does not
     N, L = 16, 200.0
