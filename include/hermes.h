@@ -359,8 +359,9 @@ int hermes_zeta_multipoles(hermes_ctx *ctx, double *out);
  *   out: [n_bins][n_bins] float64, symmetric.  Up to 16 bins form one Gram; more run
  *   every pair of 8-bin blocks (B (B + 1) / 2 runs for B blocks).
  * Device memory: min(n_bins, 16) half spectra and 2 (n_bins + 1) real fields of N^3.
- * Errors: HERMES_ERR_ARG (out NULL), HERMES_ERR_STATE (no field, no bins, explicit
- * randoms set), HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
+ * Orders: the context's p must be 1 .. 4 (the sample kernels are built for those).
+ * Errors: HERMES_ERR_ARG (out NULL, or p > 4), HERMES_ERR_STATE (no field, no bins,
+ * explicit randoms set), HERMES_ERR_NOMEM, HERMES_ERR_CUDA.
  */
 int hermes_ddd_monopole(hermes_ctx *ctx, double *out);
 

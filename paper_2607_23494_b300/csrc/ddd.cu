@@ -288,7 +288,7 @@ cudaError_t launch_ddd_filter_yz(int N, int p, const float* in, float* out, int 
         else if (lgT == 5) k_ddd_filter_yz<P, 32><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, tp); \
         else k_ddd_filter_yz<P, 16><<<(unsigned)nblk, 256, 0, st>>>(in, out, lgN, tp);            \
         break;
-        C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
+        C(1) C(2) C(3) C(4)
 #undef C
         default: return cudaErrorInvalidValue;
     }
@@ -309,7 +309,7 @@ cudaError_t launch_ddd_gram(int N, int p, const float* Y, int nw, const DddTaps&
         else if (nw == 2) k_ddd_gram<P, 2><<<nblk, 64, 0, st>>>(Y, lgN, tp, part); \
         else k_ddd_gram<P, 3><<<nblk, 96, 0, st>>>(Y, lgN, tp, part);             \
         break;
-        C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8)
+        C(1) C(2) C(3) C(4)
 #undef C
         default: return cudaErrorInvalidValue;
     }

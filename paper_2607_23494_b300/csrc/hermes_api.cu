@@ -1091,6 +1091,9 @@ static int ddd_gram_warps() {
 int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     if (check_ctx(c)) return HERMES_ERR_ARG;
     if (!out) return fail(c, HERMES_ERR_ARG, "out is NULL");
+    if (c->p > 4)
+        return fail(c, HERMES_ERR_ARG, "the monopole's sample kernels are built for orders p <= 4 (context p = %d)",
+                    c->p);
     if (c->have_randoms)
         return fail(c, HERMES_ERR_STATE, "the monopole uses analytic uniform randoms: call hermes_clear_randoms and "
                                          "hermes_assign first");
@@ -1101,9 +1104,10 @@ int hermes_ddd_monopole(hermes_ctx* c, double* out) {
     cudaStream_t st = c->stream;
     const int N = c->N, H = c->H, nb = c->n_bins, p = c->p, nf = nb + 1;
     const size_t n3 = (size_t)N * N * N;
-    // The Gram runs over field-slot sets of delta and up to 16 bins: all bins at once (three
-    // warps, tiles (0-7, 0-7), (0-7, 8-15), (8-15, 8-15)) up to 16 bins; beyond, one run per
-    // pair of 8-bin blocks I <= J (one warp: the upper triangle of block I, or the block (I, J)).
+    // The Gram runs over field-slot sets of delta and up to 16 bins: all bins at once up to 16
+    // bins (one warp up to 8 bins; above, two warps, each a diagonal 8 x 8 tile and half of the
+    // off-diagonal one, or three with one tile each); beyond, one run per pair of 8-bin blocks
+    // I <= J (one warp: the upper triangle of block I, or the block (I, J)).
     struct Run {
         int nw, I, J, tile0;
     };

@@ -104,3 +104,9 @@ def test_monopole_errors():
         with pytest.raises(H.HermesError) as ei:
             ctx.ddd_monopole()
         assert ei.value.code == H.ERR_STATE                       # explicit randoms set
+    with H.Context(L, N, 5) as ctx:
+        ctx.window_shells(np.linspace(5.0, 40.0, 5), l_max=0)
+        ctx.assign(S.poisson_uniform(2000, L, seed=3))
+        with pytest.raises(H.HermesError) as ei:
+            ctx.ddd_monopole()
+        assert ei.value.code == H.ERR_ARG                         # order above the built kernels
